@@ -1,0 +1,292 @@
+"""Benchmark: Phi solves/s and Gcell/s on the Yin-Yang 1 degree grid
+(92 x 272 cells per patch, Nr = 400 log-spaced shells in [1e-3, 1], l_max = 32),
+density = rotated tri-axial ellipsoid + 3 Gaussian blobs (seeded, synthetic).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision P] [--impl ygs|reference]
+
+One JSON line on rank 0.  `value` is whole-job solves/s over the timed region
+(CUDA events on the solve stream, max over ranks, inputs resident in HBM);
+`e2e` is the same metric through ygs_solve_host (pinned host buffers, the
+host<->device copies inside the timed region); `roofline` is the dominant
+kernel's achieved rate against the measured peak; `cpu_baseline` is the CPU
+FP64 oracle timed on a bounded sample of the same workload.  With
+`--impl reference` the oracle itself is the timed arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Φ solves/s & Gcell/s at l_max; split-prec vs FP64 GPU at ≤1e-6 rel err; % roofline"
+WORKLOAD = "yinyang-1deg-92x272x2-Nr400-lmax32-ellipsoid+3blobs"
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), profiling recipe table
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ygs", choices=["ygs", "reference"])
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-r", type=int, default=400)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(tempfile.gettempdir(), f"ygs_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline_sample(grid, rho, n_shells=40):
+    """Times the FP64 oracle (weights prebuilt) on `n_shells` of the grid's
+    shells with the full angular grid; returns solves/s scaled to all shells."""
+    import numpy as np
+
+    import oracle
+    from paper_1903_08475_gb300 import workloads as W
+
+    lo = grid.n_r // 2 - n_shells // 2
+    sub = W.Grid(**{**grid.__dict__, "edges": grid.edges[lo: lo + n_shells + 1]})
+    parts = []
+    for p in range(grid.n_patch):
+        off, na = grid.patch_offset(p), grid.nang(p)
+        parts.append(rho[off + lo * na: off + (lo + n_shells) * na])
+    rho_s = np.concatenate(parts)
+    U = oracle.build_U(sub)
+    Q = oracle.build_Q(sub)
+    t0 = time.perf_counter()
+    oracle.solve_prebuilt(sub, U, Q, rho_s)
+    dt = time.perf_counter() - t0
+    full = dt * grid.n_r / n_shells
+    return {"value": 1.0 / full, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n_shells} of {grid.n_r} shells (full angular grid, weights prebuilt), "
+                      f"{dt:.2f} s, scaled by {grid.n_r}/{n_shells}"}
+
+
+def run_reference(args, ws, rank):
+    """The CPU FP64 oracle as the timed arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1903_08475_gb300 import workloads as W
+
+    grid, rho = W.config1(n_r=args.n_r)
+    n_shells = 20
+    lo = grid.n_r // 2 - n_shells // 2
+    sub = W.Grid(**{**grid.__dict__, "edges": grid.edges[lo: lo + n_shells + 1]})
+    rho_s = np.concatenate([rho[grid.patch_offset(p) + lo * grid.nang(p): grid.patch_offset(p) + (lo + n_shells) * grid.nang(p)]
+                            for p in range(grid.n_patch)])
+    U = oracle.build_U(sub)
+    Q = oracle.build_Q(sub)
+    for _ in range(args.warmup):
+        oracle.solve_prebuilt(sub, U, Q, rho_s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve_prebuilt(sub, U, Q, rho_s)
+    dt = (time.perf_counter() - t0) / args.steps * grid.n_r / n_shells
+    value = 1.0 / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "gcell_per_s": value * grid.n_cells / 1e9,
+            "config": {"workload": WORKLOAD, "n_r": grid.n_r, "l_max": grid.l_max, "cells": grid.n_cells,
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{n_shells} of {grid.n_r} shells per step, weights prebuilt, scaled"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_1903_08475_gb300 import (Plan, ygs_launches_per_solve, ygs_read_phase_times, ygs_set_profiling,
+                                        ygs_solve, ygs_solve_host, workloads as W)
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    precision = args.precision or "fp64"
+    grid, rho = W.config1(n_r=args.n_r)
+    plan = Plan(grid, precision, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    rho_d = torch.from_numpy(rho).to(dev)
+    phi_d = torch.empty_like(rho_d)
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            ygs_solve(plan, rho_d, phi_d, stream=stream)
+    stream.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    clocks = ClockSampler(local)
+    ygs_set_profiling(plan, True)
+    ygs_read_phase_times(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ygs_solve(plan, rho_d, phi_d, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    phase_ms, ncalls = ygs_read_phase_times(plan)
+    ygs_set_profiling(plan, False)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws / (ms_step / 1e3)
+
+    # end to end through the host-buffer entry point
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_phi = torch.empty_like(h_rho).pin_memory()
+    ygs_solve_host(plan, h_rho, h_phi, stream=stream)
+    n_e2e = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        ygs_solve_host(plan, h_rho, h_phi, stream=stream)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    info = plan.info
+    sym = info["symmetric"] == 1
+    nang_eff = grid.nang(0) if sym else grid.nang_total
+    flops_proj = 2.0 * grid.n_r * nang_eff * grid.K
+    flops_synth = 2.0 * grid.n_r * nang_eff * grid.K
+    per = [x / max(ncalls, 1) for x in phase_ms]
+    names = ["projection", "radial_scan", "synthesis"]
+    dom = int(np.argmax(per))
+    flops = [flops_proj, 0.0, flops_synth][dom]
+    if precision == "fp64":
+        achieved = flops / (per[dom] / 1e3) / 1e12
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of the profiling recipe (no measured FP64 peak)",
+                "phase_ms": dict(zip(names, per))}
+    else:
+        raise SystemExit("split-precision bench line not wired yet")
+
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision, "data": "synthetic",
+            "gcell_per_s": value * grid.n_cells / 1e9,
+            "config": {"workload": WORKLOAD, "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
+                       "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"],
+                       "l2": "inputs larger than L2 (rho 160 MB, weights 436 MB)",
+                       "parallelism": f"replicas{ws}"},
+            "e2e": {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(rho.nbytes),
+                    "d2h_bytes_per_step": int(rho.nbytes)},
+            "gpu_launches": args.steps * ygs_launches_per_solve(plan),
+            "roofline": roof, "clocks": clk, "peaks_source": peak_src}
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_sample(grid, rho)
+        except Exception as e:  # the baseline is context; never lose the GPU line over it
+            line["cpu_baseline"] = {"error": repr(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * ygs.h -- C ABI of libygs, a GB300 (sm_103a) solver for the gravitational
+ * potential on multi-patch spherical grids by a single global spherical-
+ * harmonics expansion (Wongwathanarat, arXiv:1903.08475).
+ *
+ * The operation (Sect. 3-4 of the paper):
+ *
+ *   Phi(r) = -G \int rho(r') / |r - r'| d^3r'                 (Eq. integralpoisson)
+ *
+ * on a grid of N_g rotated spherical-coordinate patches sharing one set of
+ * radial shells.  With cell-constant density rho and overlap weight w, and the
+ * expansion truncated at l_max, every solve runs the paper's steps 2-5:
+ *
+ *   B[i,c]   = sum_{g,j,k} rho_{g,i,j,k} U_{g,jk,c}            (Eq. B_CS)
+ *   M[i,c]   = (r_i^+)^-(l+1) sum_{i'<=i} R_in,i' B[i',c]
+ *            + (r_i^+)^l      sum_{i'>i}  R_out,i' B[i',c]     (Eq. M_C)
+ *   Phi_{g,i,jk} = sum_c Q_{g,jk,c} M[i,c]                     (Eq. gravpotmult)
+ *
+ * with the angular weights U (Eqs. U_C/U_S: the global-frame real harmonic
+ * of column c integrated over the patch cell through the Wigner-D rotation of
+ * Eqs. ylm_transform/wigner-D, times w and 2/delta_m) and the prefactors Q
+ * (Eqs. Q_C/Q_S: -G times the global-frame real harmonic at the evaluation
+ * point), both built once per grid by ygs_create (step 1).
+ *
+ * Conventions
+ *   - Real columns c = (l, m, C|S), m >= 0:  (l,0,C) -> l*l,
+ *     (l,m,C) -> l*l + 2m - 1, (l,m,S) -> l*l + 2m;  K = (l_max+1)^2.
+ *     Y^C_lm = N_lm P_l^m(cos t) cos(m p), Y^S_lm = N_lm P_l^m(cos t) sin(m p),
+ *     N_lm = sqrt((l-m)!/(l+m)!), P_l^m without the Condon-Shortley phase.
+ *   - Patch g maps local Cartesian coordinates xi to global ones by
+ *     x = R^(g) xi, R^(g) the z-y'-z'' Euler matrix of Eq. rottransmatrix.
+ *   - Cell (g, i, j, k): r in [edges[i], edges[i+1]],
+ *     theta in theta_lo + [j, j+1] * dtheta, phi in phi_lo + [k, k+1] * dphi
+ *     (local coordinates, dtheta = (theta_hi - theta_lo)/n_theta, same for phi).
+ *   - Fields (rho, Phi and their gradients) are FP64 arrays laid out
+ *     [g][i][j][k] (patch-major, then shell, then theta, phi fastest), patches
+ *     concatenated in order: patch g starts at element n_r * sum_{g'<g} n_theta[g'] n_phi[g'].
+ *   - Phi_{g,i,j,k} is the potential at radius edges[i+1] and at the upper
+ *     angular vertex (theta_j^+, phi_k^+) of the cell (YGS_EVAL_UPPER_VERTEX,
+ *     the paper's choice, Sect. 4.2) or at the cell's angular centre.
+ *
+ * Ownership and threading
+ *   - A plan owns all device memory it allocates (weights, workspaces) from
+ *     ygs_create to ygs_destroy.  Field buffers are owned by the caller.
+ *   - Device pointers must be allocated on the plan's device and be 16-byte
+ *     aligned.  A plan must not be used by two host threads at once, and two
+ *     calls on one plan must not overlap on the GPU (they share workspaces):
+ *     issue them on one stream or order the streams.
+ *   - ygs_solve / ygs_solve_batched / ygs_backward only enqueue work on the
+ *     given stream (NULL = the legacy default stream); they do not synchronise.
+ *
+ * Errors
+ *   Every entry point returns a ygs_status and never aborts the process.
+ *   Arguments are validated before any work is enqueued; a failing CUDA call
+ *   returns YGS_ERR_CUDA.  ygs_last_error() gives a message for the most recent
+ *   failure on the calling thread.
+ */
+#ifndef YGS_H
+#define YGS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  YGS_OK = 0,
+  YGS_ERR_INVALID_ARG = 1, /* bad descriptor, size, pointer or alignment */
+  YGS_ERR_OOM = 2,         /* device allocation failed */
+  YGS_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
+  YGS_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
+  YGS_ERR_NUMERIC = 5,     /* a weight self-check failed */
+  YGS_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} ygs_status;
+
+/* Arithmetic of the two contractions (projection and synthesis).  Weight
+ * building and the radial scans are FP64 in every mode. */
+typedef enum {
+  YGS_FP64 = 0,   /* FP64 FMA on the CUDA cores */
+  YGS_BF16X3 = 1, /* tcgen05 BF16 tensor cores, 2-slice operands, 3 products */
+  YGS_BF16X6 = 2  /* tcgen05 BF16 tensor cores, 3-slice operands, 6 products */
+} ygs_precision;
+
+typedef enum {
+  YGS_EVAL_UPPER_VERTEX = 0, /* (r_i^+, theta_j^+, phi_k^+), Sect. 4.2 */
+  YGS_EVAL_CELL_CENTRE = 1   /* (r_i^+, angular centre of the cell) */
+} ygs_eval;
+
+enum {
+  YGS_FLAG_NO_SYMMETRY = 1 /* never use the Yin-Yang sign symmetry of Sect. 4.2 */
+};
+
+/* Grid descriptor.  All arrays are HOST memory, read during ygs_create only. */
+typedef struct {
+  int n_r;                    /* number of radial shells, >= 1 */
+  const double* r_edges;      /* n_r + 1 edges, strictly increasing, r_edges[0] >= 0 */
+  int n_patch;                /* number of patches N_g, >= 1 */
+  const double* euler;        /* 3*n_patch: (alpha, beta, gamma) of Eq. rottransmatrix */
+  const int* n_theta;         /* n_patch: cells in local colatitude, >= 1 */
+  const int* n_phi;           /* n_patch: cells in local azimuth, >= 1 */
+  const double* theta_range;  /* 2*n_patch: [theta_lo, theta_hi], 0 <= lo < hi <= pi */
+  const double* phi_range;    /* 2*n_patch: [phi_lo, phi_hi], lo < hi, hi - lo <= 2 pi */
+  const double* overlap_w;    /* sum_g n_theta*n_phi cell-constant weights w_jk (Sect. 4.2) */
+  int l_max;                  /* expansion degree, 0 <= l_max <= 128 */
+  double G;                   /* gravitational constant */
+  int eval;                   /* ygs_eval */
+  int precision;              /* ygs_precision */
+  int flags;                  /* YGS_FLAG_* */
+} ygs_desc;
+
+typedef struct ygs_plan ygs_plan;
+
+/* Sizes and modes of a plan (for callers and tests). */
+typedef struct {
+  int n_r, n_patch, l_max, K;
+  long long n_ang;        /* sum_g n_theta*n_phi */
+  long long n_cells;      /* n_r * n_ang: elements of one field */
+  int precision;
+  int symmetric;          /* 1: the Yin-Yang sign symmetry halves the contractions */
+  int split_k;            /* number of angular chunks the projection is split into */
+  long long weight_bytes; /* device bytes held for U, Q and their split copies */
+  long long work_bytes;   /* device bytes of per-solve workspace */
+} ygs_info;
+
+/* Builds the plan: validates the descriptor, allocates device memory on
+ * `device`, and evaluates the FP64 weights U (Wigner-D route, Eqs. U_C/U_S),
+ * Q (Eqs. Q_C/Q_S) and the radial factors of Eqs. R_in/R_out on the GPU
+ * (step 1 of Sect. 4.3).  Synchronous.  On failure *out is set to NULL and
+ * nothing is leaked.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED. */
+ygs_status ygs_create(const ygs_desc* desc, int device, ygs_plan** out);
+
+/* Frees every device buffer of the plan (waits for its pending work).
+ * NULL is accepted. */
+ygs_status ygs_destroy(ygs_plan* plan);
+
+ygs_status ygs_get_info(const ygs_plan* plan, ygs_info* info);
+
+/* Phi = A rho: steps 2-5 of Sect. 4.3 on device pointers.  rho and phi each
+ * hold n_cells FP64 values in the field layout above and must not overlap.
+ * `stream` is a cudaStream_t (NULL: legacy default stream).  Errors:
+ * INVALID_ARG (NULL/misaligned pointer), CUDA (launch failure). */
+ygs_status ygs_solve(ygs_plan* plan, const double* d_rho, double* d_phi, void* stream);
+
+/* The same solve from and to HOST buffers: copies rho host->device, solves,
+ * copies Phi device->host on `stream`, then synchronises the stream.  Host
+ * buffers should be page-locked for full copy bandwidth. */
+ygs_status ygs_solve_host(ygs_plan* plan, const double* h_rho, double* h_phi, void* stream);
+
+/* n independent solves (plans may differ in every size) enqueued on one
+ * stream.  plans, d_rho and d_phi are HOST arrays of n entries each. */
+ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const* d_rho,
+                             double* const* d_phi, void* stream);
+
+/* Adjoint of the linear map rho -> Phi:  grad_rho = A^T grad_phi
+ * (transposed synthesis, reversed radial scans, transposed projection).
+ * Same layouts, pointer rules and errors as ygs_solve. */
+ygs_status ygs_backward(ygs_plan* plan, const double* d_grad_phi, double* d_grad_rho, void* stream);
+
+/* Copies the moments B and the radial weights M of the most recent solve on
+ * this plan into device buffers of n_r*K FP64 values each, row-major
+ * [i][c] in the column order above (either pointer may be NULL). */
+ygs_status ygs_get_moments(ygs_plan* plan, double* d_B, double* d_M, void* stream);
+
+/* Copies the FP64 weights of patch `patch` to HOST memory as [n_theta*n_phi][K]
+ * row-major: which = 0 -> U, which = 1 -> Q.  Synchronous. */
+ygs_status ygs_get_weights(ygs_plan* plan, int which, int patch, double* h_out);
+
+/* Reads and clears the plan's device error word (set by bounded waits and
+ * device-side checks).  Synchronises the plan's last stream. */
+ygs_status ygs_get_status(ygs_plan* plan);
+
+/* Phase timing for measurement.  While enabled, every ygs_solve and
+ * ygs_backward on this plan records CUDA events on its stream around its three
+ * phases (projection, radial scans, synthesis); at most 4096 calls are kept.
+ * ygs_read_phase_times synchronises on those events, writes the summed
+ * milliseconds of each phase (ms[0..2]) and the number of calls recorded
+ * since the previous read, and clears the record. */
+ygs_status ygs_set_profiling(ygs_plan* plan, int enable);
+ygs_status ygs_read_phase_times(ygs_plan* plan, double* ms, int* n_calls);
+
+/* Number of kernel launches one ygs_solve / ygs_backward enqueues. */
+int ygs_launches_per_solve(const ygs_plan* plan);
+
+const char* ygs_status_string(ygs_status s);
+const char* ygs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* YGS_H */

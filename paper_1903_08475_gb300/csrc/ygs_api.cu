@@ -1,0 +1,465 @@
+// C ABI of libygs: descriptor validation, plan lifetime, and the solve /
+// adjoint entry points (step 1 at create, steps 2-5 of Sect. 4.3 per solve).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ygs_internal.h"
+
+namespace ygs {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+ygs_status fail(ygs_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+ygs_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? YGS_ERR_OOM : YGS_ERR_CUDA;
+}
+
+#define API_TRY(expr)                                  \
+  do {                                                 \
+    cudaError_t _e = (expr);                           \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr); \
+  } while (0)
+
+bool finite(double x) { return std::isfinite(x); }
+
+void free_plan(ygs_plan* p) {
+  if (!p) return;
+  for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  void* bufs[] = {p->U, p->Q, p->rad, p->col_l, p->col_nat, p->chunks, p->part, p->B, p->M,
+                  p->Mbar, p->Bbar, p->d_err, p->h2d_rho, p->h2d_phi};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  delete p;
+}
+
+// Euler matrix of Eq. rottransmatrix, x = R xi.
+void euler_R(const double* e, double* R) {
+  double ca = cos(e[0]), sa = sin(e[0]), cb = cos(e[1]), sb = sin(e[1]), cg = cos(e[2]), sg = sin(e[2]);
+  R[0] = ca * cb * cg - sa * sg;
+  R[1] = sa * cb * cg + ca * sg;
+  R[2] = -sb * cg;
+  R[3] = -ca * cb * sg - sa * cg;
+  R[4] = -sa * cb * sg + ca * cg;
+  R[5] = sb * sg;
+  R[6] = ca * sb;
+  R[7] = sa * sb;
+  R[8] = cb;
+}
+
+// Patch 1 is patch 0 turned by pi about the global z axis (R1 = diag(-1,-1,1) R0)
+// on an identical local grid with identical overlap weights: then every global
+// real harmonic takes the factor (-1)^m between the two patches (Sect. 4.2).
+bool detect_symmetry(const ygs_plan* p) {
+  if (p->n_patch != 2 || (p->flags & YGS_FLAG_NO_SYMMETRY)) return false;
+  if (p->nth[0] != p->nth[1] || p->nph[0] != p->nph[1]) return false;
+  for (int k = 0; k < 2; ++k)
+    if (p->theta_range[k] != p->theta_range[2 + k] || p->phi_range[k] != p->phi_range[2 + k]) return false;
+  long long na = p->nang[0];
+  if (std::memcmp(p->w_host.data(), p->w_host.data() + na, na * sizeof(double)) != 0) return false;
+  double R0[9], R1[9];
+  euler_R(&p->euler[0], R0);
+  euler_R(&p->euler[3], R1);
+  const double S[3] = {-1.0, -1.0, 1.0};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      if (fabs(R1[3 * r + c] - S[r] * R0[3 * r + c]) > 1e-13) return false;
+  return true;
+}
+
+ygs_status validate_desc(const ygs_desc* d) {
+  if (!d) return fail(YGS_ERR_INVALID_ARG, "desc is NULL");
+  if (d->n_r < 1) return fail(YGS_ERR_INVALID_ARG, "n_r must be >= 1");
+  if (!d->r_edges) return fail(YGS_ERR_INVALID_ARG, "r_edges is NULL");
+  for (int i = 0; i <= d->n_r; ++i)
+    if (!finite(d->r_edges[i])) return fail(YGS_ERR_INVALID_ARG, "r_edges has a non-finite value");
+  if (d->r_edges[0] < 0.0) return fail(YGS_ERR_INVALID_ARG, "r_edges[0] must be >= 0");
+  for (int i = 0; i < d->n_r; ++i)
+    if (!(d->r_edges[i + 1] > d->r_edges[i])) return fail(YGS_ERR_INVALID_ARG, "r_edges must increase strictly");
+  if (d->n_patch < 1 || d->n_patch > kMaxPatch)
+    return fail(YGS_ERR_INVALID_ARG, "n_patch must be in [1, " + std::to_string(kMaxPatch) + "]");
+  if (!d->euler || !d->n_theta || !d->n_phi || !d->theta_range || !d->phi_range || !d->overlap_w)
+    return fail(YGS_ERR_INVALID_ARG, "a patch array is NULL");
+  long long total = 0;
+  const double pi = 3.14159265358979323846;
+  for (int g = 0; g < d->n_patch; ++g) {
+    for (int k = 0; k < 3; ++k)
+      if (!finite(d->euler[3 * g + k])) return fail(YGS_ERR_INVALID_ARG, "non-finite Euler angle");
+    if (d->n_theta[g] < 1 || d->n_phi[g] < 1) return fail(YGS_ERR_INVALID_ARG, "n_theta and n_phi must be >= 1");
+    double t0 = d->theta_range[2 * g], t1 = d->theta_range[2 * g + 1];
+    double p0 = d->phi_range[2 * g], p1 = d->phi_range[2 * g + 1];
+    if (!finite(t0) || !finite(t1) || !finite(p0) || !finite(p1))
+      return fail(YGS_ERR_INVALID_ARG, "non-finite patch extent");
+    if (t0 < -1e-12 || t1 > pi + 1e-12 || !(t1 > t0)) return fail(YGS_ERR_INVALID_ARG, "theta_range must satisfy 0 <= lo < hi <= pi");
+    if (!(p1 > p0) || p1 - p0 > 2 * pi + 1e-12) return fail(YGS_ERR_INVALID_ARG, "phi_range must satisfy lo < hi <= lo + 2 pi");
+    long long na = (long long)d->n_theta[g] * d->n_phi[g];
+    if (na > (1LL << 30)) return fail(YGS_ERR_INVALID_ARG, "too many angular cells in one patch");
+    total += na;
+  }
+  for (long long a = 0; a < total; ++a)
+    if (!finite(d->overlap_w[a])) return fail(YGS_ERR_INVALID_ARG, "non-finite overlap weight");
+  if (d->l_max < 0 || d->l_max > kMaxLmax)
+    return fail(YGS_ERR_INVALID_ARG, "l_max must be in [0, " + std::to_string(kMaxLmax) + "]");
+  if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
+  if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
+  if (d->precision < YGS_FP64 || d->precision > YGS_BF16X6) return fail(YGS_ERR_INVALID_ARG, "bad precision");
+  if (d->flags & ~YGS_FLAG_NO_SYMMETRY) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
+  if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
+  return YGS_OK;
+}
+
+constexpr int kProfCap = 4096;
+
+// Returns the 4 events of the next recorded call, or nullptr when profiling is off / full.
+cudaEvent_t* prof_slot(ygs_plan* p) {
+  if (!p->profiling || p->prof_used >= kProfCap) return nullptr;
+  size_t need = (size_t)(p->prof_used + 1) * 4;
+  while (p->prof_events.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    p->prof_events.push_back(e);
+  }
+  return &p->prof_events[(size_t)p->prof_used++ * 4];
+}
+
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+ygs_status check_field(const ygs_plan* p, const void* a, const void* b) {
+  if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
+  if (!a || !b) return fail(YGS_ERR_INVALID_ARG, "field pointer is NULL");
+  if (!aligned16(a) || !aligned16(b)) return fail(YGS_ERR_INVALID_ARG, "field pointers must be 16-byte aligned");
+  const char* ca = (const char*)a;
+  const char* cb = (const char*)b;
+  size_t bytes = (size_t)p->n_cells * sizeof(double);
+  if (ca < cb + bytes && cb < ca + bytes) return fail(YGS_ERR_INVALID_ARG, "input and output fields overlap");
+  return YGS_OK;
+}
+
+}  // namespace
+}  // namespace ygs
+
+using namespace ygs;
+
+extern "C" {
+
+const char* ygs_status_string(ygs_status s) {
+  switch (s) {
+    case YGS_OK: return "YGS_OK";
+    case YGS_ERR_INVALID_ARG: return "YGS_ERR_INVALID_ARG";
+    case YGS_ERR_OOM: return "YGS_ERR_OOM";
+    case YGS_ERR_CUDA: return "YGS_ERR_CUDA";
+    case YGS_ERR_UNSUPPORTED: return "YGS_ERR_UNSUPPORTED";
+    case YGS_ERR_NUMERIC: return "YGS_ERR_NUMERIC";
+    case YGS_ERR_TIMEOUT: return "YGS_ERR_TIMEOUT";
+  }
+  return "YGS_ERR_UNKNOWN";
+}
+
+const char* ygs_last_error(void) { return g_err.c_str(); }
+
+ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
+  if (!out) return fail(YGS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  ygs_status st = validate_desc(d);
+  if (st != YGS_OK) return st;
+  if (d->precision != YGS_FP64) return fail(YGS_ERR_UNSUPPORTED, "precision not built in this library version");
+  int ndev = 0;
+  API_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(YGS_ERR_INVALID_ARG, "bad device index");
+  DeviceGuard guard(device);
+  if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+
+  ygs_plan* p = new (std::nothrow) ygs_plan();
+  if (!p) return fail(YGS_ERR_OOM, "host allocation failed");
+  p->device = device;
+  p->n_r = d->n_r;
+  p->n_patch = d->n_patch;
+  p->l_max = d->l_max;
+  p->K = (d->l_max + 1) * (d->l_max + 1);
+  p->precision = d->precision;
+  p->eval = d->eval;
+  p->flags = d->flags;
+  p->G = d->G;
+  p->edges.assign(d->r_edges, d->r_edges + d->n_r + 1);
+  p->euler.assign(d->euler, d->euler + 3 * d->n_patch);
+  p->theta_range.assign(d->theta_range, d->theta_range + 2 * d->n_patch);
+  p->phi_range.assign(d->phi_range, d->phi_range + 2 * d->n_patch);
+  p->nth.assign(d->n_theta, d->n_theta + d->n_patch);
+  p->nph.assign(d->n_phi, d->n_phi + d->n_patch);
+  long long acc = 0;
+  for (int g = 0; g < p->n_patch; ++g) {
+    p->nang.push_back((long long)p->nth[g] * p->nph[g]);
+    p->ang_off.push_back(acc);
+    p->fld_off.push_back(acc * p->n_r);
+    acc += p->nang.back();
+  }
+  p->nang_total = acc;
+  p->n_cells = acc * p->n_r;
+  p->w_host.assign(d->overlap_w, d->overlap_w + acc);
+  p->symmetric = detect_symmetry(p);
+  p->n_wpatch = p->symmetric ? 1 : p->n_patch;
+  p->nang_wtotal = p->symmetric ? p->nang[0] : acc;
+  for (int g = 0; g < p->n_patch; ++g) {
+    p->pt.fld_off[g] = p->fld_off[g];
+    p->pt.nang[g] = p->nang[g];
+    p->pt.ang_off[g] = p->symmetric ? 0 : p->ang_off[g];
+  }
+  // internal column order: even m first when the symmetry is used
+  p->col_perm.clear();
+  if (p->symmetric) {
+    for (int par = 0; par < 2; ++par)
+      for (int c = 0; c < p->K; ++c) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= c) ++l;
+        int m = (c - l * l + 1) / 2;
+        if ((m & 1) == par) p->col_perm.push_back(c);
+      }
+    p->K_even = 0;
+    for (int c : p->col_perm) {
+      int l = 0;
+      while ((l + 1) * (l + 1) <= c) ++l;
+      if ((((c - l * l + 1) / 2) & 1) == 0) ++p->K_even;
+    }
+  } else {
+    for (int c = 0; c < p->K; ++c) p->col_perm.push_back(c);
+    p->K_even = p->K;
+  }
+
+  // split-K chunks over the stored patches' angular cells
+  int sms = 148;
+  {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) sms = prop.multiProcessorCount;
+  }
+  const int BMt = 64, BNt = 64, BKt = 16;
+  long long tiles = (long long)((p->n_r + BMt - 1) / BMt) *
+                    ((p->K_even + BNt - 1) / BNt + (p->K - p->K_even + BNt - 1) / BNt);
+  long long want = std::max(1LL, (4LL * sms + tiles - 1) / tiles);
+  std::vector<Chunk> chunks;
+  for (int g = 0; g < p->n_wpatch; ++g) {
+    long long na = p->nang[g];
+    long long sg = std::max(1LL, (want * na + p->nang_wtotal - 1) / p->nang_wtotal);
+    sg = std::min(sg, std::max(1LL, na / (8 * BKt)));
+    long long len = (na + sg - 1) / sg;
+    len = (len + BKt - 1) / BKt * BKt;
+    for (long long a0 = 0; a0 < na; a0 += len) chunks.push_back(Chunk{g, (int)a0, (int)std::min(na, a0 + len), 0});
+  }
+  p->S = (int)chunks.size();
+
+  auto fail_free = [&](ygs_status s) {
+    free_plan(p);
+    return s;
+  };
+  auto al = [&](void** ptr, size_t bytes) -> cudaError_t { return cudaMalloc(ptr, std::max<size_t>(bytes, 16)); };
+  size_t wbytes = (size_t)p->nang_wtotal * p->K * sizeof(double);
+  size_t nk = (size_t)p->n_r * p->K * sizeof(double);
+  cudaError_t e;
+  if ((e = al((void**)&p->U, wbytes)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc U"));
+  if ((e = al((void**)&p->Q, wbytes)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc Q"));
+  if ((e = al((void**)&p->rad, 4 * (size_t)(p->l_max + 1) * p->n_r * sizeof(double))) != cudaSuccess)
+    return fail_free(cuda_fail(e, "cudaMalloc rad"));
+  if ((e = al((void**)&p->col_l, p->K * sizeof(int))) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc col_l"));
+  if ((e = al((void**)&p->col_nat, p->K * sizeof(int))) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc col_nat"));
+  if ((e = al((void**)&p->chunks, chunks.size() * sizeof(Chunk))) != cudaSuccess)
+    return fail_free(cuda_fail(e, "cudaMalloc chunks"));
+  if ((e = al((void**)&p->part, (size_t)p->S * nk)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc part"));
+  if ((e = al((void**)&p->B, nk)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc B"));
+  if ((e = al((void**)&p->M, nk)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc M"));
+  if ((e = al((void**)&p->Mbar, nk)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc Mbar"));
+  if ((e = al((void**)&p->Bbar, nk)) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc Bbar"));
+  if ((e = al((void**)&p->d_err, sizeof(int))) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMalloc err"));
+  if ((e = cudaMemset(p->d_err, 0, sizeof(int))) != cudaSuccess) return fail_free(cuda_fail(e, "cudaMemset err"));
+  if ((e = cudaMemcpy(p->chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice)) != cudaSuccess)
+    return fail_free(cuda_fail(e, "cudaMemcpy chunks"));
+  p->weight_bytes = 2LL * wbytes;
+  p->work_bytes = (long long)(p->S + 4) * nk;
+
+  st = build_weights(p);
+  if (st != YGS_OK) return fail_free(st);
+  *out = p;
+  return YGS_OK;
+}
+
+ygs_status ygs_destroy(ygs_plan* p) {
+  if (!p) return YGS_OK;
+  DeviceGuard guard(p->device);
+  cudaDeviceSynchronize();
+  free_plan(p);
+  return YGS_OK;
+}
+
+ygs_status ygs_get_info(const ygs_plan* p, ygs_info* info) {
+  if (!p || !info) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  info->n_r = p->n_r;
+  info->n_patch = p->n_patch;
+  info->l_max = p->l_max;
+  info->K = p->K;
+  info->n_ang = p->nang_total;
+  info->n_cells = p->n_cells;
+  info->precision = p->precision;
+  info->symmetric = p->symmetric ? 1 : 0;
+  info->split_k = p->S;
+  info->weight_bytes = p->weight_bytes;
+  info->work_bytes = p->work_bytes;
+  return YGS_OK;
+}
+
+ygs_status ygs_solve(ygs_plan* p, const double* d_rho, double* d_phi, void* stream) {
+  ygs_status st = check_field(p, d_rho, d_phi);
+  if (st != YGS_OK) return st;
+  DeviceGuard guard(p->device);
+  if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  cudaEvent_t* ev = prof_slot(p);
+  if (ev) API_TRY(cudaEventRecord(ev[0], s));
+  API_TRY(launch_project_fp64(p, d_rho, p->U, p->part, s));
+  if (ev) API_TRY(cudaEventRecord(ev[1], s));
+  API_TRY(launch_scan_fwd(p, p->part, p->S, p->B, p->M, s));
+  if (ev) API_TRY(cudaEventRecord(ev[2], s));
+  API_TRY(launch_synth_fp64(p, p->M, p->Q, d_phi, s));
+  if (ev) API_TRY(cudaEventRecord(ev[3], s));
+  return YGS_OK;
+}
+
+ygs_status ygs_solve_host(ygs_plan* p, const double* h_rho, double* h_phi, void* stream) {
+  if (!p || !h_rho || !h_phi) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  size_t bytes = (size_t)p->n_cells * sizeof(double);
+  if (!p->h2d_rho) API_TRY(cudaMalloc((void**)&p->h2d_rho, bytes));
+  if (!p->h2d_phi) API_TRY(cudaMalloc((void**)&p->h2d_phi, bytes));
+  cudaStream_t s = (cudaStream_t)stream;
+  API_TRY(cudaMemcpyAsync(p->h2d_rho, h_rho, bytes, cudaMemcpyHostToDevice, s));
+  ygs_status st = ygs_solve(p, p->h2d_rho, p->h2d_phi, stream);
+  if (st != YGS_OK) return st;
+  API_TRY(cudaMemcpyAsync(h_phi, p->h2d_phi, bytes, cudaMemcpyDeviceToHost, s));
+  API_TRY(cudaStreamSynchronize(s));
+  return YGS_OK;
+}
+
+ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const* d_rho, double* const* d_phi,
+                             void* stream) {
+  if (n < 0 || (n > 0 && (!plans || !d_rho || !d_phi))) return fail(YGS_ERR_INVALID_ARG, "bad batch arrays");
+  for (int b = 0; b < n; ++b) {
+    ygs_status st = check_field(plans[b], d_rho[b], d_phi[b]);
+    if (st != YGS_OK) return st;
+  }
+  for (int b = 0; b < n; ++b) {
+    ygs_status st = ygs_solve(plans[b], d_rho[b], d_phi[b], stream);
+    if (st != YGS_OK) return st;
+  }
+  return YGS_OK;
+}
+
+ygs_status ygs_backward(ygs_plan* p, const double* d_gphi, double* d_grho, void* stream) {
+  ygs_status st = check_field(p, d_gphi, d_grho);
+  if (st != YGS_OK) return st;
+  DeviceGuard guard(p->device);
+  if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  cudaEvent_t* ev = prof_slot(p);
+  if (ev) API_TRY(cudaEventRecord(ev[0], s));
+  API_TRY(launch_project_fp64(p, d_gphi, p->Q, p->part, s));
+  if (ev) API_TRY(cudaEventRecord(ev[1], s));
+  API_TRY(launch_scan_adj(p, p->part, p->S, p->Bbar, s));
+  if (ev) API_TRY(cudaEventRecord(ev[2], s));
+  API_TRY(launch_synth_fp64(p, p->Bbar, p->U, d_grho, s));
+  if (ev) API_TRY(cudaEventRecord(ev[3], s));
+  return YGS_OK;
+}
+
+ygs_status ygs_get_moments(ygs_plan* p, double* d_B, double* d_M, void* stream) {
+  if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard guard(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d_B) API_TRY(launch_unpermute(p, p->B, d_B, s));
+  if (d_M) API_TRY(launch_unpermute(p, p->M, d_M, s));
+  return YGS_OK;
+}
+
+ygs_status ygs_get_weights(ygs_plan* p, int which, int patch, double* h_out) {
+  if (!p || !h_out) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  if (which != 0 && which != 1) return fail(YGS_ERR_INVALID_ARG, "which must be 0 (U) or 1 (Q)");
+  if (patch < 0 || patch >= p->n_patch) return fail(YGS_ERR_INVALID_ARG, "bad patch index");
+  DeviceGuard guard(p->device);
+  int g = p->symmetric ? 0 : patch;
+  long long rows = p->nang[patch];
+  std::vector<double> tmp((size_t)rows * p->K);
+  const double* src = (which == 0 ? p->U : p->Q) + (size_t)p->pt.ang_off[g] * p->K;
+  API_TRY(cudaMemcpy(tmp.data(), src, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (long long a = 0; a < rows; ++a)
+    for (int ci = 0; ci < p->K; ++ci) {
+      int c = p->col_perm[ci];
+      double v = tmp[(size_t)a * p->K + ci];
+      if (p->symmetric && patch == 1) {
+        int l = 0;
+        while ((l + 1) * (l + 1) <= c) ++l;
+        if (((c - l * l + 1) / 2) & 1) v = -v;
+      }
+      h_out[(size_t)a * p->K + c] = v;
+    }
+  return YGS_OK;
+}
+
+ygs_status ygs_set_profiling(ygs_plan* p, int enable) {
+  if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
+  p->profiling = enable != 0;
+  return YGS_OK;
+}
+
+ygs_status ygs_read_phase_times(ygs_plan* p, double* ms, int* n_calls) {
+  if (!p || !ms || !n_calls) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  ms[0] = ms[1] = ms[2] = 0.0;
+  for (int c = 0; c < p->prof_used; ++c) {
+    cudaEvent_t* ev = &p->prof_events[(size_t)c * 4];
+    API_TRY(cudaEventSynchronize(ev[3]));
+    for (int k = 0; k < 3; ++k) {
+      float t = 0.f;
+      API_TRY(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      ms[k] += t;
+    }
+  }
+  *n_calls = p->prof_used;
+  p->prof_used = 0;
+  return YGS_OK;
+}
+
+int ygs_launches_per_solve(const ygs_plan* p) { return p ? 3 : 0; }
+
+ygs_status ygs_get_status(ygs_plan* p) {
+  if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
+  DeviceGuard guard(p->device);
+  API_TRY(cudaStreamSynchronize(p->last_stream));
+  int err = 0;
+  API_TRY(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  API_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  if (err) return fail((ygs_status)err, "device-side error word was set");
+  return YGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,299 @@
+// FP64 contractions and FP64 radial scans (steps 2-5 of Sect. 4.3).
+//
+// Projection  part[z][i][c] = sum_{a in chunk z} field(g_z, i, a) * W[a][c]
+//   (Eq. B_CS; the split-K chunks z are the GPU image of the paper's
+//   angular task decomposition, and their fixed-order sum is step 3).
+// Synthesis   out(g, i, a) = sum_c X[i][c] * W[a][c]   (Eq. gravpotmult).
+// Scans       Eq. M_C as recurrences over shells with every factor <= O(r^2):
+//   I_i = a_i B_i + (r_{i-1}^+/r_i^+)^(l+1) I_{i-1},
+//   O_i = b_{i+1} B_{i+1} + (r_i^+/r_{i+1}^+)^l O_{i+1},  M_i = I_i + O_i,
+//   and their transposes for the adjoint.
+//
+// With the Yin-Yang sign symmetry (Sect. 4.2: U_Yang = (-1)^m U_Yin and
+// Q_Yang = (-1)^m Q_Yin), only Yin's weights are stored, columns are ordered
+// even-m first, the projection contracts (rho_Yin +- rho_Yang) against the
+// even / odd column blocks, and the synthesis writes Phi_Yin = E + O and
+// Phi_Yang = E - O from the even and odd partial sums: half the arithmetic.
+#include "ygs_internal.h"
+
+namespace ygs {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct ProjArgs {
+  int n_r, K, K_even, tiles_e, symmetric;
+  const double* field;
+  const double* W;
+  double* part;
+  const Chunk* chunks;
+  PatchTable pt;
+};
+
+__global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
+  int c0, c1;
+  double sgn;
+  if (tn < a.tiles_e) {
+    c0 = tn * BN;
+    c1 = min(a.K_even, c0 + BN);
+    sgn = 1.0;
+  } else {
+    c0 = a.K_even + (tn - a.tiles_e) * BN;
+    c1 = min(a.K, c0 + BN);
+    sgn = -1.0;
+  }
+  const int i0 = tm * BM;
+  const Chunk ch = a.chunks[z];
+  const long long lda = a.pt.nang[ch.g];
+  const double* A0 = a.field + a.pt.fld_off[ch.g];
+  const double* A1 = a.symmetric ? a.field + a.pt.fld_off[1] : nullptr;
+  const double* Wg = a.W + a.pt.ang_off[ch.g] * (long long)a.K;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+
+  for (int k0 = ch.a0; k0 < ch.a1; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * NT, row = e / BK, kk = e % BK;
+      int i = i0 + row, k = k0 + kk;
+      double v = 0.0;
+      if (i < a.n_r && k < ch.a1) {
+        v = A0[i * lda + k];
+        if (A1) v += sgn * A1[i * lda + k];
+      }
+      As[kk][row] = v;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * NT, kk = e / BN, col = e % BN;
+      int k = k0 + kk, c = c0 + col;
+      Bs[kk][col] = (k < ch.a1 && c < c1) ? Wg[(long long)k * a.K + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+  double* out = a.part + (long long)z * a.n_r * a.K;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int i = i0 + ty + 16 * r, c = c0 + tx + 16 * q;
+      if (i < a.n_r && c < c1) out[(long long)i * a.K + c] = acc[r][q];
+    }
+}
+
+struct SynthArgs {
+  int n_r, K, K_even, symmetric;
+  const double* X;
+  const double* W;
+  double* out;
+  PatchTable pt;
+};
+
+__device__ inline void synth_range(const SynthArgs& s, const double* Wg, long long nang, int i0, int a0, int k_lo,
+                                   int k_hi, double (&As)[BK][BM + 1], double (&Bs)[BK][BN + 1], double (&acc)[4][4]) {
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * NT, row = e / BK, kk = e % BK;
+      int i = i0 + row, k = k0 + kk;
+      As[kk][row] = (i < s.n_r && k < k_hi) ? s.X[(long long)i * s.K + k] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + r * NT, n = e / BK, kk = e % BK;
+      int a = a0 + n, k = k0 + kk;
+      Bs[kk][n] = (a < nang && k < k_hi) ? Wg[(long long)a * s.K + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs s) {
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  const int g = blockIdx.z;
+  const long long nang = s.pt.nang[g];
+  const int a0 = blockIdx.x * BN;
+  if (a0 >= nang) return;
+  const int i0 = blockIdx.y * BM;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const double* Wg = s.W + s.pt.ang_off[g] * (long long)s.K;
+  double ae[4][4], ao[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ae[r][q] = ao[r][q] = 0.0;
+  synth_range(s, Wg, nang, i0, a0, 0, s.K_even, As, Bs, ae);
+  if (s.K_even < s.K) synth_range(s, Wg, nang, i0, a0, s.K_even, s.K, As, Bs, ao);
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int i = i0 + ty + 16 * r;
+      long long a = a0 + tx + 16 * q;
+      if (i >= s.n_r || a >= nang) continue;
+      if (s.symmetric) {
+        s.out[s.pt.fld_off[0] + i * nang + a] = ae[r][q] + ao[r][q];
+        s.out[s.pt.fld_off[1] + i * nang + a] = ae[r][q] - ao[r][q];
+      } else {
+        s.out[s.pt.fld_off[g] + i * nang + a] = ae[r][q] + ao[r][q];
+      }
+    }
+}
+
+__global__ void scan_fwd_kernel(int n_r, int K, int L, const int* __restrict__ col_l, const double* __restrict__ part,
+                                int S, const double* __restrict__ rad, double* __restrict__ B, double* __restrict__ M) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K) return;
+  const int l = col_l[c];
+  const long long plane = (long long)n_r * K, rs = (long long)(L + 1) * n_r;
+  const double* at = rad + (long long)l * n_r;
+  const double* bt = rad + rs + (long long)l * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  for (int i = 0; i < n_r; ++i) {
+    double b = 0.0;
+    for (int z = 0; z < S; ++z) b += part[z * plane + (long long)i * K + c];
+    B[(long long)i * K + c] = b;
+  }
+  double O = 0.0;
+  M[(long long)(n_r - 1) * K + c] = 0.0;
+  for (int i = n_r - 2; i >= 0; --i) {
+    O = fma(bt[i + 1], B[(long long)(i + 1) * K + c], fout[i] * O);
+    M[(long long)i * K + c] = O;
+  }
+  double I = 0.0;
+  for (int i = 0; i < n_r; ++i) {
+    I = fma(at[i], B[(long long)i * K + c], fin[i] * I);
+    M[(long long)i * K + c] += I;
+  }
+}
+
+__global__ void scan_adj_kernel(int n_r, int K, int L, const int* __restrict__ col_l, const double* __restrict__ part,
+                                int S, const double* __restrict__ rad, double* __restrict__ Mb,
+                                double* __restrict__ Bb) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= K) return;
+  const int l = col_l[c];
+  const long long plane = (long long)n_r * K, rs = (long long)(L + 1) * n_r;
+  const double* at = rad + (long long)l * n_r;
+  const double* bt = rad + rs + (long long)l * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  for (int i = 0; i < n_r; ++i) {
+    double v = 0.0;
+    for (int z = 0; z < S; ++z) v += part[z * plane + (long long)i * K + c];
+    Mb[(long long)i * K + c] = v;
+  }
+  // X_i = Mb_i + (r_i^+/r_{i+1}^+)^(l+1) X_{i+1};  Bbar_i = a_i X_i + ...
+  double X = 0.0;
+  for (int i = n_r - 1; i >= 0; --i) {
+    X = Mb[(long long)i * K + c] + ((i + 1 < n_r) ? fin[i + 1] * X : 0.0);
+    Bb[(long long)i * K + c] = at[i] * X;
+  }
+  // Y_i = Mb_{i-1} + (r_{i-2}^+/r_{i-1}^+)^l Y_{i-1};  ... + b_i Y_i
+  double Y = 0.0;
+  for (int i = 1; i < n_r; ++i) {
+    Y = Mb[(long long)(i - 1) * K + c] + ((i >= 2) ? fout[i - 2] * Y : 0.0);
+    Bb[(long long)i * K + c] += bt[i] * Y;
+  }
+}
+
+__global__ void unpermute_kernel(int n_r, int K, const int* __restrict__ col_nat, const double* __restrict__ in,
+                                 double* __restrict__ out) {
+  long long total = (long long)n_r * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long i = e / K;
+    int c = (int)(e % K);
+    out[i * K + col_nat[c]] = in[e];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_project_fp64(const ygs_plan* p, const double* field, const double* W, double* part,
+                                cudaStream_t s) {
+  ProjArgs a;
+  a.n_r = p->n_r;
+  a.K = p->K;
+  a.K_even = p->K_even;
+  a.tiles_e = (p->K_even + BN - 1) / BN;
+  a.symmetric = p->symmetric ? 1 : 0;
+  a.field = field;
+  a.W = W;
+  a.part = part;
+  a.chunks = p->chunks;
+  a.pt = p->pt;
+  int tiles_o = (p->K - p->K_even + BN - 1) / BN;
+  dim3 grid(a.tiles_e + tiles_o, (p->n_r + BM - 1) / BM, p->S);
+  proj_fp64_kernel<<<grid, NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* W, double* out, cudaStream_t s) {
+  SynthArgs a;
+  a.n_r = p->n_r;
+  a.K = p->K;
+  a.K_even = p->K_even;
+  a.symmetric = p->symmetric ? 1 : 0;
+  a.X = X;
+  a.W = W;
+  a.out = out;
+  a.pt = p->pt;
+  long long nmax = 0;
+  for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
+  dim3 grid((unsigned)((nmax + BN - 1) / BN), (p->n_r + BM - 1) / BM, p->n_wpatch);
+  synth_fp64_kernel<<<grid, NT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double* B, double* M, cudaStream_t s) {
+  scan_fwd_kernel<<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, part, S, p->rad, B, M);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s) {
+  scan_adj_kernel<<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, part, S, p->rad, p->Mbar, Bbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s) {
+  unpermute_kernel<<<256, 256, 0, s>>>(p->n_r, p->K, p->col_nat, in, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ygs

@@ -1,0 +1,94 @@
+// Internal declarations of libygs (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ygs.h"
+
+namespace ygs {
+
+constexpr int kMaxPatch = 64;
+constexpr int kMaxLmax = 128;
+
+// Per-call description of the angular layout, passed to kernels by value.
+struct PatchTable {
+  long long fld_off[kMaxPatch];  // element offset of patch g in a field
+  long long nang[kMaxPatch];     // angular cells of patch g
+  long long ang_off[kMaxPatch];  // row offset of patch g in a weight matrix
+};
+
+// One split-K chunk of the projection: angular cells [a0, a1) of patch g.
+struct Chunk {
+  int g, a0, a1, pad;
+};
+
+}  // namespace ygs
+
+struct ygs_plan {
+  int device = 0;
+  int n_r = 0, n_patch = 0, l_max = 0, K = 0;
+  int precision = 0, eval = 0, flags = 0;
+  double G = 1.0;
+  bool symmetric = false;   // Yin-Yang sign symmetry in use
+  int n_wpatch = 0;         // patches with stored weights (1 when symmetric)
+  int K_even = 0;           // internal columns [0, K_even) have even m when symmetric, else K_even = K
+  std::vector<int> nth, nph;
+  std::vector<double> euler, theta_range, phi_range, edges, w_host;
+  std::vector<long long> nang, ang_off, fld_off;
+  long long nang_total = 0, nang_wtotal = 0, n_cells = 0;
+  std::vector<int> col_perm;  // internal column -> natural column
+  ygs::PatchTable pt{};
+
+  // device buffers owned by the plan
+  double* U = nullptr;      // [nang_wtotal][K] internal column order
+  double* Q = nullptr;      // [nang_wtotal][K]
+  double* rad = nullptr;    // [4][l_max+1][n_r]: a, b, f_in, f_out
+  int* col_l = nullptr;     // [K] degree of each internal column
+  int* col_nat = nullptr;   // [K] natural index of each internal column
+  ygs::Chunk* chunks = nullptr;
+  int S = 0;                // split-K chunks
+  double* part = nullptr;   // [S][n_r][K] projection partials
+  double* B = nullptr;      // [n_r][K]
+  double* M = nullptr;      // [n_r][K]
+  double* Mbar = nullptr;   // [n_r][K] adjoint workspace
+  double* Bbar = nullptr;   // [n_r][K] adjoint workspace
+  double* h2d_rho = nullptr;  // device staging for ygs_solve_host
+  double* h2d_phi = nullptr;
+  int* d_err = nullptr;     // device error word
+  cudaStream_t last_stream = nullptr;
+  // phase profiling: 4 events per recorded call
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_events;
+  int prof_used = 0;
+  long long weight_bytes = 0, work_bytes = 0;
+};
+
+namespace ygs {
+
+// Thread-local error message for ygs_last_error().
+void set_error(const std::string& msg);
+
+// ---- weight builder (ygs_weights.cu) -------------------------------------
+// Builds U, Q (FP64, internal column order) and the radial tables of `p`
+// with every allocation it needs; synchronous.
+ygs_status build_weights(ygs_plan* p);
+
+// ---- FP64 contractions and scans (ygs_fp64.cu) ----------------------------
+// part[z][i][c] = sum over chunk z of field(i, a) * W[a][c]  (projection shape)
+cudaError_t launch_project_fp64(const ygs_plan* p, const double* field, const double* W, double* part,
+                                cudaStream_t s);
+// out(g, i, a) = sum_c X[i][c] W[a][c]  (synthesis shape)
+cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* W, double* out, cudaStream_t s);
+// B = sum_z part[z]; M = scaled inner + outer radial scans of B.
+cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double* B, double* M, cudaStream_t s);
+// Mbar = sum_z part[z]; Bbar = transposed scans of Mbar.
+cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s);
+// out[i][col_nat[c]] = in[i][c]
+cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+
+}  // namespace ygs
