@@ -43,15 +43,19 @@ __device__ inline int isqrt_col(int c) {
   return l;
 }
 
-// Pyramid of d^l_{m'm}(pi/2) following the printed recurrences (one block).
-__global__ void dpi_kernel(int L, double* D) {
+// Pyramid of d^l_{m'm}(pi/2) by the printed recurrences (one block), kept on
+// the triangle 0 <= m <= m' <= l only: starting from d^l_{l m} and running the
+// three-term recurrence down to m' = m is stable, whereas continuing it through
+// m' < m loses digits fast with l (unitarity is off by 1e-7 at l = 32 and
+// worse than O(1) at l = 64).  Values here are the recipe's (see dpi_fill_kernel).
+__global__ void dpi_kernel(int L, double* R) {
   int t = threadIdx.x;
-  if (t == 0) D[0] = 1.0;
+  if (t == 0) R[0] = 1.0;
   __syncthreads();
   for (int l = 1; l <= L; ++l) {
     int n = 2 * l + 1, np = 2 * l - 1;
-    double* A = D + blk(l);
-    const double* P = D + blk(l - 1);
+    double* A = R + blk(l);
+    const double* P = R + blk(l - 1);
     for (int m = t; m <= l; m += blockDim.x) {
       double v;
       if (m == 0)
@@ -60,7 +64,7 @@ __global__ void dpi_kernel(int L, double* D) {
         v = -sqrt(l * (2.0 * l - 1.0) / (2.0 * (l + m) * (l + m - 1.0))) * P[(2 * l - 2) * np + (m - 1 + l - 1)];
       A[(2 * l) * n + (m + l)] = v;
       double dp1 = v, dp2 = 0.0;
-      for (int mp = l - 1; mp >= -l; --mp) {
+      for (int mp = l - 1; mp >= m; --mp) {
         double den = (double)(l - mp) * (double)(l + mp + 1);
         double t1 = 2.0 * m / sqrt(den) * dp1;
         double t2 = (mp + 2 <= l) ? sqrt((double)(l - mp - 1) * (double)(l + mp + 2) / den) * dp2 : 0.0;
@@ -71,26 +75,39 @@ __global__ void dpi_kernel(int L, double* D) {
       }
     }
     __syncthreads();
-    // negative m from d_{-m',-m} = (-1)^{m'-m} d_{m'm}
-    for (int idx = t; idx < l * n; idx += blockDim.x) {
-      int m = -(idx / n) - 1;
-      int mp = idx % n - l;
-      double s = ((mp - m) & 1) ? -1.0 : 1.0;
-      A[(mp + l) * n + (m + l)] = s * A[(-mp + l) * n + (-m + l)];
-    }
-    __syncthreads();
   }
 }
 
-// Column sign (-1)^m that maps the recipe's values onto Eq. wigner-d.
-__global__ void dpi_sign_kernel(int L, double* D) {
+// Full d^l(pi/2) in the convention of Eq. wigner-d from the recipe triangle:
+// the recipe yields (-1)^m d_{m'm}; the other entries follow from
+//   d_{m'm} = (-1)^{m'-m} d_{-m',-m},   d_{-m',m}(pi/2) = (-1)^{l+m} d_{m'm}(pi/2),
+//   d_{m'm} = (-1)^{m-m'} d_{m m'}.
+__global__ void dpi_fill_kernel(int L, const double* R, double* D) {
   long long total = blk(L + 1);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     int l = 0;
     while (blk(l + 1) <= e) ++l;
     int n = 2 * l + 1;
-    int m = (int)((e - blk(l)) % n) - l;
-    if (m & 1) D[e] = -D[e];
+    int a = (int)((e - blk(l)) / n) - l, b = (int)((e - blk(l)) % n) - l;
+    int sgn = 0;  // parity of the accumulated sign
+    if (b < 0) {
+      sgn += a - b;
+      a = -a;
+      b = -b;
+    }
+    if (a < 0) {
+      sgn += l + b;
+      a = -a;
+    }
+    if (a < b) {
+      sgn += b - a;
+      int t = a;
+      a = b;
+      b = t;
+    }
+    sgn += b;
+    double v = R[blk(l) + (long long)(a + l) * n + (b + l)];
+    D[e] = (sgn & 1) ? -v : v;
   }
 }
 
@@ -474,13 +491,14 @@ ygs_status build_weights(ygs_plan* p) {
   }
 
   // Wigner tables
-  double *d_dpi, *d_db, *d_W;
+  double *d_rec, *d_dpi, *d_db, *d_W;
+  YGS_TRY(s.alloc(&d_rec, blk(L + 1)));
   YGS_TRY(s.alloc(&d_dpi, blk(L + 1)));
   YGS_TRY(s.alloc(&d_db, (size_t)nwp * blk(L + 1)));
   YGS_TRY(s.alloc(&d_W, (size_t)nwp * blk(L + 1)));
-  dpi_kernel<<<1, 256>>>(L, d_dpi);
+  dpi_kernel<<<1, 256>>>(L, d_rec);
   YGS_TRY(cudaGetLastError());
-  dpi_sign_kernel<<<256, 256>>>(L, d_dpi);
+  dpi_fill_kernel<<<256, 256>>>(L, d_rec, d_dpi);
   YGS_TRY(cudaGetLastError());
   dbeta_kernel<<<dim3(L + 1, nwp), 256, (2 * L + 1) * 2 * sizeof(double)>>>(L, d_dpi, d_beta, d_db);
   YGS_TRY(cudaGetLastError());
