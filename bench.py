@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ygs", choices=["ygs", "reference"])
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--n-r", type=int, default=400)
     return ap.parse_args()
 
@@ -188,7 +189,7 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    precision = args.precision or "fp64"
+    precision = args.precision or "bf16x6"
     grid, rho = W.config1(n_r=args.n_r)
     plan = Plan(grid, precision, device=local)
     stream = torch.cuda.Stream(device=dev)
@@ -249,20 +250,55 @@ def main():
     info = plan.info
     sym = info["symmetric"] == 1
     nang_eff = grid.nang(0) if sym else grid.nang_total
-    flops_proj = 2.0 * grid.n_r * nang_eff * grid.K
-    flops_synth = 2.0 * grid.n_r * nang_eff * grid.K
+    nprod = {"fp64": 1, "bf16x3": 3, "bf16x6": 6}[precision]
+    # algorithmic FLOPs of one contraction: one FMA per (shell, stored cell, column) and slice product
+    flops_gemm = 2.0 * nprod * grid.n_r * nang_eff * grid.K
     per = [x / max(ncalls, 1) for x in phase_ms]
-    names = ["projection", "radial_scan", "synthesis"]
+    names = ["field_slices", "projection", "radial_scan", "synthesis"]
     dom = int(np.argmax(per))
-    flops = [flops_proj, 0.0, flops_synth][dom]
     if precision == "fp64":
+        flops = [0.0, flops_gemm, 0.0, flops_gemm][dom]
         achieved = flops / (per[dom] / 1e3) / 1e12
         roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 rate of the profiling recipe (no measured FP64 peak)",
                 "phase_ms": dict(zip(names, per))}
     else:
-        raise SystemExit("split-precision bench line not wired yet")
+        if dom in (1, 3):
+            achieved = flops_gemm / (per[dom] / 1e3) / 1e12
+            peak = float(peaks["bf16_tflops"])
+            roof = {"kernel": names[dom], "bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"bf16_tflops ({peak_src}, burst)", "phase_ms": dict(zip(names, per))}
+        else:
+            # bytes of the field pass: rho in (FP64) + slices out
+            nsl = 3 if precision == "bf16x6" else 2
+            byts = grid.n_cells * 8 + grid.n_cells * 2 * nsl
+            achieved = byts / (per[dom] / 1e3) / 1e9
+            peak = float(peaks["hbm_gbs"])
+            roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_src})",
+                    "phase_ms": dict(zip(names, per))}
+
+    # the plain FP64 GPU path on the same input: speed-up and accuracy of the split path against it
+    extra = {}
+    if precision != "fp64" and not args.no_fp64_compare:
+        with Plan(grid, "fp64", device=local) as p64:
+            phi64 = torch.empty_like(rho_d)
+            ygs_solve(p64, rho_d, phi64, stream=stream)
+            stream.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(2):
+                ygs_solve(p64, rho_d, phi64, stream=stream)
+            f1.record(stream)
+            stream.synchronize()
+            ms64 = f0.elapsed_time(f1) / 2
+            ygs_solve(plan, rho_d, phi_d, stream=stream)
+            stream.synchronize()
+            rel = float(((phi_d - phi64).abs() / phi64.abs()).max().item())
+        extra = {"fp64_gpu_solves_per_s": 1e3 / ms64, "speedup_vs_fp64_gpu": ms64 / ms_step,
+                 "max_rel_err_vs_fp64_gpu": rel}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -275,7 +311,7 @@ def main():
             "e2e": {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(rho.nbytes),
                     "d2h_bytes_per_step": int(rho.nbytes)},
             "gpu_launches": args.steps * ygs_launches_per_solve(plan),
-            "roofline": roof, "clocks": clk, "peaks_source": peak_src}
+            "roofline": roof, "clocks": clk, "peaks_source": peak_src, **extra}
     if rank == 0 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(grid, rho)

@@ -152,7 +152,9 @@ ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const*
 
 /* Adjoint of the linear map rho -> Phi:  grad_rho = A^T grad_phi
  * (transposed synthesis, reversed radial scans, transposed projection).
- * Same layouts, pointer rules and errors as ygs_solve. */
+ * Same layouts, pointer rules and errors as ygs_solve.  It always runs on the
+ * plan's FP64 weights (the adjoint of the FP64 operator), whatever the plan's
+ * precision. */
 ygs_status ygs_backward(ygs_plan* plan, const double* d_grad_phi, double* d_grad_rho, void* stream);
 
 /* Copies the moments B and the radial weights M of the most recent solve on
@@ -169,10 +171,11 @@ ygs_status ygs_get_weights(ygs_plan* plan, int which, int patch, double* h_out);
 ygs_status ygs_get_status(ygs_plan* plan);
 
 /* Phase timing for measurement.  While enabled, every ygs_solve and
- * ygs_backward on this plan records CUDA events on its stream around its three
- * phases (projection, radial scans, synthesis); at most 4096 calls are kept.
+ * ygs_backward on this plan records CUDA events on its stream around its four
+ * phases (0: field preparation (BF16 slicing; empty on the FP64 path),
+ * 1: projection, 2: radial scans, 3: synthesis); at most 4096 calls are kept.
  * ygs_read_phase_times synchronises on those events, writes the summed
- * milliseconds of each phase (ms[0..2]) and the number of calls recorded
+ * milliseconds of each phase (ms[0..3]) and the number of calls recorded
  * since the previous read, and clears the record. */
 ygs_status ygs_set_profiling(ygs_plan* plan, int enable);
 ygs_status ygs_read_phase_times(ygs_plan* plan, double* ms, int* n_calls);

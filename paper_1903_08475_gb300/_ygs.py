@@ -224,8 +224,8 @@ def ygs_set_profiling(plan: Plan, enable: bool = True):
 
 
 def ygs_read_phase_times(plan: Plan):
-    """Summed (projection, scans, synthesis) milliseconds and the call count."""
-    ms = (ctypes.c_double * 3)()
+    """Summed (field prep, projection, scans, synthesis) milliseconds and the call count."""
+    ms = (ctypes.c_double * 4)()
     n = ctypes.c_int()
     _check(load_library().ygs_read_phase_times(plan.handle, ms, ctypes.byref(n)))
     return list(ms), n.value

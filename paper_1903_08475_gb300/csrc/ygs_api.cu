@@ -49,6 +49,7 @@ bool finite(double x) { return std::isfinite(x); }
 void free_plan(ygs_plan* p) {
   if (!p) return;
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  tc_free(p);
   void* bufs[] = {p->U, p->Q, p->rad, p->col_l, p->col_nat, p->chunks, p->part, p->B, p->M,
                   p->Mbar, p->Bbar, p->d_err, p->h2d_rho, p->h2d_phi};
   for (void* b : bufs)
@@ -132,17 +133,18 @@ ygs_status validate_desc(const ygs_desc* d) {
 }
 
 constexpr int kProfCap = 4096;
+constexpr int kPhases = 4;
 
-// Returns the 4 events of the next recorded call, or nullptr when profiling is off / full.
+// Returns the kPhases + 1 events of the next recorded call, or nullptr when profiling is off / full.
 cudaEvent_t* prof_slot(ygs_plan* p) {
   if (!p->profiling || p->prof_used >= kProfCap) return nullptr;
-  size_t need = (size_t)(p->prof_used + 1) * 4;
+  size_t need = (size_t)(p->prof_used + 1) * (kPhases + 1);
   while (p->prof_events.size() < need) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     p->prof_events.push_back(e);
   }
-  return &p->prof_events[(size_t)p->prof_used++ * 4];
+  return &p->prof_events[(size_t)p->prof_used++ * (kPhases + 1)];
 }
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
@@ -185,7 +187,6 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
   *out = nullptr;
   ygs_status st = validate_desc(d);
   if (st != YGS_OK) return st;
-  if (d->precision != YGS_FP64) return fail(YGS_ERR_UNSUPPORTED, "precision not built in this library version");
   int ndev = 0;
   API_TRY(cudaGetDeviceCount(&ndev));
   if (device < 0 || device >= ndev) return fail(YGS_ERR_INVALID_ARG, "bad device index");
@@ -299,6 +300,11 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
 
   st = build_weights(p);
   if (st != YGS_OK) return fail_free(st);
+  if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3) {
+    p->tc_nsl = (p->precision == YGS_BF16X6) ? 3 : 2;
+    st = tc_setup(p, sms);
+    if (st != YGS_OK) return fail_free(st);
+  }
   *out = p;
   return YGS_OK;
 }
@@ -336,12 +342,23 @@ ygs_status ygs_solve(ygs_plan* p, const double* d_rho, double* d_phi, void* stre
   p->last_stream = s;
   cudaEvent_t* ev = prof_slot(p);
   if (ev) API_TRY(cudaEventRecord(ev[0], s));
-  API_TRY(launch_project_fp64(p, d_rho, p->U, p->part, s));
-  if (ev) API_TRY(cudaEventRecord(ev[1], s));
-  API_TRY(launch_scan_fwd(p, p->part, p->S, p->B, p->M, s));
-  if (ev) API_TRY(cudaEventRecord(ev[2], s));
-  API_TRY(launch_synth_fp64(p, p->M, p->Q, d_phi, s));
-  if (ev) API_TRY(cudaEventRecord(ev[3], s));
+  if (p->tc_nsl) {
+    API_TRY(tc_field_slices(p, d_rho, s));
+    if (ev) API_TRY(cudaEventRecord(ev[1], s));
+    API_TRY(tc_project(p, s));
+    if (ev) API_TRY(cudaEventRecord(ev[2], s));
+    API_TRY(tc_scan(p, s));
+    if (ev) API_TRY(cudaEventRecord(ev[3], s));
+    API_TRY(tc_synthesize(p, d_phi, s));
+  } else {
+    if (ev) API_TRY(cudaEventRecord(ev[1], s));
+    API_TRY(launch_project_fp64(p, d_rho, p->U, p->part, s));
+    if (ev) API_TRY(cudaEventRecord(ev[2], s));
+    API_TRY(launch_scan_fwd(p, p->part, p->S, p->B, p->M, s));
+    if (ev) API_TRY(cudaEventRecord(ev[3], s));
+    API_TRY(launch_synth_fp64(p, p->M, p->Q, d_phi, s));
+  }
+  if (ev) API_TRY(cudaEventRecord(ev[4], s));
   return YGS_OK;
 }
 
@@ -383,12 +400,13 @@ ygs_status ygs_backward(ygs_plan* p, const double* d_gphi, double* d_grho, void*
   p->last_stream = s;
   cudaEvent_t* ev = prof_slot(p);
   if (ev) API_TRY(cudaEventRecord(ev[0], s));
-  API_TRY(launch_project_fp64(p, d_gphi, p->Q, p->part, s));
   if (ev) API_TRY(cudaEventRecord(ev[1], s));
-  API_TRY(launch_scan_adj(p, p->part, p->S, p->Bbar, s));
+  API_TRY(launch_project_fp64(p, d_gphi, p->Q, p->part, s));
   if (ev) API_TRY(cudaEventRecord(ev[2], s));
-  API_TRY(launch_synth_fp64(p, p->Bbar, p->U, d_grho, s));
+  API_TRY(launch_scan_adj(p, p->part, p->S, p->Bbar, s));
   if (ev) API_TRY(cudaEventRecord(ev[3], s));
+  API_TRY(launch_synth_fp64(p, p->Bbar, p->U, d_grho, s));
+  if (ev) API_TRY(cudaEventRecord(ev[4], s));
   return YGS_OK;
 }
 
@@ -396,8 +414,13 @@ ygs_status ygs_get_moments(ygs_plan* p, double* d_B, double* d_M, void* stream) 
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
   DeviceGuard guard(p->device);
   cudaStream_t s = (cudaStream_t)stream;
-  if (d_B) API_TRY(launch_unpermute(p, p->B, d_B, s));
-  if (d_M) API_TRY(launch_unpermute(p, p->M, d_M, s));
+  if (p->tc_nsl) {
+    if (d_B) API_TRY(tc_unpermute(p, p->tc_B, d_B, s));
+    if (d_M) API_TRY(tc_unpermute(p, p->tc_M, d_M, s));
+  } else {
+    if (d_B) API_TRY(launch_unpermute(p, p->B, d_B, s));
+    if (d_M) API_TRY(launch_unpermute(p, p->M, d_M, s));
+  }
   return YGS_OK;
 }
 
@@ -434,11 +457,11 @@ ygs_status ygs_set_profiling(ygs_plan* p, int enable) {
 ygs_status ygs_read_phase_times(ygs_plan* p, double* ms, int* n_calls) {
   if (!p || !ms || !n_calls) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard guard(p->device);
-  ms[0] = ms[1] = ms[2] = 0.0;
+  for (int k = 0; k < kPhases; ++k) ms[k] = 0.0;
   for (int c = 0; c < p->prof_used; ++c) {
-    cudaEvent_t* ev = &p->prof_events[(size_t)c * 4];
-    API_TRY(cudaEventSynchronize(ev[3]));
-    for (int k = 0; k < 3; ++k) {
+    cudaEvent_t* ev = &p->prof_events[(size_t)c * (kPhases + 1)];
+    API_TRY(cudaEventSynchronize(ev[kPhases]));
+    for (int k = 0; k < kPhases; ++k) {
       float t = 0.f;
       API_TRY(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
       ms[k] += t;
@@ -449,7 +472,7 @@ ygs_status ygs_read_phase_times(ygs_plan* p, double* ms, int* n_calls) {
   return YGS_OK;
 }
 
-int ygs_launches_per_solve(const ygs_plan* p) { return p ? 3 : 0; }
+int ygs_launches_per_solve(const ygs_plan* p) { return p ? (p->tc_nsl ? 6 : 3) : 0; }
 
 ygs_status ygs_get_status(ygs_plan* p) {
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");

@@ -1,6 +1,8 @@
 // Internal declarations of libygs (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -66,6 +68,21 @@ struct ygs_plan {
   std::vector<cudaEvent_t> prof_events;
   int prof_used = 0;
   long long weight_bytes = 0, work_bytes = 0;
+
+  // ---- split-precision (tcgen05) path
+  int tc_nsl = 0;            // BF16 slices per operand (0: FP64 path)
+  int tc_N = 0;              // shells per CTA tile
+  int tc_k_even = 0, tc_k_pad = 0;
+  long long tc_n_pad = 0;
+  std::vector<long long> tc_pad_off;
+  int tc_S = 0, tc_scan_chunk = 0, tc_scan_P = 0;
+  __nv_bfloat16 *tc_ut = nullptr, *tc_qs = nullptr, *tc_f = nullptr, *tc_ms = nullptr;
+  float2* tc_part = nullptr;
+  double *tc_B = nullptr, *tc_M = nullptr, *tc_summ = nullptr, *tc_carry = nullptr;
+  int2* tc_chunks = nullptr;
+  int *tc_pc_int = nullptr, *tc_pc_l = nullptr, *tc_pc_nat = nullptr;
+  long long* tc_pad_off_d = nullptr;
+  CUtensorMap tc_map_ut, tc_map_f, tc_map_q, tc_map_m;
 };
 
 namespace ygs {
@@ -90,5 +107,14 @@ cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double
 cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s);
 // out[i][col_nat[c]] = in[i][c]
 cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+
+// ---- split-precision tensor-core path (ygs_tc.cu) --------------------------
+ygs_status tc_setup(ygs_plan* p, int sms);     // slices, tensor maps, workspaces (at create)
+void tc_free(ygs_plan* p);
+cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s);
+cudaError_t tc_project(const ygs_plan* p, cudaStream_t s);
+cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s);
+cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s);
+cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
 
 }  // namespace ygs

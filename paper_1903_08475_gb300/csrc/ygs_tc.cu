@@ -1,0 +1,494 @@
+// Split-precision path: BF16-slice operands on tcgen05 tensor cores for the
+// two contractions (steps 2 and 5 of Sect. 4.3), FP64 radial scans (step 4).
+//
+// Layouts (K_pad: internal columns padded per parity block to multiples of 64;
+// n_pad: angular cells of each stored patch padded to multiples of 32):
+//   Ut  [s][K_pad][n_pad]  slices of U^T      (projection A operand)
+//   F   [h*NSL+s][Nr][n_pad] slices of the field: h = 0 sigma+ (or rho), h = 1 sigma-
+//   Qs  [s][n_wtotal][K_pad] slices of Q       (synthesis A operand)
+//   Ms  [s][Nr][K_pad]       slices of M       (synthesis B operand)
+//   part [z][Nr][K_pad] float2 (hi, lo) projection partials of chunk z
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "ygs_tc_gemm.cuh"
+
+namespace ygs {
+
+using tc::TcArgs;
+using tc::TcCfg;
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3-D BF16 tensor (kdim fastest, rows, planes) read in boxes of 32 x box_rows x 1 with 64-byte swizzle.
+bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long long planes, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)kdim * 2, (cuuint64_t)kdim * 2 * rows};
+  cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+__device__ __forceinline__ void slices_of(double x, int nsl, __nv_bfloat16 (&s)[3]) {
+  float hi, lo;
+  tc::f64_to_ff(x, hi, lo);
+  tc::ff_to_bf16x3(hi, lo, s[0], s[1], s[2]);
+  if (nsl == 2) {
+    // two slices: the second carries the rounded remainder of hi + lo
+    float r = (hi - __bfloat162float(s[0])) + lo;
+    s[1] = __float2bfloat16_rn(r);
+  }
+}
+
+// Ut[s][pc][apad] from U[row][ci] (FP64 internal order).
+__global__ void slice_ut_kernel(int nsl, int K, int K_pad, long long n_pad, const int* __restrict__ pc_int,
+                                const double* __restrict__ U, PatchTable pt, int nwp, const long long* __restrict__ pad_off,
+                                __nv_bfloat16* __restrict__ Ut) {
+  long long total = (long long)K_pad * n_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int pc = (int)(e / n_pad);
+    long long ap = e % n_pad;
+    int g = 0;
+    while (g + 1 < nwp && pad_off[g + 1] <= ap) ++g;
+    long long a = ap - pad_off[g];
+    __nv_bfloat16 s[3] = {__float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f)};
+    int ci = pc_int[pc];
+    if (ci >= 0 && a < pt.nang[g]) slices_of(U[(pt.ang_off[g] + a) * K + ci], nsl, s);
+    for (int k = 0; k < nsl; ++k) Ut[(long long)k * total + e] = s[k];
+  }
+}
+
+// Qs[s][row][pc] from Q[row][ci].
+__global__ void slice_q_kernel(int nsl, int K, int K_pad, long long rows, const int* __restrict__ pc_int,
+                               const double* __restrict__ Q, __nv_bfloat16* __restrict__ Qs) {
+  long long total = rows * K_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long row = e / K_pad;
+    int pc = (int)(e % K_pad);
+    __nv_bfloat16 s[3] = {__float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f)};
+    int ci = pc_int[pc];
+    if (ci >= 0) slices_of(Q[row * K + ci], nsl, s);
+    for (int k = 0; k < nsl; ++k) Qs[(long long)k * total + e] = s[k];
+  }
+}
+
+// Field slices.  Symmetric: sigma+- = rho_Yin +- rho_Yang in float-float, then
+// sliced; otherwise every patch's rho is sliced into its padded column range.
+__global__ void field_slices_kernel(int nsl, int n_r, int symmetric, int nwp, PatchTable pt,
+                                    const long long* __restrict__ pad_off, long long n_pad,
+                                    const double* __restrict__ rho, __nv_bfloat16* __restrict__ F) {
+  const long long plane = (long long)n_r * n_pad;
+  if (symmetric) {
+    const long long na = pt.nang[0];
+    const long long total = (long long)n_r * na;
+    const double* r0 = rho + pt.fld_off[0];
+    const double* r1 = rho + pt.fld_off[1];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+      long long i = e / na, a = e % na;
+      float h0, l0, h1, l1;
+      tc::f64_to_ff(r0[e], h0, l0);
+      tc::f64_to_ff(r1[e], h1, l1);
+      const long long o = i * n_pad + a;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float s, err;
+        tc::two_sum(h0, h ? -h1 : h1, s, err);
+        float lo = err + (h ? (l0 - l1) : (l0 + l1));
+        float hi = s + lo;            // renormalise
+        lo = lo - (hi - s);
+        __nv_bfloat16 sl[3];
+        tc::ff_to_bf16x3(hi, lo, sl[0], sl[1], sl[2]);
+        if (nsl == 2) sl[1] = __float2bfloat16_rn((hi - __bfloat162float(sl[0])) + lo);
+        for (int k = 0; k < nsl; ++k) F[(long long)(h * nsl + k) * plane + o] = sl[k];
+      }
+    }
+  } else {
+    long long tot_all = 0;
+    for (int g = 0; g < nwp; ++g) tot_all += (long long)n_r * pt.nang[g];
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_all; e += (long long)gridDim.x * blockDim.x) {
+      int g = 0;
+      long long rem = e;
+      while (g + 1 < nwp && rem >= (long long)n_r * pt.nang[g]) {
+        rem -= (long long)n_r * pt.nang[g];
+        ++g;
+      }
+      const long long na = pt.nang[g];
+      long long i = rem / na, a = rem % na;
+      __nv_bfloat16 sl[3];
+      slices_of(rho[pt.fld_off[g] + rem], nsl, sl);
+      const long long o = i * n_pad + pad_off[g] + a;
+      for (int k = 0; k < nsl; ++k) F[(long long)k * plane + o] = sl[k];
+    }
+  }
+}
+
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
+  return tc::f32_to_f64(hi) + tc::f32_to_f64(lo);
+}
+
+// Phase 1 of the chunked scans: B from the partials, local inner / outer
+// recurrences of one chunk of shells with zero carry, and their summaries.
+__global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, const int* __restrict__ pc_l,
+                                  const float2* __restrict__ part, const double* __restrict__ rad,
+                                  double* __restrict__ B, double* __restrict__ summ) {
+  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (pc >= K_pad) return;
+  const int l = pc_l[pc];
+  const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
+  const int P = gridDim.y;
+  if (l < 0 || i0 >= n_r) {
+    for (int i = i0; i < i1; ++i) B[(long long)i * K_pad + pc] = 0.0;
+    for (int k = 0; k < 4; ++k) summ[((long long)k * P + p) * K_pad + pc] = (k == 1 || k == 3) ? 1.0 : 0.0;
+    return;
+  }
+  const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
+  const double* at = rad + (long long)l * n_r;
+  const double* bt = rad + rs + (long long)l * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  double I = 0.0, FI = 1.0;
+  for (int i = i0; i < i1; ++i) {
+    float h = 0.f, lo = 0.f;
+    for (int z = 0; z < S; ++z) {
+      const float2 v = part[z * plane + (long long)i * K_pad + pc];
+      float s, e;
+      tc::two_sum(h, v.x, s, e);
+      h = s;
+      lo += e + v.y;
+    }
+    const double b = ff_to_f64(h, lo);
+    B[(long long)i * K_pad + pc] = b;
+    I = fma(at[i], b, fin[i] * I);
+    FI *= fin[i];
+  }
+  // P_i = b_i B_i + fout_{i-1} P_{i+1}, descending
+  double Pv = 0.0, FP = 1.0;
+  for (int i = i1 - 1; i >= i0; --i) {
+    const double fo = (i > 0) ? fout[i - 1] : 0.0;
+    Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+    FP *= fo;
+  }
+  summ[((long long)0 * P + p) * K_pad + pc] = I;
+  summ[((long long)1 * P + p) * K_pad + pc] = FI;
+  summ[((long long)2 * P + p) * K_pad + pc] = Pv;
+  summ[((long long)3 * P + p) * K_pad + pc] = FP;
+}
+
+// Phase 2: carries between chunks (sequential over chunks, one thread per column).
+__global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ summ, double* __restrict__ carry) {
+  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pc >= K_pad) return;
+  double ci = 0.0;
+  for (int p = 0; p < P; ++p) {
+    carry[((long long)0 * P + p) * K_pad + pc] = ci;  // I at the shell before chunk p
+    ci = summ[((long long)0 * P + p) * K_pad + pc] + summ[((long long)1 * P + p) * K_pad + pc] * ci;
+  }
+  double co = 0.0;
+  for (int p = P - 1; p >= 0; --p) {
+    carry[((long long)1 * P + p) * K_pad + pc] = co;  // P at the shell after chunk p
+    co = summ[((long long)2 * P + p) * K_pad + pc] + summ[((long long)3 * P + p) * K_pad + pc] * co;
+  }
+}
+
+// Phase 3: the recurrences again with the carries; M = I_i + P_{i+1} in FP64
+// and its BF16 slices for the synthesis.
+__global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk, const int* __restrict__ pc_l,
+                                  const double* __restrict__ B, const double* __restrict__ rad,
+                                  const double* __restrict__ carry, double* __restrict__ M,
+                                  __nv_bfloat16* __restrict__ Ms) {
+  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  const int P = gridDim.y;
+  if (pc >= K_pad) return;
+  const int l = pc_l[pc];
+  const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
+  const long long splane = (long long)n_r * K_pad;
+  if (l < 0) {
+    for (int i = i0; i < i1; ++i) {
+      M[(long long)i * K_pad + pc] = 0.0;
+      for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
+    }
+    return;
+  }
+  const long long rs = (long long)(L + 1) * n_r;
+  const double* at = rad + (long long)l * n_r;
+  const double* bt = rad + rs + (long long)l * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  // outer part first: M_i <- P_{i+1}
+  double Pv = carry[((long long)1 * P + p) * K_pad + pc];
+  for (int i = i1 - 1; i >= i0; --i) {
+    M[(long long)i * K_pad + pc] = Pv;
+    const double fo = (i > 0) ? fout[i - 1] : 0.0;
+    Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+  }
+  double I = carry[((long long)0 * P + p) * K_pad + pc];
+  for (int i = i0; i < i1; ++i) {
+    I = fma(at[i], B[(long long)i * K_pad + pc], fin[i] * I);
+    const double m = M[(long long)i * K_pad + pc] + I;
+    M[(long long)i * K_pad + pc] = m;
+    __nv_bfloat16 sl[3];
+    slices_of(m, nsl, sl);
+    for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
+  }
+}
+
+// out[i][nat] = in[i][pc] for every real padded column.
+__global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __restrict__ pc_nat,
+                                    const double* __restrict__ in, double* __restrict__ out) {
+  long long total = (long long)n_r * K_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long i = e / K_pad;
+    int pc = (int)(e % K_pad);
+    int c = pc_nat[pc];
+    if (c >= 0) out[i * K + c] = in[e];
+  }
+}
+
+template <int N, int NSL, int MODE>
+cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(tc::tc_gemm_kernel<N, NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TcCfg<N, NSL>::SMEM);
+}
+
+template <int N, int NSL, int MODE>
+cudaError_t launch_gemm(dim3 grid, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
+  tc::tc_gemm_kernel<N, NSL, MODE><<<grid, tc::kThreads, TcCfg<N, NSL>::SMEM, s>>>(a, b, args);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_gemm(int N, int nsl, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args,
+                          cudaStream_t s) {
+  if (N == 80 && nsl == 3) return launch_gemm<80, 3, MODE>(grid, a, b, args, s);
+  if (N == 128 && nsl == 3) return launch_gemm<128, 3, MODE>(grid, a, b, args, s);
+  if (N == 80 && nsl == 2) return launch_gemm<80, 2, MODE>(grid, a, b, args, s);
+  if (N == 128 && nsl == 2) return launch_gemm<128, 2, MODE>(grid, a, b, args, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// Chooses the N tile: the fewest padded shells among the built widths.
+int tc_choose_n(int n_r) {
+  const int cand[2] = {80, 128};
+  int best = 80;
+  long long best_pad = (long long)1 << 60;
+  for (int n : cand) {
+    long long padded = (long long)((n_r + n - 1) / n) * n;
+    if (padded < best_pad || (padded == best_pad && n > best)) {
+      best_pad = padded;
+      best = n;
+    }
+  }
+  return best;
+}
+
+ygs_status tc_setup(ygs_plan* p, int sms) {
+  const int nsl = p->tc_nsl;
+  const int K = p->K;
+  auto r64 = [](long long x) { return (x + 63) / 64 * 64; };
+  auto r32 = [](long long x) { return (x + 31) / 32 * 32; };
+  // padded column layout: [even block | pad | odd block | pad]
+  const int Ke = p->K_even, Ko = K - p->K_even;
+  p->tc_k_even = (int)r64(Ke);
+  p->tc_k_pad = p->tc_k_even + (int)r64(Ko);
+  std::vector<int> pc_int(p->tc_k_pad, -1), pc_l(p->tc_k_pad, -1), pc_nat(p->tc_k_pad, -1);
+  for (int ci = 0; ci < K; ++ci) {
+    int pc = (ci < Ke) ? ci : p->tc_k_even + (ci - Ke);
+    int c = p->col_perm[ci], l = 0;
+    while ((l + 1) * (l + 1) <= c) ++l;
+    pc_int[pc] = ci;
+    pc_l[pc] = l;
+    pc_nat[pc] = c;
+  }
+  // padded angular layout of the stored patches
+  p->tc_pad_off.assign(p->n_wpatch + 1, 0);
+  for (int g = 0; g < p->n_wpatch; ++g) p->tc_pad_off[g + 1] = p->tc_pad_off[g] + r32(p->nang[g]);
+  p->tc_n_pad = p->tc_pad_off[p->n_wpatch];
+  p->tc_N = tc_choose_n(p->n_r);
+
+  // split-K chunks: about one wave of CTAs
+  const int tiles_m = (p->tc_k_even + tc::BM - 1) / tc::BM +
+                      ((p->tc_k_pad - p->tc_k_even) + tc::BM - 1) / tc::BM;
+  const int tiles_n = (p->n_r + p->tc_N - 1) / p->tc_N;
+  const long long tiles = (long long)tiles_m * tiles_n;
+  long long want = std::max(1LL, (long long)sms / tiles);
+  std::vector<int2> chunks;
+  for (int g = 0; g < p->n_wpatch; ++g) {
+    const long long kb_g = r32(p->nang[g]) / tc::BK;
+    long long sg = std::max(1LL, (want * p->nang[g] + p->nang_wtotal - 1) / p->nang_wtotal);
+    sg = std::min(sg, std::max(1LL, kb_g / 4));
+    const long long per = (kb_g + sg - 1) / sg;
+    for (long long k0 = 0; k0 < kb_g; k0 += per)
+      chunks.push_back(make_int2((int)((p->tc_pad_off[g] + k0 * tc::BK)),
+                                 (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
+  }
+  p->tc_S = (int)chunks.size();
+  p->tc_scan_chunk = 8;
+  p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
+
+  const size_t kp = (size_t)p->tc_k_pad;
+  size_t bytes_ut = (size_t)nsl * kp * p->tc_n_pad * 2;
+  size_t bytes_q = (size_t)nsl * p->nang_wtotal * kp * 2;
+  size_t bytes_f = (size_t)(p->symmetric ? 2 : 1) * nsl * p->n_r * p->tc_n_pad * 2;
+  size_t bytes_m = (size_t)nsl * p->n_r * kp * 2;
+  size_t bytes_part = (size_t)p->tc_S * p->n_r * kp * sizeof(float2);
+  size_t bytes_nk = (size_t)p->n_r * kp * sizeof(double);
+  size_t bytes_sum = (size_t)4 * p->tc_scan_P * kp * sizeof(double);
+  cudaError_t e;
+#define TC_ALLOC(ptr, bytes)                                                          \
+  if ((e = cudaMalloc((void**)&(ptr), std::max<size_t>((bytes), 16))) != cudaSuccess) { \
+    set_error(std::string("cudaMalloc ") + #ptr + ": " + cudaGetErrorString(e));      \
+    return YGS_ERR_OOM;                                                                \
+  }
+  TC_ALLOC(p->tc_ut, bytes_ut);
+  TC_ALLOC(p->tc_qs, bytes_q);
+  TC_ALLOC(p->tc_f, bytes_f);
+  TC_ALLOC(p->tc_ms, bytes_m);
+  TC_ALLOC(p->tc_part, bytes_part);
+  TC_ALLOC(p->tc_B, bytes_nk);
+  TC_ALLOC(p->tc_M, bytes_nk);
+  TC_ALLOC(p->tc_summ, bytes_sum);
+  TC_ALLOC(p->tc_carry, bytes_sum / 2);
+  TC_ALLOC(p->tc_chunks, chunks.size() * sizeof(int2));
+  TC_ALLOC(p->tc_pc_int, kp * sizeof(int));
+  TC_ALLOC(p->tc_pc_l, kp * sizeof(int));
+  TC_ALLOC(p->tc_pc_nat, kp * sizeof(int));
+  TC_ALLOC(p->tc_pad_off_d, (p->n_wpatch + 1) * sizeof(long long));
+#undef TC_ALLOC
+  p->weight_bytes += (long long)(bytes_ut + bytes_q);
+  p->work_bytes += (long long)(bytes_f + bytes_m + bytes_part + 2 * bytes_nk + bytes_sum * 3 / 2);
+#define TC_TRY(x)                                                                  \
+  if ((e = (x)) != cudaSuccess) {                                                  \
+    set_error(std::string("tc setup: ") + #x + ": " + cudaGetErrorString(e));       \
+    return YGS_ERR_CUDA;                                                           \
+  }
+  TC_TRY(cudaMemcpy(p->tc_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  TC_TRY(cudaMemcpy(p->tc_pc_int, pc_int.data(), kp * sizeof(int), cudaMemcpyHostToDevice));
+  TC_TRY(cudaMemcpy(p->tc_pc_l, pc_l.data(), kp * sizeof(int), cudaMemcpyHostToDevice));
+  TC_TRY(cudaMemcpy(p->tc_pc_nat, pc_nat.data(), kp * sizeof(int), cudaMemcpyHostToDevice));
+  TC_TRY(cudaMemcpy(p->tc_pad_off_d, p->tc_pad_off.data(), (p->n_wpatch + 1) * sizeof(long long),
+                    cudaMemcpyHostToDevice));
+  TC_TRY(cudaMemset(p->tc_f, 0, bytes_f));  // padding columns stay zero
+  slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
+                                 p->tc_pad_off_d, p->tc_ut);
+  TC_TRY(cudaGetLastError());
+  slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->Q, p->tc_qs);
+  TC_TRY(cudaGetLastError());
+  TC_TRY(cudaDeviceSynchronize());
+
+  const int N = p->tc_N;
+  if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM) ||
+      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, (p->symmetric ? 2 : 1) * nsl, N) ||
+      !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM) ||
+      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N)) {
+    set_error("cuTensorMapEncodeTiled failed or is unavailable");
+    return YGS_ERR_CUDA;
+  }
+  {
+    cudaError_t a1 = cudaSuccess, a2 = cudaSuccess;
+    if (N == 80 && nsl == 3) { a1 = set_smem_attr<80, 3, tc::kProject>(); a2 = set_smem_attr<80, 3, tc::kSynthesize>(); }
+    if (N == 128 && nsl == 3) { a1 = set_smem_attr<128, 3, tc::kProject>(); a2 = set_smem_attr<128, 3, tc::kSynthesize>(); }
+    if (N == 80 && nsl == 2) { a1 = set_smem_attr<80, 2, tc::kProject>(); a2 = set_smem_attr<80, 2, tc::kSynthesize>(); }
+    if (N == 128 && nsl == 2) { a1 = set_smem_attr<128, 2, tc::kProject>(); a2 = set_smem_attr<128, 2, tc::kSynthesize>(); }
+    TC_TRY(a1);
+    TC_TRY(a2);
+  }
+#undef TC_TRY
+  return YGS_OK;
+}
+
+void tc_free(ygs_plan* p) {
+  void* bufs[] = {p->tc_ut, p->tc_qs, p->tc_f, p->tc_ms, p->tc_part, p->tc_B, p->tc_M, p->tc_summ, p->tc_carry,
+                  p->tc_chunks, p->tc_pc_int, p->tc_pc_l, p->tc_pc_nat, p->tc_pad_off_d};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+}
+
+cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
+  field_slices_kernel<<<4 * 152, 256, 0, s>>>(p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt,
+                                              p->tc_pad_off_d, p->tc_n_pad, rho, p->tc_f);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) {
+  TcArgs a{};
+  a.err = p->d_err;
+  a.flush_kb = 2;
+  a.n_b = p->n_r;
+  a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
+  a.a_row_odd = p->tc_k_even;
+  a.a_rows_total = p->tc_k_pad;
+  a.b_plane_odd = p->symmetric ? p->tc_nsl : 0;
+  a.chunks = p->tc_chunks;
+  a.part = p->tc_part;
+  a.ldp = p->tc_k_pad;
+  const int tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
+  dim3 grid(tiles_m, (p->n_r + p->tc_N - 1) / p->tc_N, p->tc_S);
+  return dispatch_gemm<tc::kProject>(p->tc_N, p->tc_nsl, grid, p->tc_map_ut, p->tc_map_f, a, s);
+}
+
+cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
+  const int P = p->tc_scan_P;
+  dim3 g1((p->tc_k_pad + 127) / 128, P);
+  scan_local_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_pc_l,
+                                       p->tc_part, p->rad, p->tc_B, p->tc_summ);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scan_carry_kernel<<<(p->tc_k_pad + 127) / 128, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  scan_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
+                                       p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
+  TcArgs a{};
+  a.err = p->d_err;
+  a.flush_kb = 2;
+  a.n_b = p->n_r;
+  a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
+  a.k_total = p->tc_k_pad;
+  a.symmetric = p->symmetric ? 1 : 0;
+  a.pt = p->pt;
+  long long row = 0, nmax = 0;
+  for (int g = 0; g < p->n_wpatch; ++g) {
+    a.a_row0[g] = row;
+    row += p->nang[g];
+    nmax = std::max(nmax, p->nang[g]);
+  }
+  a.phi = phi;
+  dim3 grid((unsigned)((nmax + tc::BM - 1) / tc::BM), (p->n_r + p->tc_N - 1) / p->tc_N, p->n_wpatch);
+  return dispatch_gemm<tc::kSynthesize>(p->tc_N, p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, a, s);
+}
+
+cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s) {
+  tc_unpermute_kernel<<<256, 256, 0, s>>>(p->n_r, p->K, p->tc_k_pad, p->tc_pc_nat, in, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ygs

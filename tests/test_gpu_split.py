@@ -1,0 +1,89 @@
+"""GPU parity of the split-precision tensor-core path (BF16 slices on tcgen05)
+against the CPU FP64 oracle, through the C ABI.
+
+BF16x6 (three slices, six products) is held to 1e-6 relative error in Phi;
+BF16x3 (two slices, three products) to 5e-4.  The FP32 accumulation of the
+tensor cores is flushed into float-float sums every 64 k-elements, which keeps
+its bias far below these bounds."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_08475_gb300 import Plan, ygs_get_moments, ygs_solve, workloads as W
+from tests._util import rel_max, small_yinyang
+from tests.test_gpu_fp64 import three_patch_grid, hole_grid
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16x6": 1e-6, "bf16x3": 5e-4}
+
+CASES = {
+    "yy_small": lambda: small_yinyang(W),
+    "yy_ragged": lambda: small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9),
+    "yy_centre_eval": lambda: small_yinyang(W, eval=1),
+    "polar": lambda: W.polar_grid(7, 13, W.linear_edges(6, 0.1, 1.0), 5),
+    "three_patch": three_patch_grid,
+    "hole": hole_grid,
+    "lmax0": lambda: small_yinyang(W, l_max=0),
+    "one_shell": lambda: small_yinyang(W, n_r=1, l_max=3),
+    "many_shells": lambda: small_yinyang(W, n_theta=8, n_phi=20, n_r=300, l_max=7),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, cuda):
+    grid = CASES[request.param]()
+    rho = W.random_density(grid, 11)
+    phi_ref, B_ref, M_ref = oracle.solve(grid, rho, moments=True)
+    return request.param, grid, rho, phi_ref, B_ref, M_ref
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "bf16x3"])
+def test_phi_matches_oracle(case, precision):
+    import torch
+    name, grid, rho, phi_ref, B_ref, M_ref = case
+    with Plan(grid, precision) as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        B, M = ygs_get_moments(plan)
+        torch.cuda.synchronize()
+        err = rel_max(phi.cpu().numpy(), phi_ref)
+        assert err <= TOL[precision], f"{name} {precision}: {err:.3e}"
+        # monopole moments (all-positive sums) to the same bound
+        assert rel_max(B.cpu().numpy()[:, 0], B_ref[:, 0]) <= TOL[precision]
+        assert rel_max(M.cpu().numpy()[:, 0], M_ref[:, 0]) <= TOL[precision]
+
+
+def test_config0_bf16x6(cuda):
+    import torch
+    grid, rho = W.config0()
+    ref = oracle.solve(grid, rho)
+    with Plan(grid, "bf16x6") as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        torch.cuda.synchronize()
+        assert rel_max(phi.cpu().numpy(), ref) <= TOL["bf16x6"]
+
+
+def test_split_deterministic(cuda):
+    import torch
+    grid = small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9)
+    rho = torch.from_numpy(W.random_density(grid, 2)).cuda()
+    with Plan(grid, "bf16x6") as plan:
+        a = ygs_solve(plan, rho).clone()
+        b = ygs_solve(plan, rho)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+def test_large_dynamic_range(cuda):
+    """Density spanning 1e-30 .. 1e30 (the BF16 exponent range covers it)."""
+    import torch
+    grid = small_yinyang(W, n_theta=8, n_phi=24, n_r=20, l_max=6)
+    rng = np.random.default_rng(4)
+    rho = 10.0 ** rng.uniform(-30, 30, grid.n_cells)
+    ref = oracle.solve(grid, rho)
+    with Plan(grid, "bf16x6") as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        torch.cuda.synchronize()
+        assert rel_max(phi.cpu().numpy(), ref) <= TOL["bf16x6"]
