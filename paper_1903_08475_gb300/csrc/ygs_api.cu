@@ -301,6 +301,7 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
   st = build_weights(p);
   if (st != YGS_OK) return fail_free(st);
   if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3) {
+    if (p->n_r > 65535) return fail_free(fail(YGS_ERR_UNSUPPORTED, "split precision supports n_r <= 65535"));
     p->tc_nsl = (p->precision == YGS_BF16X6) ? 3 : 2;
     st = tc_setup(p, sms);
     if (st != YGS_OK) return fail_free(st);

@@ -2,7 +2,7 @@
 // two contractions (steps 2 and 5 of Sect. 4.3), FP64 radial scans (step 4).
 //
 // Layouts (K_pad: internal columns padded per parity block to multiples of 64;
-// n_pad: angular cells of each stored patch padded to multiples of 32):
+// n_pad: angular cells of each stored patch padded to whole k-blocks of BK):
 //   Ut  [s][K_pad][n_pad]  slices of U^T      (projection A operand)
 //   F   [h*NSL+s][Nr][n_pad] slices of the field: h = 0 sigma+ (or rho), h = 1 sigma-
 //   Qs  [s][n_wtotal][K_pad] slices of Q       (synthesis A operand)
@@ -38,7 +38,8 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D BF16 tensor (kdim fastest, rows, planes) read in boxes of 32 x box_rows x 1 with 64-byte swizzle.
+// 3-D BF16 tensor (kdim fastest, rows, planes) read in boxes of BK x box_rows x 1, swizzled to match
+// the UMMA shared-memory descriptors (128-byte swizzle for BK = 64).
 bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long long planes, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
@@ -47,7 +48,7 @@ bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long l
   cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             tc::BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -96,51 +97,67 @@ __global__ void slice_q_kernel(int nsl, int K, int K_pad, long long rows, const 
 
 // Field slices.  Symmetric: sigma+- = rho_Yin +- rho_Yang in float-float, then
 // sliced; otherwise every patch's rho is sliced into its padded column range.
-__global__ void field_slices_kernel(int nsl, int n_r, int symmetric, int nwp, PatchTable pt,
+// Grid: (x over angular cells in steps of 2 per thread, y over shells, z over
+// stored patches); each thread handles two neighbouring cells (16-byte loads,
+// 4-byte stores).
+__device__ __forceinline__ void ff_slices(float hi, float lo, int nsl, __nv_bfloat16 (&sl)[3]) {
+  tc::ff_to_bf16x3(hi, lo, sl[0], sl[1], sl[2]);
+  if (nsl == 2) sl[1] = __float2bfloat16_rn((hi - __bfloat162float(sl[0])) + lo);
+}
+
+__global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable pt,
                                     const long long* __restrict__ pad_off, long long n_pad,
                                     const double* __restrict__ rho, __nv_bfloat16* __restrict__ F) {
   const long long plane = (long long)n_r * n_pad;
-  if (symmetric) {
-    const long long na = pt.nang[0];
-    const long long total = (long long)n_r * na;
-    const double* r0 = rho + pt.fld_off[0];
-    const double* r1 = rho + pt.fld_off[1];
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-      long long i = e / na, a = e % na;
-      float h0, l0, h1, l1;
-      tc::f64_to_ff(r0[e], h0, l0);
-      tc::f64_to_ff(r1[e], h1, l1);
-      const long long o = i * n_pad + a;
+  const int g = blockIdx.z;
+  const int i = blockIdx.y;
+  const int na = (int)pt.nang[g];
+  const long long row_in = pt.fld_off[g] + (long long)i * na;
+  const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
+  for (int a = 2 * (blockIdx.x * blockDim.x + threadIdx.x); a < na; a += 2 * gridDim.x * blockDim.x) {
+    const bool two = (a + 1 < na);
+    double v0[2], v1[2];
+    v0[0] = rho[row_in + a];
+    v0[1] = two ? rho[row_in + a + 1] : 0.0;
+    if (symmetric) {
+      const long long r1 = pt.fld_off[1] + (long long)i * na;
+      v1[0] = rho[r1 + a];
+      v1[1] = two ? rho[r1 + a + 1] : 0.0;
+    }
+    __nv_bfloat16 out[2][2][3];  // [h][cell][slice]
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        float s, err;
-        tc::two_sum(h0, h ? -h1 : h1, s, err);
-        float lo = err + (h ? (l0 - l1) : (l0 + l1));
-        float hi = s + lo;            // renormalise
-        lo = lo - (hi - s);
-        __nv_bfloat16 sl[3];
-        tc::ff_to_bf16x3(hi, lo, sl[0], sl[1], sl[2]);
-        if (nsl == 2) sl[1] = __float2bfloat16_rn((hi - __bfloat162float(sl[0])) + lo);
-        for (int k = 0; k < nsl; ++k) F[(long long)(h * nsl + k) * plane + o] = sl[k];
+    for (int c = 0; c < 2; ++c) {
+      float h0, l0;
+      tc::f64_to_ff(v0[c], h0, l0);
+      if (!symmetric) {
+        ff_slices(h0, l0, nsl, out[0][c]);
+      } else {
+        float h1, l1;
+        tc::f64_to_ff(v1[c], h1, l1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float s, err;
+          tc::two_sum(h0, h ? -h1 : h1, s, err);
+          float lo = err + (h ? (l0 - l1) : (l0 + l1));
+          float hi = s + lo;  // renormalise
+          lo = lo - (hi - s);
+          ff_slices(hi, lo, nsl, out[h][c]);
+        }
       }
     }
-  } else {
-    long long tot_all = 0;
-    for (int g = 0; g < nwp; ++g) tot_all += (long long)n_r * pt.nang[g];
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_all; e += (long long)gridDim.x * blockDim.x) {
-      int g = 0;
-      long long rem = e;
-      while (g + 1 < nwp && rem >= (long long)n_r * pt.nang[g]) {
-        rem -= (long long)n_r * pt.nang[g];
-        ++g;
+    const int nh = symmetric ? 2 : 1;
+    for (int h = 0; h < nh; ++h)
+      for (int k = 0; k < nsl; ++k) {
+        __nv_bfloat16* dst = F + (long long)(h * nsl + k) * plane + row_out + a;
+        if (two) {
+          __nv_bfloat162 pr;
+          pr.x = out[h][0][k];
+          pr.y = out[h][1][k];
+          *reinterpret_cast<__nv_bfloat162*>(dst) = pr;
+        } else {
+          dst[0] = out[h][0][k];
+        }
       }
-      const long long na = pt.nang[g];
-      long long i = rem / na, a = rem % na;
-      __nv_bfloat16 sl[3];
-      slices_of(rho[pt.fld_off[g] + rem], nsl, sl);
-      const long long o = i * n_pad + pad_off[g] + a;
-      for (int k = 0; k < nsl; ++k) F[(long long)k * plane + o] = sl[k];
-    }
   }
 }
 
@@ -311,7 +328,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   const int nsl = p->tc_nsl;
   const int K = p->K;
   auto r64 = [](long long x) { return (x + 63) / 64 * 64; };
-  auto r32 = [](long long x) { return (x + 31) / 32 * 32; };
+  auto r32 = [](long long x) { return (x + tc::BK - 1) / tc::BK * tc::BK; };  // angular padding to whole k-blocks
   // padded column layout: [even block | pad | odd block | pad]
   const int Ke = p->K_even, Ko = K - p->K_even;
   p->tc_k_even = (int)r64(Ke);
@@ -430,15 +447,20 @@ void tc_free(ygs_plan* p) {
 }
 
 cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
-  field_slices_kernel<<<4 * 152, 256, 0, s>>>(p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt,
-                                              p->tc_pad_off_d, p->tc_n_pad, rho, p->tc_f);
+  long long nmax = 0;
+  for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
+  const int threads = 128;
+  const int bx = (int)std::min<long long>(64, (nmax / 2 + threads - 1) / threads);
+  dim3 grid(std::max(1, bx), p->n_r, p->n_wpatch);
+  field_slices_kernel<<<grid, threads, 0, s>>>(p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d,
+                                               p->tc_n_pad, rho, p->tc_f);
   return cudaGetLastError();
 }
 
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) {
   TcArgs a{};
   a.err = p->d_err;
-  a.flush_kb = 2;
+  a.flush_kb = 64 / tc::BK;  // flush the leading product every 64 k-elements
   a.n_b = p->n_r;
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.a_row_odd = p->tc_k_even;
@@ -469,7 +491,7 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
   TcArgs a{};
   a.err = p->d_err;
-  a.flush_kb = 2;
+  a.flush_kb = 64 / tc::BK;
   a.n_b = p->n_r;
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
@@ -482,7 +504,8 @@ cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
     nmax = std::max(nmax, p->nang[g]);
   }
   a.phi = phi;
-  dim3 grid((unsigned)((nmax + tc::BM - 1) / tc::BM), (p->n_r + p->tc_N - 1) / p->tc_N, p->n_wpatch);
+  // shell tiles vary fastest so the CTAs that share one Q tile run together (L2 reuse)
+  dim3 grid((p->n_r + p->tc_N - 1) / p->tc_N, (unsigned)((nmax + tc::BM - 1) / tc::BM), p->n_wpatch);
   return dispatch_gemm<tc::kSynthesize>(p->tc_N, p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, a, s);
 }
 

@@ -127,6 +127,17 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
   return d;
 }
 
+// Same for 128-byte rows (64 bf16) with 128-byte swizzle: 8-row atoms of 1 KB.
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);       // start address
+  d |= (uint64_t)1 << 16;                        // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;              // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                        // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                        // layout: SWIZZLE_128B
+  return d;
+}
+
 // Instruction descriptor of kind::f16 with fp32 accumulation, both operands K-major.
 // ab_fmt: 0 = fp16, 1 = bf16.
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int ab_fmt) {

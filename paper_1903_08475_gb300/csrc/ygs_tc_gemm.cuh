@@ -30,7 +30,10 @@
 namespace ygs {
 namespace tc {
 
-constexpr int BK = 32;   // k elements per stage
+#ifndef YGS_TC_BK
+#define YGS_TC_BK 64
+#endif
+constexpr int BK = YGS_TC_BK;  // k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
 constexpr int BM = 128;  // output rows per CTA (TMEM lanes)
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -49,7 +52,7 @@ struct TcArgs {
   const int2* chunks;   // k range [x, y) of chunk z, in elements (multiples of BK)
   float2* part;         // [z][n_b][ldp] (hi, lo)
   int ldp;
-  // ---- synthesis: blockIdx = (m-tile within the patch, n-tile, patch)
+  // ---- synthesis: blockIdx = (n-tile, m-tile within the patch, patch)
   int k_even;           // length of the even column block (elements, multiple of BK)
   int k_total;          // total padded columns
   int symmetric;
@@ -65,7 +68,11 @@ struct TcCfg {
   static constexpr int A_SLICE = BM * BK * 2;
   static constexpr int B_SLICE = N * BK * 2;
   static constexpr int STAGE = NSL * (A_SLICE + B_SLICE);
-  static constexpr int STAGES = (200 * 1024) / STAGE > 8 ? 8 : (200 * 1024) / STAGE;
+#ifdef YGS_TC_STAGES
+  static constexpr int STAGES = YGS_TC_STAGES;
+#else
+  static constexpr int STAGES = (220 * 1024) / STAGE > 8 ? 8 : (220 * 1024) / STAGE;
+#endif
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
   static constexpr uint32_t IDESC = idesc_f16(BM, N, 1);
   // TMEM columns: correction accumulators of up to two segments, then rotating
@@ -137,10 +144,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     g_patch = blockIdx.z;
     const long long nang = args.pt.nang[g_patch];
-    if ((long long)blockIdx.x * BM >= nang) return;  // the whole CTA leaves before any setup
-    a_row0 = (int)(args.a_row0[g_patch] + (long long)blockIdx.x * BM);
+    if ((long long)blockIdx.y * BM >= nang) return;  // the whole CTA leaves before any setup
+    a_row0 = (int)(args.a_row0[g_patch] + (long long)blockIdx.y * BM);
     a_rows_end = 0;
-    b_row0 = blockIdx.y * N;
+    b_row0 = blockIdx.x * N;
     kstart = 0;
     const bool two = args.symmetric && args.k_even < args.k_total;
     seg_kb[0] = (two ? args.k_even : args.k_total) / BK;
@@ -255,8 +262,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
             for (int p = 0; p < C::NPROD; ++p) {
-              const uint64_t ad = sdesc_kmajor_sw64(sA + prod_s(p) * C::A_SLICE + kk * 32);
-              const uint64_t bd = sdesc_kmajor_sw64(sB + prod_t(p) * C::B_SLICE + kk * 32);
+              const uint64_t ad = BK == 64 ? sdesc_kmajor_sw128(sA + prod_s(p) * C::A_SLICE + kk * 32)
+                                           : sdesc_kmajor_sw64(sA + prod_s(p) * C::A_SLICE + kk * 32);
+              const uint64_t bd = BK == 64 ? sdesc_kmajor_sw128(sB + prod_t(p) * C::B_SLICE + kk * 32)
+                                           : sdesc_kmajor_sw64(sB + prod_t(p) * C::B_SLICE + kk * 32);
               if (p == 0) {
                 umma_f16(d_main, ad, bd, C::IDESC, main_init ? 1u : 0u);
                 main_init = true;
@@ -362,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     } else {
       const long long nang = args.pt.nang[g_patch];
-      const long long a_loc = (long long)blockIdx.x * BM + r;
+      const long long a_loc = (long long)blockIdx.y * BM + r;
       if (a_loc < nang) {
 #pragma unroll
         for (int j = 0; j < NH; ++j) {
