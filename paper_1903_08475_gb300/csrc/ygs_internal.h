@@ -82,6 +82,8 @@ struct ygs_plan {
   int2* tc_chunks = nullptr;
   int *tc_pc_int = nullptr, *tc_pc_l = nullptr, *tc_pc_nat = nullptr;
   long long* tc_pad_off_d = nullptr;
+  float2* tc_mono = nullptr;  // -G M[i][0] per shell as (hi, lo)
+  double* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells
   CUtensorMap tc_map_ut, tc_map_f, tc_map_q, tc_map_m;
 };
 

@@ -81,16 +81,18 @@ __global__ void slice_ut_kernel(int nsl, int K, int K_pad, long long n_pad, cons
   }
 }
 
-// Qs[s][row][pc] from Q[row][ci].
+// Qs[s][row][pc] from Q[row][ci]; the monopole column (natural column 0) is
+// left zero: the synthesis epilogue adds -G M[i][0] for it.
 __global__ void slice_q_kernel(int nsl, int K, int K_pad, long long rows, const int* __restrict__ pc_int,
-                               const double* __restrict__ Q, __nv_bfloat16* __restrict__ Qs) {
+                               const int* __restrict__ pc_nat, const double* __restrict__ Q,
+                               __nv_bfloat16* __restrict__ Qs) {
   long long total = rows * K_pad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     long long row = e / K_pad;
     int pc = (int)(e % K_pad);
     __nv_bfloat16 s[3] = {__float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f)};
     int ci = pc_int[pc];
-    if (ci >= 0) slices_of(Q[row * K + ci], nsl, s);
+    if (ci >= 0 && pc_nat[pc] != 0) slices_of(Q[row * K + ci], nsl, s);
     for (int k = 0; k < nsl; ++k) Qs[(long long)k * total + e] = s[k];
   }
 }
@@ -161,6 +163,26 @@ __global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable 
   }
 }
 
+// Products of the radial ratios over every chunk of shells (per degree l):
+// cp[0][l][p] = prod_{i in chunk p} (r_{i-1}^+/r_i^+)^(l+1),
+// cp[1][l][p] = prod_{i in chunk p} (r_{i-1}^+/r_i^+)^l   (0 for chunks that contain shell 0).
+__global__ void chunk_prod_kernel(int n_r, int L, int chunk, int P, const double* __restrict__ rad,
+                                  double* __restrict__ cp) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (L + 1) * P) return;
+  int l = t / P, p = t % P;
+  const long long rs = (long long)(L + 1) * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  double a = 1.0, b = 1.0;
+  for (int i = p * chunk; i < min(n_r, (p + 1) * chunk); ++i) {
+    a *= fin[i];
+    b *= (i > 0) ? fout[i - 1] : 0.0;
+  }
+  cp[(long long)l * P + p] = a;
+  cp[(long long)(L + 1) * P + (long long)l * P + p] = b;
+}
+
 __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
   return tc::f32_to_f64(hi) + tc::f32_to_f64(lo);
 }
@@ -169,7 +191,7 @@ __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
 // recurrences of one chunk of shells with zero carry, and their summaries.
 __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, const int* __restrict__ pc_l,
                                   const float2* __restrict__ part, const double* __restrict__ rad,
-                                  double* __restrict__ B, double* __restrict__ summ) {
+                                  const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ summ) {
   const int pc = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (pc >= K_pad) return;
@@ -186,7 +208,7 @@ __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, c
   const double* bt = rad + rs + (long long)l * n_r;
   const double* fin = rad + 2 * rs + (long long)l * n_r;
   const double* fout = rad + 3 * rs + (long long)l * n_r;
-  double I = 0.0, FI = 1.0;
+  double I = 0.0;
   for (int i = i0; i < i1; ++i) {
     float h = 0.f, lo = 0.f;
     for (int z = 0; z < S; ++z) {
@@ -199,34 +221,63 @@ __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, c
     const double b = ff_to_f64(h, lo);
     B[(long long)i * K_pad + pc] = b;
     I = fma(at[i], b, fin[i] * I);
-    FI *= fin[i];
   }
   // P_i = b_i B_i + fout_{i-1} P_{i+1}, descending
-  double Pv = 0.0, FP = 1.0;
+  double Pv = 0.0;
   for (int i = i1 - 1; i >= i0; --i) {
     const double fo = (i > 0) ? fout[i - 1] : 0.0;
     Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
-    FP *= fo;
   }
+  const double FI = cp[(long long)l * P + p];
+  const double FP = cp[(long long)(L + 1) * P + (long long)l * P + p];
   summ[((long long)0 * P + p) * K_pad + pc] = I;
   summ[((long long)1 * P + p) * K_pad + pc] = FI;
   summ[((long long)2 * P + p) * K_pad + pc] = Pv;
   summ[((long long)3 * P + p) * K_pad + pc] = FP;
 }
 
-// Phase 2: carries between chunks (sequential over chunks, one thread per column).
+// Phase 2: carries between chunks (sequential over chunks, one thread per
+// column).  Summaries are fetched in batches of independent loads before the
+// dependent FP64 chain runs over them.
 __global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ summ, double* __restrict__ carry) {
   const int pc = blockIdx.x * blockDim.x + threadIdx.x;
   if (pc >= K_pad) return;
+  constexpr int BT = 16;
   double ci = 0.0;
-  for (int p = 0; p < P; ++p) {
-    carry[((long long)0 * P + p) * K_pad + pc] = ci;  // I at the shell before chunk p
-    ci = summ[((long long)0 * P + p) * K_pad + pc] + summ[((long long)1 * P + p) * K_pad + pc] * ci;
+  for (int p0 = 0; p0 < P; p0 += BT) {
+    double sI[BT], fI[BT];
+#pragma unroll
+    for (int q = 0; q < BT; ++q) {
+      const int p = p0 + q;
+      sI[q] = (p < P) ? summ[((long long)0 * P + p) * K_pad + pc] : 0.0;
+      fI[q] = (p < P) ? summ[((long long)1 * P + p) * K_pad + pc] : 1.0;
+    }
+#pragma unroll
+    for (int q = 0; q < BT; ++q) {
+      const int p = p0 + q;
+      if (p < P) {
+        carry[((long long)0 * P + p) * K_pad + pc] = ci;  // I at the shell before chunk p
+        ci = fma(fI[q], ci, sI[q]);
+      }
+    }
   }
   double co = 0.0;
-  for (int p = P - 1; p >= 0; --p) {
-    carry[((long long)1 * P + p) * K_pad + pc] = co;  // P at the shell after chunk p
-    co = summ[((long long)2 * P + p) * K_pad + pc] + summ[((long long)3 * P + p) * K_pad + pc] * co;
+  for (int p1 = P - 1; p1 >= 0; p1 -= BT) {
+    double sP[BT], fP[BT];
+#pragma unroll
+    for (int q = 0; q < BT; ++q) {
+      const int p = p1 - q;
+      sP[q] = (p >= 0) ? summ[((long long)2 * P + p) * K_pad + pc] : 0.0;
+      fP[q] = (p >= 0) ? summ[((long long)3 * P + p) * K_pad + pc] : 1.0;
+    }
+#pragma unroll
+    for (int q = 0; q < BT; ++q) {
+      const int p = p1 - q;
+      if (p >= 0) {
+        carry[((long long)1 * P + p) * K_pad + pc] = co;  // P at the shell after chunk p
+        co = fma(fP[q], co, sP[q]);
+      }
+    }
   }
 }
 
@@ -235,7 +286,7 @@ __global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ s
 __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk, const int* __restrict__ pc_l,
                                   const double* __restrict__ B, const double* __restrict__ rad,
                                   const double* __restrict__ carry, double* __restrict__ M,
-                                  __nv_bfloat16* __restrict__ Ms) {
+                                  __nv_bfloat16* __restrict__ Ms, double G, float2* __restrict__ mono) {
   const int pc = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   const int P = gridDim.y;
@@ -267,6 +318,11 @@ __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk,
     I = fma(at[i], B[(long long)i * K_pad + pc], fin[i] * I);
     const double m = M[(long long)i * K_pad + pc] + I;
     M[(long long)i * K_pad + pc] = m;
+    if (pc == 0) {  // natural column 0 (l = 0) is padded column 0: the monopole
+      float h, lo;
+      tc::f64_to_ff(-G * m, h, lo);
+      mono[i] = make_float2(h, lo);
+    }
     __nv_bfloat16 sl[3];
     slices_of(m, nsl, sl);
     for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
@@ -365,7 +421,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
                                  (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
   }
   p->tc_S = (int)chunks.size();
-  p->tc_scan_chunk = 8;
+  p->tc_scan_chunk = 16;
   p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
 
   const size_t kp = (size_t)p->tc_k_pad;
@@ -396,6 +452,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_ALLOC(p->tc_pc_l, kp * sizeof(int));
   TC_ALLOC(p->tc_pc_nat, kp * sizeof(int));
   TC_ALLOC(p->tc_pad_off_d, (p->n_wpatch + 1) * sizeof(long long));
+  TC_ALLOC(p->tc_mono, (size_t)p->n_r * sizeof(float2));
+  TC_ALLOC(p->tc_cp, (size_t)2 * (p->l_max + 1) * p->tc_scan_P * sizeof(double));
 #undef TC_ALLOC
   p->weight_bytes += (long long)(bytes_ut + bytes_q);
   p->work_bytes += (long long)(bytes_f + bytes_m + bytes_part + 2 * bytes_nk + bytes_sum * 3 / 2);
@@ -411,10 +469,13 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_TRY(cudaMemcpy(p->tc_pad_off_d, p->tc_pad_off.data(), (p->n_wpatch + 1) * sizeof(long long),
                     cudaMemcpyHostToDevice));
   TC_TRY(cudaMemset(p->tc_f, 0, bytes_f));  // padding columns stay zero
+  chunk_prod_kernel<<<((p->l_max + 1) * p->tc_scan_P + 127) / 128, 128>>>(p->n_r, p->l_max, p->tc_scan_chunk,
+                                                                          p->tc_scan_P, p->rad, p->tc_cp);
+  TC_TRY(cudaGetLastError());
   slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
                                  p->tc_pad_off_d, p->tc_ut);
   TC_TRY(cudaGetLastError());
-  slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->Q, p->tc_qs);
+  slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_qs);
   TC_TRY(cudaGetLastError());
   TC_TRY(cudaDeviceSynchronize());
 
@@ -441,7 +502,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
 
 void tc_free(ygs_plan* p) {
   void* bufs[] = {p->tc_ut, p->tc_qs, p->tc_f, p->tc_ms, p->tc_part, p->tc_B, p->tc_M, p->tc_summ, p->tc_carry,
-                  p->tc_chunks, p->tc_pc_int, p->tc_pc_l, p->tc_pc_nat, p->tc_pad_off_d};
+                  p->tc_chunks, p->tc_pc_int, p->tc_pc_l, p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -478,13 +539,13 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   const int P = p->tc_scan_P;
   dim3 g1((p->tc_k_pad + 127) / 128, P);
   scan_local_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_pc_l,
-                                       p->tc_part, p->rad, p->tc_B, p->tc_summ);
+                                       p->tc_part, p->rad, p->tc_cp, p->tc_B, p->tc_summ);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   scan_carry_kernel<<<(p->tc_k_pad + 127) / 128, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   scan_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
-                                       p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms);
+                                       p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms, p->G, p->tc_mono);
   return cudaGetLastError();
 }
 
@@ -504,6 +565,7 @@ cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
     nmax = std::max(nmax, p->nang[g]);
   }
   a.phi = phi;
+  a.mono = p->tc_mono;
   // shell tiles vary fastest so the CTAs that share one Q tile run together (L2 reuse)
   dim3 grid((p->n_r + p->tc_N - 1) / p->tc_N, (unsigned)((nmax + tc::BM - 1) / tc::BM), p->n_wpatch);
   return dispatch_gemm<tc::kSynthesize>(p->tc_N, p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, a, s);

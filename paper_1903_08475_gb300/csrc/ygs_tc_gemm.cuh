@@ -59,6 +59,11 @@ struct TcArgs {
   PatchTable pt;        // field offsets / angular sizes per patch
   long long a_row0[kMaxPatch];  // first A row of each patch
   double* phi;
+  // Monopole term of Eq. gravpotmult: Q_00 = -G at every cell, so
+  // mono[n] = -G M[n][0] (a float-float pair per shell) is added here instead
+  // of being accumulated on the tensor cores (its column is zero in the Q
+  // slices).  nullptr disables it.
+  const float2* mono;
 };
 
 template <int N, int NSL>
@@ -377,7 +382,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < NH; ++j) {
           const int n = b_row0 + col0 + j;
           if (n >= args.n_b) continue;
-          const float v = hi[j] + lo[j];
+          float v = hi[j] + lo[j];
+          if (args.mono) {
+            // the monopole belongs to the even block (E) or, without the symmetry, to the only block
+            const float2 mm = args.mono[n];
+            const float mh = mm.x, ml = mm.y;
+            if (ng1 > 0) {
+              float s, e;
+              two_sum(ev[j], mh, s, e);
+              ev[j] = s + (e + ml);
+            } else {
+              float s, e;
+              two_sum(hi[j], mh, s, e);
+              v = s + (e + ml + lo[j]);
+            }
+          }
           if (args.symmetric) {
             // Yin-Yang: Phi_Yin = E + O, Phi_Yang = E - O (O = 0 when there are no odd columns)
             const float e = (ng1 > 0) ? ev[j] : v, o = (ng1 > 0) ? v : 0.0f;
