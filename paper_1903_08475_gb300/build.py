@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libygs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-              "-Xptxas", "-warn-spills"] + ARCH
+              "-Xptxas", "-warn-spills"] + ARCH + [f for f in os.environ.get("YGS_NVCC_EXTRA", "").split() if f]
 
 
 def nvcc() -> str:

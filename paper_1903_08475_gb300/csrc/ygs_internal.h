@@ -71,7 +71,10 @@ struct ygs_plan {
 
   // ---- split-precision (tcgen05) path
   int tc_nsl = 0;            // BF16 slices per operand (0: FP64 path)
-  int tc_N = 0;              // shells per CTA tile
+  int tc_N = 0;              // shells per full tile
+  int tc_n_full = 0;         // full shell tiles
+  int tc_n_tail = 0;         // width of the tail shell tile (0: none)
+  int tc_sms = 0;            // CTAs of the persistent contraction kernels
   int tc_k_even = 0, tc_k_pad = 0;
   long long tc_n_pad = 0;
   std::vector<long long> tc_pad_off;
@@ -84,7 +87,7 @@ struct ygs_plan {
   long long* tc_pad_off_d = nullptr;
   float2* tc_mono = nullptr;  // -G M[i][0] per shell as (hi, lo)
   double* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells
-  CUtensorMap tc_map_ut, tc_map_f, tc_map_q, tc_map_m;
+  CUtensorMap tc_map_ut, tc_map_f, tc_map_f_tail, tc_map_q, tc_map_m, tc_map_m_tail;
 };
 
 namespace ygs {

@@ -341,44 +341,26 @@ __global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __rest
   }
 }
 
-template <int N, int NSL, int MODE>
+template <int NSL, int MODE>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(tc::tc_gemm_kernel<N, NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<N, NSL>::SMEM);
-}
-
-template <int N, int NSL, int MODE>
-cudaError_t launch_gemm(dim3 grid, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args, cudaStream_t s) {
-  tc::tc_gemm_kernel<N, NSL, MODE><<<grid, tc::kThreads, TcCfg<N, NSL>::SMEM, s>>>(a, b, args);
-  return cudaGetLastError();
+  return cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              TcCfg<NSL>::SMEM);
 }
 
 template <int MODE>
-cudaError_t dispatch_gemm(int N, int nsl, dim3 grid, const CUtensorMap& a, const CUtensorMap& b, const TcArgs& args,
-                          cudaStream_t s) {
-  if (N == 80 && nsl == 3) return launch_gemm<80, 3, MODE>(grid, a, b, args, s);
-  if (N == 128 && nsl == 3) return launch_gemm<128, 3, MODE>(grid, a, b, args, s);
-  if (N == 80 && nsl == 2) return launch_gemm<80, 2, MODE>(grid, a, b, args, s);
-  if (N == 128 && nsl == 2) return launch_gemm<128, 2, MODE>(grid, a, b, args, s);
-  return cudaErrorInvalidValue;
+cudaError_t dispatch_gemm(int nsl, int grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& bt,
+                          const TcArgs& args, cudaStream_t s) {
+  if (nsl == 3) {
+    tc::tc_gemm_kernel<3, MODE><<<grid, tc::kThreads, TcCfg<3>::SMEM, s>>>(a, b, bt, args);
+  } else if (nsl == 2) {
+    tc::tc_gemm_kernel<2, MODE><<<grid, tc::kThreads, TcCfg<2>::SMEM, s>>>(a, b, bt, args);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
-
-// Chooses the N tile: the fewest padded shells among the built widths.
-int tc_choose_n(int n_r) {
-  const int cand[2] = {80, 128};
-  int best = 80;
-  long long best_pad = (long long)1 << 60;
-  for (int n : cand) {
-    long long padded = (long long)((n_r + n - 1) / n) * n;
-    if (padded < best_pad || (padded == best_pad && n > best)) {
-      best_pad = padded;
-      best = n;
-    }
-  }
-  return best;
-}
 
 ygs_status tc_setup(ygs_plan* p, int sms) {
   const int nsl = p->tc_nsl;
@@ -402,14 +384,16 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   p->tc_pad_off.assign(p->n_wpatch + 1, 0);
   for (int g = 0; g < p->n_wpatch; ++g) p->tc_pad_off[g + 1] = p->tc_pad_off[g] + r32(p->nang[g]);
   p->tc_n_pad = p->tc_pad_off[p->n_wpatch];
-  p->tc_N = tc_choose_n(p->n_r);
+  p->tc_N = tc::NMAX;
+  p->tc_n_full = p->n_r / tc::NMAX;
+  p->tc_n_tail = ((p->n_r % tc::NMAX) + 15) / 16 * 16;
+  p->tc_sms = sms;
 
-  // split-K chunks: about one wave of CTAs
+  // split-K chunks: the full tiles of the projection fill about one wave
   const int tiles_m = (p->tc_k_even + tc::BM - 1) / tc::BM +
                       ((p->tc_k_pad - p->tc_k_even) + tc::BM - 1) / tc::BM;
-  const int tiles_n = (p->n_r + p->tc_N - 1) / p->tc_N;
-  const long long tiles = (long long)tiles_m * tiles_n;
-  long long want = std::max(1LL, (long long)sms / tiles);
+  const long long tiles = (long long)tiles_m * std::max(1, p->tc_n_full);
+  long long want = std::max(1LL, ((long long)sms + tiles / 2) / tiles);
   std::vector<int2> chunks;
   for (int g = 0; g < p->n_wpatch; ++g) {
     const long long kb_g = r32(p->nang[g]) / tc::BK;
@@ -479,20 +463,27 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_TRY(cudaGetLastError());
   TC_TRY(cudaDeviceSynchronize());
 
-  const int N = p->tc_N;
+  const int N = tc::NMAX;
+  const int Nt = p->tc_n_tail > 0 ? p->tc_n_tail : N;
+  const int fplanes = (p->symmetric ? 2 : 1) * nsl;
   if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM) ||
-      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, (p->symmetric ? 2 : 1) * nsl, N) ||
+      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, N) ||
+      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Nt) ||
       !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM) ||
-      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N)) {
+      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N) ||
+      !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return YGS_ERR_CUDA;
   }
   {
     cudaError_t a1 = cudaSuccess, a2 = cudaSuccess;
-    if (N == 80 && nsl == 3) { a1 = set_smem_attr<80, 3, tc::kProject>(); a2 = set_smem_attr<80, 3, tc::kSynthesize>(); }
-    if (N == 128 && nsl == 3) { a1 = set_smem_attr<128, 3, tc::kProject>(); a2 = set_smem_attr<128, 3, tc::kSynthesize>(); }
-    if (N == 80 && nsl == 2) { a1 = set_smem_attr<80, 2, tc::kProject>(); a2 = set_smem_attr<80, 2, tc::kSynthesize>(); }
-    if (N == 128 && nsl == 2) { a1 = set_smem_attr<128, 2, tc::kProject>(); a2 = set_smem_attr<128, 2, tc::kSynthesize>(); }
+    if (nsl == 3) {
+      a1 = set_smem_attr<3, tc::kProject>();
+      a2 = set_smem_attr<3, tc::kSynthesize>();
+    } else {
+      a1 = set_smem_attr<2, tc::kProject>();
+      a2 = set_smem_attr<2, tc::kSynthesize>();
+    }
     TC_TRY(a1);
     TC_TRY(a2);
   }
@@ -518,21 +509,30 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   return cudaGetLastError();
 }
 
+static void fill_tiles(const ygs_plan* p, TcArgs& a) {
+  a.err = p->d_err;
+  a.flush_kb = std::max(1, 64 / tc::BK);  // flush the leading product every 64 k-elements
+  a.n_b = p->n_r;
+  a.n_full = p->tc_n_full;
+  a.n_tail = p->tc_n_tail;
+  a.n_tiles = p->tc_n_full + (p->tc_n_tail > 0 ? 1 : 0);
+}
+
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) {
   TcArgs a{};
-  a.err = p->d_err;
-  a.flush_kb = 64 / tc::BK;  // flush the leading product every 64 k-elements
-  a.n_b = p->n_r;
+  fill_tiles(p, a);
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
+  a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
   a.a_row_odd = p->tc_k_even;
   a.a_rows_total = p->tc_k_pad;
   a.b_plane_odd = p->symmetric ? p->tc_nsl : 0;
+  a.n_chunks = p->tc_S;
   a.chunks = p->tc_chunks;
   a.part = p->tc_part;
   a.ldp = p->tc_k_pad;
-  const int tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
-  dim3 grid(tiles_m, (p->n_r + p->tc_N - 1) / p->tc_N, p->tc_S);
-  return dispatch_gemm<tc::kProject>(p->tc_N, p->tc_nsl, grid, p->tc_map_ut, p->tc_map_f, a, s);
+  a.total_tiles = a.tiles_m * a.n_chunks * a.n_tiles;
+  const int grid = std::min(a.total_tiles, p->tc_sms);
+  return dispatch_gemm<tc::kProject>(p->tc_nsl, grid, p->tc_map_ut, p->tc_map_f, p->tc_map_f_tail, a, s);
 }
 
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
@@ -551,24 +551,26 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
 
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
   TcArgs a{};
-  a.err = p->d_err;
-  a.flush_kb = 64 / tc::BK;
-  a.n_b = p->n_r;
+  fill_tiles(p, a);
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;
+  a.n_wpatch = p->n_wpatch;
   a.pt = p->pt;
-  long long row = 0, nmax = 0;
+  long long row = 0;
+  int t = 0;
   for (int g = 0; g < p->n_wpatch; ++g) {
     a.a_row0[g] = row;
+    a.tile0[g] = t;
     row += p->nang[g];
-    nmax = std::max(nmax, p->nang[g]);
+    t += (int)((p->nang[g] + tc::BM - 1) / tc::BM) * a.n_tiles;  // cell tiles x shell tiles, shells fastest
   }
+  a.tile0[p->n_wpatch] = t;
+  a.total_tiles = t;
   a.phi = phi;
   a.mono = p->tc_mono;
-  // shell tiles vary fastest so the CTAs that share one Q tile run together (L2 reuse)
-  dim3 grid((p->n_r + p->tc_N - 1) / p->tc_N, (unsigned)((nmax + tc::BM - 1) / tc::BM), p->n_wpatch);
-  return dispatch_gemm<tc::kSynthesize>(p->tc_N, p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, a, s);
+  const int grid = std::min(a.total_tiles, p->tc_sms);
+  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, p->tc_map_m_tail, a, s);
 }
 
 cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s) {
