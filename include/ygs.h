@@ -145,8 +145,13 @@ ygs_status ygs_solve(ygs_plan* plan, const double* d_rho, double* d_phi, void* s
  * buffers should be page-locked for full copy bandwidth. */
 ygs_status ygs_solve_host(ygs_plan* plan, const double* h_rho, double* h_phi, void* stream);
 
-/* n independent solves (plans may differ in every size) enqueued on one
- * stream.  plans, d_rho and d_phi are HOST arrays of n entries each. */
+/* n independent solves (plans may differ in every size) as one unit of work
+ * on `stream`: the fields are forked onto a pool of internal worker streams
+ * (fields of the same plan stay in order on one worker, since they share its
+ * workspaces) and joined back onto `stream` with events, so independent
+ * fields run concurrently and the whole batch can be captured into one CUDA
+ * graph.  plans, d_rho and d_phi are HOST arrays of n entries each; all plans
+ * must live on one device.  Errors: as ygs_solve. */
 ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const* d_rho,
                              double* const* d_phi, void* stream);
 

@@ -340,21 +340,26 @@ int ora_build_Q(const ora_grid* g, double* Q) {
 
 /* ------------------------------------------------------------ the steps --- */
 
-/* B[i][c] = sum_{g,a} rho[g][i][a] U[a][c]  (Eq. B_CS, steps 2-3). */
+/* B[i][c] = sum_{g,a} rho[g][i][a] U[a][c]  (Eq. B_CS, steps 2-3).  Each
+ * B[i][c] is the sum over (g, a) in ascending order; a whole row of B is
+ * accumulated at once so that U is read row by row. */
 void ora_project(const ora_grid* g, const double* rho, const double* U, double* B) {
   int K = ncols(g->l_max);
   int nr = g->n_r;
-#pragma omp parallel for collapse(2) schedule(static)
-  for (int i = 0; i < nr; ++i)
-    for (int c = 0; c < K; ++c) {
-      double s = 0.0;
-      for (int p = 0; p < g->n_patch; ++p) {
-        long base = nang_before(g, p), na = nang_patch(g, p);
-        const double* r = rho + base * nr + (long)i * na;
-        for (long a = 0; a < na; ++a) s += r[a] * U[(base + a) * K + c];
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < nr; ++i) {
+    double* b = B + (long)i * K;
+    for (int c = 0; c < K; ++c) b[c] = 0.0;
+    for (int p = 0; p < g->n_patch; ++p) {
+      long base = nang_before(g, p), na = nang_patch(g, p);
+      const double* r = rho + base * nr + (long)i * na;
+      for (long a = 0; a < na; ++a) {
+        const double ra = r[a];
+        const double* u = U + (base + a) * K;
+        for (int c = 0; c < K; ++c) b[c] += ra * u[c];
       }
-      B[(long)i * K + c] = s;
     }
+  }
 }
 
 /* M[i][c] by the direct sums of Eq. M_C (no recurrence). */
@@ -426,16 +431,18 @@ void ora_apply_T(const ora_grid* g, const double* U, const double* Q, const doub
   int nr = g->n_r;
   double* Mb = (double*)calloc((size_t)nr * K, sizeof(double));
   double* Bb = (double*)calloc((size_t)nr * K, sizeof(double));
-#pragma omp parallel for collapse(2) schedule(static)
-  for (int i = 0; i < nr; ++i)
-    for (int c = 0; c < K; ++c) {
-      double s = 0.0;
-      for (int p = 0; p < g->n_patch; ++p) {
-        long base = nang_before(g, p), na = nang_patch(g, p);
-        for (long a = 0; a < na; ++a) s += Q[(base + a) * K + c] * gphi[base * nr + (long)i * na + a];
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < nr; ++i) {
+    double* m = Mb + (long)i * K;  /* zeroed by calloc */
+    for (int p = 0; p < g->n_patch; ++p) {
+      long base = nang_before(g, p), na = nang_patch(g, p);
+      for (long a = 0; a < na; ++a) {
+        const double ga = gphi[base * nr + (long)i * na + a];
+        const double* q = Q + (base + a) * K;
+        for (int c = 0; c < K; ++c) m[c] += q[c] * ga;
       }
-      Mb[(long)i * K + c] = s;
     }
+  }
 #pragma omp parallel for collapse(2) schedule(static)
   for (int ip = 0; ip < nr; ++ip)
     for (int c = 0; c < K; ++c) {

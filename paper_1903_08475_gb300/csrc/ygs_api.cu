@@ -3,6 +3,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -145,6 +147,40 @@ cudaEvent_t* prof_slot(ygs_plan* p) {
     p->prof_events.push_back(e);
   }
   return &p->prof_events[(size_t)p->prof_used++ * (kPhases + 1)];
+}
+
+// Per-device pool of worker streams for batched solves (created on first use,
+// kept until process exit).  Events fork the caller's stream onto the workers
+// and join them back, which also works under CUDA stream capture.
+constexpr int kPoolStreams = 8;
+struct StreamPool {
+  cudaStream_t s[kPoolStreams];
+  cudaEvent_t fork;
+  cudaEvent_t join[kPoolStreams];
+};
+std::mutex g_pool_mu;
+std::map<int, StreamPool*> g_pools;
+
+StreamPool* get_pool(int device, ygs_status* st) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(device);
+  if (it != g_pools.end()) return it->second;
+  StreamPool* P = new (std::nothrow) StreamPool();
+  if (!P) {
+    *st = fail(YGS_ERR_OOM, "host allocation failed");
+    return nullptr;
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+  for (int k = 0; k < kPoolStreams && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&P->s[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join[k], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    *st = cuda_fail(e, "stream pool");
+    return nullptr;
+  }
+  g_pools[device] = P;
+  return P;
 }
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
@@ -381,14 +417,40 @@ ygs_status ygs_solve_host(ygs_plan* p, const double* h_rho, double* h_phi, void*
 ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const* d_rho, double* const* d_phi,
                              void* stream) {
   if (n < 0 || (n > 0 && (!plans || !d_rho || !d_phi))) return fail(YGS_ERR_INVALID_ARG, "bad batch arrays");
+  if (n == 0) return YGS_OK;
+  const int dev = plans[0] ? plans[0]->device : 0;
   for (int b = 0; b < n; ++b) {
     ygs_status st = check_field(plans[b], d_rho[b], d_phi[b]);
     if (st != YGS_OK) return st;
+    if (plans[b]->device != dev) return fail(YGS_ERR_INVALID_ARG, "all plans of a batch must share one device");
   }
+  if (n == 1) return ygs_solve(plans[0], d_rho[0], d_phi[0], stream);
+  DeviceGuard guard(dev);
+  ygs_status st = YGS_OK;
+  StreamPool* P = get_pool(dev, &st);
+  if (!P) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  API_TRY(cudaEventRecord(P->fork, s));
+  // fields of one plan share its workspaces: they go to one worker stream, in order
+  std::map<const ygs_plan*, int> lane;
+  int next = 0;
+  bool used[kPoolStreams] = {false};
   for (int b = 0; b < n; ++b) {
-    ygs_status st = ygs_solve(plans[b], d_rho[b], d_phi[b], stream);
+    auto it = lane.find(plans[b]);
+    int k = (it != lane.end()) ? it->second : (lane[plans[b]] = (next++ % kPoolStreams));
+    if (!used[k]) {
+      API_TRY(cudaStreamWaitEvent(P->s[k], P->fork, 0));
+      used[k] = true;
+    }
+    st = ygs_solve(plans[b], d_rho[b], d_phi[b], (void*)P->s[k]);
     if (st != YGS_OK) return st;
+    plans[b]->last_stream = s;
   }
+  for (int k = 0; k < kPoolStreams; ++k)
+    if (used[k]) {
+      API_TRY(cudaEventRecord(P->join[k], P->s[k]));
+      API_TRY(cudaStreamWaitEvent(s, P->join[k], 0));
+    }
   return YGS_OK;
 }
 

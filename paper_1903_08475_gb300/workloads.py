@@ -445,6 +445,16 @@ def config2(seed: int = SEED_BASE + 2, n_fft: int = 256):
     return grid, lognormal_density(grid, rng, n_fft=n_fft)
 
 
+def config4(seed: int = SEED_BASE + 4):
+    """Adjoint workload: Yin-Yang 1 degree, Nr = 256, l_max = 32, the config-1
+    density, and seeded N(0, 1) weights w of J = sum_cells w Phi(rho)."""
+    grid = config1_grid(n_r=256)
+    tag = f"cfg4-density-v1-{seed}"
+    rho = cached(tag, lambda: config1_density(grid, SEED_BASE + 1))
+    w = np.random.default_rng(seed).standard_normal(grid.n_cells)
+    return grid, rho, w
+
+
 def random_density(grid: Grid, seed: int) -> np.ndarray:
     """Positive random density, uniform in [0.5, 1.5) (for parity cases)."""
     return np.random.default_rng(seed).uniform(0.5, 1.5, grid.n_cells)

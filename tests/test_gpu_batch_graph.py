@@ -1,0 +1,71 @@
+"""Batched solves and CUDA-graph capture through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1903_08475_gb300 import Plan, ygs_solve, ygs_solve_batched, workloads as W
+from tests._util import small_yinyang
+from tests.test_gpu_fp64 import three_patch_grid
+
+pytestmark = pytest.mark.gpu
+
+
+def _fields(cuda):
+    import torch
+    grids = [small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9),
+             small_yinyang(W, n_theta=8, n_phi=20, n_r=150, l_max=7),
+             three_patch_grid(),
+             W.polar_grid(7, 13, W.linear_edges(6, 0.1, 1.0), 5)]
+    precs = ["bf16x6", "fp64", "bf16x6", "bf16x3"]
+    plans = [Plan(g, p) for g, p in zip(grids, precs)]
+    rhos = [torch.from_numpy(W.random_density(g, 20 + i)).cuda() for i, g in enumerate(grids)]
+    return plans, rhos
+
+
+def test_batched_equals_per_field(cuda):
+    import torch
+    plans, rhos = _fields(cuda)
+    ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
+    # the first plan twice: same workspaces, kept in order on one worker stream
+    bp = plans + [plans[0]]
+    br = rhos + [rhos[0] * 2.0]
+    outs = [torch.empty_like(r) for r in br]
+    ygs_solve_batched(bp, br, outs)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, outs[:-1]):
+        assert torch.equal(a, b)
+    assert torch.allclose(outs[-1], 2.0 * ref[0], rtol=1e-6, atol=0)
+    for p in plans:
+        p.close()
+
+
+def test_graph_capture_single_and_batched(cuda):
+    import torch
+    plans, rhos = _fields(cuda)
+    outs = [torch.empty_like(r) for r in rhos]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ygs_solve_batched(plans, rhos, outs, stream=s)  # warm-up outside the capture
+        ygs_solve(plans[0], rhos[0], outs[0], stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    eager = [o.clone() for o in outs]
+    g1 = torch.cuda.CUDAGraph()
+    single = torch.empty_like(rhos[0])
+    with torch.cuda.graph(g1):
+        ygs_solve(plans[0], rhos[0], single)
+    g2 = torch.cuda.CUDAGraph()
+    gouts = [torch.empty_like(r) for r in rhos]
+    with torch.cuda.graph(g2):
+        ygs_solve_batched(plans, rhos, gouts)
+    for _ in range(2):
+        g1.replay()
+        g2.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(single, eager[0])
+    for a, b in zip(gouts, eager):
+        assert torch.equal(a, b)
+    for p in plans:
+        p.close()
