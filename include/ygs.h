@@ -125,7 +125,9 @@ typedef struct {
  * `device`, and evaluates the FP64 weights U (Wigner-D route, Eqs. U_C/U_S),
  * Q (Eqs. Q_C/Q_S) and the radial factors of Eqs. R_in/R_out on the GPU
  * (step 1 of Sect. 4.3).  Synchronous.  On failure *out is set to NULL and
- * nothing is leaked.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED. */
+ * nothing is leaked.  Errors: INVALID_ARG, OOM, CUDA, UNSUPPORTED.
+ * Testing hook: with YGS_INJECT_ALLOC_FAILURE=k in the environment, the k-th
+ * device allocation of this call fails as if the device were out of memory. */
 ygs_status ygs_create(const ygs_desc* desc, int device, ygs_plan** out);
 
 /* Frees every device buffer of the plan (waits for its pending work).
@@ -184,6 +186,13 @@ ygs_status ygs_get_status(ygs_plan* plan);
  * since the previous read, and clears the record. */
 ygs_status ygs_set_profiling(ygs_plan* plan, int enable);
 ygs_status ygs_read_phase_times(ygs_plan* plan, double* ms, int* n_calls);
+
+/* Diagnostic of the failure path.  Enqueues a kernel that polls an mbarrier
+ * nothing arrives at, at most `spins` times (the bounded wait every kernel of
+ * this library uses), and then records YGS_ERR_TIMEOUT in the plan's error
+ * word; ygs_get_status reports it once and clears it.  No GPU fault is
+ * involved and the context stays usable. */
+ygs_status ygs_debug_wait_timeout(ygs_plan* plan, int spins, void* stream);
 
 /* Number of kernel launches one ygs_solve / ygs_backward enqueues. */
 int ygs_launches_per_solve(const ygs_plan* plan);

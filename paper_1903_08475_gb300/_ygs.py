@@ -26,7 +26,8 @@ FLAG_NO_SYMMETRY = 1
 
 EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_batched",
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
-           "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve")
+           "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
+           "ygs_debug_wait_timeout")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -87,6 +88,7 @@ def load_library(path: Optional[str] = None):
         L.ygs_set_profiling.argtypes = [vp, ctypes.c_int]
         L.ygs_read_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         L.ygs_launches_per_solve.argtypes = [vp]
+        L.ygs_debug_wait_timeout.argtypes = [vp, ctypes.c_int, vp]
         for f in EXPORTS:
             if f not in ("ygs_status_string", "ygs_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -233,6 +235,10 @@ def ygs_read_phase_times(plan: Plan):
 
 def ygs_launches_per_solve(plan: Plan) -> int:
     return load_library().ygs_launches_per_solve(plan.handle)
+
+
+def ygs_debug_wait_timeout(plan: Plan, spins: int = 1000, stream=None):
+    _check(load_library().ygs_debug_wait_timeout(plan.handle, spins, _stream_handle(stream)))
 
 
 def ygs_get_status(plan: Plan):

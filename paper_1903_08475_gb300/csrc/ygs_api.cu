@@ -13,8 +13,22 @@
 namespace ygs {
 
 static thread_local std::string g_err;
+static thread_local long long g_alloc_countdown = 0;  // 0: no injection
 
 void set_error(const std::string& msg) { g_err = msg; }
+
+void arm_alloc_injection() {
+  const char* v = getenv("YGS_INJECT_ALLOC_FAILURE");
+  g_alloc_countdown = v ? atoll(v) : 0;
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+  if (g_alloc_countdown > 0 && --g_alloc_countdown == 0) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
 
 namespace {
 
@@ -228,6 +242,7 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
   if (device < 0 || device >= ndev) return fail(YGS_ERR_INVALID_ARG, "bad device index");
   DeviceGuard guard(device);
   if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  arm_alloc_injection();
 
   ygs_plan* p = new (std::nothrow) ygs_plan();
   if (!p) return fail(YGS_ERR_OOM, "host allocation failed");
@@ -310,7 +325,7 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
     free_plan(p);
     return s;
   };
-  auto al = [&](void** ptr, size_t bytes) -> cudaError_t { return cudaMalloc(ptr, std::max<size_t>(bytes, 16)); };
+  auto al = [&](void** ptr, size_t bytes) -> cudaError_t { return dev_malloc(ptr, std::max<size_t>(bytes, 16)); };
   size_t wbytes = (size_t)p->nang_wtotal * p->K * sizeof(double);
   size_t nk = (size_t)p->n_r * p->K * sizeof(double);
   cudaError_t e;
@@ -403,8 +418,8 @@ ygs_status ygs_solve_host(ygs_plan* p, const double* h_rho, double* h_phi, void*
   if (!p || !h_rho || !h_phi) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
   DeviceGuard guard(p->device);
   size_t bytes = (size_t)p->n_cells * sizeof(double);
-  if (!p->h2d_rho) API_TRY(cudaMalloc((void**)&p->h2d_rho, bytes));
-  if (!p->h2d_phi) API_TRY(cudaMalloc((void**)&p->h2d_phi, bytes));
+  if (!p->h2d_rho) API_TRY(dev_malloc((void**)&p->h2d_rho, bytes));
+  if (!p->h2d_phi) API_TRY(dev_malloc((void**)&p->h2d_phi, bytes));
   cudaStream_t s = (cudaStream_t)stream;
   API_TRY(cudaMemcpyAsync(p->h2d_rho, h_rho, bytes, cudaMemcpyHostToDevice, s));
   ygs_status st = ygs_solve(p, p->h2d_rho, p->h2d_phi, stream);
@@ -532,6 +547,15 @@ ygs_status ygs_read_phase_times(ygs_plan* p, double* ms, int* n_calls) {
   }
   *n_calls = p->prof_used;
   p->prof_used = 0;
+  return YGS_OK;
+}
+
+ygs_status ygs_debug_wait_timeout(ygs_plan* p, int spins, void* stream) {
+  if (!p || spins < 1) return fail(YGS_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard guard(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  API_TRY(debug_wait_timeout(p, spins, s));
   return YGS_OK;
 }
 

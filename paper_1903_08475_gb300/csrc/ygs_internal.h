@@ -95,6 +95,12 @@ namespace ygs {
 // Thread-local error message for ygs_last_error().
 void set_error(const std::string& msg);
 
+// cudaMalloc through one door: when YGS_INJECT_ALLOC_FAILURE=k is set in the
+// environment at ygs_create, the k-th device allocation of that create fails
+// with cudaErrorMemoryAllocation (host-side fault injection for tests).
+cudaError_t dev_malloc(void** ptr, size_t bytes);
+void arm_alloc_injection();
+
 // ---- weight builder (ygs_weights.cu) -------------------------------------
 // Builds U, Q (FP64, internal column order) and the radial tables of `p`
 // with every allocation it needs; synchronous.
@@ -121,5 +127,6 @@ cudaError_t tc_project(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s);
 cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+cudaError_t debug_wait_timeout(const ygs_plan* p, int spins, cudaStream_t s);
 
 }  // namespace ygs

@@ -418,7 +418,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   size_t bytes_sum = (size_t)4 * p->tc_scan_P * kp * sizeof(double);
   cudaError_t e;
 #define TC_ALLOC(ptr, bytes)                                                          \
-  if ((e = cudaMalloc((void**)&(ptr), std::max<size_t>((bytes), 16))) != cudaSuccess) { \
+  if ((e = dev_malloc((void**)&(ptr), std::max<size_t>((bytes), 16))) != cudaSuccess) { \
     set_error(std::string("cudaMalloc ") + #ptr + ": " + cudaGetErrorString(e));      \
     return YGS_ERR_OOM;                                                                \
   }
@@ -571,6 +571,26 @@ cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
   a.mono = p->tc_mono;
   const int grid = std::min(a.total_tiles, p->tc_sms);
   return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, p->tc_map_m_tail, a, s);
+}
+
+namespace {
+// Waits on an mbarrier that nothing arrives at, with the same bounded polling
+// as the contraction kernels, then records the timeout in the error word.
+__global__ void wait_timeout_kernel(int spins, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    bool done = false;
+    for (int it = 0; it < spins && !done; ++it) done = tc::mbar_try_wait(&bar, 0);
+    if (!done) tc::set_err(err, YGS_ERR_TIMEOUT);
+  }
+}
+}  // namespace
+
+cudaError_t debug_wait_timeout(const ygs_plan* p, int spins, cudaStream_t s) {
+  wait_timeout_kernel<<<1, 32, 0, s>>>(spins, p->d_err);
+  return cudaGetLastError();
 }
 
 cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s) {

@@ -397,7 +397,7 @@ struct Scratch {
   }
   template <class T>
   cudaError_t alloc(T** p, size_t n) {
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+    cudaError_t e = dev_malloc((void**)p, n * sizeof(T) + 16);
     if (e == cudaSuccess) ptrs.push_back((void*)*p);
     return e;
   }
