@@ -107,6 +107,30 @@ __device__ __forceinline__ void ff_slices(float hi, float lo, int nsl, __nv_bflo
   if (nsl == 2) sl[1] = __float2bfloat16_rn((hi - __bfloat162float(sl[0])) + lo);
 }
 
+__device__ __forceinline__ void sigma_slices(double r0, double r1, int nsl, int symmetric,
+                                             __nv_bfloat16 (&out)[2][3]) {
+  float h0, l0;
+  tc::f64_to_ff(r0, h0, l0);
+  if (!symmetric) {
+    ff_slices(h0, l0, nsl, out[0]);
+    return;
+  }
+  float h1, l1;
+  tc::f64_to_ff(r1, h1, l1);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float s, err;
+    tc::two_sum(h0, h ? -h1 : h1, s, err);
+    float lo = err + (h ? (l0 - l1) : (l0 + l1));
+    float hi = s + lo;  // renormalise
+    lo = lo - (hi - s);
+    ff_slices(hi, lo, nsl, out[h]);
+  }
+}
+
+// Grid: (x over groups of 4 angular cells, y over shells, z over stored
+// patches).  Rows of rho whose start is 16-byte aligned are read with 16-byte
+// loads; slices are written 4 cells (8 bytes) at a time.
 __global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable pt,
                                     const long long* __restrict__ pad_off, long long n_pad,
                                     const double* __restrict__ rho, __nv_bfloat16* __restrict__ F) {
@@ -115,49 +139,47 @@ __global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable 
   const int i = blockIdx.y;
   const int na = (int)pt.nang[g];
   const long long row_in = pt.fld_off[g] + (long long)i * na;
+  const long long row_in1 = symmetric ? pt.fld_off[1] + (long long)i * na : row_in;
   const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
-  for (int a = 2 * (blockIdx.x * blockDim.x + threadIdx.x); a < na; a += 2 * gridDim.x * blockDim.x) {
-    const bool two = (a + 1 < na);
-    double v0[2], v1[2];
-    v0[0] = rho[row_in + a];
-    v0[1] = two ? rho[row_in + a + 1] : 0.0;
-    if (symmetric) {
-      const long long r1 = pt.fld_off[1] + (long long)i * na;
-      v1[0] = rho[r1 + a];
-      v1[1] = two ? rho[r1 + a + 1] : 0.0;
-    }
-    __nv_bfloat16 out[2][2][3];  // [h][cell][slice]
+  const bool vec = ((row_in | row_in1) & 1) == 0;
+  for (int a = 4 * (blockIdx.x * blockDim.x + threadIdx.x); a < na; a += 4 * gridDim.x * blockDim.x) {
+    double v0[4], v1[4];
+    if (vec && a + 4 <= na) {
+      const double2 x0 = *reinterpret_cast<const double2*>(rho + row_in + a);
+      const double2 x1 = *reinterpret_cast<const double2*>(rho + row_in + a + 2);
+      v0[0] = x0.x; v0[1] = x0.y; v0[2] = x1.x; v0[3] = x1.y;
+      if (symmetric) {
+        const double2 y0 = *reinterpret_cast<const double2*>(rho + row_in1 + a);
+        const double2 y1 = *reinterpret_cast<const double2*>(rho + row_in1 + a + 2);
+        v1[0] = y0.x; v1[1] = y0.y; v1[2] = y1.x; v1[3] = y1.y;
+      }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      float h0, l0;
-      tc::f64_to_ff(v0[c], h0, l0);
-      if (!symmetric) {
-        ff_slices(h0, l0, nsl, out[0][c]);
-      } else {
-        float h1, l1;
-        tc::f64_to_ff(v1[c], h1, l1);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float s, err;
-          tc::two_sum(h0, h ? -h1 : h1, s, err);
-          float lo = err + (h ? (l0 - l1) : (l0 + l1));
-          float hi = s + lo;  // renormalise
-          lo = lo - (hi - s);
-          ff_slices(hi, lo, nsl, out[h][c]);
-        }
+      for (int c = 0; c < 4; ++c) {
+        v0[c] = (a + c < na) ? rho[row_in + a + c] : 0.0;
+        v1[c] = (symmetric && a + c < na) ? rho[row_in1 + a + c] : 0.0;
       }
     }
+    __nv_bfloat16 out[4][2][3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sigma_slices(v0[c], v1[c], nsl, symmetric, out[c]);
     const int nh = symmetric ? 2 : 1;
+    const bool whole = a + 4 <= na;
     for (int h = 0; h < nh; ++h)
       for (int k = 0; k < nsl; ++k) {
         __nv_bfloat16* dst = F + (long long)(h * nsl + k) * plane + row_out + a;
-        if (two) {
-          __nv_bfloat162 pr;
-          pr.x = out[h][0][k];
-          pr.y = out[h][1][k];
-          *reinterpret_cast<__nv_bfloat162*>(dst) = pr;
+        if (whole) {
+          __nv_bfloat162 p0, p1;
+          p0.x = out[0][h][k];
+          p0.y = out[1][h][k];
+          p1.x = out[2][h][k];
+          p1.y = out[3][h][k];
+          uint2 w;
+          w.x = *reinterpret_cast<unsigned int*>(&p0);
+          w.y = *reinterpret_cast<unsigned int*>(&p1);
+          *reinterpret_cast<uint2*>(dst) = w;
         } else {
-          dst[0] = out[h][0][k];
+          for (int c = 0; c < 4 && a + c < na; ++c) dst[c] = out[c][h][k];
         }
       }
   }
@@ -236,48 +258,41 @@ __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, c
   summ[((long long)3 * P + p) * K_pad + pc] = FP;
 }
 
-// Phase 2: carries between chunks (sequential over chunks, one thread per
-// column).  Summaries are fetched in batches of independent loads before the
-// dependent FP64 chain runs over them.
-__global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ summ, double* __restrict__ carry) {
-  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pc >= K_pad) return;
-  constexpr int BT = 16;
-  double ci = 0.0;
-  for (int p0 = 0; p0 < P; p0 += BT) {
-    double sI[BT], fI[BT];
+// Phase 2: carries between chunks.  The chunk summaries define affine maps
+// c -> F c + s; one warp per column composes them with a shuffle scan over
+// up to 32 chunks (inner recurrence upward, outer downward).
+__device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
+  // inclusive scan: after it lane p holds the composition of chunks 0..p
 #pragma unroll
-    for (int q = 0; q < BT; ++q) {
-      const int p = p0 + q;
-      sI[q] = (p < P) ? summ[((long long)0 * P + p) * K_pad + pc] : 0.0;
-      fI[q] = (p < P) ? summ[((long long)1 * P + p) * K_pad + pc] : 1.0;
-    }
-#pragma unroll
-    for (int q = 0; q < BT; ++q) {
-      const int p = p0 + q;
-      if (p < P) {
-        carry[((long long)0 * P + p) * K_pad + pc] = ci;  // I at the shell before chunk p
-        ci = fma(fI[q], ci, sI[q]);
-      }
+  for (int d = 1; d < 32; d <<= 1) {
+    const double Fo = __shfl_up_sync(0xffffffffu, F, d);
+    const double so = __shfl_up_sync(0xffffffffu, s, d);
+    if (lane >= d) {
+      s = fma(F, so, s);
+      F = F * Fo;
     }
   }
-  double co = 0.0;
-  for (int p1 = P - 1; p1 >= 0; p1 -= BT) {
-    double sP[BT], fP[BT];
-#pragma unroll
-    for (int q = 0; q < BT; ++q) {
-      const int p = p1 - q;
-      sP[q] = (p >= 0) ? summ[((long long)2 * P + p) * K_pad + pc] : 0.0;
-      fP[q] = (p >= 0) ? summ[((long long)3 * P + p) * K_pad + pc] : 1.0;
-    }
-#pragma unroll
-    for (int q = 0; q < BT; ++q) {
-      const int p = p1 - q;
-      if (p >= 0) {
-        carry[((long long)1 * P + p) * K_pad + pc] = co;  // P at the shell after chunk p
-        co = fma(fP[q], co, sP[q]);
-      }
-    }
+}
+
+__global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ summ, double* __restrict__ carry) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  const int pc = warp / 2, dir = warp % 2;
+  if (pc >= K_pad) return;
+  if (dir == 0) {
+    // inner: c_{p+1} = FI_p c_p + I_p, c_0 = 0; carry into chunk p = c_p
+    double F = (lane < P) ? summ[((long long)1 * P + lane) * K_pad + pc] : 1.0;
+    double sv = (lane < P) ? summ[((long long)0 * P + lane) * K_pad + pc] : 0.0;
+    affine_scan_up(F, sv, lane);
+    const double prev = __shfl_up_sync(0xffffffffu, sv, 1);
+    if (lane < P) carry[((long long)0 * P + lane) * K_pad + pc] = lane == 0 ? 0.0 : prev;
+  } else {
+    // outer: c_{p-1} = FP_p c_p + P_p, c_{P-1} = 0 (lanes run over reversed chunks)
+    const int p = P - 1 - lane;
+    double F = (lane < P) ? summ[((long long)3 * P + p) * K_pad + pc] : 1.0;
+    double sv = (lane < P) ? summ[((long long)2 * P + p) * K_pad + pc] : 0.0;
+    affine_scan_up(F, sv, lane);
+    const double prev = __shfl_up_sync(0xffffffffu, sv, 1);
+    if (lane < P) carry[((long long)1 * P + p) * K_pad + pc] = lane == 0 ? 0.0 : prev;
   }
 }
 
@@ -405,7 +420,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
                                  (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
   }
   p->tc_S = (int)chunks.size();
-  p->tc_scan_chunk = 16;
+  // chunks of shells for the parallel scans: at most 32 (one warp lane each in the carry pass)
+  p->tc_scan_chunk = std::max(8, (p->n_r + 31) / 32);
   p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
 
   const size_t kp = (size_t)p->tc_k_pad;
@@ -502,7 +518,7 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   long long nmax = 0;
   for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
   const int threads = 128;
-  const int bx = (int)std::min<long long>(64, (nmax / 2 + threads - 1) / threads);
+  const int bx = (int)std::min<long long>(64, (nmax / 4 + threads - 1) / threads);
   dim3 grid(std::max(1, bx), p->n_r, p->n_wpatch);
   field_slices_kernel<<<grid, threads, 0, s>>>(p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d,
                                                p->tc_n_pad, rho, p->tc_f);
@@ -542,7 +558,7 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
                                        p->tc_part, p->rad, p->tc_cp, p->tc_B, p->tc_summ);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  scan_carry_kernel<<<(p->tc_k_pad + 127) / 128, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
+  scan_carry_kernel<<<(p->tc_k_pad * 2 + 3) / 4, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   scan_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
                                        p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms, p->G, p->tc_mono);
