@@ -72,7 +72,9 @@ struct ygs_plan {
   // ---- split-precision (tcgen05) path
   int tc_nsl = 0;            // BF16 slices per operand (0: FP64 path)
   int tc_N = 0;              // shells per full tile
-  int tc_n_full = 0;         // full shell tiles
+  int tc_np_full = 0;        // full shell tiles of the projection
+  int tc_np_tail = 0;        // width of the projection's tail shell tile (0: none)
+  int tc_n_full = 0;         // full shell tiles of the synthesis
   int tc_n_tail = 0;         // width of the tail shell tile (0: none)
   int tc_sms = 0;            // CTAs of the persistent contraction kernels
   int tc_k_even = 0, tc_k_pad = 0;

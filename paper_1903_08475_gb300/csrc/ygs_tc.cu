@@ -359,16 +359,17 @@ __global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __rest
 template <int NSL, int MODE>
 cudaError_t set_smem_attr() {
   return cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<NSL>::SMEM);
+                              TcCfg<NSL, MODE>::SMEM);
 }
 
 template <int MODE>
 cudaError_t dispatch_gemm(int nsl, int grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& bt,
                           const TcArgs& args, cudaStream_t s) {
+  constexpr int threads = tc::TileShape<MODE>::THREADS;
   if (nsl == 3) {
-    tc::tc_gemm_kernel<3, MODE><<<grid, tc::kThreads, TcCfg<3>::SMEM, s>>>(a, b, bt, args);
+    tc::tc_gemm_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(a, b, bt, args);
   } else if (nsl == 2) {
-    tc::tc_gemm_kernel<2, MODE><<<grid, tc::kThreads, TcCfg<2>::SMEM, s>>>(a, b, bt, args);
+    tc::tc_gemm_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -399,16 +400,21 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   p->tc_pad_off.assign(p->n_wpatch + 1, 0);
   for (int g = 0; g < p->n_wpatch; ++g) p->tc_pad_off[g + 1] = p->tc_pad_off[g] + r32(p->nang[g]);
   p->tc_n_pad = p->tc_pad_off[p->n_wpatch];
-  p->tc_N = tc::NMAX;
-  p->tc_n_full = p->n_r / tc::NMAX;
-  p->tc_n_tail = ((p->n_r % tc::NMAX) + 15) / 16 * 16;
+  const int NP = tc::kNmaxProject, NS = tc::kNmaxSynth;
+  p->tc_N = NS;
+  p->tc_np_full = p->n_r / NP;
+  p->tc_np_tail = ((p->n_r % NP) + 15) / 16 * 16;
+  p->tc_n_full = p->n_r / NS;
+  p->tc_n_tail = ((p->n_r % NS) + 15) / 16 * 16;
   p->tc_sms = sms;
 
-  // split-K chunks: the full tiles of the projection fill about one wave
+  // split-K chunks: the projection's tiles (a tail tile counted by its width) fill about one wave
   const int tiles_m = (p->tc_k_even + tc::BM - 1) / tc::BM +
                       ((p->tc_k_pad - p->tc_k_even) + tc::BM - 1) / tc::BM;
-  const long long tiles = (long long)tiles_m * std::max(1, p->tc_n_full);
-  long long want = std::max(1LL, ((long long)sms + tiles / 2) / tiles);
+  const double per_chunk = tiles_m * (p->tc_np_full + (double)p->tc_np_tail / NP);
+  const int n_tiles_p = p->tc_np_full + (p->tc_np_tail > 0 ? 1 : 0);
+  long long want = std::max(1LL, (long long)std::floor(sms / std::max(1.0, per_chunk) + 0.5));
+  while (want > 1 && (long long)tiles_m * n_tiles_p * want > sms) --want;
   std::vector<int2> chunks;
   for (int g = 0; g < p->n_wpatch; ++g) {
     const long long kb_g = r32(p->nang[g]) / tc::BK;
@@ -479,12 +485,13 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_TRY(cudaGetLastError());
   TC_TRY(cudaDeviceSynchronize());
 
-  const int N = tc::NMAX;
+  const int N = NS;
   const int Nt = p->tc_n_tail > 0 ? p->tc_n_tail : N;
+  const int Npt = p->tc_np_tail > 0 ? p->tc_np_tail : NP;
   const int fplanes = (p->symmetric ? 2 : 1) * nsl;
   if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM) ||
-      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, N) ||
-      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Nt) ||
+      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, NP) ||
+      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Npt) ||
       !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM) ||
       !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N) ||
       !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt)) {
@@ -525,18 +532,18 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   return cudaGetLastError();
 }
 
-static void fill_tiles(const ygs_plan* p, TcArgs& a) {
+static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.err = p->d_err;
   a.flush_kb = std::max(1, 64 / tc::BK);  // flush the leading product every 64 k-elements
   a.n_b = p->n_r;
-  a.n_full = p->tc_n_full;
-  a.n_tail = p->tc_n_tail;
-  a.n_tiles = p->tc_n_full + (p->tc_n_tail > 0 ? 1 : 0);
+  a.n_full = n_full;
+  a.n_tail = n_tail;
+  a.n_tiles = n_full + (n_tail > 0 ? 1 : 0);
 }
 
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) {
   TcArgs a{};
-  fill_tiles(p, a);
+  fill_tiles(p, a, p->tc_np_full, p->tc_np_tail);
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
   a.a_row_odd = p->tc_k_even;
@@ -567,7 +574,7 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
 
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
   TcArgs a{};
-  fill_tiles(p, a);
+  fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;

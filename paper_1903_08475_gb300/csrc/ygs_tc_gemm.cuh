@@ -39,17 +39,25 @@ namespace tc {
 #endif
 constexpr int BK = YGS_TC_BK;  // k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
 constexpr int BM = 128;        // output rows per tile (TMEM lanes)
-#ifndef YGS_TC_NMAX
-#define YGS_TC_NMAX 80
-#endif
-#ifndef YGS_TC_NH
-#define YGS_TC_NH 40
-#endif
-constexpr int NMAX = YGS_TC_NMAX;  // shells per full tile
-constexpr int NH = YGS_TC_NH;      // columns per epilogue warp
-static_assert(NMAX % 16 == 0 && NMAX <= 128 && NMAX % NH == 0 && NH % 8 == 0, "tile shape");
-constexpr int kEpiWarps = 4 * (NMAX / NH);
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+// Tile shapes (shells per tile, columns per epilogue warp).  The projection
+// has one k segment (one correction accumulator), the synthesis two (even /
+// odd columns).  Both use 80-shell tiles: wider tiles lengthen the epilogue's
+// flushes more than they shorten the MMA stream.
+constexpr int kNmaxProject = 80, kNhProject = 40;
+constexpr int kNmaxSynth = 80, kNhSynth = 40;
+
+template <int MODE>
+struct TileShape {
+  static constexpr int NMAX = MODE == 0 ? kNmaxProject : kNmaxSynth;  // shells per full tile
+  static constexpr int NH = MODE == 0 ? kNhProject : kNhSynth;        // columns per epilogue warp
+  static constexpr int NCORR = MODE == 0 ? 1 : 2;                     // correction accumulators
+  static constexpr int EPI_WARPS = 4 * (NMAX / NH);
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static_assert(NMAX % 16 == 0 && NMAX <= 256 && NMAX % NH == 0 && NH % 8 == 0, "tile shape");
+  // rotating leading-product buffers: as many as TMEM holds, at most 4
+  static constexpr int NBUF = (512 / NMAX - NCORR) > 4 ? 4 : (512 / NMAX - NCORR);
+  static_assert(NBUF >= 2, "TMEM holds 512 columns: need two leading-product buffers");
+};
 
 enum Mode { kProject = 0, kSynthesize = 1 };
 
@@ -87,8 +95,9 @@ struct TcArgs {
   const float2* mono;
 };
 
-template <int NSL>
+template <int NSL, int MODE>
 struct TcCfg {
+  static constexpr int NMAX = TileShape<MODE>::NMAX;
   static constexpr int NPROD = (NSL == 3) ? 6 : (NSL == 2 ? 3 : 1);
   static constexpr int A_SLICE = BM * BK * 2;
   static constexpr int B_SLICE = NMAX * BK * 2;
@@ -99,10 +108,10 @@ struct TcCfg {
   static constexpr int STAGES = (220 * 1024) / STAGE > 8 ? 8 : (220 * 1024) / STAGE;
 #endif
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
-  // TMEM columns: [corr seg 0 | corr seg 1 | main buf 0 | main buf 1], NMAX each.
-  static constexpr int NBUF = 2;
+  // TMEM columns: [corr seg 0 | (corr seg 1) | main buf 0 .. NBUF-1], NMAX each.
+  static constexpr int NBUF = TileShape<MODE>::NBUF;
+  static constexpr int MAIN0 = TileShape<MODE>::NCORR;  // first main buffer, in units of NMAX columns
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
-  static_assert(4 * NMAX <= 512, "TMEM holds 512 columns");
 };
 
 // (s, t) slice pairs in issue order; pair 0 is the leading product.
@@ -137,6 +146,7 @@ struct Tile {
 
 template <int MODE>
 __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
+  constexpr int NMAX = TileShape<MODE>::NMAX;
   Tile T;
   int n;
   if (MODE == kProject) {
@@ -178,10 +188,13 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
 }
 
 template <int NSL, int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapBt, TcArgs args) {
-  using C = TcCfg<NSL>;
+  using C = TcCfg<NSL, MODE>;
+  constexpr int NMAX = TileShape<MODE>::NMAX;
+  constexpr int NH = TileShape<MODE>::NH;
+  constexpr int kEpiWarps = TileShape<MODE>::EPI_WARPS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const uint32_t d_corr = tmem + seg * NMAX;
+          const uint32_t d_corr = tmem + seg * NMAX;  // seg < NCORR
           bool corr_init = false;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
             const int buf = gglob % C::NBUF, use = gglob / C::NBUF;
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t d_main = tmem + (2 + buf) * NMAX;
+            const uint32_t d_main = tmem + (C::MAIN0 + buf) * NMAX;
             bool main_init = false;
             const int kg1 = min(nkb, kg + flush);
             for (int kb = kg; kb < kg1; ++kb) {
@@ -299,16 +312,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
               }
               tc_fence_after();
+              // one descriptor per operand and stage; slices and k-steps are compile-time
+              // offsets added to the start-address field (addresses stay below 256 KB)
               const uint32_t sA = smem_u32(smem + stage * C::STAGE);
-              const uint32_t sB = sA + NSL * C::A_SLICE;
+              const uint64_t a0 = BK == 64 ? sdesc_kmajor_sw128(sA) : sdesc_kmajor_sw64(sA);
+              const uint64_t b0 = BK == 64 ? sdesc_kmajor_sw128(sA + NSL * C::A_SLICE)
+                                           : sdesc_kmajor_sw64(sA + NSL * C::A_SLICE);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
 #pragma unroll
                 for (int p = 0; p < C::NPROD; ++p) {
-                  const uint64_t ad = BK == 64 ? sdesc_kmajor_sw128(sA + prod_s(p) * C::A_SLICE + kk * 32)
-                                               : sdesc_kmajor_sw64(sA + prod_s(p) * C::A_SLICE + kk * 32);
-                  const uint64_t bd = BK == 64 ? sdesc_kmajor_sw128(sB + prod_t(p) * C::B_SLICE + kk * 32)
-                                               : sdesc_kmajor_sw64(sB + prod_t(p) * C::B_SLICE + kk * 32);
+                  const uint64_t ad = a0 + (uint64_t)((prod_s(p) * C::A_SLICE + kk * 32) >> 4);
+                  const uint64_t bd = b0 + (uint64_t)((prod_t(p) * C::B_SLICE + kk * 32) >> 4);
                   if (p == 0) {
                     umma_f16(d_main, ad, bd, idesc, main_init ? 1u : 0u);
                     main_init = true;
@@ -338,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ================= epilogue warps 2 .. 2 + kEpiWarps - 1 =================
+    static_assert(MODE == kSynthesize || TileShape<MODE>::NCORR >= 1, "");
     const int ew = warp - 2;
     const int q = warp % 4;                // TMEM lane quadrant this warp may access
     const int colq = ew / 4;               // which group of NH columns
@@ -364,18 +380,18 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           if (active) {
+            // all loads of the flush in flight before one wait
+            uint32_t vm[NH];
 #pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += 8) {
-              uint32_t vm[8];
-              tmem_ld8(tmem + t_lane + (2 + buf) * NMAX + col0 + c0, vm);
-              tmem_ld_wait();
+            for (int c0 = 0; c0 < NH; c0 += 8)
+              tmem_ld8(tmem + t_lane + (C::MAIN0 + buf) * NMAX + col0 + c0, *reinterpret_cast<uint32_t(*)[8]>(&vm[c0]));
+            tmem_ld_wait();
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                float s, e;
-                two_sum(hi[c0 + j], __uint_as_float(vm[j]), s, e);
-                hi[c0 + j] = s;
-                lo[c0 + j] += e;
-              }
+            for (int j = 0; j < NH; ++j) {
+              float s, e;
+              two_sum(hi[j], __uint_as_float(vm[j]), s, e);
+              hi[j] = s;
+              lo[j] += e;
             }
           }
           tc_fence_before();
@@ -389,14 +405,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         if (NSL > 1 && active) {
+          uint32_t vc[NH];
 #pragma unroll
-          for (int c0 = 0; c0 < NH; c0 += 8) {
-            uint32_t vc[8];
-            tmem_ld8(tmem + t_lane + seg * NMAX + col0 + c0, vc);
-            tmem_ld_wait();
+          for (int c0 = 0; c0 < NH; c0 += 8)
+            tmem_ld8(tmem + t_lane + seg * NMAX + col0 + c0, *reinterpret_cast<uint32_t(*)[8]>(&vc[c0]));
+          tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 8; ++j) lo[c0 + j] += __uint_as_float(vc[j]);
-          }
+          for (int j = 0; j < NH; ++j) lo[j] += __uint_as_float(vc[j]);
         }
         tc_fence_before();
         __syncwarp();
