@@ -194,6 +194,27 @@ ygs_status ygs_read_phase_times(ygs_plan* plan, double* ms, int* n_calls);
  * involved and the context stays usable. */
 ygs_status ygs_debug_wait_timeout(ygs_plan* plan, int spins, void* stream);
 
+/* Size of the device array behind ygs_solve_static, in bytes. */
+#define YGS_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* Phi = A rho like ygs_solve, always in FP64 on the plan's FP64 weights, with
+ * no device allocation: the split-K partial sums and the moments B and M live
+ * in one file-scope device array of YGS_STATIC_SCRATCH_BYTES (32 MiB) per
+ * device instead of the plan's workspaces.  The paper has no counterpart; it
+ * serves callers that may not allocate at solve time (a host code that has
+ * given all free device memory to its own pool, a running time-step loop that
+ * forbids allocator calls).
+ * Limit: the plan must need at most YGS_STATIC_SCRATCH_BYTES of scratch,
+ * (split_k + 2) * n_r * K * 8 bytes (split_k from ygs_get_info); a larger plan
+ * returns UNSUPPORTED with the sizes in ygs_last_error() and enqueues nothing.
+ * The first call on a device resolves the array's device address (module
+ * set-up); make that first call before any stream capture.
+ * The array is shared by all calls on a device in the process: calls whose GPU
+ * work overlaps (unordered streams, concurrent host threads) race on it.  No
+ * part of it has to start at zero.  The plan's own moments (ygs_get_moments)
+ * are not updated.  Errors: as ygs_solve, plus UNSUPPORTED for the limit. */
+ygs_status ygs_solve_static(ygs_plan* plan, const double* d_rho, double* d_phi, void* stream);
+
 /* Number of kernel launches one ygs_solve / ygs_backward enqueues. */
 int ygs_launches_per_solve(const ygs_plan* plan);
 

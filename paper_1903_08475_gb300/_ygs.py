@@ -27,7 +27,7 @@ FLAG_NO_SYMMETRY = 1
 EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_batched",
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
            "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
-           "ygs_debug_wait_timeout")
+           "ygs_debug_wait_timeout", "ygs_solve_static")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -89,6 +89,7 @@ def load_library(path: Optional[str] = None):
         L.ygs_read_phase_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         L.ygs_launches_per_solve.argtypes = [vp]
         L.ygs_debug_wait_timeout.argtypes = [vp, ctypes.c_int, vp]
+        L.ygs_solve_static.argtypes = [vp, vp, vp, vp]
         for f in EXPORTS:
             if f not in ("ygs_status_string", "ygs_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -179,6 +180,14 @@ def ygs_solve(plan: Plan, rho, phi=None, stream=None):
     """Phi = A rho on device tensors (FP64, n_cells elements)."""
     phi = _field_out(plan, rho) if phi is None else phi
     _check(load_library().ygs_solve(plan.handle, _ptr(rho), _ptr(phi), _stream_handle(stream)))
+    return phi
+
+
+def ygs_solve_static(plan: Plan, rho, phi=None, stream=None):
+    """Phi = A rho in FP64 with the library's static device scratch (no device
+    allocation inside the call; the plan must fit its 32 MiB limit)."""
+    phi = _field_out(plan, rho) if phi is None else phi
+    _check(load_library().ygs_solve_static(plan.handle, _ptr(rho), _ptr(phi), _stream_handle(stream)))
     return phi
 
 
