@@ -10,13 +10,11 @@
 // through a ring of shared-memory stages with TMA; warp 1 issues tcgen05.mma
 // into FP32 TMEM accumulators; warps 2-17 drain them with tcgen05.ld.  The
 // tensor core's FP32 accumulation loses about one unit in the last place per
-// accumulation step, always in the same direction, so the leading product
-// A_0 B_0 is accumulated only over a short "group" of k-blocks in one of two
-// rotating TMEM buffers and then flushed into a float-float register sum
-// (TwoSum, in the spirit of the compensated sums of Sect. 4.3), while the
-// correction products (2^-8 smaller, so their rounding is negligible) share
-// one TMEM accumulator per segment.  TMEM buffers are tracked across tiles,
-// so the epilogue of one tile overlaps the MMAs of the next.
+// accumulation step, always in the same direction, so every product is
+// accumulated only over a short "group" of k-blocks in one of NBUF rotating
+// TMEM buffers and then flushed into a float-float register sum (TwoSum, in
+// the spirit of the compensated sums of Sect. 4.3).  TMEM buffers are tracked
+// across tiles, so the epilogue of one tile overlaps the MMAs of the next.
 //
 //   kProject:    tile = (column tile m, shell tile n, angular chunk z); the
 //                epilogue stores (hi, lo) pairs of the chunk's partial
@@ -39,24 +37,24 @@ namespace tc {
 #endif
 constexpr int BK = YGS_TC_BK;  // k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
 constexpr int BM = 128;        // output rows per tile (TMEM lanes)
-// Tile shapes (shells per tile, columns per epilogue warp).  The projection
-// has one k segment (one correction accumulator), the synthesis two (even /
-// odd columns).  Both use 80-shell tiles: wider tiles lengthen the epilogue's
-// flushes more than they shorten the MMA stream.
-constexpr int kNmaxProject = 80, kNhProject = 40;
-constexpr int kNmaxSynth = 80, kNhSynth = 40;
+// Tile shapes (shells per tile, columns per epilogue warp).  144-shell tiles
+// keep the tensor core compute-bound (a 128 x 80 x 16 MMA is bound by reading
+// its operands from shared memory) and cut the operand bytes per flop.
+constexpr int kNmaxProject = 144, kNhProject = 48;
+constexpr int kNmaxSynth = 144, kNhSynth = 48;
 
 template <int MODE>
 struct TileShape {
   static constexpr int NMAX = MODE == 0 ? kNmaxProject : kNmaxSynth;  // shells per full tile
   static constexpr int NH = MODE == 0 ? kNhProject : kNhSynth;        // columns per epilogue warp
-  static constexpr int NCORR = MODE == 0 ? 1 : 2;                     // correction accumulators
   static constexpr int EPI_WARPS = 4 * (NMAX / NH);
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static_assert(NMAX % 16 == 0 && NMAX <= 256 && NMAX % NH == 0 && NH % 8 == 0, "tile shape");
-  // rotating leading-product buffers: as many as TMEM holds, at most 4
-  static constexpr int NBUF = (512 / NMAX - NCORR) > 4 ? 4 : (512 / NMAX - NCORR);
-  static_assert(NBUF >= 2, "TMEM holds 512 columns: need two leading-product buffers");
+  // TMEM (512 columns): NBUF rotating accumulators of NMAX columns, plus, in
+  // the synthesis, NMAX columns that hold the even-block result E of a tile.
+  static constexpr int E_COLS = MODE == 0 ? 0 : NMAX;
+  static constexpr int NBUF = (512 - E_COLS) / NMAX > 4 ? 4 : (512 - E_COLS) / NMAX;
+  static_assert(NBUF >= 2, "TMEM holds 512 columns: need two accumulators");
 };
 
 enum Mode { kProject = 0, kSynthesize = 1 };
@@ -108,9 +106,8 @@ struct TcCfg {
   static constexpr int STAGES = (220 * 1024) / STAGE > 8 ? 8 : (220 * 1024) / STAGE;
 #endif
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
-  // TMEM columns: [corr seg 0 | (corr seg 1) | main buf 0 .. NBUF-1], NMAX each.
   static constexpr int NBUF = TileShape<MODE>::NBUF;
-  static constexpr int MAIN0 = TileShape<MODE>::NCORR;  // first main buffer, in units of NMAX columns
+  static constexpr int E_COL0 = NBUF * NMAX;  // first TMEM column of the parked E (synthesis)
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
 };
 
@@ -199,11 +196,9 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* tfull = empty + C::STAGES;  // [NBUF] leading-product buffer ready
-  uint64_t* tempty = tfull + C::NBUF;   // [NBUF] leading-product buffer drained
-  uint64_t* cfull = tempty + C::NBUF;   // [2] correction accumulator of a segment final
-  uint64_t* cempty = cfull + 2;         // [2] correction accumulator drained
-  uint64_t* mma_done = cempty + 2;
+  uint64_t* tfull = empty + C::STAGES;  // [NBUF] accumulator ready
+  uint64_t* tempty = tfull + C::NBUF;   // [NBUF] accumulator drained
+  uint64_t* mma_done = tempty + C::NBUF;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
@@ -218,10 +213,6 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     for (int b = 0; b < C::NBUF; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);
-    }
-    for (int r = 0; r < 2; ++r) {
-      mbar_init(&cfull[r], 1);
-      mbar_init(&cempty[r], kEpiWarps);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
@@ -279,21 +270,12 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     // ================= MMA issuer =================
     if (lane == 0) {
       int consumed = 0, gglob = 0;
-      int cuse[2] = {0, 0};
       bool ok = true;
       for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
         const Tile T = decode_tile<MODE>(args, t);
         const uint32_t idesc = idesc_f16(BM, T.n_eff, 1);
         for (int seg = 0; seg < 2 && ok; ++seg) {
           const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
-          if (nkb == 0) continue;
-          // the correction accumulator of this segment must have been drained
-          if (cuse[seg] >= 1 && !mbar_wait(&cempty[seg], (cuse[seg] - 1) & 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          const uint32_t d_corr = tmem + seg * NMAX;  // seg < NCORR
-          bool corr_init = false;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
             const int buf = gglob % C::NBUF, use = gglob / C::NBUF;
             if (use >= 1 && !mbar_wait(&tempty[buf], (use - 1) & 1, abort_flag)) {
@@ -301,8 +283,8 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t d_main = tmem + (C::MAIN0 + buf) * NMAX;
-            bool main_init = false;
+            const uint32_t d = tmem + buf * NMAX;
+            bool init = false;
             const int kg1 = min(nkb, kg + flush);
             for (int kb = kg; kb < kg1; ++kb) {
               const int stage = consumed % C::STAGES;
@@ -318,20 +300,18 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
               const uint64_t a0 = BK == 64 ? sdesc_kmajor_sw128(sA) : sdesc_kmajor_sw64(sA);
               const uint64_t b0 = BK == 64 ? sdesc_kmajor_sw128(sA + NSL * C::A_SLICE)
                                            : sdesc_kmajor_sw64(sA + NSL * C::A_SLICE);
+              // correction products first, while the accumulator is still small (their
+              // rounding then stays ~2^-8 below the leading product's), the leading
+              // product A_0 B_0 last: one FP32 rounding per MMA at its own scale
 #pragma unroll
-              for (int kk = 0; kk < BK / 16; ++kk) {
-#pragma unroll
-                for (int p = 0; p < C::NPROD; ++p) {
-                  const uint64_t ad = a0 + (uint64_t)((prod_s(p) * C::A_SLICE + kk * 32) >> 4);
-                  const uint64_t bd = b0 + (uint64_t)((prod_t(p) * C::B_SLICE + kk * 32) >> 4);
-                  if (p == 0) {
-                    umma_f16(d_main, ad, bd, idesc, main_init ? 1u : 0u);
-                    main_init = true;
-                  } else {
-                    umma_f16(d_corr, ad, bd, idesc, corr_init ? 1u : 0u);
-                    corr_init = true;
-                  }
-                }
+              for (int i = 0; i < C::NPROD * (BK / 16); ++i) {
+                constexpr int NC = C::NPROD - 1, NCd = NC > 0 ? NC : 1;  // correction products
+                const int p = (i < NC * (BK / 16)) ? 1 + i % NCd : 0;
+                const int kk = (i < NC * (BK / 16)) ? i / NCd : i - NC * (BK / 16);
+                const uint64_t ad = a0 + (uint64_t)((prod_s(p) * C::A_SLICE + kk * 32) >> 4);
+                const uint64_t bd = b0 + (uint64_t)((prod_t(p) * C::B_SLICE + kk * 32) >> 4);
+                umma_f16(d, ad, bd, idesc, init ? 1u : 0u);
+                init = true;
               }
               umma_commit(&empty[stage]);
               ++consumed;
@@ -339,9 +319,6 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
             if (!ok) break;
             umma_commit(&tfull[buf]);
           }
-          if (!ok) break;
-          umma_commit(&cfull[seg]);
-          ++cuse[seg];
         }
       }
       if (!ok) {
@@ -353,7 +330,6 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     }
   } else {
     // ================= epilogue warps 2 .. 2 + kEpiWarps - 1 =================
-    static_assert(MODE == kSynthesize || TileShape<MODE>::NCORR >= 1, "");
     const int ew = warp - 2;
     const int q = warp % 4;                // TMEM lane quadrant this warp may access
     const int colq = ew / 4;               // which group of NH columns
@@ -361,14 +337,14 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     const uint32_t t_lane = (uint32_t)(q * 32) << 16;
     const int col0 = colq * NH;
     int gglob = 0;
-    int cuse[2] = {0, 0};
     bool ok = true;
     for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
       const Tile T = decode_tile<MODE>(args, t);
       const bool active = col0 < T.n_eff;  // this warp's columns exist in the tile (warp-uniform)
-      float hi[NH], lo[NH], ev[NH];
+      // float-float sums of column pairs (2j, 2j+1), packed for the f32x2 pipes
+      uint64_t H[NH / 2], L[NH / 2];
 #pragma unroll
-      for (int j = 0; j < NH; ++j) hi[j] = lo[j] = ev[j] = 0.0f;
+      for (int j = 0; j < NH / 2; ++j) H[j] = L[j] = 0ull;
       const int nseg = T.seg_kb1 > 0 ? 2 : 1;
       for (int seg = 0; seg < nseg && ok; ++seg) {
         const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
@@ -380,18 +356,21 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
           }
           tc_fence_after();
           if (active) {
-            // all loads of the flush in flight before one wait
-            uint32_t vm[NH];
+            // 24 columns in flight per wait
 #pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += 8)
-              tmem_ld8(tmem + t_lane + (C::MAIN0 + buf) * NMAX + col0 + c0, *reinterpret_cast<uint32_t(*)[8]>(&vm[c0]));
-            tmem_ld_wait();
+            for (int c0 = 0; c0 < NH; c0 += 24) {
+              uint32_t vm[24];
 #pragma unroll
-            for (int j = 0; j < NH; ++j) {
-              float s, e;
-              two_sum(hi[j], __uint_as_float(vm[j]), s, e);
-              hi[j] = s;
-              lo[j] += e;
+              for (int c1 = 0; c1 < 24 && c0 + c1 < NH; c1 += 8)
+                tmem_ld8(tmem + t_lane + buf * NMAX + col0 + c0 + c1, *reinterpret_cast<uint32_t(*)[8]>(&vm[c1]));
+              tmem_ld_wait();
+#pragma unroll
+              for (int j = 0; j < 12 && c0 + 2 * j < NH; ++j) {
+                uint64_t s, e;
+                two_sum2(H[c0 / 2 + j], pk2(__uint_as_float(vm[2 * j]), __uint_as_float(vm[2 * j + 1])), s, e);
+                H[c0 / 2 + j] = s;
+                L[c0 / 2 + j] = add2(L[c0 / 2 + j], e);
+              }
             }
           }
           tc_fence_before();
@@ -399,57 +378,59 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         if (!ok) break;
-        if (!mbar_wait(&cfull[seg], cuse[seg] & 1, abort_flag)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        if (NSL > 1 && active) {
-          uint32_t vc[NH];
+        if (MODE == kSynthesize && seg == 0 && nseg == 2 && active) {
+          // even block done: park E = hi + lo in TMEM, restart the sums for the odd block
 #pragma unroll
-          for (int c0 = 0; c0 < NH; c0 += 8)
-            tmem_ld8(tmem + t_lane + seg * NMAX + col0 + c0, *reinterpret_cast<uint32_t(*)[8]>(&vc[c0]));
-          tmem_ld_wait();
+          for (int c0 = 0; c0 < NH; c0 += 8) {
+            uint32_t ve[8];
 #pragma unroll
-          for (int j = 0; j < NH; ++j) lo[j] += __uint_as_float(vc[j]);
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&cempty[seg]);
-        ++cuse[seg];
-        if (MODE == kSynthesize && seg == 0 && nseg == 2) {
-          // even block done: keep E, restart the sums for the odd block
-#pragma unroll
-          for (int j = 0; j < NH; ++j) {
-            ev[j] = hi[j] + lo[j];
-            hi[j] = lo[j] = 0.0f;
+            for (int j = 0; j < 4; ++j) {
+              float e0, e1;
+              upk2(add2(H[c0 / 2 + j], L[c0 / 2 + j]), e0, e1);
+              ve[2 * j] = __float_as_uint(e0);
+              ve[2 * j + 1] = __float_as_uint(e1);
+              H[c0 / 2 + j] = L[c0 / 2 + j] = 0ull;
+            }
+            tmem_st8(tmem + t_lane + C::E_COL0 + col0 + c0, ve);
           }
+          tmem_st_wait();
         }
       }
       if (!ok || !active) continue;
-      if (MODE == kProject) {
-        if (T.a_row0 + r < T.a_rows_end) {
-          float2* out = args.part + (long long)T.z * args.n_b * args.ldp;
+      // output, 8 columns at a time (keeps the register footprint of the sums)
 #pragma unroll
-          for (int j = 0; j < NH; ++j) {
-            const int n = T.b_row0 + col0 + j;
-            if (n < args.n_b) {
-              float s, e;
-              two_sum(hi[j], lo[j], s, e);
-              out[(long long)n * args.ldp + T.a_row0 + r] = make_float2(s, e);
-            }
-          }
+      for (int c0 = 0; c0 < NH; c0 += 8) {
+        float ev[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) ev[jj] = 0.0f;
+        if (MODE == kSynthesize && nseg == 2) {
+          uint32_t eu[8];
+          tmem_ld8(tmem + t_lane + C::E_COL0 + col0 + c0, eu);
+          tmem_ld_wait();
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) ev[jj] = __uint_as_float(eu[jj]);
         }
-      } else {
-        const long long nang = args.pt.nang[T.g_patch];
-        const long long a_loc = (long long)T.m_loc * BM + r;
-        if (a_loc < nang) {
 #pragma unroll
-          for (int j = 0; j < NH; ++j) {
-            const int n = T.b_row0 + col0 + j;
-            if (n >= args.n_b) continue;
-            float v = hi[j] + lo[j];
-            float e0 = (nseg == 2) ? ev[j] : 0.0f;
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = c0 + jj;
+          float h0, h1, l0, l1;
+          upk2(H[j / 2], h0, h1);
+          upk2(L[j / 2], l0, l1);
+          const float hj = (j & 1) ? h1 : h0, lj = (j & 1) ? l1 : l0;
+          const int n = T.b_row0 + col0 + j;
+          if (n >= args.n_b) continue;
+          if (MODE == kProject) {
+            if (T.a_row0 + r < T.a_rows_end) {
+              float s, e;
+              two_sum(hj, lj, s, e);
+              args.part[((long long)T.z * args.n_b + n) * args.ldp + T.a_row0 + r] = make_float2(s, e);
+            }
+          } else {
+            const long long nang = args.pt.nang[T.g_patch];
+            const long long a_loc = (long long)T.m_loc * BM + r;
+            if (a_loc >= nang) continue;
+            float v = hj + lj;
+            float e0 = ev[jj];
             if (args.mono) {
               // the monopole belongs to the even block (E) or, without the symmetry, to the only block
               const float2 mm = args.mono[n];
@@ -458,8 +439,8 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
                 two_sum(e0, mm.x, s, e);
                 e0 = s + (e + mm.y);
               } else {
-                two_sum(hi[j], mm.x, s, e);
-                v = s + (e + mm.y + lo[j]);
+                two_sum(hj, mm.x, s, e);
+                v = s + (e + mm.y + lj);
               }
             }
             if (args.symmetric) {
