@@ -35,8 +35,8 @@ NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), profiling recipe t
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ygs", choices=["ygs", "reference"])
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -145,7 +145,8 @@ def run_reference(args, ws, rank):
     from paper_1903_08475_gb300 import workloads as W
 
     grid, rho = W.config1(n_r=args.n_r)
-    n_shells = 20
+    # shells per step: ~12 ms of 16-core oracle time per shell, so the run stays near a minute
+    n_shells = max(1, min(20, 4000 // max(1, args.steps + args.warmup)))
     lo = grid.n_r // 2 - n_shells // 2
     sub = W.Grid(**{**grid.__dict__, "edges": grid.edges[lo: lo + n_shells + 1]})
     rho_s = np.concatenate([rho[grid.patch_offset(p) + lo * grid.nang(p): grid.patch_offset(p) + (lo + n_shells) * grid.nang(p)]
@@ -250,7 +251,7 @@ def main():
     info = plan.info
     sym = info["symmetric"] == 1
     nang_eff = grid.nang(0) if sym else grid.nang_total
-    nprod = {"fp64": 1, "bf16x3": 3, "bf16x6": 6}[precision]
+    nprod = {"fp64": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}[precision]
     # algorithmic FLOPs of one contraction: one FMA per (shell, stored cell, column) and slice product
     flops_gemm = 2.0 * nprod * grid.n_r * nang_eff * grid.K
     per = [x / max(ncalls, 1) for x in phase_ms]

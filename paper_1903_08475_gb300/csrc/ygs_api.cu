@@ -142,7 +142,7 @@ ygs_status validate_desc(const ygs_desc* d) {
     return fail(YGS_ERR_INVALID_ARG, "l_max must be in [0, " + std::to_string(kMaxLmax) + "]");
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
-  if (d->precision < YGS_FP64 || d->precision > YGS_BF16X6) return fail(YGS_ERR_INVALID_ARG, "bad precision");
+  if (d->precision < YGS_FP64 || d->precision > YGS_FP16X3) return fail(YGS_ERR_INVALID_ARG, "bad precision");
   if (d->flags & ~YGS_FLAG_NO_SYMMETRY) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;
@@ -351,9 +351,10 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
 
   st = build_weights(p);
   if (st != YGS_OK) return fail_free(st);
-  if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3) {
+  if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3 || p->precision == YGS_FP16X3) {
     if (p->n_r > 65535) return fail_free(fail(YGS_ERR_UNSUPPORTED, "split precision supports n_r <= 65535"));
     p->tc_nsl = (p->precision == YGS_BF16X6) ? 3 : 2;
+    p->tc_fp16 = (p->precision == YGS_FP16X3) ? 1 : 0;
     st = tc_setup(p, sms);
     if (st != YGS_OK) return fail_free(st);
   }
@@ -559,7 +560,7 @@ ygs_status ygs_debug_wait_timeout(ygs_plan* p, int spins, void* stream) {
   return YGS_OK;
 }
 
-int ygs_launches_per_solve(const ygs_plan* p) { return p ? (p->tc_nsl ? 6 : 3) : 0; }
+int ygs_launches_per_solve(const ygs_plan* p) { return p ? (p->tc_nsl ? (p->tc_fp16 ? 7 : 6) : 3) : 0; }
 
 ygs_status ygs_get_status(ygs_plan* p) {
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");

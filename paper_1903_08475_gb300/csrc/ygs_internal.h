@@ -89,6 +89,12 @@ struct ygs_plan {
   long long* tc_pad_off_d = nullptr;
   float2* tc_mono = nullptr;  // -G M[i][0] per shell as (hi, lo)
   double* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells
+  // FP16 slices (YGS_FP16X3): power-of-two exponents that scale each operand row into FP16's range
+  int tc_fp16 = 0;
+  int tc_eq = 0;              // Q (all rows)
+  int* tc_eu = nullptr;       // [K_pad] U^T row (column c)
+  int* tc_ef = nullptr;       // [2][n_r][S] field row (plane, shell) per split-K chunk, written by every solve
+  int* tc_em = nullptr;       // [n_r] M row (shell), written by every solve
   CUtensorMap tc_map_ut, tc_map_f, tc_map_f_tail, tc_map_q, tc_map_m, tc_map_m_tail;
 };
 

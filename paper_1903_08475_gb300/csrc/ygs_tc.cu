@@ -9,9 +9,12 @@
 //   Ms  [s][Nr][K_pad]       slices of M       (synthesis B operand)
 //   part [z][Nr][K_pad] float2 (hi, lo) projection partials of chunk z
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdio>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "ygs_tc_gemm.cuh"
 
@@ -40,21 +43,21 @@ EncodeTiledFn encode_fn() {
 
 // 3-D BF16 tensor (kdim fastest, rows, planes) read in boxes of BK x box_rows x 1, swizzled to match
 // the UMMA shared-memory descriptors (128-byte swizzle for BK = 64).
-bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long long planes, int box_rows) {
+bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long long planes, int box_rows, bool fp16) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)planes};
   cuuint64_t strides[2] = {(cuuint64_t)kdim * 2, (cuuint64_t)kdim * 2 * rows};
   cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  return enc(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              tc::BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 __device__ __forceinline__ void slices_of(double x, int nsl, __nv_bfloat16 (&s)[3]) {
   float hi, lo;
-  tc::f64_to_ff(x, hi, lo);
+  tc::f64_to_ff_fast(x, hi, lo);
   tc::ff_to_bf16x3(hi, lo, s[0], s[1], s[2]);
   if (nsl == 2) {
     // two slices: the second carries the rounded remainder of hi + lo
@@ -110,13 +113,13 @@ __device__ __forceinline__ void ff_slices(float hi, float lo, int nsl, __nv_bflo
 __device__ __forceinline__ void sigma_slices(double r0, double r1, int nsl, int symmetric,
                                              __nv_bfloat16 (&out)[2][3]) {
   float h0, l0;
-  tc::f64_to_ff(r0, h0, l0);
+  tc::f64_to_ff_fast(r0, h0, l0);
   if (!symmetric) {
     ff_slices(h0, l0, nsl, out[0]);
     return;
   }
   float h1, l1;
-  tc::f64_to_ff(r1, h1, l1);
+  tc::f64_to_ff_fast(r1, h1, l1);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     float s, err;
@@ -185,6 +188,251 @@ __global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable 
   }
 }
 
+// ---- FP16 slices (two per value, 22 significant bits) of power-of-two-scaled rows ----
+
+__device__ __forceinline__ void half2_slices(double v, __half& s0, __half& s1) {
+  s0 = __double2half(v);
+  s1 = __double2half(v - (double)__half2float(s0));
+}
+
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* red) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, d));
+  const int w = threadIdx.x / 32, nw = blockDim.x / 32;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  T r = red[0];
+  for (int k = 1; k < nw; ++k) r = max(r, red[k]);
+  return r;
+}
+
+// eu[pc] for the row pc of U^T (column ci of U) over every stored cell; one CTA per padded column.
+__global__ void colexp_u_kernel(int K, const int* __restrict__ pc_int, long long rows, const double* __restrict__ U,
+                                int* __restrict__ eu) {
+  __shared__ double red[32];
+  const int pc = blockIdx.x, ci = pc_int[pc];
+  double m = 0.0;
+  if (ci >= 0)
+    for (long long r = threadIdx.x; r < rows; r += blockDim.x) m = fmax(m, fabs(U[r * K + ci]));
+  m = block_max(m, red);
+  if (threadIdx.x == 0) eu[pc] = tc::fp16_row_exp(m);
+}
+
+// Ut[s][pc][apad]: slices of U^T rows scaled by 2^eu[pc].
+__global__ void slice_ut16_kernel(int K, int K_pad, long long n_pad, const int* __restrict__ pc_int,
+                                  const double* __restrict__ U, PatchTable pt, int nwp,
+                                  const long long* __restrict__ pad_off, const int* __restrict__ eu,
+                                  __half* __restrict__ Ut) {
+  long long total = (long long)K_pad * n_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int pc = (int)(e / n_pad);
+    long long ap = e % n_pad;
+    int g = 0;
+    while (g + 1 < nwp && pad_off[g + 1] <= ap) ++g;
+    long long a = ap - pad_off[g];
+    double v = 0.0;
+    int ci = pc_int[pc];
+    if (ci >= 0 && a < pt.nang[g]) v = ldexp(U[(pt.ang_off[g] + a) * K + ci], eu[pc]);
+    __half s0, s1;
+    half2_slices(v, s0, s1);
+    Ut[e] = s0;
+    Ut[total + e] = s1;
+  }
+}
+
+// Largest |Q| over the real columns other than the monopole (bits of a positive double, atomically maxed).
+__global__ void qmax_kernel(int K, int K_pad, long long rows, const int* __restrict__ pc_int,
+                            const int* __restrict__ pc_nat, const double* __restrict__ Q,
+                            unsigned long long* __restrict__ out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  const long long total = rows * K_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int pc = (int)(e % K_pad);
+    const int ci = pc_int[pc];
+    if (ci >= 0 && pc_nat[pc] != 0) m = fmax(m, fabs(Q[(e / K_pad) * K + ci]));
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// Qs[s][row][pc]: slices of Q * 2^eq; the monopole column stays zero.
+__global__ void slice_q16_kernel(int K, int K_pad, long long rows, const int* __restrict__ pc_int,
+                                 const int* __restrict__ pc_nat, const double* __restrict__ Q, int eq,
+                                 __half* __restrict__ Qs) {
+  long long total = rows * K_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long row = e / K_pad;
+    int pc = (int)(e % K_pad);
+    int ci = pc_int[pc];
+    double v = (ci >= 0 && pc_nat[pc] != 0) ? ldexp(Q[row * K + ci], eq) : 0.0;
+    __half s0, s1;
+    half2_slices(v, s0, s1);
+    Qs[e] = s0;
+    Qs[total + e] = s1;
+  }
+}
+
+// sigma+- (or rho) of one cell as float-float pairs.
+__device__ __forceinline__ void sigma_ff(double r0, double r1, int symmetric, float (&hi)[2], float (&lo)[2]) {
+  float h0, l0;
+  tc::f64_to_ff_fast(r0, h0, l0);
+  if (!symmetric) {
+    hi[0] = h0;
+    lo[0] = l0;
+    hi[1] = lo[1] = 0.0f;
+    return;
+  }
+  float h1, l1;
+  tc::f64_to_ff_fast(r1, h1, l1);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float s, err;
+    tc::two_sum(h0, h ? -h1 : h1, s, err);
+    float l = err + (h ? (l0 - l1) : (l0 + l1));
+    hi[h] = s + l;
+    lo[h] = l - (hi[h] - s);
+  }
+}
+
+// 8 consecutive values of a row (two 16-byte loads per pair when aligned), zero past n.
+__device__ __forceinline__ void load8(const double* __restrict__ p, long long n, bool vec, double (&x)[8]) {
+  if (vec && n >= 8) {
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(p + c);
+      x[c] = v.x;
+      x[c + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = (c < n) ? p[c] : 0.0;
+  }
+}
+
+// Field slices in FP16, one CTA per (split-K chunk z, shell i), 8 cells per
+// thread and step: pass 1 finds the largest |sigma| of each plane over the
+// chunk's cells (ef[h][i][z]), pass 2 (the chunk now in L2) writes the scaled
+// slices F[h*2+s][i][apad], 16 bytes per store.  Every projection partial of
+// chunk z then carries one power of two per shell.  Symmetric: planes sigma+
+// (h = 0) and sigma- (h = 1) of the Yin/Yang rows; otherwise plane 0, each
+// chunk lying inside one stored patch.
+__global__ void __launch_bounds__(256) field_slices16_kernel(int n_r, int symmetric, int nwp, PatchTable pt,
+                                                             const long long* __restrict__ pad_off, long long n_pad,
+                                                             const int2* __restrict__ chunks, int S,
+                                                             const double* __restrict__ rho, __half* __restrict__ F,
+                                                             int* __restrict__ ef) {
+  __shared__ float red[32];
+  const int z = blockIdx.x, i = blockIdx.y;
+  const long long plane = (long long)n_r * n_pad;
+  const int2 ch = chunks[z];
+  int g = 0;
+  while (g + 1 < nwp && pad_off[g + 1] <= ch.x) ++g;
+  const long long na = pt.nang[g];
+  const long long a0 = ch.x - pad_off[g], n = min((long long)ch.y - pad_off[g], na) - a0;  // real cells of the chunk
+  const double* x0p = rho + pt.fld_off[g] + i * na + a0;
+  const double* x1p = symmetric ? rho + pt.fld_off[1] + i * na + a0 : x0p;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x0p) | reinterpret_cast<uintptr_t>(x1p)) & 15) == 0;
+  __half* out = F + (long long)i * n_pad + pad_off[g] + a0;  // 16-byte aligned: every offset is a multiple of 8
+  // pass 1 from truncated FP32 values (a few ulp from the float-float heads of
+  // pass 2); the maxima are raised by 2^-16 so that m 2^e still bounds every head
+  float mx0 = 0.0f, mx1 = 0.0f;
+  for (long long j = 8LL * threadIdx.x; j < n; j += 8LL * blockDim.x) {
+    double x0[8], x1[8];
+    load8(x0p + j, n - j, vec, x0);
+    if (symmetric) load8(x1p + j, n - j, vec, x1);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float f0 = tc::f64_trunc_f32(x0[c]), f1 = symmetric ? tc::f64_trunc_f32(x1[c]) : 0.0f;
+      mx0 = fmaxf(mx0, fabsf(f0 + f1));
+      mx1 = fmaxf(mx1, fabsf(f0 - f1));
+    }
+  }
+  const int e0 = tc::fp16_row_exp((double)block_max(mx0, red) * (1.0 + 0x1p-16));
+  const int e1 = symmetric ? tc::fp16_row_exp((double)block_max(mx1, red) * (1.0 + 0x1p-16)) : 0;
+  if (threadIdx.x == 0) {
+    ef[(long long)i * S + z] = e0;
+    ef[((long long)n_r + i) * S + z] = e1;
+  }
+  float f[2][2];  // 2^e0, 2^e1 as two exact factors each
+  tc::pow2_pair(e0, f[0][0], f[0][1]);
+  tc::pow2_pair(e1, f[1][0], f[1][1]);
+  for (long long j = 8LL * threadIdx.x; j < n; j += 8LL * blockDim.x) {
+    double x0[8], x1[8];
+    load8(x0p + j, n - j, vec, x0);
+    if (symmetric) load8(x1p + j, n - j, vec, x1);
+    uint32_t w[2][2][4];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float hi[2], lo[2];
+      sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi, lo);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float hs = (hi[h] * f[h][0]) * f[h][1], ls = (lo[h] * f[h][0]) * f[h][1];
+        const __half s0 = __float2half_rn(hs);
+        const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
+        const uint32_t b0 = __half_as_ushort(s0), b1 = __half_as_ushort(s1);
+        if (c & 1) {
+          w[h][0][c / 2] |= b0 << 16;
+          w[h][1][c / 2] |= b1 << 16;
+        } else {
+          w[h][0][c / 2] = b0;
+          w[h][1][c / 2] = b1;
+        }
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1 && !symmetric) break;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        __half* dst = out + (long long)(h * 2 + k) * plane + j;
+        if (n - j >= 8) {
+          *reinterpret_cast<uint4*>(dst) = make_uint4(w[h][k][0], w[h][k][1], w[h][k][2], w[h][k][3]);
+        } else {
+          for (int c = 0; c < n - j; ++c)
+            dst[c] = __ushort_as_half((unsigned short)(w[h][k][c / 2] >> (16 * (c & 1))));
+        }
+      }
+    }
+  }
+}
+
+// Ms[s][i][pc]: FP16 slices of M's row i scaled by 2^em[i] (largest |M| over the
+// real columns other than the monopole, whose Q column is zero; it is written
+// as 0).  One CTA per shell; FP64 values enter as float-float pairs.
+__global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_nat, const double* __restrict__ M,
+                                 __half* __restrict__ Ms, int* __restrict__ em) {
+  __shared__ float red[32];
+  const int i = blockIdx.x;
+  const long long splane = (long long)n_r * K_pad;
+  const double* row = M + (long long)i * K_pad;
+  float m = 0.0f;
+#pragma unroll 4
+  for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {
+    const double v = row[pc];
+    const int nat = pc_nat[pc];
+    m = fmaxf(m, nat > 0 ? fabsf(tc::f64_trunc_f32(v)) : 0.0f);
+  }
+  // the truncated maximum is every float-float head's bound below (same truncation)
+  const int e = tc::fp16_row_exp((double)block_max(m, red));
+  if (threadIdx.x == 0) em[i] = e;
+#pragma unroll 4
+  for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {
+    const double v = row[pc];
+    const int nat = pc_nat[pc];
+    float hi = 0.0f, lo = 0.0f;
+    if (nat > 0) tc::f64_to_ff_fast(v, hi, lo);
+    const float hs = tc::mul_pow2f(hi, e), ls = tc::mul_pow2f(lo, e);
+    const __half s0 = __float2half_rn(hs);
+    const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
+    Ms[(long long)i * K_pad + pc] = s0;
+    Ms[splane + (long long)i * K_pad + pc] = s1;
+  }
+}
+
 // Products of the radial ratios over every chunk of shells (per degree l):
 // cp[0][l][p] = prod_{i in chunk p} (r_{i-1}^+/r_i^+)^(l+1),
 // cp[1][l][p] = prod_{i in chunk p} (r_{i-1}^+/r_i^+)^l   (0 for chunks that contain shell 0).
@@ -211,9 +459,12 @@ __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
 
 // Phase 1 of the chunked scans: B from the partials, local inner / outer
 // recurrences of one chunk of shells with zero carry, and their summaries.
+// With FP16 slices (ef, eu not null) the partial of chunk z is unscaled exactly
+// by 2^-(ef[h][i][z] + eu[pc]), h = 1 for the odd column block of a symmetric plan.
 __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, const int* __restrict__ pc_l,
                                   const float2* __restrict__ part, const double* __restrict__ rad,
-                                  const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ summ) {
+                                  const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ summ,
+                                  const int* __restrict__ ef, const int* __restrict__ eu, int k_split) {
   const int pc = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   if (pc >= K_pad) return;
@@ -233,8 +484,14 @@ __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, c
   double I = 0.0;
   for (int i = i0; i < i1; ++i) {
     float h = 0.f, lo = 0.f;
+    const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
     for (int z = 0; z < S; ++z) {
-      const float2 v = part[z * plane + (long long)i * K_pad + pc];
+      float2 v = part[z * plane + (long long)i * K_pad + pc];
+      if (efi) {
+        const int es = -(efi[z] + eu[pc]);
+        v.x = tc::mul_pow2f(v.x, es);
+        v.y = tc::mul_pow2f(v.y, es);
+      }
       float s, e;
       tc::two_sum(h, v.x, s, e);
       h = s;
@@ -259,8 +516,9 @@ __global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, c
 }
 
 // Phase 2: carries between chunks.  The chunk summaries define affine maps
-// c -> F c + s; one warp per column composes them with a shuffle scan over
-// up to 32 chunks (inner recurrence upward, outer downward).
+// c -> F c + s; one warp per column and direction composes them: each lane
+// folds up to 32 consecutive chunks, a shuffle scan joins the lanes (inner
+// recurrence upward, outer downward), and each lane walks its chunks again.
 __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
   // inclusive scan: after it lane p holds the composition of chunks 0..p
 #pragma unroll
@@ -278,21 +536,24 @@ __global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ s
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   const int pc = warp / 2, dir = warp % 2;
   if (pc >= K_pad) return;
-  if (dir == 0) {
-    // inner: c_{p+1} = FI_p c_p + I_p, c_0 = 0; carry into chunk p = c_p
-    double F = (lane < P) ? summ[((long long)1 * P + lane) * K_pad + pc] : 1.0;
-    double sv = (lane < P) ? summ[((long long)0 * P + lane) * K_pad + pc] : 0.0;
-    affine_scan_up(F, sv, lane);
-    const double prev = __shfl_up_sync(0xffffffffu, sv, 1);
-    if (lane < P) carry[((long long)0 * P + lane) * K_pad + pc] = lane == 0 ? 0.0 : prev;
-  } else {
-    // outer: c_{p-1} = FP_p c_p + P_p, c_{P-1} = 0 (lanes run over reversed chunks)
-    const int p = P - 1 - lane;
-    double F = (lane < P) ? summ[((long long)3 * P + p) * K_pad + pc] : 1.0;
-    double sv = (lane < P) ? summ[((long long)2 * P + p) * K_pad + pc] : 0.0;
-    affine_scan_up(F, sv, lane);
-    const double prev = __shfl_up_sync(0xffffffffu, sv, 1);
-    if (lane < P) carry[((long long)1 * P + p) * K_pad + pc] = lane == 0 ? 0.0 : prev;
+  // scan order t: chunks upward (inner, dir 0) or downward (outer, dir 1); lane
+  // holds the q consecutive positions [lane q, lane q + q) (P <= 32 q)
+  const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
+  const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
+  double F = 1.0, sv = 0.0;
+  for (int t = t0; t < t1; ++t) {
+    const int p = dir ? P - 1 - t : t;
+    const double Ft = summ[((long long)kF * P + p) * K_pad + pc], st = summ[((long long)ks * P + p) * K_pad + pc];
+    sv = fma(Ft, sv, st);
+    F = Ft * F;
+  }
+  affine_scan_up(F, sv, lane);
+  double c = __shfl_up_sync(0xffffffffu, sv, 1);
+  if (lane == 0) c = 0.0;  // nothing enters the first chunk in scan order
+  for (int t = t0; t < t1; ++t) {
+    const int p = dir ? P - 1 - t : t;
+    carry[((long long)dir * P + p) * K_pad + pc] = c;
+    c = fma(summ[((long long)kF * P + p) * K_pad + pc], c, summ[((long long)ks * P + p) * K_pad + pc]);
   }
 }
 
@@ -301,7 +562,8 @@ __global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ s
 __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk, const int* __restrict__ pc_l,
                                   const double* __restrict__ B, const double* __restrict__ rad,
                                   const double* __restrict__ carry, double* __restrict__ M,
-                                  __nv_bfloat16* __restrict__ Ms, double G, float2* __restrict__ mono) {
+                                  __nv_bfloat16* __restrict__ Ms, double G, float2* __restrict__ mono,
+                                  int write_slices) {
   const int pc = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = blockIdx.y;
   const int P = gridDim.y;
@@ -312,7 +574,8 @@ __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk,
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
       M[(long long)i * K_pad + pc] = 0.0;
-      for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
+      if (write_slices)
+        for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
     }
     return;
   }
@@ -338,9 +601,11 @@ __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk,
       tc::f64_to_ff(-G * m, h, lo);
       mono[i] = make_float2(h, lo);
     }
-    __nv_bfloat16 sl[3];
-    slices_of(m, nsl, sl);
-    for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
+    if (write_slices) {
+      __nv_bfloat16 sl[3];
+      slices_of(m, nsl, sl);
+      for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
+    }
   }
 }
 
@@ -426,8 +691,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
                                  (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
   }
   p->tc_S = (int)chunks.size();
-  // chunks of shells for the parallel scans: at most 32 (one warp lane each in the carry pass)
-  p->tc_scan_chunk = std::max(8, (p->n_r + 31) / 32);
+  // chunks of 4 shells for the parallel scans (more for n_r > 4096: at most 1024 chunks, 32 per carry lane)
+  p->tc_scan_chunk = std::max(4, (p->n_r + 1023) / 1024);
   p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
 
   const size_t kp = (size_t)p->tc_k_pad;
@@ -460,6 +725,11 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_ALLOC(p->tc_pad_off_d, (p->n_wpatch + 1) * sizeof(long long));
   TC_ALLOC(p->tc_mono, (size_t)p->n_r * sizeof(float2));
   TC_ALLOC(p->tc_cp, (size_t)2 * (p->l_max + 1) * p->tc_scan_P * sizeof(double));
+  if (p->tc_fp16) {
+    TC_ALLOC(p->tc_eu, kp * sizeof(int));
+    TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * p->tc_S * sizeof(int));
+    TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
+  }
 #undef TC_ALLOC
   p->weight_bytes += (long long)(bytes_ut + bytes_q);
   p->work_bytes += (long long)(bytes_f + bytes_m + bytes_part + 2 * bytes_nk + bytes_sum * 3 / 2);
@@ -478,23 +748,45 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   chunk_prod_kernel<<<((p->l_max + 1) * p->tc_scan_P + 127) / 128, 128>>>(p->n_r, p->l_max, p->tc_scan_chunk,
                                                                           p->tc_scan_P, p->rad, p->tc_cp);
   TC_TRY(cudaGetLastError());
-  slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
-                                 p->tc_pad_off_d, p->tc_ut);
-  TC_TRY(cudaGetLastError());
-  slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_qs);
-  TC_TRY(cudaGetLastError());
+  if (p->tc_fp16) {
+    colexp_u_kernel<<<p->tc_k_pad, 256>>>(K, p->tc_pc_int, p->nang_wtotal, p->U, p->tc_eu);
+    TC_TRY(cudaGetLastError());
+    slice_ut16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
+                                     p->tc_pad_off_d, p->tc_eu, reinterpret_cast<__half*>(p->tc_ut));
+    TC_TRY(cudaGetLastError());
+    // Q as a whole: its largest magnitude (through a scratch word in the M buffer) sets eq
+    unsigned long long* qm = reinterpret_cast<unsigned long long*>(p->tc_M);
+    TC_TRY(cudaMemset(qm, 0, sizeof(unsigned long long)));
+    qmax_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, qm);
+    TC_TRY(cudaGetLastError());
+    unsigned long long bits = 0;
+    TC_TRY(cudaMemcpy(&bits, qm, sizeof(bits), cudaMemcpyDeviceToHost));
+    double qmax;
+    memcpy(&qmax, &bits, sizeof(qmax));
+    p->tc_eq = tc::fp16_row_exp(qmax);
+    slice_q16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_eq,
+                                    reinterpret_cast<__half*>(p->tc_qs));
+    TC_TRY(cudaGetLastError());
+  } else {
+    slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
+                                   p->tc_pad_off_d, p->tc_ut);
+    TC_TRY(cudaGetLastError());
+    slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_qs);
+    TC_TRY(cudaGetLastError());
+  }
   TC_TRY(cudaDeviceSynchronize());
 
   const int N = NS;
   const int Nt = p->tc_n_tail > 0 ? p->tc_n_tail : N;
   const int Npt = p->tc_np_tail > 0 ? p->tc_np_tail : NP;
   const int fplanes = (p->symmetric ? 2 : 1) * nsl;
-  if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM) ||
-      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, NP) ||
-      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Npt) ||
-      !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM) ||
-      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N) ||
-      !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt)) {
+  const bool h16 = p->tc_fp16 != 0;
+  if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM, h16) ||
+      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, NP, h16) ||
+      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Npt, h16) ||
+      !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, h16) ||
+      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N, h16) ||
+      !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt, h16)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return YGS_ERR_CUDA;
   }
@@ -515,13 +807,20 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
 }
 
 void tc_free(ygs_plan* p) {
-  void* bufs[] = {p->tc_ut, p->tc_qs, p->tc_f, p->tc_ms, p->tc_part, p->tc_B, p->tc_M, p->tc_summ, p->tc_carry,
-                  p->tc_chunks, p->tc_pc_int, p->tc_pc_l, p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp};
+  void* bufs[] = {p->tc_ut,    p->tc_qs,     p->tc_f,      p->tc_ms,     p->tc_part,      p->tc_B,
+                  p->tc_M,     p->tc_summ,   p->tc_carry,  p->tc_chunks, p->tc_pc_int,    p->tc_pc_l,
+                  p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_eu, p->tc_ef, p->tc_em};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
 
 cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
+  if (p->tc_fp16) {
+    field_slices16_kernel<<<dim3(p->tc_S, p->n_r), 256, 0, s>>>(p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt,
+                                                                 p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, p->tc_S,
+                                                                 rho, reinterpret_cast<__half*>(p->tc_f), p->tc_ef);
+    return cudaGetLastError();
+  }
   long long nmax = 0;
   for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
   const int threads = 128;
@@ -534,7 +833,9 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
 
 static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.err = p->d_err;
-  a.flush_kb = std::max(1, 64 / tc::BK);  // flush the leading product every 64 k-elements
+  a.ab_fmt = p->tc_fp16 ? 0 : 1;
+  // flush the FP32 accumulators into the float-float sums every 64 k-elements
+  a.flush_kb = std::max(1, 64 / tc::BK);
   a.n_b = p->n_r;
   a.n_full = n_full;
   a.n_tail = n_tail;
@@ -562,13 +863,18 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   const int P = p->tc_scan_P;
   dim3 g1((p->tc_k_pad + 127) / 128, P);
   scan_local_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_pc_l,
-                                       p->tc_part, p->rad, p->tc_cp, p->tc_B, p->tc_summ);
+                                       p->tc_part, p->rad, p->tc_cp, p->tc_B, p->tc_summ, p->tc_ef, p->tc_eu,
+                                       p->symmetric ? p->tc_k_even : p->tc_k_pad);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   scan_carry_kernel<<<(p->tc_k_pad * 2 + 3) / 4, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   scan_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
-                                       p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms, p->G, p->tc_mono);
+                                       p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms, p->G, p->tc_mono,
+                                       p->tc_fp16 ? 0 : 1);
+  if ((e = cudaGetLastError()) != cudaSuccess || !p->tc_fp16) return e;
+  slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M,
+                                          reinterpret_cast<__half*>(p->tc_ms), p->tc_em);
   return cudaGetLastError();
 }
 
@@ -592,6 +898,8 @@ cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
   a.total_tiles = t;
   a.phi = phi;
   a.mono = p->tc_mono;
+  a.m_exp = p->tc_fp16 ? p->tc_em : nullptr;
+  a.q_exp = p->tc_eq;
   const int grid = std::min(a.total_tiles, p->tc_sms);
   return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, p->tc_map_m_tail, a, s);
 }

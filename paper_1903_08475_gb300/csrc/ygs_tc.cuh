@@ -186,6 +186,77 @@ __device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t& s, ui
   e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
+// x * 2^e for |e| <= 252, as two exact multiplications by representable powers of two.
+__device__ __forceinline__ float mul_pow2f(float x, int e) {
+  e = max(-252, min(252, e));
+  const int e1 = e / 2, e2 = e - e1;
+  return (x * __int_as_float((127 + e1) << 23)) * __int_as_float((127 + e2) << 23);
+}
+
+// Exponent e with m * 2^e in [2^14, 2^15) for m > 0 (0 for m = 0): scales a
+// row whose largest magnitude is m to the top of FP16's range.
+__host__ __device__ __forceinline__ int fp16_row_exp(double m) {
+  if (!(m > 0.0)) return 0;
+  int e = 0;
+  const double f = frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+  (void)f;
+  const int r = 15 - e;            // m 2^r in [2^14, 2^15)
+  return r < -200 ? -200 : (r > 200 ? 200 : r);
+}
+
+// Lane-wise FastTwoSum: s = fl(a + b), e = b - (s - a); exact (a + b = s + e)
+// when |a| >= |b| or a = 0, otherwise within one rounding of b.
+__device__ __forceinline__ void fast_two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e) {
+  s = add2(a, b);
+  e = sub2(b, sub2(s, a));
+}
+
+// FP64 -> FP32 by truncation with integer operations only (GB300 runs FP64
+// conversions on its narrow FP64 pipe): the head of f64_to_ff.
+__device__ __forceinline__ float f64_trunc_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126) return __int_as_float((int)sign);
+  if (e > 127) return __int_as_float((int)(sign | 0x7F800000u));
+  return __int_as_float((int)(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu)));
+}
+
+// FP64 -> (hi, lo) FP32 pair with integer operations and one exact FP32
+// subtraction: hi = the top 24 significant bits (truncated), lo = the next 23
+// bits (truncated), so hi + lo keeps 47 bits.  Exponents below FP32's normal
+// range give zeros; above it, an infinite hi.
+__device__ __forceinline__ void f64_to_ff_fast(double x, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(b >> 63) << 31;
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -126) {
+    hi = lo = __int_as_float((int)sign);
+    return;
+  }
+  if (e > 127) {
+    hi = __int_as_float((int)(sign | 0x7F800000u));
+    lo = 0.0f;
+    return;
+  }
+  hi = __int_as_float((int)(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu)));
+  if (e < -103) {
+    lo = 0.0f;
+    return;
+  }
+  // 1.f x 2^(e-23) minus 2^(e-23): the low mantissa bits, exactly (same exponent)
+  const unsigned int eb = sign | ((unsigned int)(e - 23 + 127) << 23);
+  lo = __int_as_float((int)(eb | (unsigned int)((b >> 6) & 0x7FFFFFu))) - __int_as_float((int)eb);
+}
+
+// x * f1 * f2 with the factors of pow2_pair(e): an exact power-of-two scaling.
+__device__ __forceinline__ void pow2_pair(int e, float& f1, float& f2) {
+  e = max(-252, min(252, e));
+  const int e1 = e / 2, e2 = e - e1;
+  f1 = __int_as_float((127 + e1) << 23);
+  f2 = __int_as_float((127 + e2) << 23);
+}
+
 // FP64 -> (hi, lo) FP32 pair by bit manipulation (no FP64 arithmetic): hi keeps
 // the top 24 significant bits (truncated), lo the next 24.  Values whose
 // exponent is outside the normal FP32 range flush to zero / saturate.

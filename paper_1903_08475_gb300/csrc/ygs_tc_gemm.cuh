@@ -35,6 +35,9 @@ namespace tc {
 #ifndef YGS_TC_BK
 #define YGS_TC_BK 64
 #endif
+#ifndef YGS_EPI_CHUNK
+#define YGS_EPI_CHUNK 24  // TMEM columns an epilogue warp loads per wait (multiple of 8)
+#endif
 constexpr int BK = YGS_TC_BK;  // k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
 constexpr int BM = 128;        // output rows per tile (TMEM lanes)
 // Tile shapes (shells per tile, columns per epilogue warp).  144-shell tiles
@@ -91,6 +94,11 @@ struct TcArgs {
   // of being accumulated on the tensor cores (its column is zero in the Q
   // slices).  nullptr disables it.
   const float2* mono;
+  int ab_fmt;           // operand type of the slices: 1 = BF16, 0 = FP16
+  // FP16 slices are scaled rows: the synthesis result of shell n is multiplied
+  // by 2^-(q_exp + m_exp[n]).  nullptr: unscaled (BF16).
+  const int* m_exp;
+  int q_exp;
 };
 
 template <int NSL, int MODE>
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
       bool ok = true;
       for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
         const Tile T = decode_tile<MODE>(args, t);
-        const uint32_t idesc = idesc_f16(BM, T.n_eff, 1);
+        const uint32_t idesc = idesc_f16(BM, T.n_eff, args.ab_fmt);
         for (int seg = 0; seg < 2 && ok; ++seg) {
           const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
@@ -356,18 +364,22 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
           }
           tc_fence_after();
           if (active) {
-            // 24 columns in flight per wait
+            // CH columns in flight per wait
+            constexpr int CH = YGS_EPI_CHUNK < NH ? YGS_EPI_CHUNK : NH;
 #pragma unroll
-            for (int c0 = 0; c0 < NH; c0 += 24) {
-              uint32_t vm[24];
+            for (int c0 = 0; c0 < NH; c0 += CH) {
+              uint32_t vm[CH];
 #pragma unroll
-              for (int c1 = 0; c1 < 24 && c0 + c1 < NH; c1 += 8)
+              for (int c1 = 0; c1 < CH && c0 + c1 < NH; c1 += 8)
                 tmem_ld8(tmem + t_lane + buf * NMAX + col0 + c0 + c1, *reinterpret_cast<uint32_t(*)[8]>(&vm[c1]));
               tmem_ld_wait();
 #pragma unroll
-              for (int j = 0; j < 12 && c0 + 2 * j < NH; ++j) {
+              for (int j = 0; j < CH / 2 && c0 + 2 * j < NH; ++j) {
+                // FastTwoSum: the running sum dominates the flush after the first few
+                // (always for same-sign terms); where it does not, the pair still
+                // holds the sum within one rounding of that flush
                 uint64_t s, e;
-                two_sum2(H[c0 / 2 + j], pk2(__uint_as_float(vm[2 * j]), __uint_as_float(vm[2 * j + 1])), s, e);
+                fast_two_sum2(H[c0 / 2 + j], pk2(__uint_as_float(vm[2 * j]), __uint_as_float(vm[2 * j + 1])), s, e);
                 H[c0 / 2 + j] = s;
                 L[c0 / 2 + j] = add2(L[c0 / 2 + j], e);
               }
@@ -429,8 +441,14 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
             const long long nang = args.pt.nang[T.g_patch];
             const long long a_loc = (long long)T.m_loc * BM + r;
             if (a_loc >= nang) continue;
-            float v = hj + lj;
-            float e0 = ev[jj];
+            float hs = hj, ls = lj, e0 = ev[jj];
+            if (args.m_exp) {  // exact unscaling of FP16-slice results
+              const int es = -(args.q_exp + args.m_exp[n]);
+              hs = mul_pow2f(hs, es);
+              ls = mul_pow2f(ls, es);
+              e0 = mul_pow2f(e0, es);
+            }
+            float v = hs + ls;
             if (args.mono) {
               // the monopole belongs to the even block (E) or, without the symmetry, to the only block
               const float2 mm = args.mono[n];
@@ -439,8 +457,8 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
                 two_sum(e0, mm.x, s, e);
                 e0 = s + (e + mm.y);
               } else {
-                two_sum(hj, mm.x, s, e);
-                v = s + (e + mm.y + lj);
+                two_sum(hs, mm.x, s, e);
+                v = s + (e + mm.y + ls);
               }
             }
             if (args.symmetric) {

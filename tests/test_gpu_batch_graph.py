@@ -17,7 +17,7 @@ def _fields(cuda):
              small_yinyang(W, n_theta=8, n_phi=20, n_r=150, l_max=7),
              three_patch_grid(),
              W.polar_grid(7, 13, W.linear_edges(6, 0.1, 1.0), 5)]
-    precs = ["bf16x6", "fp64", "bf16x6", "bf16x3"]
+    precs = ["bf16x6", "fp64", "fp16x3", "bf16x3"]
     plans = [Plan(g, p) for g, p in zip(grids, precs)]
     rhos = [torch.from_numpy(W.random_density(g, 20 + i)).cuda() for i, g in enumerate(grids)]
     return plans, rhos

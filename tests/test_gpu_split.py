@@ -1,8 +1,9 @@
-"""GPU parity of the split-precision tensor-core path (BF16 slices on tcgen05)
-against the CPU FP64 oracle, through the C ABI.
+"""GPU parity of the split-precision tensor-core path (BF16 or FP16 slices on
+tcgen05) against the CPU FP64 oracle, through the C ABI.
 
-BF16x6 (three slices, six products) is held to 1e-6 relative error in Phi;
-BF16x3 (two slices, three products) to 5e-4.  The FP32 accumulation of the
+BF16x6 (three slices, six products) and FP16x3 (two power-of-two-scaled FP16
+slices, three products) are held to 1e-6 relative error in Phi; BF16x3 (two
+slices, three products) to 5e-4.  The FP32 accumulation of the
 tensor cores is flushed into float-float sums every 64 k-elements, which keeps
 its bias far below these bounds."""
 import math
@@ -17,7 +18,7 @@ from tests.test_gpu_fp64 import three_patch_grid, hole_grid
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x6": 1e-6, "bf16x3": 5e-4}
+TOL = {"bf16x6": 1e-6, "bf16x3": 5e-4, "fp16x3": 1e-6}
 
 CASES = {
     "yy_small": lambda: small_yinyang(W),
@@ -40,7 +41,7 @@ def case(request, cuda):
     return request.param, grid, rho, phi_ref, B_ref, M_ref
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "bf16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "bf16x3", "fp16x3"])
 def test_phi_matches_oracle(case, precision):
     import torch
     name, grid, rho, phi_ref, B_ref, M_ref = case
@@ -55,14 +56,15 @@ def test_phi_matches_oracle(case, precision):
         assert rel_max(M.cpu().numpy()[:, 0], M_ref[:, 0]) <= TOL[precision]
 
 
-def test_config0_bf16x6(cuda):
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+def test_config0(cuda, precision):
     import torch
     grid, rho = W.config0()
     ref = oracle.solve(grid, rho)
-    with Plan(grid, "bf16x6") as plan:
+    with Plan(grid, precision) as plan:
         phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
         torch.cuda.synchronize()
-        assert rel_max(phi.cpu().numpy(), ref) <= TOL["bf16x6"]
+        assert rel_max(phi.cpu().numpy(), ref) <= TOL[precision]
 
 
 def test_split_deterministic(cuda):
@@ -76,14 +78,32 @@ def test_split_deterministic(cuda):
         assert torch.equal(a, b)
 
 
-def test_large_dynamic_range(cuda):
-    """Density spanning 1e-30 .. 1e30 (the BF16 exponent range covers it)."""
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+def test_large_dynamic_range(cuda, precision):
+    """Density spanning 1e-30 .. 1e30 (BF16's exponent range covers it; FP16
+    rows are scaled by powers of two, and cells far below a row's largest
+    value contribute below the tolerance)."""
     import torch
     grid = small_yinyang(W, n_theta=8, n_phi=24, n_r=20, l_max=6)
     rng = np.random.default_rng(4)
     rho = 10.0 ** rng.uniform(-30, 30, grid.n_cells)
     ref = oracle.solve(grid, rho)
-    with Plan(grid, "bf16x6") as plan:
+    with Plan(grid, precision) as plan:
         phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
         torch.cuda.synchronize()
-        assert rel_max(phi.cpu().numpy(), ref) <= TOL["bf16x6"]
+        assert rel_max(phi.cpu().numpy(), ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("scale", [1e-12, 1e12])
+def test_fp16_scaling_physical_units(cuda, scale):
+    """FP16 slices outside FP16's own range: G = 6.674e-8 (cgs) and densities
+    of order 1e12 or 1e-12 are brought into range by the per-row powers of two."""
+    import torch
+    base = small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9)
+    grid = W.yinyang_grid(13, 37, math.radians(4.0), base.edges, 9, G=6.674e-8)
+    rho = W.random_density(grid, 21) * scale
+    ref = oracle.solve(grid, rho)
+    with Plan(grid, "fp16x3") as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        torch.cuda.synchronize()
+        assert rel_max(phi.cpu().numpy(), ref) <= TOL["fp16x3"]
