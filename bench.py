@@ -28,7 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Φ solves/s & Gcell/s at l_max; split-prec vs FP64 GPU at ≤1e-6 rel err; % roofline"
-WORKLOAD = "yinyang-1deg-92x272x2-Nr400-lmax32-ellipsoid+3blobs"
+
+
+def workload_name(n_r: int) -> str:
+    return f"yinyang-1deg-92x272x2-Nr{n_r}-lmax32-ellipsoid+3blobs"
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), profiling recipe table
 
 
@@ -46,10 +49,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1903_08475_gb300 import dist
+    return dist.env()
 
 
 def load_peaks():
@@ -164,7 +165,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "gcell_per_s": value * grid.n_cells / 1e9,
-            "config": {"workload": WORKLOAD, "n_r": grid.n_r, "l_max": grid.l_max, "cells": grid.n_cells,
+            "config": {"workload": workload_name(grid.n_r), "n_r": grid.n_r, "l_max": grid.l_max, "cells": grid.n_cells,
                        "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": f"{n_shells} of {grid.n_r} shells per step, weights prebuilt, scaled"},
@@ -184,13 +185,14 @@ def main():
 
     from paper_1903_08475_gb300 import (Plan, ygs_launches_per_solve, ygs_read_phase_times, ygs_set_profiling,
                                         ygs_solve, ygs_solve_host, workloads as W)
+    from paper_1903_08475_gb300 import dist as D
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    precision = args.precision or "bf16x6"
+    precision = args.precision or "fp16x3"
     grid, rho = W.config1(n_r=args.n_r)
     plan = Plan(grid, precision, device=local)
     stream = torch.cuda.Stream(device=dev)
@@ -224,10 +226,7 @@ def main():
     ms = e0.elapsed_time(e1)
     phase_ms, ncalls = ygs_read_phase_times(plan)
     ygs_set_profiling(plan, False)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = D.max_over_ranks(ms, dev)  # the job's time is the slowest rank's
     ms_step = ms / args.steps
     value = ws / (ms_step / 1e3)
 
@@ -241,10 +240,7 @@ def main():
     for _ in range(n_e2e):
         ygs_solve_host(plan, h_rho, h_phi, stream=stream)
     e2e_s = (time.perf_counter() - t0) / n_e2e
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = D.max_over_ranks(e2e_s, dev)
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -305,7 +301,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision, "data": "synthetic",
             "gcell_per_s": value * grid.n_cells / 1e9,
-            "config": {"workload": WORKLOAD, "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
+            "config": {"workload": workload_name(grid.n_r), "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
                        "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"],
                        "l2": "inputs larger than L2 (rho 160 MB, weights 436 MB)",
                        "parallelism": f"replicas{ws}"},
