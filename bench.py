@@ -53,6 +53,13 @@ def dist_env():
     return dist.env()
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
+# pass on this workload at Nr = 400) of the current kernels, by precision and
+# phase; absent entries report null.  Source: profiles/tc_gemm_yinyang1deg_fp16x3.md.
+MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119534336 + 101723136,
+                    ("fp16x3", "projection", 400): 196923648 + 3835136}
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -265,8 +272,11 @@ def main():
             achieved = flops_gemm / (per[dom] / 1e3) / 1e12
             peak = float(peaks["bf16_tflops"])
             roof = {"kernel": names[dom], "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"bf16_tflops ({peak_src}, burst)", "phase_ms": dict(zip(names, per))}
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": MEASURED_TRAFFIC.get((precision, names[dom], grid.n_r)),
+                    "peak_source": f"bf16_tflops ({peak_src}, burst)" + (
+                        "; FP16 dense rate = BF16's (nominal ratio 1)" if precision == "fp16x3" else ""),
+                    "phase_ms": dict(zip(names, per))}
         else:
             # bytes of the field pass: rho in (FP64) + slices out
             nsl = 3 if precision == "bf16x6" else 2
