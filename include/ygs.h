@@ -162,9 +162,11 @@ ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const*
 
 /* Adjoint of the linear map rho -> Phi:  grad_rho = A^T grad_phi
  * (transposed synthesis, reversed radial scans, transposed projection).
- * Same layouts, pointer rules and errors as ygs_solve.  It always runs on the
- * plan's FP64 weights (the adjoint of the FP64 operator), whatever the plan's
- * precision. */
+ * Same layouts, pointer rules and errors as ygs_solve.  It runs in the plan's
+ * precision: FP64 plans on the FP64 kernels; split-precision plans on the
+ * tensor cores with slices of Q^T and U made at ygs_create (grad_phi Q, the
+ * transposed scans in FP64, then U), within the same relative bound of the
+ * FP64 adjoint as ygs_solve of the FP64 solve. */
 ygs_status ygs_backward(ygs_plan* plan, const double* d_grad_phi, double* d_grad_rho, void* stream);
 
 /* Copies the moments B and the radial weights M of the most recent solve on

@@ -479,6 +479,11 @@ ygs_status ygs_backward(ygs_plan* p, const double* d_gphi, double* d_grho, void*
   p->last_stream = s;
   cudaEvent_t* ev = prof_slot(p);
   if (ev) API_TRY(cudaEventRecord(ev[0], s));
+  if (p->tc_nsl) {
+    API_TRY(tc_backward(p, d_gphi, d_grho, s, ev));
+    if (ev) API_TRY(cudaEventRecord(ev[4], s));
+    return YGS_OK;
+  }
   if (ev) API_TRY(cudaEventRecord(ev[1], s));
   API_TRY(launch_project_fp64(p, d_gphi, p->Q, p->part, s));
   if (ev) API_TRY(cudaEventRecord(ev[2], s));

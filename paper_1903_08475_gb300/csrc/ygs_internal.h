@@ -96,6 +96,15 @@ struct ygs_plan {
   int* tc_ef = nullptr;       // [2][n_r][S] field row (plane, shell) per split-K chunk, written by every solve
   int* tc_em = nullptr;       // [n_r] M row (shell), written by every solve
   CUtensorMap tc_map_ut, tc_map_f, tc_map_f_tail, tc_map_q, tc_map_m, tc_map_m_tail;
+  // adjoint on the tensor cores: Q^T slices in the projection layout, U slices
+  // in the synthesis layout (monopole column kept), their FP16 exponents, and
+  // FP64 Mbar / Bbar in the padded column order (the field, partial, summary,
+  // carry and M-slice buffers of the forward solve are reused)
+  __nv_bfloat16 *tc_qt = nullptr, *tc_us = nullptr;
+  int* tc_eqt = nullptr;      // [K_pad] Q^T row (column c)
+  int tc_eus = 0;             // U (all rows)
+  double *tc_Mbar = nullptr, *tc_Bbar = nullptr;
+  CUtensorMap tc_map_qt, tc_map_us;
 };
 
 namespace ygs {
@@ -135,6 +144,9 @@ cudaError_t tc_project(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s);
 cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// grad_rho = A^T grad_phi on the tensor cores: slices of grad_phi, projection
+// with Q, transposed scans, synthesis with U.
+cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t debug_wait_timeout(const ygs_plan* p, int spins, cudaStream_t s);
 
 }  // namespace ygs

@@ -84,10 +84,11 @@ __global__ void slice_ut_kernel(int nsl, int K, int K_pad, long long n_pad, cons
   }
 }
 
-// Qs[s][row][pc] from Q[row][ci]; the monopole column (natural column 0) is
-// left zero: the synthesis epilogue adds -G M[i][0] for it.
+// Qs[s][row][pc] from W[row][ci] (Q, or U for the adjoint).  With zero_mono
+// the monopole column (natural column 0) is left zero: the synthesis epilogue
+// adds -G M[i][0] for it.
 __global__ void slice_q_kernel(int nsl, int K, int K_pad, long long rows, const int* __restrict__ pc_int,
-                               const int* __restrict__ pc_nat, const double* __restrict__ Q,
+                               const int* __restrict__ pc_nat, const double* __restrict__ Q, int zero_mono,
                                __nv_bfloat16* __restrict__ Qs) {
   long long total = rows * K_pad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -95,7 +96,7 @@ __global__ void slice_q_kernel(int nsl, int K, int K_pad, long long rows, const 
     int pc = (int)(e % K_pad);
     __nv_bfloat16 s[3] = {__float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f), __float2bfloat16_rn(0.f)};
     int ci = pc_int[pc];
-    if (ci >= 0 && pc_nat[pc] != 0) slices_of(Q[row * K + ci], nsl, s);
+    if (ci >= 0 && (!zero_mono || pc_nat[pc] != 0)) slices_of(Q[row * K + ci], nsl, s);
     for (int k = 0; k < nsl; ++k) Qs[(long long)k * total + e] = s[k];
   }
 }
@@ -244,7 +245,7 @@ __global__ void slice_ut16_kernel(int K, int K_pad, long long n_pad, const int* 
 
 // Largest |Q| over the real columns other than the monopole (bits of a positive double, atomically maxed).
 __global__ void qmax_kernel(int K, int K_pad, long long rows, const int* __restrict__ pc_int,
-                            const int* __restrict__ pc_nat, const double* __restrict__ Q,
+                            const int* __restrict__ pc_nat, const double* __restrict__ Q, int skip_mono,
                             unsigned long long* __restrict__ out) {
   __shared__ double red[32];
   double m = 0.0;
@@ -252,22 +253,23 @@ __global__ void qmax_kernel(int K, int K_pad, long long rows, const int* __restr
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int pc = (int)(e % K_pad);
     const int ci = pc_int[pc];
-    if (ci >= 0 && pc_nat[pc] != 0) m = fmax(m, fabs(Q[(e / K_pad) * K + ci]));
+    if (ci >= 0 && (!skip_mono || pc_nat[pc] != 0)) m = fmax(m, fabs(Q[(e / K_pad) * K + ci]));
   }
   m = block_max(m, red);
   if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// Qs[s][row][pc]: slices of Q * 2^eq; the monopole column stays zero.
+// Qs[s][row][pc]: slices of W * 2^eq (Q, or U for the adjoint); with
+// zero_mono the monopole column stays zero.
 __global__ void slice_q16_kernel(int K, int K_pad, long long rows, const int* __restrict__ pc_int,
-                                 const int* __restrict__ pc_nat, const double* __restrict__ Q, int eq,
+                                 const int* __restrict__ pc_nat, const double* __restrict__ Q, int eq, int zero_mono,
                                  __half* __restrict__ Qs) {
   long long total = rows * K_pad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     long long row = e / K_pad;
     int pc = (int)(e % K_pad);
     int ci = pc_int[pc];
-    double v = (ci >= 0 && pc_nat[pc] != 0) ? ldexp(Q[row * K + ci], eq) : 0.0;
+    double v = (ci >= 0 && (!zero_mono || pc_nat[pc] != 0)) ? ldexp(Q[row * K + ci], eq) : 0.0;
     __half s0, s1;
     half2_slices(v, s0, s1);
     Qs[e] = s0;
@@ -401,10 +403,10 @@ __global__ void __launch_bounds__(256) field_slices16_kernel(int n_r, int symmet
 }
 
 // Ms[s][i][pc]: FP16 slices of M's row i scaled by 2^em[i] (largest |M| over the
-// real columns other than the monopole, whose Q column is zero; it is written
-// as 0).  One CTA per shell; FP64 values enter as float-float pairs.
+// real columns; without keep_mono the monopole, whose Q column is zero, is
+// left out and written as 0).  One CTA per shell; FP64 values enter as float-float pairs.
 __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_nat, const double* __restrict__ M,
-                                 __half* __restrict__ Ms, int* __restrict__ em) {
+                                 int keep_mono, __half* __restrict__ Ms, int* __restrict__ em) {
   __shared__ float red[32];
   const int i = blockIdx.x;
   const long long splane = (long long)n_r * K_pad;
@@ -414,7 +416,7 @@ __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_
   for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {
     const double v = row[pc];
     const int nat = pc_nat[pc];
-    m = fmaxf(m, nat > 0 ? fabsf(tc::f64_trunc_f32(v)) : 0.0f);
+    m = fmaxf(m, nat > (keep_mono ? -1 : 0) ? fabsf(tc::f64_trunc_f32(v)) : 0.0f);
   }
   // the truncated maximum is every float-float head's bound below (same truncation)
   const int e = tc::fp16_row_exp((double)block_max(m, red));
@@ -424,7 +426,7 @@ __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_
     const double v = row[pc];
     const int nat = pc_nat[pc];
     float hi = 0.0f, lo = 0.0f;
-    if (nat > 0) tc::f64_to_ff_fast(v, hi, lo);
+    if (nat > (keep_mono ? -1 : 0)) tc::f64_to_ff_fast(v, hi, lo);
     const float hs = tc::mul_pow2f(hi, e), ls = tc::mul_pow2f(lo, e);
     const __half s0 = __float2half_rn(hs);
     const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
@@ -609,6 +611,116 @@ __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk,
   }
 }
 
+// ---- adjoint scans (transposes of the recurrences above) ----
+// With Mbar the adjoint of M, the transposed recurrences are
+//   X_i = Mbar_i + fin_{i+1} X_{i+1}      (downward; X_{Nr} = 0)
+//   Z_i = Mbar_i + fout_{i-1} Z_{i-1}     (upward; Z_{-1} = 0, fout_{-1} = 0)
+//   Bbar_i = a_i X_i + b_i Z_{i-1},
+// chunked like the forward scans: the summaries [0] Z at the chunk's end and
+// [1] the product of its fout factors (upward), [2] X at its start and [3] the
+// product of its fin factors (downward), all with zero carry, feed the same
+// carry kernel.
+
+// Phase 1: Mbar from the partials (unscaled by 2^-(ef + ew) with FP16 slices)
+// and the chunk summaries.
+__global__ void scan_adj_local_kernel(int n_r, int K_pad, int L, int S, int chunk, const int* __restrict__ pc_l,
+                                      const float2* __restrict__ part, const double* __restrict__ rad,
+                                      double* __restrict__ Mbar, double* __restrict__ summ,
+                                      const int* __restrict__ ef, const int* __restrict__ ew, int k_split) {
+  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (pc >= K_pad) return;
+  const int l = pc_l[pc];
+  const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
+  const int P = gridDim.y;
+  if (l < 0 || i0 >= n_r) {
+    for (int i = i0; i < i1; ++i) Mbar[(long long)i * K_pad + pc] = 0.0;
+    for (int k = 0; k < 4; ++k) summ[((long long)k * P + p) * K_pad + pc] = (k == 1 || k == 3) ? 1.0 : 0.0;
+    return;
+  }
+  const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  double Z = 0.0, FZ = 1.0;
+  for (int i = i0; i < i1; ++i) {
+    float h = 0.f, lo = 0.f;
+    const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
+    for (int z = 0; z < S; ++z) {
+      float2 v = part[z * plane + (long long)i * K_pad + pc];
+      if (efi) {
+        const int es = -(efi[z] + ew[pc]);
+        v.x = tc::mul_pow2f(v.x, es);
+        v.y = tc::mul_pow2f(v.y, es);
+      }
+      float s, e;
+      tc::two_sum(h, v.x, s, e);
+      h = s;
+      lo += e + v.y;
+    }
+    const double m = ff_to_f64(h, lo);
+    Mbar[(long long)i * K_pad + pc] = m;
+    const double hz = (i > 0) ? fout[i - 1] : 0.0;
+    Z = fma(hz, Z, m);
+    FZ *= hz;
+  }
+  double X = 0.0, FX = 1.0;
+  for (int i = i1 - 1; i >= i0; --i) {
+    const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
+    X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
+    FX *= gx;
+  }
+  summ[((long long)0 * P + p) * K_pad + pc] = Z;
+  summ[((long long)1 * P + p) * K_pad + pc] = FZ;
+  summ[((long long)2 * P + p) * K_pad + pc] = X;
+  summ[((long long)3 * P + p) * K_pad + pc] = FX;
+}
+
+// Phase 3: the transposed recurrences with the carries; Bbar in FP64 and, for
+// BF16 operands, its slices (the B operand of the adjoint synthesis).
+__global__ void scan_adj_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk, const int* __restrict__ pc_l,
+                                      const double* __restrict__ Mbar, const double* __restrict__ rad,
+                                      const double* __restrict__ carry, double* __restrict__ Bbar,
+                                      __nv_bfloat16* __restrict__ Bs, int write_slices) {
+  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  const int P = gridDim.y;
+  if (pc >= K_pad) return;
+  const int l = pc_l[pc];
+  const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
+  const long long splane = (long long)n_r * K_pad;
+  if (l < 0) {
+    for (int i = i0; i < i1; ++i) {
+      Bbar[(long long)i * K_pad + pc] = 0.0;
+      if (write_slices)
+        for (int k = 0; k < nsl; ++k) Bs[k * splane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
+    }
+    return;
+  }
+  const long long rs = (long long)(L + 1) * n_r;
+  const double* at = rad + (long long)l * n_r;
+  const double* bt = rad + rs + (long long)l * n_r;
+  const double* fin = rad + 2 * rs + (long long)l * n_r;
+  const double* fout = rad + 3 * rs + (long long)l * n_r;
+  double X = carry[((long long)1 * P + p) * K_pad + pc];  // X_{i1}
+  for (int i = i1 - 1; i >= i0; --i) {
+    const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
+    X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
+    Bbar[(long long)i * K_pad + pc] = at[i] * X;
+  }
+  double Z = carry[((long long)0 * P + p) * K_pad + pc];  // Z_{i0-1}
+  for (int i = i0; i < i1; ++i) {
+    const double b = fma(bt[i], Z, Bbar[(long long)i * K_pad + pc]);
+    Bbar[(long long)i * K_pad + pc] = b;
+    const double hz = (i > 0) ? fout[i - 1] : 0.0;
+    Z = fma(hz, Z, Mbar[(long long)i * K_pad + pc]);
+    if (write_slices) {
+      __nv_bfloat16 sl[3];
+      slices_of(b, nsl, sl);
+      for (int k = 0; k < nsl; ++k) Bs[k * splane + (long long)i * K_pad + pc] = sl[k];
+    }
+  }
+}
+
 // out[i][nat] = in[i][pc] for every real padded column.
 __global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __restrict__ pc_nat,
                                     const double* __restrict__ in, double* __restrict__ out) {
@@ -711,6 +823,10 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   }
   TC_ALLOC(p->tc_ut, bytes_ut);
   TC_ALLOC(p->tc_qs, bytes_q);
+  TC_ALLOC(p->tc_qt, bytes_ut);
+  TC_ALLOC(p->tc_us, bytes_q);
+  TC_ALLOC(p->tc_Mbar, bytes_nk);
+  TC_ALLOC(p->tc_Bbar, bytes_nk);
   TC_ALLOC(p->tc_f, bytes_f);
   TC_ALLOC(p->tc_ms, bytes_m);
   TC_ALLOC(p->tc_part, bytes_part);
@@ -726,13 +842,14 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_ALLOC(p->tc_mono, (size_t)p->n_r * sizeof(float2));
   TC_ALLOC(p->tc_cp, (size_t)2 * (p->l_max + 1) * p->tc_scan_P * sizeof(double));
   if (p->tc_fp16) {
+    TC_ALLOC(p->tc_eqt, kp * sizeof(int));
     TC_ALLOC(p->tc_eu, kp * sizeof(int));
     TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * p->tc_S * sizeof(int));
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
   }
 #undef TC_ALLOC
-  p->weight_bytes += (long long)(bytes_ut + bytes_q);
-  p->work_bytes += (long long)(bytes_f + bytes_m + bytes_part + 2 * bytes_nk + bytes_sum * 3 / 2);
+  p->weight_bytes += (long long)(2 * (bytes_ut + bytes_q));
+  p->work_bytes += (long long)(bytes_f + bytes_m + bytes_part + 4 * bytes_nk + bytes_sum * 3 / 2);
 #define TC_TRY(x)                                                                  \
   if ((e = (x)) != cudaSuccess) {                                                  \
     set_error(std::string("tc setup: ") + #x + ": " + cudaGetErrorString(e));       \
@@ -757,21 +874,42 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     // Q as a whole: its largest magnitude (through a scratch word in the M buffer) sets eq
     unsigned long long* qm = reinterpret_cast<unsigned long long*>(p->tc_M);
     TC_TRY(cudaMemset(qm, 0, sizeof(unsigned long long)));
-    qmax_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, qm);
+    qmax_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, 1, qm);
     TC_TRY(cudaGetLastError());
     unsigned long long bits = 0;
     TC_TRY(cudaMemcpy(&bits, qm, sizeof(bits), cudaMemcpyDeviceToHost));
     double qmax;
     memcpy(&qmax, &bits, sizeof(qmax));
     p->tc_eq = tc::fp16_row_exp(qmax);
-    slice_q16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_eq,
+    slice_q16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_eq, 1,
                                     reinterpret_cast<__half*>(p->tc_qs));
+    TC_TRY(cudaGetLastError());
+    // adjoint operands: Q^T per column, U as a whole (monopole kept)
+    colexp_u_kernel<<<p->tc_k_pad, 256>>>(K, p->tc_pc_int, p->nang_wtotal, p->Q, p->tc_eqt);
+    TC_TRY(cudaGetLastError());
+    slice_ut16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->Q, p->pt, p->n_wpatch,
+                                     p->tc_pad_off_d, p->tc_eqt, reinterpret_cast<__half*>(p->tc_qt));
+    TC_TRY(cudaGetLastError());
+    TC_TRY(cudaMemset(qm, 0, sizeof(unsigned long long)));
+    qmax_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, 0, qm);
+    TC_TRY(cudaGetLastError());
+    TC_TRY(cudaMemcpy(&bits, qm, sizeof(bits), cudaMemcpyDeviceToHost));
+    memcpy(&qmax, &bits, sizeof(qmax));
+    p->tc_eus = tc::fp16_row_exp(qmax);
+    slice_q16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, p->tc_eus, 0,
+                                    reinterpret_cast<__half*>(p->tc_us));
     TC_TRY(cudaGetLastError());
   } else {
     slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
                                    p->tc_pad_off_d, p->tc_ut);
     TC_TRY(cudaGetLastError());
-    slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, p->tc_qs);
+    slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, 1, p->tc_qs);
+    TC_TRY(cudaGetLastError());
+    // adjoint operands: Q^T in the projection layout, U in the synthesis layout (monopole kept)
+    slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->Q, p->pt, p->n_wpatch,
+                                   p->tc_pad_off_d, p->tc_qt);
+    TC_TRY(cudaGetLastError());
+    slice_q_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, 0, p->tc_us);
     TC_TRY(cudaGetLastError());
   }
   TC_TRY(cudaDeviceSynchronize());
@@ -785,6 +923,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
       !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, NP, h16) ||
       !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Npt, h16) ||
       !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, h16) ||
+      !make_map(&p->tc_map_qt, p->tc_qt, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM, h16) ||
+      !make_map(&p->tc_map_us, p->tc_us, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, h16) ||
       !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N, h16) ||
       !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt, h16)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
@@ -809,7 +949,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
 void tc_free(ygs_plan* p) {
   void* bufs[] = {p->tc_ut,    p->tc_qs,     p->tc_f,      p->tc_ms,     p->tc_part,      p->tc_B,
                   p->tc_M,     p->tc_summ,   p->tc_carry,  p->tc_chunks, p->tc_pc_int,    p->tc_pc_l,
-                  p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_eu, p->tc_ef, p->tc_em};
+                  p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_eu, p->tc_ef, p->tc_em,
+                  p->tc_qt,    p->tc_us,     p->tc_eqt,    p->tc_Mbar,   p->tc_Bbar};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -842,7 +983,7 @@ static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.n_tiles = n_full + (n_tail > 0 ? 1 : 0);
 }
 
-cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) {
+static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cudaStream_t s) {
   TcArgs a{};
   fill_tiles(p, a, p->tc_np_full, p->tc_np_tail);
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
@@ -856,8 +997,10 @@ cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) {
   a.ldp = p->tc_k_pad;
   a.total_tiles = a.tiles_m * a.n_chunks * a.n_tiles;
   const int grid = std::min(a.total_tiles, p->tc_sms);
-  return dispatch_gemm<tc::kProject>(p->tc_nsl, grid, p->tc_map_ut, p->tc_map_f, p->tc_map_f_tail, a, s);
+  return dispatch_gemm<tc::kProject>(p->tc_nsl, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
 }
+
+cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) { return project_with(p, p->tc_map_ut, s); }
 
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   const int P = p->tc_scan_P;
@@ -873,12 +1016,13 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
                                        p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms, p->G, p->tc_mono,
                                        p->tc_fp16 ? 0 : 1);
   if ((e = cudaGetLastError()) != cudaSuccess || !p->tc_fp16) return e;
-  slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M,
+  slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M, 0,
                                           reinterpret_cast<__half*>(p->tc_ms), p->tc_em);
   return cudaGetLastError();
 }
 
-cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
+static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, double* phi, const float2* mono,
+                                   int q_exp, cudaStream_t s) {
   TcArgs a{};
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
@@ -897,11 +1041,47 @@ cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
   a.tile0[p->n_wpatch] = t;
   a.total_tiles = t;
   a.phi = phi;
-  a.mono = p->tc_mono;
+  a.mono = mono;
   a.m_exp = p->tc_fp16 ? p->tc_em : nullptr;
-  a.q_exp = p->tc_eq;
+  a.q_exp = q_exp;
   const int grid = std::min(a.total_tiles, p->tc_sms);
-  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, p->tc_map_q, p->tc_map_m, p->tc_map_m_tail, a, s);
+  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
+}
+
+cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
+  return synthesize_with(p, p->tc_map_q, phi, p->tc_mono, p->tc_eq, s);
+}
+
+// The adjoint: grad_phi's slices (sigma+- of the Yin/Yang rows, as the
+// forward field: Q_Yang = (-1)^m Q_Yin), Mbar = grad_phi Q on the tensor
+// cores, Bbar by the transposed scans, grad_rho = Bbar U^T with E +- O.  The
+// monopole needs no special case here (its U column is an ordinary one).
+// ev (optional) receives the phase events 1..4 after each phase.
+cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cudaStream_t s, cudaEvent_t* ev) {
+  cudaError_t e;
+  if ((e = tc_field_slices(p, gphi, s)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+  if ((e = project_with(p, p->tc_map_qt, s)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+  const int P = p->tc_scan_P;
+  dim3 g1((p->tc_k_pad + 127) / 128, P);
+  scan_adj_local_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_pc_l,
+                                           p->tc_part, p->rad, p->tc_Mbar, p->tc_summ, p->tc_ef, p->tc_eqt,
+                                           p->symmetric ? p->tc_k_even : p->tc_k_pad);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  scan_carry_kernel<<<(p->tc_k_pad * 2 + 3) / 4, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  scan_adj_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
+                                           p->tc_Mbar, p->rad, p->tc_carry, p->tc_Bbar, p->tc_ms,
+                                           p->tc_fp16 ? 0 : 1);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (p->tc_fp16) {
+    slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_Bbar, 1,
+                                            reinterpret_cast<__half*>(p->tc_ms), p->tc_em);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+  return synthesize_with(p, p->tc_map_us, grho, nullptr, p->tc_eus, s);
 }
 
 namespace {

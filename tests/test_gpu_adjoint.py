@@ -12,7 +12,7 @@ from tests._util import rel_norm, small_yinyang
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("bf16x6", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("bf16x6", 1e-6), ("fp16x3", 1e-6)])
 def test_central_differences_on_64_cells(cuda, precision, tol):
     """J(rho) = sum w Phi(rho) is linear: (J(rho + h e_k) - J(rho - h e_k)) / 2h
     equals (A^T w)_k.  Phi is differenced elementwise before the dot product,
@@ -24,6 +24,9 @@ def test_central_differences_on_64_cells(cuda, precision, tol):
     cells = np.random.default_rng(7).choice(grid.n_cells, 64, replace=False)
     with Plan(grid, precision) as plan, Plan(grid, "fp64") as p64:
         g = ygs_backward(p64, w).cpu().numpy()
+        # the plan's own adjoint (tensor cores for split precisions) against the FP64 one
+        gs = ygs_backward(plan, w).cpu().numpy()
+        assert np.max(np.abs(gs - g)) <= tol * np.max(np.abs(g)), precision
         base = torch.from_numpy(rho).cuda()
         h = 1e8
         for k in cells:
@@ -48,15 +51,25 @@ def test_autograd_matches_backward(cuda):
         assert torch.equal(rho.grad, ref)
 
 
-def test_adjoint_full_size_vs_oracle_transpose(cuda):
-    import torch
+@pytest.fixture(scope="module")
+def config4_transpose():
     grid, rho, w = W.config4()
     U = oracle.build_U(grid)
     Q = oracle.build_Q(grid)
-    ref = oracle.apply_T(grid, w, U=U, Q=Q)
-    with Plan(grid, "fp64") as plan:
+    return grid, rho, w, oracle.apply_T(grid, w, U=U, Q=Q)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6)])
+def test_adjoint_full_size_vs_oracle_transpose(cuda, config4_transpose, precision, tol):
+    """Yin-Yang 1 degree, Nr = 256, l_max = 32, w ~ N(0, 1): the plan's adjoint
+    (FP64 kernels, or the tensor cores for split precisions) against the
+    oracle's transposed loops."""
+    import torch
+    grid, rho, w, ref = config4_transpose
+    with Plan(grid, precision) as plan:
         got = ygs_backward(plan, torch.from_numpy(w).cuda()).cpu().numpy()
         phi = ygs_solve(plan, torch.from_numpy(rho).cuda()).cpu().numpy()
-    assert rel_norm(got, ref) <= 1e-12
+    assert rel_norm(got, ref) <= tol
+    assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref))
     # dot-product identity <w, A rho> = <A^T w, rho>
-    assert abs(w @ phi - got @ rho) <= 1e-12 * (np.abs(w) @ np.abs(phi))
+    assert abs(w @ phi - got @ rho) <= tol * (np.abs(w) @ np.abs(phi))
