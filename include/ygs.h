@@ -160,6 +160,28 @@ ygs_status ygs_solve_host(ygs_plan* plan, const double* h_rho, double* h_phi, vo
 ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const* d_rho,
                              double* const* d_phi, void* stream);
 
+/* A fixed set of plans whose solves run together (the paper solves one field;
+ * batching many independent fields of uneven sizes is this library's).
+ * ygs_batch_create prepares, once, device descriptors of every split-precision
+ * plan's contractions; plans are grouped by slice count (BF16x6 apart from the
+ * two-slice precisions) and each group's projection and synthesis tiles then run
+ * in ONE persistent launch each per ygs_batch_solve, instead of one launch per
+ * field.  FP64 plans of the batch run their ordinary solves.  All plans must
+ * live on one device and appear once; they must outlive the batch.  At most
+ * 128 split plans per slice count, 1024 plans in all.  Errors: INVALID_ARG,
+ * OOM, CUDA, UNSUPPORTED. */
+typedef struct ygs_batch ygs_batch;
+ygs_status ygs_batch_create(int n, ygs_plan* const* plans, ygs_batch** out);
+/* Solves every field of the batch on `stream`: d_rho[k] -> d_phi[k] for plan k
+ * (HOST arrays of device pointers, layouts and pointer rules of ygs_solve).
+ * Enqueues work only: no allocation and no synchronisation, so a whole batch
+ * can be captured into one CUDA graph.  Results equal ygs_solve's bitwise. */
+ygs_status ygs_batch_solve(ygs_batch* batch, const double* const* d_rho, double* const* d_phi, void* stream);
+/* Frees the descriptors (waits for the device).  NULL is accepted. */
+ygs_status ygs_batch_destroy(ygs_batch* batch);
+/* Kernel launches one ygs_batch_solve enqueues. */
+int ygs_batch_launches(const ygs_batch* batch);
+
 /* Adjoint of the linear map rho -> Phi:  grad_rho = A^T grad_phi
  * (transposed synthesis, reversed radial scans, transposed projection).
  * Same layouts, pointer rules and errors as ygs_solve.  It runs in the plan's

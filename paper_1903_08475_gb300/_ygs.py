@@ -27,7 +27,8 @@ FLAG_NO_SYMMETRY = 1
 EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_batched",
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
            "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
-           "ygs_debug_wait_timeout", "ygs_solve_static")
+           "ygs_debug_wait_timeout", "ygs_solve_static", "ygs_batch_create", "ygs_batch_solve",
+           "ygs_batch_destroy", "ygs_batch_launches")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -90,6 +91,10 @@ def load_library(path: Optional[str] = None):
         L.ygs_launches_per_solve.argtypes = [vp]
         L.ygs_debug_wait_timeout.argtypes = [vp, ctypes.c_int, vp]
         L.ygs_solve_static.argtypes = [vp, vp, vp, vp]
+        L.ygs_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.ygs_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        L.ygs_batch_destroy.argtypes = [vp]
+        L.ygs_batch_launches.argtypes = [vp]
         for f in EXPORTS:
             if f not in ("ygs_status_string", "ygs_last_error"):
                 getattr(L, f).restype = ctypes.c_int
@@ -181,6 +186,51 @@ def ygs_solve(plan: Plan, rho, phi=None, stream=None):
     phi = _field_out(plan, rho) if phi is None else phi
     _check(load_library().ygs_solve(plan.handle, _ptr(rho), _ptr(phi), _stream_handle(stream)))
     return phi
+
+
+class Batch:
+    """A fixed set of plans solved together: each group's contractions in one
+    persistent launch (ygs_batch_create / ygs_batch_solve)."""
+
+    def __init__(self, plans: Sequence[Plan]):
+        L = load_library()
+        n = len(plans)
+        hp = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+        h = ctypes.c_void_p()
+        _check(L.ygs_batch_create(n, hp, ctypes.byref(h)))
+        self._h = h
+        self.plans = list(plans)
+
+    def solve(self, rhos, phis=None, stream=None):
+        """phis[k] = A_k rhos[k] for every plan of the batch."""
+        n = len(self.plans)
+        if phis is None:
+            phis = [_field_out(p, r) for p, r in zip(self.plans, rhos)]
+        rp = (ctypes.c_void_p * n)(*[_ptr(r) for r in rhos])
+        pp = (ctypes.c_void_p * n)(*[_ptr(x) for x in phis])
+        _check(load_library().ygs_batch_solve(self._h, rp, pp, _stream_handle(stream)))
+        return phis
+
+    @property
+    def launches(self) -> int:
+        return int(load_library().ygs_batch_launches(self._h))
+
+    def close(self):
+        if self._h:
+            load_library().ygs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def ygs_solve_static(plan: Plan, rho, phi=None, stream=None):

@@ -470,6 +470,97 @@ ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const*
   return YGS_OK;
 }
 
+struct ygs_batch {
+  int device = 0;
+  std::vector<ygs_plan*> plans;
+  std::vector<int> split, fp64;  // indices into plans
+  TcBatch tc;
+};
+
+ygs_status ygs_batch_create(int n, ygs_plan* const* plans, ygs_batch** out) {
+  if (!out) return fail(YGS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > 1024 || !plans) return fail(YGS_ERR_INVALID_ARG, "a batch holds 1 to 1024 plans");
+  std::map<const ygs_plan*, int> seen;
+  for (int k = 0; k < n; ++k) {
+    if (!plans[k]) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
+    if (plans[k]->device != plans[0]->device) return fail(YGS_ERR_INVALID_ARG, "all plans of a batch must share one device");
+    if (seen.count(plans[k])) return fail(YGS_ERR_INVALID_ARG, "a plan may appear once in a batch (its workspaces serve one field)");
+    seen[plans[k]] = k;
+  }
+  ygs_batch* b = new (std::nothrow) ygs_batch;
+  if (!b) return fail(YGS_ERR_OOM, "host allocation failed");
+  b->device = plans[0]->device;
+  b->plans.assign(plans, plans + n);
+  std::vector<ygs_plan*> sp;
+  for (int k = 0; k < n; ++k) {
+    if (plans[k]->tc_nsl) {
+      b->split.push_back(k);
+      sp.push_back(plans[k]);
+    } else {
+      b->fp64.push_back(k);
+    }
+  }
+  DeviceGuard guard(b->device);
+  if (!guard.ok) {
+    delete b;
+    return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  }
+  ygs_status st = tc_batch_build(&b->tc, sp);
+  if (st != YGS_OK) {
+    tc_batch_free(&b->tc);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return YGS_OK;
+}
+
+ygs_status ygs_batch_destroy(ygs_batch* b) {
+  if (!b) return YGS_OK;
+  DeviceGuard guard(b->device);
+  cudaDeviceSynchronize();
+  tc_batch_free(&b->tc);
+  delete b;
+  return YGS_OK;
+}
+
+ygs_status ygs_batch_solve(ygs_batch* b, const double* const* d_rho, double* const* d_phi, void* stream) {
+  if (!b || !d_rho || !d_phi) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  const int n = (int)b->plans.size();
+  for (int k = 0; k < n; ++k) {
+    ygs_status st = check_field(b->plans[k], d_rho[k], d_phi[k]);
+    if (st != YGS_OK) return st;
+  }
+  DeviceGuard guard(b->device);
+  if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int k : b->split) API_TRY(tc_field_slices(b->plans[k], d_rho[k], s));
+  for (const TcBatchGroup& G : b->tc.groups) API_TRY(tc_batch_project(G, s));
+  for (int k : b->split) API_TRY(tc_scan(b->plans[k], s));
+  for (const TcBatchGroup& G : b->tc.groups) {
+    std::vector<double*> phi;
+    for (const ygs_plan* m : G.members)
+      for (int k : b->split)
+        if (b->plans[k] == m) phi.push_back(d_phi[k]);
+    API_TRY(tc_batch_synthesize(G, phi.data(), s));
+  }
+  for (int k : b->fp64) {
+    ygs_status st = ygs_solve(b->plans[k], d_rho[k], d_phi[k], stream);
+    if (st != YGS_OK) return st;
+  }
+  for (ygs_plan* p : b->plans) p->last_stream = s;
+  return YGS_OK;
+}
+
+int ygs_batch_launches(const ygs_batch* b) {
+  if (!b) return 0;
+  int n = 0;
+  for (int k : b->split) n += b->plans[k]->tc_fp16 ? 5 : 4;
+  n += 2 * (int)b->tc.groups.size() + 3 * (int)b->fp64.size();
+  return n;
+}
+
 ygs_status ygs_backward(ygs_plan* p, const double* d_gphi, double* d_grho, void* stream) {
   ygs_status st = check_field(p, d_gphi, d_grho);
   if (st != YGS_OK) return st;

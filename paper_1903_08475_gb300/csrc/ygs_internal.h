@@ -144,6 +144,27 @@ cudaError_t tc_project(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s);
 cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// Batches: the split-precision plans of a batch grouped by slice count; each
+// group's projection and synthesis tiles run in one persistent launch, with
+// the problems' tensor maps and arguments in device memory.
+namespace tc {
+struct TcProblem;
+}
+struct TcBatchGroup {
+  int nsl = 0, flush = 1, sms = 0, total_p = 0, total_s = 0;
+  std::vector<ygs_plan*> members;
+  tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
+  int *d_start_p = nullptr, *d_start_s = nullptr;
+};
+struct TcBatch {
+  std::vector<TcBatchGroup> groups;
+};
+ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans);
+void tc_batch_free(TcBatch* b);
+cudaError_t tc_batch_project(const TcBatchGroup& g, cudaStream_t s);
+// phi[k]: output of the group's k-th member
+cudaError_t tc_batch_synthesize(const TcBatchGroup& g, double* const* phi, cudaStream_t s);
+
 // grad_rho = A^T grad_phi on the tensor cores: slices of grad_phi, projection
 // with Q, transposed scans, synthesis with U.
 cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cudaStream_t s, cudaEvent_t* ev);

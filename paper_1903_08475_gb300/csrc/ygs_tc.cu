@@ -735,7 +735,10 @@ __global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __rest
 
 template <int NSL, int MODE>
 cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       TcCfg<NSL, MODE>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               TcCfg<NSL, MODE>::SMEM);
 }
 
@@ -747,6 +750,20 @@ cudaError_t dispatch_gemm(int nsl, int grid, const CUtensorMap& a, const CUtenso
     tc::tc_gemm_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(a, b, bt, args);
   } else if (nsl == 2) {
     tc::tc_gemm_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t dispatch_group(int nsl, int grid, const tc::TcProblem* probs, const int* start, int n, int total,
+                          int flush, const tc::TcPhiList& phis, cudaStream_t s) {
+  constexpr int threads = tc::TileShape<MODE>::THREADS;
+  if (nsl == 3) {
+    tc::tc_gemm_group_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(probs, start, n, total, flush, phis);
+  } else if (nsl == 2) {
+    tc::tc_gemm_group_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, flush, phis);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -983,8 +1000,8 @@ static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.n_tiles = n_full + (n_tail > 0 ? 1 : 0);
 }
 
-static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cudaStream_t s) {
-  TcArgs a{};
+static void project_args(const ygs_plan* p, TcArgs& a) {
+  a = TcArgs{};
   fill_tiles(p, a, p->tc_np_full, p->tc_np_tail);
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
@@ -996,6 +1013,11 @@ static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cuda
   a.part = p->tc_part;
   a.ldp = p->tc_k_pad;
   a.total_tiles = a.tiles_m * a.n_chunks * a.n_tiles;
+}
+
+static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cudaStream_t s) {
+  TcArgs a;
+  project_args(p, a);
   const int grid = std::min(a.total_tiles, p->tc_sms);
   return dispatch_gemm<tc::kProject>(p->tc_nsl, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
 }
@@ -1021,9 +1043,8 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, double* phi, const float2* mono,
-                                   int q_exp, cudaStream_t s) {
-  TcArgs a{};
+static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono, int q_exp) {
+  a = TcArgs{};
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
@@ -1044,6 +1065,12 @@ static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, d
   a.mono = mono;
   a.m_exp = p->tc_fp16 ? p->tc_em : nullptr;
   a.q_exp = q_exp;
+}
+
+static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, double* phi, const float2* mono,
+                                   int q_exp, cudaStream_t s) {
+  TcArgs a;
+  synth_args(p, a, phi, mono, q_exp);
   const int grid = std::min(a.total_tiles, p->tc_sms);
   return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
 }
@@ -1082,6 +1109,84 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   }
   if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
   return synthesize_with(p, p->tc_map_us, grho, nullptr, p->tc_eus, s);
+}
+
+// ---- batches: the contractions of many plans in one persistent launch each ----
+
+ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
+  b->groups.clear();
+  for (int nsl = 2; nsl <= 3; ++nsl) {
+    std::vector<ygs_plan*> mem;
+    for (ygs_plan* p : plans)
+      if (p->tc_nsl == nsl) mem.push_back(p);
+    if (mem.empty()) continue;
+    if ((int)mem.size() > tc::kMaxGroup) {
+      set_error("a batch holds at most 128 split-precision plans of one slice count");
+      return YGS_ERR_UNSUPPORTED;
+    }
+    TcBatchGroup G;
+    G.nsl = nsl;
+    G.members = mem;
+    std::vector<tc::TcProblem> proj(mem.size()), syn(mem.size());
+    std::vector<int> sp(mem.size() + 1, 0), ss(mem.size() + 1, 0);
+    for (size_t k = 0; k < mem.size(); ++k) {
+      const ygs_plan* p = mem[k];
+      proj[k].a = p->tc_map_ut;
+      proj[k].b = p->tc_map_f;
+      proj[k].bt = p->tc_map_f_tail;
+      project_args(p, proj[k].args);
+      syn[k].a = p->tc_map_q;
+      syn[k].b = p->tc_map_m;
+      syn[k].bt = p->tc_map_m_tail;
+      synth_args(p, syn[k].args, nullptr, p->tc_mono, p->tc_eq);  // outputs come per call
+      sp[k + 1] = sp[k] + proj[k].args.total_tiles;
+      ss[k + 1] = ss[k] + syn[k].args.total_tiles;
+      G.flush = proj[k].args.flush_kb;
+    }
+    G.total_p = sp.back();
+    G.total_s = ss.back();
+    G.sms = mem[0]->tc_sms;
+    const size_t pb = mem.size() * sizeof(tc::TcProblem), sb = (mem.size() + 1) * sizeof(int);
+    cudaError_t e;
+    if ((e = dev_malloc((void**)&G.d_proj, pb)) != cudaSuccess || (e = dev_malloc((void**)&G.d_synth, pb)) != cudaSuccess ||
+        (e = dev_malloc((void**)&G.d_start_p, sb)) != cudaSuccess ||
+        (e = dev_malloc((void**)&G.d_start_s, sb)) != cudaSuccess) {
+      b->groups.push_back(G);
+      set_error(std::string("batch descriptors: ") + cudaGetErrorString(e));
+      return YGS_ERR_OOM;
+    }
+    b->groups.push_back(G);
+    if ((e = cudaMemcpy(G.d_proj, proj.data(), pb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(G.d_synth, syn.data(), pb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(G.d_start_p, sp.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(G.d_start_s, ss.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      set_error(std::string("batch descriptors: ") + cudaGetErrorString(e));
+      return YGS_ERR_CUDA;
+    }
+  }
+  return YGS_OK;
+}
+
+void tc_batch_free(TcBatch* b) {
+  for (TcBatchGroup& G : b->groups) {
+    void* bufs[] = {G.d_proj, G.d_synth, G.d_start_p, G.d_start_s};
+    for (void* q : bufs)
+      if (q) cudaFree(q);
+  }
+  b->groups.clear();
+}
+
+cudaError_t tc_batch_project(const TcBatchGroup& G, cudaStream_t s) {
+  tc::TcPhiList none{};
+  return dispatch_group<tc::kProject>(G.nsl, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
+                                      (int)G.members.size(), G.total_p, G.flush, none, s);
+}
+
+cudaError_t tc_batch_synthesize(const TcBatchGroup& G, double* const* phi, cudaStream_t s) {
+  tc::TcPhiList out{};
+  for (size_t k = 0; k < G.members.size(); ++k) out.p[k] = phi[k];
+  return dispatch_group<tc::kSynthesize>(G.nsl, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
+                                         (int)G.members.size(), G.total_s, G.flush, out, s);
 }
 
 namespace {

@@ -192,10 +192,52 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
   return T;
 }
 
-template <int NSL, int MODE>
-__global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const __grid_constant__ CUtensorMap mapBt, TcArgs args) {
+// One problem of a grouped launch: its tensor maps and arguments (in global
+// memory, written by the host before the launch; aligned like CUtensorMap).
+struct alignas(128) TcProblem {
+  CUtensorMap a, b, bt;
+  TcArgs args;
+};
+constexpr int kMaxGroup = 128;          // problems per grouped launch
+struct TcPhiList {                      // synthesis outputs of a grouped launch
+  double* p[kMaxGroup];
+};
+
+// What a role needs for one tile: the problem's arguments and maps, its
+// output and the tile's index within the problem.
+struct TileRef {
+  const TcArgs* A;
+  const CUtensorMap *ma, *mb, *mbt;
+  double* phi;
+  int t;
+};
+
+struct SingleSrc {  // one problem, everything in kernel parameters
+  const TcArgs* A;
+  const CUtensorMap *ma, *mb, *mbt;
+  __device__ __forceinline__ int total() const { return A->total_tiles; }
+  __device__ __forceinline__ TileRef locate(int t) const { return TileRef{A, ma, mb, mbt, A->phi, t}; }
+};
+
+struct GroupSrc {  // tiles of several problems concatenated: problem k owns [start[k], start[k+1])
+  const TcProblem* probs;
+  const int* start;
+  int n, tot;
+  const TcPhiList* phis;
+  __device__ __forceinline__ int total() const { return tot; }
+  __device__ __forceinline__ TileRef locate(int t) const {
+    int lo = 0, hi = n - 1;  // last problem with start <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (start[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const TcProblem& P = probs[lo];
+    return TileRef{&P.args, &P.a, &P.b, &P.bt, phis->p[lo], t - start[lo]};
+  }
+};
+
+template <int NSL, int MODE, class Src>
+__device__ __forceinline__ void gemm_body(const Src& src, const int flush) {
   using C = TcCfg<NSL, MODE>;
   constexpr int NMAX = TileShape<MODE>::NMAX;
   constexpr int NH = TileShape<MODE>::NH;
@@ -211,7 +253,6 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int flush = args.flush_kb;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -225,9 +266,6 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_mbar_init();
-    prefetch_tmap(&mapA);
-    prefetch_tmap(&mapB);
-    prefetch_tmap(&mapBt);
   }
   if (warp == 0) {
     tmem_alloc(tmem_slot, 512);
@@ -243,9 +281,12 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
-        const Tile T = decode_tile<MODE>(args, t);
-        const CUtensorMap* mb = T.use_tail ? &mapBt : &mapB;
+      int* err = nullptr;
+      for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
+        const TileRef R = src.locate(t);
+        const Tile T = decode_tile<MODE>(*R.A, R.t);
+        err = R.A->err;
+        const CUtensorMap* mb = T.use_tail ? R.mbt : R.mb;
         const uint32_t bytes = NSL * (C::A_SLICE + T.n_eff * BK * 2);
         const int nkb = T.seg_kb0 + T.seg_kb1;
         for (int kb = 0; kb < nkb; ++kb) {
@@ -260,14 +301,14 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
           mbar_arrive_expect_tx(&full[stage], bytes);
           const int kx = T.kstart + kb * BK;
 #pragma unroll
-          for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, &mapA, &full[stage], kx, T.a_row0, s);
+          for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, R.ma, &full[stage], kx, T.a_row0, s);
 #pragma unroll
           for (int s = 0; s < NSL; ++s) tma_load_3d(sB + s * C::B_SLICE, mb, &full[stage], kx, T.b_row0, T.b_plane0 + s);
           ++issued;
         }
       }
       if (!ok) {
-        set_err(args.err, YGS_ERR_TIMEOUT);
+        set_err(err, YGS_ERR_TIMEOUT);
         *abort_flag = 1;
       }
       // every issued copy has landed before shared memory can be released
@@ -279,9 +320,12 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     if (lane == 0) {
       int consumed = 0, gglob = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
-        const Tile T = decode_tile<MODE>(args, t);
-        const uint32_t idesc = idesc_f16(BM, T.n_eff, args.ab_fmt);
+      int* err = nullptr;
+      for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
+        const TileRef R = src.locate(t);
+        const Tile T = decode_tile<MODE>(*R.A, R.t);
+        err = R.A->err;
+        const uint32_t idesc = idesc_f16(BM, T.n_eff, R.A->ab_fmt);
         for (int seg = 0; seg < 2 && ok; ++seg) {
           const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
@@ -330,7 +374,7 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
         }
       }
       if (!ok) {
-        set_err(args.err, YGS_ERR_TIMEOUT);
+        set_err(err, YGS_ERR_TIMEOUT);
         *abort_flag = 1;
       }
       umma_commit(mma_done);
@@ -346,8 +390,11 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     const int col0 = colq * NH;
     int gglob = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < args.total_tiles && ok; t += gridDim.x) {
-      const Tile T = decode_tile<MODE>(args, t);
+    int* err = nullptr;
+    for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
+      const TileRef R = src.locate(t);
+      const Tile T = decode_tile<MODE>(*R.A, R.t);
+      err = R.A->err;
       const bool active = col0 < T.n_eff;  // this warp's columns exist in the tile (warp-uniform)
       // float-float sums of column pairs (2j, 2j+1), packed for the f32x2 pipes
       uint64_t H[NH / 2], L[NH / 2];
@@ -409,6 +456,15 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
         }
       }
       if (!ok || !active) continue;
+      // this tile's output arguments in registers (the stores below cannot alias them)
+      const int n_b = R.A->n_b, ldp = R.A->ldp, q_exp = R.A->q_exp, symmetric = R.A->symmetric;
+      float2* const part = R.A->part;
+      const int* const m_exp = R.A->m_exp;
+      const float2* const mono = R.A->mono;
+      double* const phi = R.phi;
+      const long long nang = MODE == kSynthesize ? R.A->pt.nang[T.g_patch] : 0;
+      const long long off0 = MODE == kSynthesize ? R.A->pt.fld_off[symmetric ? 0 : T.g_patch] : 0;
+      const long long off1 = MODE == kSynthesize && symmetric ? R.A->pt.fld_off[1] : 0;
       // output, 8 columns at a time (keeps the register footprint of the sums)
 #pragma unroll
       for (int c0 = 0; c0 < NH; c0 += 8) {
@@ -430,28 +486,27 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
           upk2(L[j / 2], l0, l1);
           const float hj = (j & 1) ? h1 : h0, lj = (j & 1) ? l1 : l0;
           const int n = T.b_row0 + col0 + j;
-          if (n >= args.n_b) continue;
+          if (n >= n_b) continue;
           if (MODE == kProject) {
             if (T.a_row0 + r < T.a_rows_end) {
               float s, e;
               two_sum(hj, lj, s, e);
-              args.part[((long long)T.z * args.n_b + n) * args.ldp + T.a_row0 + r] = make_float2(s, e);
+              part[((long long)T.z * n_b + n) * ldp + T.a_row0 + r] = make_float2(s, e);
             }
           } else {
-            const long long nang = args.pt.nang[T.g_patch];
             const long long a_loc = (long long)T.m_loc * BM + r;
             if (a_loc >= nang) continue;
             float hs = hj, ls = lj, e0 = ev[jj];
-            if (args.m_exp) {  // exact unscaling of FP16-slice results
-              const int es = -(args.q_exp + args.m_exp[n]);
+            if (m_exp) {  // exact unscaling of FP16-slice results
+              const int es = -(q_exp + m_exp[n]);
               hs = mul_pow2f(hs, es);
               ls = mul_pow2f(ls, es);
               e0 = mul_pow2f(e0, es);
             }
             float v = hs + ls;
-            if (args.mono) {
+            if (mono) {
               // the monopole belongs to the even block (E) or, without the symmetry, to the only block
-              const float2 mm = args.mono[n];
+              const float2 mm = mono[n];
               float s, e;
               if (nseg == 2) {
                 two_sum(e0, mm.x, s, e);
@@ -461,20 +516,20 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
                 v = s + (e + mm.y + ls);
               }
             }
-            if (args.symmetric) {
+            if (symmetric) {
               // Yin-Yang: Phi_Yin = E + O, Phi_Yang = E - O (O = 0 when there are no odd columns)
               const float ee = (nseg == 2) ? e0 : v, oo = (nseg == 2) ? v : 0.0f;
-              args.phi[args.pt.fld_off[0] + (long long)n * nang + a_loc] = f32_to_f64(ee + oo);
-              args.phi[args.pt.fld_off[1] + (long long)n * nang + a_loc] = f32_to_f64(ee - oo);
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64(ee + oo);
+              phi[off1 + (long long)n * nang + a_loc] = f32_to_f64(ee - oo);
             } else {
-              args.phi[args.pt.fld_off[T.g_patch] + (long long)n * nang + a_loc] = f32_to_f64(v);
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64(v);
             }
           }
         }
       }
     }
     if (!ok) {
-      set_err(args.err, YGS_ERR_TIMEOUT);
+      set_err(err, YGS_ERR_TIMEOUT);
       *abort_flag = 1;
     }
   }
@@ -483,6 +538,31 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// One problem: maps and arguments in kernel parameters.
+template <int NSL, int MODE>
+__global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ TcArgs args) {
+  if (threadIdx.x == 0) {
+    prefetch_tmap(&mapA);
+    prefetch_tmap(&mapB);
+    prefetch_tmap(&mapBt);
+  }
+  const SingleSrc src{&args, &mapA, &mapB, &mapBt};
+  gemm_body<NSL, MODE>(src, args.flush_kb);
+}
+
+// Several problems of one operand type in one persistent launch (a batch of
+// fields): every CTA walks the concatenated tile list; TMEM accumulators and
+// shared-memory stages carry over from one problem to the next.
+template <int NSL, int MODE>
+__global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
+    tc_gemm_group_kernel(const TcProblem* __restrict__ probs, const int* __restrict__ start, int n, int total,
+                         int flush, const __grid_constant__ TcPhiList phis) {
+  const GroupSrc src{probs, start, n, total, &phis};
+  gemm_body<NSL, MODE>(src, flush);
 }
 
 }  // namespace tc

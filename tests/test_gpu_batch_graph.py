@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from paper_1903_08475_gb300 import Plan, ygs_solve, ygs_solve_batched, workloads as W
+from paper_1903_08475_gb300 import Batch, Plan, YgsError, ygs_solve, ygs_solve_batched, workloads as W
 from tests._util import small_yinyang
 from tests.test_gpu_fp64 import three_patch_grid
 
@@ -67,5 +67,74 @@ def test_graph_capture_single_and_batched(cuda):
     assert torch.equal(single, eager[0])
     for a, b in zip(gouts, eager):
         assert torch.equal(a, b)
+    for p in plans:
+        p.close()
+
+
+def _uneven_fields(cuda):
+    """Split-precision and FP64 plans of different sizes, patch sets and l_max."""
+    import torch
+    grids = [small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9),
+             small_yinyang(W, n_theta=8, n_phi=20, n_r=150, l_max=7),
+             three_patch_grid(),
+             W.polar_grid(7, 13, W.linear_edges(6, 0.1, 1.0), 5),
+             small_yinyang(W, n_theta=10, n_phi=28, n_r=300, l_max=12),
+             small_yinyang(W, n_theta=6, n_phi=18, n_r=9, l_max=0)]
+    precs = ["fp16x3", "bf16x6", "fp16x3", "fp64", "bf16x3", "fp16x3"]
+    plans = [Plan(g, p) for g, p in zip(grids, precs)]
+    rhos = [torch.from_numpy(W.random_density(g, 40 + i)).cuda() for i, g in enumerate(grids)]
+    return plans, rhos
+
+
+def test_grouped_batch_equals_per_field(cuda):
+    """One persistent launch per slice count for the contractions of every
+    field gives bit-identical results to the per-field solves."""
+    import torch
+    plans, rhos = _uneven_fields(cuda)
+    ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
+    with Batch(plans) as b:
+        # 6 fields: field slices + 3 scans (+ M slicing for FP16) per split field,
+        # 2 grouped launches for each of the two slice counts, 3 for the FP64 field
+        assert b.launches == 3 * 5 + 4 + 4 + 2 * 2 + 3
+        for _ in range(2):
+            outs = b.solve(rhos)
+            torch.cuda.synchronize()
+            for a, o in zip(ref, outs):
+                assert torch.equal(a, o)
+    for p in plans:
+        p.close()
+
+
+def test_grouped_batch_in_a_cuda_graph(cuda):
+    import torch
+    plans, rhos = _uneven_fields(cuda)
+    ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
+    with Batch(plans) as b:
+        outs = [torch.empty_like(r) for r in rhos]
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            b.solve(rhos, outs, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        gin = [r.clone() for r in rhos]
+        gout = [torch.empty_like(r) for r in rhos]
+        with torch.cuda.graph(g):
+            b.solve(gin, gout)
+        for k, r in enumerate(rhos):  # new inputs into the captured buffers
+            gin[k].copy_(2.0 * r)
+        g.replay()
+        torch.cuda.synchronize()
+        for a, o in zip(ref, gout):
+            assert torch.allclose(o, 2.0 * a, rtol=1e-6, atol=0)
+    for p in plans:
+        p.close()
+
+
+def test_batch_rejects_repeated_plan(cuda):
+    plans, _ = _uneven_fields(cuda)
+    with pytest.raises(YgsError):
+        Batch([plans[0], plans[1], plans[0]])
     for p in plans:
         p.close()
