@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--n-r", type=int, default=400)
+    ap.add_argument("--workload", default="config1", choices=["config1", "config3"],
+                    help="config1: the 1-degree Yin-Yang field (default); config3: a batch of 64 uneven fields")
     return ap.parse_args()
 
 
@@ -56,8 +58,8 @@ def dist_env():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
 # pass on this workload at Nr = 400) of the current kernels, by precision and
 # phase; absent entries report null.  Source: profiles/tc_gemm_yinyang1deg_fp16x3.md.
-MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119534336 + 101723136,
-                    ("fp16x3", "projection", 400): 196923648 + 3835136}
+MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119302912 + 102079488,
+                    ("fp16x3", "projection", 400): 196923648 + 4420864}
 
 
 def load_peaks():
@@ -180,11 +182,93 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_config3(args, ws, rank, local):
+    """64 uneven fields (config 3): the grouped persistent batch replayed from a
+    CUDA graph against per-field launches; fields/s over K steps of the whole
+    batch, every field resident in HBM (1.0e9 cells, inputs far above L2)."""
+    import torch
+
+    from paper_1903_08475_gb300 import Batch, Plan, ygs_launches_per_solve, ygs_solve, workloads as W
+    from paper_1903_08475_gb300 import dist as D
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    precision = args.precision or "fp16x3"
+    fields = W.config3()
+    plans = [Plan(g, precision, device=local) for g, _, _ in fields]
+    rhos = [W.batch_density(g, kind, seed, device=dev) for g, kind, seed in fields]
+    cells = sum(g.n_cells for g, _, _ in fields)
+    stream = torch.cuda.Stream(device=dev)
+    ref = [torch.empty_like(r) for r in rhos]
+    out = [torch.empty_like(r) for r in rhos]
+
+    def per_field():
+        for p, r, o in zip(plans, rhos, ref):
+            ygs_solve(p, r, o, stream=stream)
+
+    batch = Batch(plans)
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            per_field()
+            batch.solve(rhos, out, stream=stream)
+    stream.synchronize()
+    identical = all(torch.equal(a, b) for a, b in zip(ref, out))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batch.solve(rhos, out, stream=stream)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.steps):
+                fn()
+        e1.record(stream)
+        stream.synchronize()
+        return D.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_graph = timed(graph.replay)
+    clk = clocks.stop()
+    ms_each = timed(per_field)
+    n = len(fields)
+    line = {"metric": "fields/s on a batch of 64 uneven fields (config 3)", "value": ws * n / (ms_graph / 1e3),
+            "unit": "fields/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
+            "data": "synthetic", "gcell_per_s": ws * cells / (ms_graph / 1e3) / 1e9,
+            "config": {"workload": "batch64-uneven-Nr128..600-deg2/1.5/1-lmax16..48-yinyang/6patch",
+                       "fields": n, "cells": cells, "precision": precision,
+                       "l2": "inputs larger than L2 (1.0e9 cells)", "parallelism": f"replicas{ws}"},
+            "per_field_launches": {"fields_per_s": ws * n / (ms_each / 1e3), "ms_per_step": ms_each,
+                                   "launches_per_step": sum(ygs_launches_per_solve(p) for p in plans)},
+            "speedup_vs_per_field": ms_each / ms_graph, "bitwise_equal_to_per_field": identical,
+            "gpu_launches": args.steps * batch.launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "config3":
+        run_config3(args, ws, rank, local)
         return
 
     import numpy as np

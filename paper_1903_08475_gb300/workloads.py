@@ -458,3 +458,106 @@ def config4(seed: int = SEED_BASE + 4):
 def random_density(grid: Grid, seed: int) -> np.ndarray:
     """Positive random density, uniform in [0.5, 1.5) (for parity cases)."""
     return np.random.default_rng(seed).uniform(0.5, 1.5, grid.n_cells)
+
+
+# ------------------------------------------------------- config 3 (batches)
+
+def six_patch_grid(n_theta: int, n_phi: int, delta: float, edges, l_max: int, frames, w=None,
+                   nsub_w: int = 8) -> Grid:
+    """Three Yin-Yang pairs, pair q rotated as a whole by the Euler angles
+    frames[q]: six patches covering every direction three times."""
+    tr, pr = yinyang_extents(delta)
+    eul = [compose_euler(f, e) for f in frames for e in (YIN_EULER, YANG_EULER)]
+    return make_grid(edges, eul, [n_theta] * 6, [n_phi] * 6, [tr] * 6, [pr] * 6, l_max, w=w, nsub_w=nsub_w)
+
+
+def config3(n_fields: int = 64, seed: int = SEED_BASE + 3):
+    """A batch of uneven fields: Nr uniform in [128, 600] (log-spaced shells
+    in [1e-3, 1]), resolution 2, 1.5 or 1 degree, l_max uniform in [16, 48],
+    patch set Yin-Yang or six patches (three rotated Yin-Yang pairs drawn from a
+    pool of four; six-patch sets at 2 and 1.5 degrees only), densities
+    alternating between the config-1 kind (rotated ellipsoid plus three
+    blobs) and the config-2 kind (lognormal times a central profile), both
+    sampled at cell centres (see batch_density).  Overlap weights depend only on
+    the angular layout, so they are computed once per (patch set, resolution)
+    and shared.  Returns a list of (grid, density kind, density seed)."""
+    rng = np.random.default_rng(seed)
+    frames_pool = [[random_euler(rng) for _ in range(3)] for _ in range(4)]
+    w_pool = {}
+    out = []
+    for k in range(n_fields):
+        n_r = int(rng.integers(128, 601))
+        deg = float(rng.choice([2.0, 1.5, 1.0]))
+        l_max = int(rng.integers(16, 49))
+        six = bool(rng.random() < 0.5) and deg != 1.0
+        pick = int(rng.integers(0, 4))
+        nt, nf, d = yinyang_resolution(deg)
+        edges = log_edges(n_r, 1e-3, 1.0)
+        key = (deg, pick if six else -1)
+        if key not in w_pool:
+            g0 = (six_patch_grid(nt, nf, d, edges[:2], 0, frames_pool[pick]) if six
+                  else yinyang_grid(nt, nf, d, edges[:2], 0, nsub_w=8))
+            w_pool[key] = g0.w
+        if six:
+            grid = six_patch_grid(nt, nf, d, edges, l_max, frames_pool[pick], w=w_pool[key])
+        else:
+            tr, pr = yinyang_extents(d)
+            grid = make_grid(edges, [YIN_EULER, YANG_EULER], [nt, nt], [nf, nf], [tr, tr], [pr, pr], l_max,
+                             w=w_pool[key])
+        out.append((grid, "blobs" if k % 2 == 0 else "lognormal", seed * 1000 + k))
+    return out
+
+
+def batch_density(grid: Grid, kind: str, seed: int, device="cpu"):
+    """Density of a config-3 field at cell centres as a torch FP64 tensor on
+    ``device`` (fast enough for tens of millions of cells on a GPU).
+    "blobs": 1 inside the ellipsoid (0.6, 0.5, 0.4) rotated by seeded Euler
+    angles plus three Gaussian blobs (sigma 0.05, amplitude 5, centres in
+    r < 0.7).  "lognormal": exp(0.5 g - 0.125) (1 + (r/0.05)^2)^-1.5 with g a
+    unit-variance sum of 32 random Fourier modes, amplitudes ~ 1/k (power
+    spectrum k^-2) for wavenumbers pi .. 16 pi."""
+    import torch
+    rng = np.random.default_rng(seed)
+    e = grid.edges
+    rc = torch.tensor(0.5 * (e[:-1] + e[1:]), dtype=torch.float64, device=device)
+    if kind == "blobs":
+        Rb = random_rotation(rng)
+        ax = np.array([0.6, 0.5, 0.4])
+        centres = []
+        while len(centres) < 3:
+            c = rng.uniform(-0.7, 0.7, 3)
+            if np.linalg.norm(c) < 0.7:
+                centres.append(c)
+    else:
+        kdir = rng.standard_normal((32, 3))
+        kdir /= np.linalg.norm(kdir, axis=1, keepdims=True)
+        kmag = np.pi * np.exp(rng.uniform(0.0, np.log(16.0), 32))
+        kv = torch.tensor(kdir * kmag[:, None], dtype=torch.float64, device=device)
+        amp = torch.tensor(1.0 / kmag, dtype=torch.float64, device=device)
+        amp = amp / torch.sqrt(0.5 * (amp * amp).sum())
+        phase = torch.tensor(rng.uniform(0, 2 * np.pi, 32), dtype=torch.float64, device=device)
+    parts = []
+    for p in range(grid.n_patch):
+        te = cell_edges_1d(*grid.theta_range[p], int(grid.n_theta[p]))
+        pe = cell_edges_1d(*grid.phi_range[p], int(grid.n_phi[p]))
+        TH, PH = np.meshgrid(0.5 * (te[:-1] + te[1:]), 0.5 * (pe[:-1] + pe[1:]), indexing="ij")
+        d = local_dirs(TH, PH).reshape(-1, 3) @ rotation_matrix(*grid.euler[p]).T
+        if kind == "blobs":
+            db = torch.tensor(d @ Rb, dtype=torch.float64, device=device)     # body-frame directions
+            q = ((db / torch.tensor(ax, dtype=torch.float64, device=device)) ** 2).sum(1)
+            rho = ((rc[:, None] ** 2) * q[None, :] <= 1.0).to(torch.float64)
+            dg = torch.tensor(d, dtype=torch.float64, device=device)
+            for c in centres:
+                ct = torch.tensor(c, dtype=torch.float64, device=device)
+                d2 = rc[:, None] ** 2 - 2 * rc[:, None] * (dg @ ct)[None, :] + float(c @ c)
+                rho += 5.0 * torch.exp(-d2 / (2 * 0.05 ** 2))
+        else:
+            dg = torch.tensor(d, dtype=torch.float64, device=device)
+            kd = dg @ kv.T                                                   # (na, 32)
+            g = torch.zeros(len(rc), dg.shape[0], dtype=torch.float64, device=device)
+            for m in range(32):
+                g += amp[m] * torch.cos(rc[:, None] * kd[None, :, m] + phase[m])
+            prof = (1.0 + (rc / 0.05) ** 2) ** -1.5
+            rho = torch.exp(0.5 * g - 0.125) * prof[:, None]
+        parts.append(rho.reshape(-1))
+    return torch.cat(parts)
