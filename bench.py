@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--n-r", type=int, default=400)
+    ap.add_argument("--autotune", action="store_true",
+                    help="plans pick their split-K count by timing candidates at create")
     ap.add_argument("--workload", default="config1", choices=["config1", "config3"],
                     help="config1: the 1-degree Yin-Yang field (default); config3: a batch of 64 uneven fields")
     return ap.parse_args()
@@ -198,7 +200,7 @@ def run_config3(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     precision = args.precision or "fp16x3"
     fields = W.config3()
-    plans = [Plan(g, precision, device=local) for g, _, _ in fields]
+    plans = [Plan(g, precision, device=local, autotune=args.autotune) for g, _, _ in fields]
     rhos = [W.batch_density(g, kind, seed, device=dev) for g, kind, seed in fields]
     cells = sum(g.n_cells for g, _, _ in fields)
     stream = torch.cuda.Stream(device=dev)
@@ -285,7 +287,7 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     precision = args.precision or "fp16x3"
     grid, rho = W.config1(n_r=args.n_r)
-    plan = Plan(grid, precision, device=local)
+    plan = Plan(grid, precision, device=local, autotune=args.autotune)
     stream = torch.cuda.Stream(device=dev)
     rho_d = torch.from_numpy(rho).to(dev)
     phi_d = torch.empty_like(rho_d)
@@ -396,7 +398,7 @@ def main():
             "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision, "data": "synthetic",
             "gcell_per_s": value * grid.n_cells / 1e9,
             "config": {"workload": workload_name(grid.n_r), "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
-                       "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"],
+                       "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"], "autotune": args.autotune,
                        "l2": "inputs larger than L2 (rho 160 MB, weights 436 MB)",
                        "parallelism": f"replicas{ws}"},
             "e2e": {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(rho.nbytes),

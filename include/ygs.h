@@ -89,7 +89,12 @@ typedef enum {
 } ygs_eval;
 
 enum {
-  YGS_FLAG_NO_SYMMETRY = 1 /* never use the Yin-Yang sign symmetry of Sect. 4.2 */
+  YGS_FLAG_NO_SYMMETRY = 1, /* never use the Yin-Yang sign symmetry of Sect. 4.2 */
+  YGS_FLAG_AUTOTUNE = 2     /* split precisions: ygs_create times the projection with several
+                               split-K counts (angular chunks per shell tile) on this GPU and
+                               keeps the fastest (a few ms more at create; results then differ
+                               from an untuned plan's within the precision's bound, as the
+                               chunk sums are added in another grouping) */
 };
 
 /* Grid descriptor.  All arrays are HOST memory, read during ygs_create only. */

@@ -23,6 +23,7 @@ STATUS = {0: "YGS_OK", 1: "YGS_ERR_INVALID_ARG", 2: "YGS_ERR_OOM", 3: "YGS_ERR_C
 PRECISION = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp16x3": 3}
 EVAL = {"upper_vertex": 0, "cell_centre": 1}
 FLAG_NO_SYMMETRY = 1
+FLAG_AUTOTUNE = 2
 
 EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_batched",
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
@@ -127,7 +128,8 @@ def _stream_handle(stream) -> Optional[int]:
 class Plan:
     """A grid plan (``ygs_create``): FP64 weights live on the device until close()."""
 
-    def __init__(self, grid, precision: str = "fp64", device: int = 0, symmetry: bool = True):
+    def __init__(self, grid, precision: str = "fp64", device: int = 0, symmetry: bool = True,
+                 autotune: bool = False):
         L = load_library()
         self._keep = keep = {
             "edges": np.ascontiguousarray(grid.edges, dtype=np.float64),
@@ -141,7 +143,7 @@ class Plan:
         d = _Desc(grid.n_r, keep["edges"].ctypes.data_as(_dp), grid.n_patch, keep["euler"].ctypes.data_as(_dp),
                   keep["nt"].ctypes.data_as(_ip), keep["nf"].ctypes.data_as(_ip), keep["tr"].ctypes.data_as(_dp),
                   keep["pr"].ctypes.data_as(_dp), keep["w"].ctypes.data_as(_dp), grid.l_max, grid.G, grid.eval,
-                  PRECISION[precision], 0 if symmetry else FLAG_NO_SYMMETRY)
+                  PRECISION[precision], (0 if symmetry else FLAG_NO_SYMMETRY) | (FLAG_AUTOTUNE if autotune else 0))
         h = ctypes.c_void_p()
         _check(L.ygs_create(ctypes.byref(d), device, ctypes.byref(h)))
         self._h = h

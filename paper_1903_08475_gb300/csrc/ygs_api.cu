@@ -143,7 +143,7 @@ ygs_status validate_desc(const ygs_desc* d) {
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
   if (d->precision < YGS_FP64 || d->precision > YGS_FP16X3) return fail(YGS_ERR_INVALID_ARG, "bad precision");
-  if (d->flags & ~YGS_FLAG_NO_SYMMETRY) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
+  if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;
 }
@@ -380,7 +380,7 @@ ygs_status ygs_get_info(const ygs_plan* p, ygs_info* info) {
   info->n_cells = p->n_cells;
   info->precision = p->precision;
   info->symmetric = p->symmetric ? 1 : 0;
-  info->split_k = p->S;
+  info->split_k = p->tc_nsl ? p->tc_S : p->S;
   info->weight_bytes = p->weight_bytes;
   info->work_bytes = p->work_bytes;
   return YGS_OK;

@@ -809,16 +809,28 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   const int n_tiles_p = p->tc_np_full + (p->tc_np_tail > 0 ? 1 : 0);
   long long want = std::max(1LL, (long long)std::floor(sms / std::max(1.0, per_chunk) + 0.5));
   while (want > 1 && (long long)tiles_m * n_tiles_p * want > sms) --want;
-  std::vector<int2> chunks;
-  for (int g = 0; g < p->n_wpatch; ++g) {
-    const long long kb_g = r32(p->nang[g]) / tc::BK;
-    long long sg = std::max(1LL, (want * p->nang[g] + p->nang_wtotal - 1) / p->nang_wtotal);
-    sg = std::min(sg, std::max(1LL, kb_g / 4));
-    const long long per = (kb_g + sg - 1) / sg;
-    for (long long k0 = 0; k0 < kb_g; k0 += per)
-      chunks.push_back(make_int2((int)((p->tc_pad_off[g] + k0 * tc::BK)),
-                                 (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
+  // candidate split-K targets: the one-wave rule, and, when autotuning, half, two and three waves
+  std::vector<long long> wants = {want};
+  if (p->flags & YGS_FLAG_AUTOTUNE)
+    for (long long w2 : {std::max(1LL, want / 2), 2 * want, 3 * want})
+      if (std::find(wants.begin(), wants.end(), w2) == wants.end()) wants.push_back(w2);
+  std::vector<std::vector<int2>> cand;
+  for (long long wv : wants) {
+    std::vector<int2> chunks;
+    for (int g = 0; g < p->n_wpatch; ++g) {
+      const long long kb_g = r32(p->nang[g]) / tc::BK;
+      long long sg = std::max(1LL, (wv * p->nang[g] + p->nang_wtotal - 1) / p->nang_wtotal);
+      sg = std::min(sg, std::max(1LL, kb_g / 4));
+      const long long per = (kb_g + sg - 1) / sg;
+      for (long long k0 = 0; k0 < kb_g; k0 += per)
+        chunks.push_back(make_int2((int)((p->tc_pad_off[g] + k0 * tc::BK)),
+                                   (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
+    }
+    cand.push_back(chunks);
   }
+  size_t s_max = 0;
+  for (const auto& c : cand) s_max = std::max(s_max, c.size());
+  std::vector<int2> chunks = cand[0];
   p->tc_S = (int)chunks.size();
   // chunks of 4 shells for the parallel scans (more for n_r > 4096: at most 1024 chunks, 32 per carry lane)
   p->tc_scan_chunk = std::max(4, (p->n_r + 1023) / 1024);
@@ -829,7 +841,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   size_t bytes_q = (size_t)nsl * p->nang_wtotal * kp * 2;
   size_t bytes_f = (size_t)(p->symmetric ? 2 : 1) * nsl * p->n_r * p->tc_n_pad * 2;
   size_t bytes_m = (size_t)nsl * p->n_r * kp * 2;
-  size_t bytes_part = (size_t)p->tc_S * p->n_r * kp * sizeof(float2);
+  size_t bytes_part = s_max * p->n_r * kp * sizeof(float2);
   size_t bytes_nk = (size_t)p->n_r * kp * sizeof(double);
   size_t bytes_sum = (size_t)4 * p->tc_scan_P * kp * sizeof(double);
   cudaError_t e;
@@ -851,7 +863,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_ALLOC(p->tc_M, bytes_nk);
   TC_ALLOC(p->tc_summ, bytes_sum);
   TC_ALLOC(p->tc_carry, bytes_sum / 2);
-  TC_ALLOC(p->tc_chunks, chunks.size() * sizeof(int2));
+  TC_ALLOC(p->tc_chunks, s_max * sizeof(int2));
   TC_ALLOC(p->tc_pc_int, kp * sizeof(int));
   TC_ALLOC(p->tc_pc_l, kp * sizeof(int));
   TC_ALLOC(p->tc_pc_nat, kp * sizeof(int));
@@ -861,7 +873,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   if (p->tc_fp16) {
     TC_ALLOC(p->tc_eqt, kp * sizeof(int));
     TC_ALLOC(p->tc_eu, kp * sizeof(int));
-    TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * p->tc_S * sizeof(int));
+    TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * s_max * sizeof(int));
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
   }
 #undef TC_ALLOC
@@ -958,6 +970,35 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     }
     TC_TRY(a1);
     TC_TRY(a2);
+  }
+  if (cand.size() > 1) {
+    // time the projection of a zero field with each candidate; keep the fastest
+    cudaEvent_t e0, e1;
+    TC_TRY(cudaEventCreate(&e0));
+    TC_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    size_t pick = 0;
+    for (size_t c = 0; c < cand.size(); ++c) {
+      TC_TRY(cudaMemcpy(p->tc_chunks, cand[c].data(), cand[c].size() * sizeof(int2), cudaMemcpyHostToDevice));
+      p->tc_S = (int)cand[c].size();
+      TC_TRY(tc_project(p, 0));
+      TC_TRY(cudaEventRecord(e0, 0));
+      for (int r = 0; r < 5; ++r) TC_TRY(tc_project(p, 0));
+      TC_TRY(cudaEventRecord(e1, 0));
+      TC_TRY(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      TC_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        pick = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    chunks = cand[pick];
+    p->tc_S = (int)chunks.size();
+    TC_TRY(cudaMemcpy(p->tc_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    TC_TRY(cudaDeviceSynchronize());
   }
 #undef TC_TRY
   return YGS_OK;

@@ -107,3 +107,19 @@ def test_fp16_scaling_physical_units(cuda, scale):
         phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
         torch.cuda.synchronize()
         assert rel_max(phi.cpu().numpy(), ref) <= TOL["fp16x3"]
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+def test_autotuned_split_k(cuda, precision):
+    """A plan whose split-K count was picked by timing candidates at create
+    (YGS_FLAG_AUTOTUNE) stays within the precision's bound of the oracle."""
+    import torch
+    grid = small_yinyang(W, n_theta=16, n_phi=46, deg=4.0, n_r=150, l_max=12)
+    rho = W.random_density(grid, 31)
+    ref = oracle.solve(grid, rho)
+    with Plan(grid, precision) as p0, Plan(grid, precision, autotune=True) as p1:
+        assert p1.info["split_k"] >= 1
+        for p in (p0, p1):
+            phi = ygs_solve(p, torch.from_numpy(rho).cuda())
+            torch.cuda.synchronize()
+            assert rel_max(phi.cpu().numpy(), ref) <= TOL[precision]
