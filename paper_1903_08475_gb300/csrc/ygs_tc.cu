@@ -314,18 +314,72 @@ __device__ __forceinline__ void load8(const double* __restrict__ p, long long n,
   }
 }
 
+// Largest |sigma+-| of 8 cells from truncated FP32 values (a few ulp from the
+// float-float heads used for the slices; the caller raises the maxima by 2^-16).
+__device__ __forceinline__ void f16_group_max(const double (&x0)[8], const double (&x1)[8], int symmetric,
+                                              float& mx0, float& mx1) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float f0 = tc::f64_trunc_f32(x0[c]), f1 = symmetric ? tc::f64_trunc_f32(x1[c]) : 0.0f;
+    mx0 = fmaxf(mx0, fabsf(f0 + f1));
+    mx1 = fmaxf(mx1, fabsf(f0 - f1));
+  }
+}
+
+// Scaled FP16 slices of 8 cells written as 16-byte stores (fewer at a ragged end).
+__device__ __forceinline__ void f16_group_store(const double (&x0)[8], const double (&x1)[8], int symmetric,
+                                                const float (&f)[2][2], __half* __restrict__ out, long long plane,
+                                                long long j, long long n) {
+  uint32_t w[2][2][4];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float hi[2], lo[2];
+    sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi, lo);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float hs = (hi[h] * f[h][0]) * f[h][1], ls = (lo[h] * f[h][0]) * f[h][1];
+      const __half s0 = __float2half_rn(hs);
+      const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
+      const uint32_t b0 = __half_as_ushort(s0), b1 = __half_as_ushort(s1);
+      if (c & 1) {
+        w[h][0][c / 2] |= b0 << 16;
+        w[h][1][c / 2] |= b1 << 16;
+      } else {
+        w[h][0][c / 2] = b0;
+        w[h][1][c / 2] = b1;
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (h == 1 && !symmetric) break;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      __half* dst = out + (long long)(h * 2 + k) * plane + j;
+      if (n - j >= 8) {
+        *reinterpret_cast<uint4*>(dst) = make_uint4(w[h][k][0], w[h][k][1], w[h][k][2], w[h][k][3]);
+      } else {
+        for (int c = 0; c < n - j; ++c) dst[c] = __ushort_as_half((unsigned short)(w[h][k][c / 2] >> (16 * (c & 1))));
+      }
+    }
+  }
+}
+
+constexpr int kF16Threads = 256;
+
 // Field slices in FP16, one CTA per (split-K chunk z, shell i), 8 cells per
 // thread and step: pass 1 finds the largest |sigma| of each plane over the
 // chunk's cells (ef[h][i][z]), pass 2 (the chunk now in L2) writes the scaled
 // slices F[h*2+s][i][apad], 16 bytes per store.  Every projection partial of
-// chunk z then carries one power of two per shell.  Symmetric: planes sigma+
-// (h = 0) and sigma- (h = 1) of the Yin/Yang rows; otherwise plane 0, each
-// chunk lying inside one stored patch.
-__global__ void __launch_bounds__(256) field_slices16_kernel(int n_r, int symmetric, int nwp, PatchTable pt,
-                                                             const long long* __restrict__ pad_off, long long n_pad,
-                                                             const int2* __restrict__ chunks, int S,
-                                                             const double* __restrict__ rho, __half* __restrict__ F,
-                                                             int* __restrict__ ef) {
+// chunk z then carries one power of two per shell.  (Keeping a chunk in
+// registers between the passes instead ran at half the speed: one CTA per SM
+// could not hide the loads.)  Symmetric: planes sigma+ (h = 0) and sigma-
+// (h = 1) of the Yin/Yang rows; otherwise plane 0, each chunk lying inside one
+// stored patch.
+__global__ void __launch_bounds__(kF16Threads) field_slices16_kernel(
+    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
+    const int2* __restrict__ chunks, int S, const double* __restrict__ rho, __half* __restrict__ F,
+    int* __restrict__ ef) {
   __shared__ float red[32];
   const int z = blockIdx.x, i = blockIdx.y;
   const long long plane = (long long)n_r * n_pad;
@@ -338,19 +392,18 @@ __global__ void __launch_bounds__(256) field_slices16_kernel(int n_r, int symmet
   const double* x1p = symmetric ? rho + pt.fld_off[1] + i * na + a0 : x0p;
   const bool vec = ((reinterpret_cast<uintptr_t>(x0p) | reinterpret_cast<uintptr_t>(x1p)) & 15) == 0;
   __half* out = F + (long long)i * n_pad + pad_off[g] + a0;  // 16-byte aligned: every offset is a multiple of 8
-  // pass 1 from truncated FP32 values (a few ulp from the float-float heads of
-  // pass 2); the maxima are raised by 2^-16 so that m 2^e still bounds every head
+  const long long step = 8LL * blockDim.x;
   float mx0 = 0.0f, mx1 = 0.0f;
-  for (long long j = 8LL * threadIdx.x; j < n; j += 8LL * blockDim.x) {
+  for (long long j = 8LL * threadIdx.x; j < n; j += step) {
     double x0[8], x1[8];
     load8(x0p + j, n - j, vec, x0);
-    if (symmetric) load8(x1p + j, n - j, vec, x1);
+    if (symmetric) {
+      load8(x1p + j, n - j, vec, x1);
+    } else {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float f0 = tc::f64_trunc_f32(x0[c]), f1 = symmetric ? tc::f64_trunc_f32(x1[c]) : 0.0f;
-      mx0 = fmaxf(mx0, fabsf(f0 + f1));
-      mx1 = fmaxf(mx1, fabsf(f0 - f1));
+      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
     }
+    f16_group_max(x0, x1, symmetric, mx0, mx1);
   }
   const int e0 = tc::fp16_row_exp((double)block_max(mx0, red) * (1.0 + 0x1p-16));
   const int e1 = symmetric ? tc::fp16_row_exp((double)block_max(mx1, red) * (1.0 + 0x1p-16)) : 0;
@@ -358,47 +411,19 @@ __global__ void __launch_bounds__(256) field_slices16_kernel(int n_r, int symmet
     ef[(long long)i * S + z] = e0;
     ef[((long long)n_r + i) * S + z] = e1;
   }
-  float f[2][2];  // 2^e0, 2^e1 as two exact factors each
+  float f[2][2];
   tc::pow2_pair(e0, f[0][0], f[0][1]);
   tc::pow2_pair(e1, f[1][0], f[1][1]);
-  for (long long j = 8LL * threadIdx.x; j < n; j += 8LL * blockDim.x) {
+  for (long long j = 8LL * threadIdx.x; j < n; j += step) {
     double x0[8], x1[8];
     load8(x0p + j, n - j, vec, x0);
-    if (symmetric) load8(x1p + j, n - j, vec, x1);
-    uint32_t w[2][2][4];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
+    if (symmetric) {
+      load8(x1p + j, n - j, vec, x1);
+    } else {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      float hi[2], lo[2];
-      sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi, lo);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float hs = (hi[h] * f[h][0]) * f[h][1], ls = (lo[h] * f[h][0]) * f[h][1];
-        const __half s0 = __float2half_rn(hs);
-        const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
-        const uint32_t b0 = __half_as_ushort(s0), b1 = __half_as_ushort(s1);
-        if (c & 1) {
-          w[h][0][c / 2] |= b0 << 16;
-          w[h][1][c / 2] |= b1 << 16;
-        } else {
-          w[h][0][c / 2] = b0;
-          w[h][1][c / 2] = b1;
-        }
-      }
+      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
     }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1 && !symmetric) break;
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        __half* dst = out + (long long)(h * 2 + k) * plane + j;
-        if (n - j >= 8) {
-          *reinterpret_cast<uint4*>(dst) = make_uint4(w[h][k][0], w[h][k][1], w[h][k][2], w[h][k][3]);
-        } else {
-          for (int c = 0; c < n - j; ++c)
-            dst[c] = __ushort_as_half((unsigned short)(w[h][k][c / 2] >> (16 * (c & 1))));
-        }
-      }
-    }
+    f16_group_store(x0, x1, symmetric, f, out, plane, j, n);
   }
 }
 
@@ -1015,7 +1040,7 @@ void tc_free(ygs_plan* p) {
 
 cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
   if (p->tc_fp16) {
-    field_slices16_kernel<<<dim3(p->tc_S, p->n_r), 256, 0, s>>>(p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt,
+    field_slices16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt,
                                                                  p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, p->tc_S,
                                                                  rho, reinterpret_cast<__half*>(p->tc_f), p->tc_ef);
     return cudaGetLastError();
