@@ -340,13 +340,13 @@ def main():
     info = plan.info
     sym = info["symmetric"] == 1
     nang_eff = grid.nang(0) if sym else grid.nang_total
-    nprod = {"fp64": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}[precision]
+    nprod = {"fp64": 1, "fp64tc": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}[precision]
     # algorithmic FLOPs of one contraction: one FMA per (shell, stored cell, column) and slice product
     flops_gemm = 2.0 * nprod * grid.n_r * nang_eff * grid.K
     per = [x / max(ncalls, 1) for x in phase_ms]
     names = ["field_slices", "projection", "radial_scan", "synthesis"]
     dom = int(np.argmax(per))
-    if precision == "fp64":
+    if precision in ("fp64", "fp64tc"):
         flops = [0.0, flops_gemm, 0.0, flops_gemm][dom]
         achieved = flops / (per[dom] / 1e3) / 1e12
         roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS,
@@ -395,7 +395,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else precision, "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if precision in ("fp64", "fp64tc") else precision, "data": "synthetic",
             "gcell_per_s": value * grid.n_cells / 1e9,
             "config": {"workload": workload_name(grid.n_r), "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
                        "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"], "autotune": args.autotune,

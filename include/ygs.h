@@ -78,9 +78,11 @@ typedef enum {
   YGS_FP64 = 0,   /* FP64 FMA on the CUDA cores */
   YGS_BF16X3 = 1, /* tcgen05 BF16 tensor cores, 2-slice operands, 3 products */
   YGS_BF16X6 = 2, /* tcgen05 BF16 tensor cores, 3-slice operands, 6 products */
-  YGS_FP16X3 = 3  /* tcgen05 FP16 tensor cores, 2-slice operands (22 significant bits), 3 products;
+  YGS_FP16X3 = 3, /* tcgen05 FP16 tensor cores, 2-slice operands (22 significant bits), 3 products;
                      every operand row is scaled by a power of two into FP16's range (U per
                      column, the field and M per shell, Q as a whole) and unscaled exactly */
+  YGS_FP64_TC = 4 /* the FP64 path with its contractions on the FP64 tensor cores (DMMA 8x8x4):
+                     FP64 products and sums, another order of additions */
 } ygs_precision;
 
 typedef enum {

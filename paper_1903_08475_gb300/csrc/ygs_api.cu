@@ -142,7 +142,7 @@ ygs_status validate_desc(const ygs_desc* d) {
     return fail(YGS_ERR_INVALID_ARG, "l_max must be in [0, " + std::to_string(kMaxLmax) + "]");
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
-  if (d->precision < YGS_FP64 || d->precision > YGS_FP16X3) return fail(YGS_ERR_INVALID_ARG, "bad precision");
+  if (d->precision < YGS_FP64 || d->precision > YGS_FP64_TC) return fail(YGS_ERR_INVALID_ARG, "bad precision");
   if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;

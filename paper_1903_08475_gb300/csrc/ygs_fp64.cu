@@ -21,6 +21,70 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
+// D (8x8) += A (8x4, row) B (4x8, col) on the FP64 tensor cores (DMMA).  Lane
+// l holds A[l/4][l%4], B[l%4][l/4] and D[l/4][2(l%4) + {0, 1}].
+__device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+// One BK-deep step of a 64 x 64 tile held in registers, from As[k][row] and
+// Bs[k][col] in shared memory.  CUDA cores: 16 x 16 threads, 4 x 4 outputs
+// each at (ty + 16 r, tx + 16 q).  Tensor cores (TC): 8 warps, each a 16 x 32
+// block of 2 x 4 DMMA tiles; acc[2 mb + i][nb] is element i of the lane's pair
+// in tile (mb, nb) (tile_out gives the position).  Both keep FP64 products and
+// FP64 accumulation; only the order of the additions differs.
+template <bool TC>
+__device__ __forceinline__ void tile_step(const double (&As)[BK][BM + 1], const double (&Bs)[BK][BN + 1],
+                                          double (&acc)[4][4]) {
+  const int tid = threadIdx.x;
+  if (TC) {
+    const int lane = tid % 32, w = tid / 32, g = lane >> 2, t4 = lane & 3;
+    const int wr = (w >> 1) * 16, wc = (w & 1) * 32;
+#pragma unroll
+    for (int k0 = 0; k0 < BK; k0 += 4) {
+      double av[2], bv[4];
+#pragma unroll
+      for (int mb = 0; mb < 2; ++mb) av[mb] = As[k0 + t4][wr + mb * 8 + g];
+#pragma unroll
+      for (int nb = 0; nb < 4; ++nb) bv[nb] = Bs[k0 + t4][wc + nb * 8 + g];
+#pragma unroll
+      for (int mb = 0; mb < 2; ++mb)
+#pragma unroll
+        for (int nb = 0; nb < 4; ++nb) dmma_8x8x4(acc[2 * mb][nb], acc[2 * mb + 1][nb], av[mb], bv[nb]);
+    }
+  } else {
+    const int tx = tid % 16, ty = tid / 16;
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+    }
+  }
+}
+
+// Row and column within the 64 x 64 tile of acc[r][q].
+template <bool TC>
+__device__ __forceinline__ void tile_out(int r, int q, int& row, int& col) {
+  const int tid = threadIdx.x;
+  if (TC) {
+    const int lane = tid % 32, w = tid / 32, g = lane >> 2, t4 = lane & 3;
+    row = (w >> 1) * 16 + (r >> 1) * 8 + g;
+    col = (w & 1) * 32 + q * 8 + 2 * t4 + (r & 1);
+  } else {
+    row = tid / 16 + 16 * r;
+    col = tid % 16 + 16 * q;
+  }
+}
+
 struct ProjArgs {
   int n_r, K, K_even, tiles_e, symmetric;
   const double* field;
@@ -30,10 +94,11 @@ struct ProjArgs {
   PatchTable pt;
 };
 
+template <bool TC>
 __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x;
   const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
   int c0, c1;
   double sgn;
@@ -77,18 +142,7 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
       Bs[kk][col] = (k < ch.a1 && c < c1) ? Wg[(long long)k * a.K + c] : 0.0;
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
-    }
+    tile_step<TC>(As, Bs, acc);
     __syncthreads();
   }
   double* out = a.part + (long long)z * a.n_r * a.K;
@@ -96,7 +150,9 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      int i = i0 + ty + 16 * r, c = c0 + tx + 16 * q;
+      int row, col;
+      tile_out<TC>(r, q, row, col);
+      int i = i0 + row, c = c0 + col;
       if (i < a.n_r && c < c1) out[(long long)i * a.K + c] = acc[r][q];
     }
 }
@@ -109,6 +165,7 @@ struct SynthArgs {
   PatchTable pt;
 };
 
+template <bool TC>
 __device__ inline void synth_range(const SynthArgs& s, const double* Wg, long long nang, int i0, int a0, int k_lo,
                                    int k_hi, double (&As)[BK][BM + 1], double (&Bs)[BK][BN + 1], double (&acc)[4][4]) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -126,22 +183,12 @@ __device__ inline void synth_range(const SynthArgs& s, const double* Wg, long lo
       Bs[kk][n] = (a < nang && k < k_hi) ? Wg[(long long)a * s.K + k] : 0.0;
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double av[4], bv[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx + 16 * q];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
-    }
+    tile_step<TC>(As, Bs, acc);
     __syncthreads();
   }
 }
 
+template <bool TC>
 __global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs s) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -157,14 +204,16 @@ __global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs s) {
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) ae[r][q] = ao[r][q] = 0.0;
-  synth_range(s, Wg, nang, i0, a0, 0, s.K_even, As, Bs, ae);
-  if (s.K_even < s.K) synth_range(s, Wg, nang, i0, a0, s.K_even, s.K, As, Bs, ao);
+  synth_range<TC>(s, Wg, nang, i0, a0, 0, s.K_even, As, Bs, ae);
+  if (s.K_even < s.K) synth_range<TC>(s, Wg, nang, i0, a0, s.K_even, s.K, As, Bs, ao);
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      int i = i0 + ty + 16 * r;
-      long long a = a0 + tx + 16 * q;
+      int row, col;
+      tile_out<TC>(r, q, row, col);
+      int i = i0 + row;
+      long long a = a0 + col;
       if (i >= s.n_r || a >= nang) continue;
       if (s.symmetric) {
         s.out[s.pt.fld_off[0] + i * nang + a] = ae[r][q] + ao[r][q];
@@ -260,7 +309,10 @@ cudaError_t launch_project_fp64(const ygs_plan* p, const double* field, const do
   a.pt = p->pt;
   int tiles_o = (p->K - p->K_even + BN - 1) / BN;
   dim3 grid(a.tiles_e + tiles_o, (p->n_r + BM - 1) / BM, p->S);
-  proj_fp64_kernel<<<grid, NT, 0, s>>>(a);
+  if (p->precision == YGS_FP64_TC)
+    proj_fp64_kernel<true><<<grid, NT, 0, s>>>(a);
+  else
+    proj_fp64_kernel<false><<<grid, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -277,7 +329,10 @@ cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* 
   long long nmax = 0;
   for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
   dim3 grid((unsigned)((nmax + BN - 1) / BN), (p->n_r + BM - 1) / BM, p->n_wpatch);
-  synth_fp64_kernel<<<grid, NT, 0, s>>>(a);
+  if (p->precision == YGS_FP64_TC)
+    synth_fp64_kernel<true><<<grid, NT, 0, s>>>(a);
+  else
+    synth_fp64_kernel<false><<<grid, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 

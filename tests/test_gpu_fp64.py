@@ -40,15 +40,18 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=sorted(CASES))
+@pytest.fixture(scope="module", params=[(c, p) for c in sorted(CASES) for p in ("fp64", "fp64tc")],
+                ids=lambda cp: f"{cp[0]}-{cp[1]}")
 def case(request, cuda):
+    """Every case on the FP64 CUDA-core kernels and on the FP64 tensor cores (DMMA)."""
     import torch
-    make, sym = CASES[request.param]
+    name, precision = request.param
+    make, sym = CASES[name]
     grid = make()
     rho = W.random_density(grid, 11)
-    plan = Plan(grid, "fp64", symmetry=sym)
+    plan = Plan(grid, precision, symmetry=sym)
     phi_ref, B_ref, M_ref = oracle.solve(grid, rho, moments=True)
-    yield request.param, grid, rho, plan, phi_ref, B_ref, M_ref
+    yield f"{name}-{precision}", grid, rho, plan, phi_ref, B_ref, M_ref
     plan.close()
 
 
@@ -73,6 +76,8 @@ def test_moments_match_oracle(case):
 
 def test_weights_match_oracle_quadrature(case):
     name, grid, rho, plan, _, _, _ = case
+    if name.endswith("fp64tc"):
+        pytest.skip("the same weights as the fp64 plan")
     U_ref = oracle.build_U(grid)
     Q_ref = oracle.build_Q(grid)
     off = 0
