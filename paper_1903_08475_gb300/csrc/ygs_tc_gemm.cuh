@@ -497,11 +497,12 @@ __device__ __forceinline__ void gemm_body(const Src& src, const int flush) {
             const long long a_loc = (long long)T.m_loc * BM + r;
             if (a_loc >= nang) continue;
             float hs = hj, ls = lj, e0 = ev[jj];
-            if (m_exp) {  // exact unscaling of FP16-slice results
-              const int es = -(q_exp + m_exp[n]);
-              hs = mul_pow2f(hs, es);
-              ls = mul_pow2f(ls, es);
-              e0 = mul_pow2f(e0, es);
+            if (m_exp) {  // exact unscaling of FP16-slice results: two power-of-two factors per shell
+              float f1, f2;
+              pow2_pair(-(q_exp + m_exp[n]), f1, f2);
+              hs = (hs * f1) * f2;
+              ls = (ls * f1) * f2;
+              e0 = (e0 * f1) * f2;
             }
             float v = hs + ls;
             if (mono) {
