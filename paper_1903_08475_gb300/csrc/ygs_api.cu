@@ -556,7 +556,7 @@ ygs_status ygs_batch_solve(ygs_batch* b, const double* const* d_rho, double* con
 int ygs_batch_launches(const ygs_batch* b) {
   if (!b) return 0;
   int n = 0;
-  for (int k : b->split) n += b->plans[k]->tc_fp16 ? 5 : 4;
+  for (int k : b->split) n += b->plans[k]->tc_fp16 ? 3 : 2;  // field slices, scan (+ M slicing)
   n += 2 * (int)b->tc.groups.size() + 3 * (int)b->fp64.size();
   return n;
 }
@@ -656,7 +656,7 @@ ygs_status ygs_debug_wait_timeout(ygs_plan* p, int spins, void* stream) {
   return YGS_OK;
 }
 
-int ygs_launches_per_solve(const ygs_plan* p) { return p ? (p->tc_nsl ? (p->tc_fp16 ? 7 : 6) : 3) : 0; }
+int ygs_launches_per_solve(const ygs_plan* p) { return p ? (p->tc_nsl ? (p->tc_fp16 ? 5 : 4) : 3) : 0; }
 
 ygs_status ygs_get_status(ygs_plan* p) {
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");

@@ -484,64 +484,6 @@ __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
   return tc::f32_to_f64(hi) + tc::f32_to_f64(lo);
 }
 
-// Phase 1 of the chunked scans: B from the partials, local inner / outer
-// recurrences of one chunk of shells with zero carry, and their summaries.
-// With FP16 slices (ef, eu not null) the partial of chunk z is unscaled exactly
-// by 2^-(ef[h][i][z] + eu[pc]), h = 1 for the odd column block of a symmetric plan.
-__global__ void scan_local_kernel(int n_r, int K_pad, int L, int S, int chunk, const int* __restrict__ pc_l,
-                                  const float2* __restrict__ part, const double* __restrict__ rad,
-                                  const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ summ,
-                                  const int* __restrict__ ef, const int* __restrict__ eu, int k_split) {
-  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
-  if (pc >= K_pad) return;
-  const int l = pc_l[pc];
-  const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
-  const int P = gridDim.y;
-  if (l < 0 || i0 >= n_r) {
-    for (int i = i0; i < i1; ++i) B[(long long)i * K_pad + pc] = 0.0;
-    for (int k = 0; k < 4; ++k) summ[((long long)k * P + p) * K_pad + pc] = (k == 1 || k == 3) ? 1.0 : 0.0;
-    return;
-  }
-  const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
-  const double* at = rad + (long long)l * n_r;
-  const double* bt = rad + rs + (long long)l * n_r;
-  const double* fin = rad + 2 * rs + (long long)l * n_r;
-  const double* fout = rad + 3 * rs + (long long)l * n_r;
-  double I = 0.0;
-  for (int i = i0; i < i1; ++i) {
-    float h = 0.f, lo = 0.f;
-    const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
-    for (int z = 0; z < S; ++z) {
-      float2 v = part[z * plane + (long long)i * K_pad + pc];
-      if (efi) {
-        const int es = -(efi[z] + eu[pc]);
-        v.x = tc::mul_pow2f(v.x, es);
-        v.y = tc::mul_pow2f(v.y, es);
-      }
-      float s, e;
-      tc::two_sum(h, v.x, s, e);
-      h = s;
-      lo += e + v.y;
-    }
-    const double b = ff_to_f64(h, lo);
-    B[(long long)i * K_pad + pc] = b;
-    I = fma(at[i], b, fin[i] * I);
-  }
-  // P_i = b_i B_i + fout_{i-1} P_{i+1}, descending
-  double Pv = 0.0;
-  for (int i = i1 - 1; i >= i0; --i) {
-    const double fo = (i > 0) ? fout[i - 1] : 0.0;
-    Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
-  }
-  const double FI = cp[(long long)l * P + p];
-  const double FP = cp[(long long)(L + 1) * P + (long long)l * P + p];
-  summ[((long long)0 * P + p) * K_pad + pc] = I;
-  summ[((long long)1 * P + p) * K_pad + pc] = FI;
-  summ[((long long)2 * P + p) * K_pad + pc] = Pv;
-  summ[((long long)3 * P + p) * K_pad + pc] = FP;
-}
-
 // Phase 2: carries between chunks.  The chunk summaries define affine maps
 // c -> F c + s; one warp per column and direction composes them: each lane
 // folds up to 32 consecutive chunks, a shuffle scan joins the lanes (inner
@@ -584,20 +526,96 @@ __global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ s
   }
 }
 
-// Phase 3: the recurrences again with the carries; M = I_i + P_{i+1} in FP64
-// and its BF16 slices for the synthesis.
-__global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk, const int* __restrict__ pc_l,
-                                  const double* __restrict__ B, const double* __restrict__ rad,
-                                  const double* __restrict__ carry, double* __restrict__ M,
-                                  __nv_bfloat16* __restrict__ Ms, double G, float2* __restrict__ mono,
-                                  int write_slices) {
-  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
-  const int P = gridDim.y;
-  if (pc >= K_pad) return;
-  const int l = pc_l[pc];
+// All three phases in one launch: a CTA owns kScanCols columns and up to
+// kScanMaxP chunks of shells (thread = column + kScanCols * chunk), keeps the
+// chunk summaries and carries in shared memory and separates the phases with
+// block barriers (no CTA waits on another).  Same arithmetic, in the same
+// order, as scan_local / scan_carry / scan_final.
+constexpr int kScanCols = 8, kScanMaxP = 128, kScanThreads = kScanCols * kScanMaxP;
+
+__global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
+    int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
+    const double* __restrict__ rad, const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ M,
+    __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, double G, float2* __restrict__ mono,
+    const int* __restrict__ ef, const int* __restrict__ eu, int k_split) {
+  __shared__ double sm[4][kScanMaxP][kScanCols];
+  __shared__ double cr[2][kScanMaxP][kScanCols];
+  const int c = threadIdx.x % kScanCols, p = threadIdx.x / kScanCols;
+  const int pc = blockIdx.x * kScanCols + c;
+  const int l = pc < K_pad ? pc_l[pc] : -1;
   const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
-  const long long splane = (long long)n_r * K_pad;
+  const bool live = l >= 0 && p < P && i0 < n_r;
+  const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
+  const long long splane = plane;
+  const int lq = l < 0 ? 0 : l;
+  const double* at = rad + (long long)lq * n_r;
+  const double* bt = rad + rs + (long long)lq * n_r;
+  const double* fin = rad + 2 * rs + (long long)lq * n_r;
+  const double* fout = rad + 3 * rs + (long long)lq * n_r;
+  // ---- phase 1: B from the partials, local recurrences with zero carry, summaries
+  if (p < kScanMaxP) {
+    double I = 0.0, Pv = 0.0, FI = 1.0, FP = 1.0;
+    if (live) {
+      for (int i = i0; i < i1; ++i) {
+        float h = 0.f, lo = 0.f;
+        const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
+        for (int z = 0; z < S; ++z) {
+          float2 v = part[z * plane + (long long)i * K_pad + pc];
+          if (efi) {
+            const int es = -(efi[z] + eu[pc]);
+            v.x = tc::mul_pow2f(v.x, es);
+            v.y = tc::mul_pow2f(v.y, es);
+          }
+          float s, e;
+          tc::two_sum(h, v.x, s, e);
+          h = s;
+          lo += e + v.y;
+        }
+        const double b = ff_to_f64(h, lo);
+        B[(long long)i * K_pad + pc] = b;
+        I = fma(at[i], b, fin[i] * I);
+      }
+      for (int i = i1 - 1; i >= i0; --i) {
+        const double fo = (i > 0) ? fout[i - 1] : 0.0;
+        Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+      }
+      FI = cp[(long long)l * P + p];
+      FP = cp[(long long)(L + 1) * P + (long long)l * P + p];
+    } else if (pc < K_pad && l < 0) {
+      for (int i = i0; i < i1; ++i) B[(long long)i * K_pad + pc] = 0.0;
+    }
+    sm[0][p][c] = I;
+    sm[1][p][c] = FI;
+    sm[2][p][c] = Pv;
+    sm[3][p][c] = FP;
+  }
+  __syncthreads();
+  // ---- phase 2: carries; warp w < 2 kScanCols scans column w/2 upward (inner) or downward (outer)
+  {
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (w < 2 * kScanCols) {
+      const int cc = w >> 1, dir = w & 1;
+      const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
+      const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
+      double F = 1.0, sv = 0.0;
+      for (int t = t0; t < t1; ++t) {
+        const int pp = dir ? P - 1 - t : t;
+        sv = fma(sm[kF][pp][cc], sv, sm[ks][pp][cc]);
+        F = sm[kF][pp][cc] * F;
+      }
+      affine_scan_up(F, sv, lane);
+      double cin = __shfl_up_sync(0xffffffffu, sv, 1);
+      if (lane == 0) cin = 0.0;
+      for (int t = t0; t < t1; ++t) {
+        const int pp = dir ? P - 1 - t : t;
+        cr[dir][pp][cc] = cin;
+        cin = fma(sm[kF][pp][cc], cin, sm[ks][pp][cc]);
+      }
+    }
+  }
+  __syncthreads();
+  // ---- phase 3: the recurrences with the carries; M (FP64), its BF16 slices, the monopole
+  if (pc >= K_pad || p >= P || i0 >= n_r) return;
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
       M[(long long)i * K_pad + pc] = 0.0;
@@ -606,19 +624,13 @@ __global__ void scan_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk,
     }
     return;
   }
-  const long long rs = (long long)(L + 1) * n_r;
-  const double* at = rad + (long long)l * n_r;
-  const double* bt = rad + rs + (long long)l * n_r;
-  const double* fin = rad + 2 * rs + (long long)l * n_r;
-  const double* fout = rad + 3 * rs + (long long)l * n_r;
-  // outer part first: M_i <- P_{i+1}
-  double Pv = carry[((long long)1 * P + p) * K_pad + pc];
+  double Pv = cr[1][p][c];
   for (int i = i1 - 1; i >= i0; --i) {
     M[(long long)i * K_pad + pc] = Pv;
     const double fo = (i > 0) ? fout[i - 1] : 0.0;
     Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
   }
-  double I = carry[((long long)0 * P + p) * K_pad + pc];
+  double I = cr[0][p][c];
   for (int i = i0; i < i1; ++i) {
     I = fma(at[i], B[(long long)i * K_pad + pc], fin[i] * I);
     const double m = M[(long long)i * K_pad + pc] + I;
@@ -857,8 +869,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   for (const auto& c : cand) s_max = std::max(s_max, c.size());
   std::vector<int2> chunks = cand[0];
   p->tc_S = (int)chunks.size();
-  // chunks of 4 shells for the parallel scans (more for n_r > 4096: at most 1024 chunks, 32 per carry lane)
-  p->tc_scan_chunk = std::max(4, (p->n_r + 1023) / 1024);
+  // chunks of 4 shells for the parallel scans (more for n_r > 512: at most 128 chunks, one CTA column)
+  p->tc_scan_chunk = std::max(4, (p->n_r + 127) / 128);
   p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
 
   const size_t kp = (size_t)p->tc_k_pad;
@@ -1092,18 +1104,12 @@ cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) { return project_with(
 
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   const int P = p->tc_scan_P;
-  dim3 g1((p->tc_k_pad + 127) / 128, P);
-  scan_local_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_pc_l,
-                                       p->tc_part, p->rad, p->tc_cp, p->tc_B, p->tc_summ, p->tc_ef, p->tc_eu,
-                                       p->symmetric ? p->tc_k_even : p->tc_k_pad);
+  scan_fused_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
+      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, P, p->tc_pc_l, p->tc_part, p->rad, p->tc_cp, p->tc_B,
+      p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->G, p->tc_mono, p->tc_ef, p->tc_eu,
+      p->symmetric ? p->tc_k_even : p->tc_k_pad);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  scan_carry_kernel<<<(p->tc_k_pad * 2 + 3) / 4, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  scan_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
-                                       p->tc_B, p->rad, p->tc_carry, p->tc_M, p->tc_ms, p->G, p->tc_mono,
-                                       p->tc_fp16 ? 0 : 1);
-  if ((e = cudaGetLastError()) != cudaSuccess || !p->tc_fp16) return e;
+  if (e != cudaSuccess || !p->tc_fp16) return e;
   slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M, 0,
                                           reinterpret_cast<__half*>(p->tc_ms), p->tc_em);
   return cudaGetLastError();

@@ -93,9 +93,9 @@ def test_grouped_batch_equals_per_field(cuda):
     plans, rhos = _uneven_fields(cuda)
     ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
     with Batch(plans) as b:
-        # 6 fields: field slices + 3 scans (+ M slicing for FP16) per split field,
+        # 6 fields: field slices + one scan (+ M slicing for FP16) per split field,
         # 2 grouped launches for each of the two slice counts, 3 for the FP64 field
-        assert b.launches == 3 * 5 + 4 + 4 + 2 * 2 + 3
+        assert b.launches == 3 * 3 + 2 + 2 + 2 * 2 + 3
         for _ in range(2):
             outs = b.solve(rhos)
             torch.cuda.synchronize()
