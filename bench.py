@@ -47,8 +47,10 @@ def parse():
     ap.add_argument("--n-r", type=int, default=400)
     ap.add_argument("--autotune", action="store_true",
                     help="plans pick their split-K count by timing candidates at create")
-    ap.add_argument("--workload", default="config1", choices=["config1", "config3"],
-                    help="config1: the 1-degree Yin-Yang field (default); config3: a batch of 64 uneven fields")
+    ap.add_argument("--workload", default="config1", choices=["config1", "config2", "config3"],
+                    help="config1: the 1-degree Yin-Yang field (default); config2: 0.5 degree, Nr 800, "
+                         "l_max 64, split precision against the FP64 tensor-core path; "
+                         "config3: a batch of 64 uneven fields")
     return ap.parse_args()
 
 
@@ -263,6 +265,83 @@ def run_config3(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def run_config2(args, ws, rank, local):
+    """0.5-degree Yin-Yang, Nr = 800, l_max = 64 (1.6e8 cells, 4225 columns): the
+    split path timed against the FP64 tensor-core and FP64 CUDA-core paths on
+    the same field, with the error of Phi and of B and M per degree band."""
+    import torch
+
+    from paper_1903_08475_gb300 import Plan, ygs_get_moments, ygs_solve, workloads as W
+    from paper_1903_08475_gb300 import dist as D
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    precision = args.precision or "fp16x3"
+    grid = W.config2_grid()
+    rho = W.lognormal_density_torch(grid, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def timed(plan, steps, out):
+        with torch.cuda.stream(stream):
+            for _ in range(max(1, min(3, args.warmup))):
+                ygs_solve(plan, rho, out, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                ygs_solve(plan, rho, out, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        return D.max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+
+    res = {}
+    outs = {}
+    moments = {}
+    clocks = ClockSampler(local)
+    for prec, steps in ((precision, args.steps), ("fp64tc", 2), ("fp64", 2)):
+        with Plan(grid, prec, device=local) as plan:
+            out = torch.empty_like(rho)
+            if prec == precision:
+                clocks.start()
+                time.sleep(0.3)
+            res[prec] = timed(plan, steps, out)
+            if prec == precision:
+                clk = clocks.stop()
+            ygs_solve(plan, rho, out, stream=stream)
+            B, M = ygs_get_moments(plan, stream=stream)
+            stream.synchronize()
+            outs[prec], moments[prec] = out, (B, M)
+    ref, got = outs["fp64tc"], outs[precision]
+    rel = float(((got - ref).abs() / ref.abs()).max().item())
+    same = bool(torch.equal(outs["fp64"], outs["fp64tc"]))
+
+    def bands(X, Y):
+        errs = []
+        for l in range(grid.l_max + 1):
+            a, b = X[:, l * l:(l + 1) ** 2], Y[:, l * l:(l + 1) ** 2]
+            errs.append(float(torch.linalg.norm(a - b) / max(float(torch.linalg.norm(b)), 1e-300)))
+        return errs
+
+    eB = bands(moments[precision][0], moments["fp64tc"][0])
+    eM = bands(moments[precision][1], moments["fp64tc"][1])
+    ms = res[precision]
+    line = {"metric": "Phi solves/s, 0.5-degree Yin-Yang Nr 800 l_max 64 (config 2)", "value": ws * 1e3 / ms,
+            "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
+            "data": "synthetic", "gcell_per_s": ws * grid.n_cells / (ms / 1e3) / 1e9,
+            "config": {"workload": "yinyang-0.5deg-184x544x2-Nr800-lmax64-lognormal", "cells": grid.n_cells,
+                       "K": grid.K, "precision": precision, "l2": "inputs larger than L2 (rho 1.3 GB)"},
+            "fp64_tensor_solves_per_s": 1e3 / res["fp64tc"], "fp64_cuda_core_solves_per_s": 1e3 / res["fp64"],
+            "speedup_vs_fp64_tensor": res["fp64tc"] / ms, "max_rel_err_phi_vs_fp64_tensor": rel,
+            "fp64_tensor_equals_cuda_core_bitwise": same,
+            "B_rel_err_per_l_band": {l: eB[l] for l in range(0, grid.l_max + 1, 8)},
+            "M_rel_err_per_l_band": {l: eM[l] for l in range(0, grid.l_max + 1, 8)},
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -271,6 +350,9 @@ def main():
         return
     if args.workload == "config3":
         run_config3(args, ws, rank, local)
+        return
+    if args.workload == "config2":
+        run_config2(args, ws, rank, local)
         return
 
     import numpy as np

@@ -561,3 +561,51 @@ def batch_density(grid: Grid, kind: str, seed: int, device="cpu"):
             rho = torch.exp(0.5 * g - 0.125) * prof[:, None]
         parts.append(rho.reshape(-1))
     return torch.cat(parts)
+
+
+def config2_grid() -> Grid:
+    """The config-2 grid (0.5 degree Yin-Yang, Nr = 800, l_max = 64) alone."""
+    return yinyang_grid(184, 544, math.radians(1.0), log_edges(800, 1e-3, 1.0), 64)
+
+
+def lognormal_density_torch(grid: Grid, seed: int = SEED_BASE + 2, n_fft: int = 256, sigma_ln: float = 0.5,
+                            r_core: float = 0.05, device="cpu"):
+    """lognormal_density computed with torch on ``device`` (the same recipe: a
+    unit-variance k^-2 Gaussian field from a seeded n_fft^3 FFT on [-1,1]^3,
+    sampled trilinearly at cell centres, exp(s g - s^2/2) (1 + (r/r_core)^2)^-1.5),
+    for grids of 1e8 cells.  Returns an FP64 tensor."""
+    import torch
+    rng = np.random.default_rng(seed)
+    white = torch.from_numpy(rng.standard_normal((n_fft,) * 3)).to(device)
+    f = torch.fft.rfftn(white)
+    k1 = torch.fft.fftfreq(n_fft, device=device, dtype=torch.float64) * n_fft
+    k3 = torch.fft.rfftfreq(n_fft, device=device, dtype=torch.float64) * n_fft
+    kk = torch.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + k3[None, None, :] ** 2)
+    amp = torch.where(kk > 0, 1.0 / torch.clamp(kk, min=1e-300), torch.zeros_like(kk))
+    g = torch.fft.irfftn(f * amp, s=(n_fft,) * 3)
+    g = (g - g.mean()) / g.std(correction=0)
+    e = grid.edges
+    rc = torch.tensor(0.5 * (e[:-1] + e[1:]), dtype=torch.float64, device=device)
+    parts = []
+    for p in range(grid.n_patch):
+        te = cell_edges_1d(*grid.theta_range[p], int(grid.n_theta[p]))
+        pe = cell_edges_1d(*grid.phi_range[p], int(grid.n_phi[p]))
+        TH, PH = np.meshgrid(0.5 * (te[:-1] + te[1:]), 0.5 * (pe[:-1] + pe[1:]), indexing="ij")
+        d = torch.tensor(local_dirs(TH, PH).reshape(-1, 3) @ rotation_matrix(*grid.euler[p]).T,
+                         dtype=torch.float64, device=device)
+        out = torch.empty(grid.n_r, d.shape[0], dtype=torch.float64, device=device)
+        for i in range(grid.n_r):
+            u = (rc[i] * d + 1.0) * 0.5 * (n_fft - 1)
+            i0 = torch.clamp(torch.floor(u).long(), 0, n_fft - 2)
+            t = torch.clamp(u - i0, 0.0, 1.0)
+            val = torch.zeros(d.shape[0], dtype=torch.float64, device=device)
+            for dx in (0, 1):
+                for dy in (0, 1):
+                    for dz in (0, 1):
+                        wgt = ((t[:, 0] if dx else 1 - t[:, 0]) * (t[:, 1] if dy else 1 - t[:, 1]) *
+                               (t[:, 2] if dz else 1 - t[:, 2]))
+                        val += wgt * g[i0[:, 0] + dx, i0[:, 1] + dy, i0[:, 2] + dz]
+            prof = (1.0 + (rc[i] / r_core) ** 2) ** -1.5
+            out[i] = torch.exp(sigma_ln * val - 0.5 * sigma_ln ** 2) * prof
+        parts.append(out.reshape(-1))
+    return torch.cat(parts)
