@@ -159,8 +159,10 @@ def run_reference(args, ws, rank):
     from paper_1903_08475_gb300 import workloads as W
 
     grid, rho = W.config1(n_r=args.n_r)
-    # shells per step: ~12 ms of 16-core oracle time per shell, so the run stays near a minute
-    n_shells = max(1, min(20, 4000 // max(1, args.steps + args.warmup)))
+    # shells per step: ~4.5 ms of 16-core oracle time per shell plus ~9 ms per call (streaming
+    # U and Q once), sized so the whole run stays near two and a half minutes; more shells per
+    # call amortise the fixed part (16 shells at the default 2000 + 20 steps)
+    n_shells = max(1, min(40, int(150.0 / (max(1, args.steps + args.warmup) * 0.0045))))
     lo = grid.n_r // 2 - n_shells // 2
     sub = W.Grid(**{**grid.__dict__, "edges": grid.edges[lo: lo + n_shells + 1]})
     rho_s = np.concatenate([rho[grid.patch_offset(p) + lo * grid.nang(p): grid.patch_offset(p) + (lo + n_shells) * grid.nang(p)]
