@@ -47,10 +47,10 @@ def parse():
     ap.add_argument("--n-r", type=int, default=400)
     ap.add_argument("--autotune", action="store_true",
                     help="plans pick their split-K count by timing candidates at create")
-    ap.add_argument("--workload", default="config1", choices=["config1", "config2", "config3"],
+    ap.add_argument("--workload", default="config1", choices=["config1", "config2", "config3", "config4"],
                     help="config1: the 1-degree Yin-Yang field (default); config2: 0.5 degree, Nr 800, "
                          "l_max 64, split precision against the FP64 tensor-core path; "
-                         "config3: a batch of 64 uneven fields")
+                         "config3: a batch of 64 uneven fields; config4: forward + adjoint, 1 degree, Nr 256")
     return ap.parse_args()
 
 
@@ -344,6 +344,67 @@ def run_config2(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_config4(args, ws, rank, local):
+    """The adjoint workload (1 degree Yin-Yang, Nr = 256, l_max = 32, w ~ N(0, 1)):
+    one step = Phi = A rho and grad = A^T w (what a gradient of J = sum w Phi
+    costs), split precision against the FP64 adjoint."""
+    import torch
+
+    from paper_1903_08475_gb300 import Plan, ygs_backward, ygs_solve, workloads as W
+    from paper_1903_08475_gb300 import dist as D
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    precision = args.precision or "fp16x3"
+    grid, rho_h, w_h = W.config4()
+    rho = torch.from_numpy(rho_h).to(dev)
+    w = torch.from_numpy(w_h).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def run(plan, steps):
+        phi, g = torch.empty_like(rho), torch.empty_like(rho)
+        with torch.cuda.stream(stream):
+            for _ in range(max(3, args.warmup)):
+                ygs_solve(plan, rho, phi, stream=stream)
+                ygs_backward(plan, w, g, stream=stream)
+        stream.synchronize()
+        t = []
+        for part in ("both", "backward"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                for _ in range(steps):
+                    if part == "both":
+                        ygs_solve(plan, rho, phi, stream=stream)
+                    ygs_backward(plan, w, g, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            t.append(D.max_over_ranks(e0.elapsed_time(e1) / steps, dev))
+        return t, phi, g
+
+    clocks = ClockSampler(local)
+    with Plan(grid, precision, device=local) as plan:
+        clocks.start()
+        time.sleep(0.3)
+        (ms_both, ms_bwd), phi, g = run(plan, args.steps)
+        clk = clocks.stop()
+    with Plan(grid, "fp64", device=local) as p64:
+        (ms64, ms64_bwd), phi64, g64 = run(p64, 2)
+    rel_g = float(((g - g64).abs().max() / g64.abs().max()).item())
+    dot = abs(float((w * phi).sum()) - float((g * rho).sum())) / float((w.abs() * phi.abs()).sum())
+    line = {"metric": "forward + adjoint steps/s, 1 degree Yin-Yang Nr 256 l_max 32 (config 4)",
+            "value": ws * 1e3 / ms_both, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_both, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": precision, "data": "synthetic",
+            "config": {"workload": "yinyang-1deg-92x272x2-Nr256-lmax32-adjoint-w~N(0,1)", "cells": grid.n_cells,
+                       "precision": precision},
+            "backward_ms": ms_bwd, "fp64_step_ms": ms64, "fp64_backward_ms": ms64_bwd,
+            "speedup_vs_fp64": ms64 / ms_both, "adjoint_max_err_vs_fp64_rel_to_max": rel_g,
+            "dot_product_identity_residual": dot, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -355,6 +416,9 @@ def main():
         return
     if args.workload == "config2":
         run_config2(args, ws, rank, local)
+        return
+    if args.workload == "config4":
+        run_config4(args, ws, rank, local)
         return
 
     import numpy as np

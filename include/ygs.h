@@ -249,8 +249,7 @@ ygs_status ygs_debug_wait_timeout(ygs_plan* plan, int spins, void* stream);
  * are not updated.  Errors: as ygs_solve, plus UNSUPPORTED for the limit. */
 ygs_status ygs_solve_static(ygs_plan* plan, const double* d_rho, double* d_phi, void* stream);
 
-/* Number of kernel launches one ygs_solve enqueues (ygs_backward of a split
- * plan enqueues two more: its transposed scans run in three kernels). */
+/* Number of kernel launches one ygs_solve (or ygs_backward) enqueues. */
 int ygs_launches_per_solve(const ygs_plan* plan);
 
 const char* ygs_status_string(ygs_status s);

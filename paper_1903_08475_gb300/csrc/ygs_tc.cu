@@ -484,10 +484,10 @@ __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
   return tc::f32_to_f64(hi) + tc::f32_to_f64(lo);
 }
 
-// Phase 2: carries between chunks.  The chunk summaries define affine maps
-// c -> F c + s; one warp per column and direction composes them: each lane
-// folds up to 32 consecutive chunks, a shuffle scan joins the lanes (inner
-// recurrence upward, outer downward), and each lane walks its chunks again.
+// Carries between chunks.  The chunk summaries define affine maps c -> F c + s;
+// one warp per column and direction composes them: each lane folds up to 32
+// consecutive chunks, this shuffle scan joins the lanes (inner recurrence
+// upward, outer downward), and each lane walks its chunks again.
 __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
   // inclusive scan: after it lane p holds the composition of chunks 0..p
 #pragma unroll
@@ -501,30 +501,6 @@ __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
   }
 }
 
-__global__ void scan_carry_kernel(int K_pad, int P, const double* __restrict__ summ, double* __restrict__ carry) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  const int pc = warp / 2, dir = warp % 2;
-  if (pc >= K_pad) return;
-  // scan order t: chunks upward (inner, dir 0) or downward (outer, dir 1); lane
-  // holds the q consecutive positions [lane q, lane q + q) (P <= 32 q)
-  const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
-  const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
-  double F = 1.0, sv = 0.0;
-  for (int t = t0; t < t1; ++t) {
-    const int p = dir ? P - 1 - t : t;
-    const double Ft = summ[((long long)kF * P + p) * K_pad + pc], st = summ[((long long)ks * P + p) * K_pad + pc];
-    sv = fma(Ft, sv, st);
-    F = Ft * F;
-  }
-  affine_scan_up(F, sv, lane);
-  double c = __shfl_up_sync(0xffffffffu, sv, 1);
-  if (lane == 0) c = 0.0;  // nothing enters the first chunk in scan order
-  for (int t = t0; t < t1; ++t) {
-    const int p = dir ? P - 1 - t : t;
-    carry[((long long)dir * P + p) * K_pad + pc] = c;
-    c = fma(summ[((long long)kF * P + p) * K_pad + pc], c, summ[((long long)ks * P + p) * K_pad + pc]);
-  }
-}
 
 // All three phases in one launch: a CTA owns kScanCols columns and up to
 // kScanMaxP chunks of shells (thread = column + kScanCols * chunk), keeps the
@@ -655,96 +631,112 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
 //   Bbar_i = a_i X_i + b_i Z_{i-1},
 // chunked like the forward scans: the summaries [0] Z at the chunk's end and
 // [1] the product of its fout factors (upward), [2] X at its start and [3] the
-// product of its fin factors (downward), all with zero carry, feed the same
-// carry kernel.
+// product of its fin factors (downward), all with zero carry, are composed by
+// the same carry scan (scan_adj_fused_kernel).
 
-// Phase 1: Mbar from the partials (unscaled by 2^-(ef + ew) with FP16 slices)
-// and the chunk summaries.
-__global__ void scan_adj_local_kernel(int n_r, int K_pad, int L, int S, int chunk, const int* __restrict__ pc_l,
-                                      const float2* __restrict__ part, const double* __restrict__ rad,
-                                      double* __restrict__ Mbar, double* __restrict__ summ,
-                                      const int* __restrict__ ef, const int* __restrict__ ew, int k_split) {
-  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
-  if (pc >= K_pad) return;
-  const int l = pc_l[pc];
+
+
+// The transposed scans in one launch, organised like scan_fused_kernel.
+__global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
+    int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
+    const double* __restrict__ rad, double* __restrict__ Mbar, double* __restrict__ Bbar,
+    __nv_bfloat16* __restrict__ Bs, int nsl, int write_slices, const int* __restrict__ ef,
+    const int* __restrict__ ew, int k_split) {
+  __shared__ double sm[4][kScanMaxP][kScanCols];
+  __shared__ double cr[2][kScanMaxP][kScanCols];
+  const int c = threadIdx.x % kScanCols, p = threadIdx.x / kScanCols;
+  const int pc = blockIdx.x * kScanCols + c;
+  const int l = pc < K_pad ? pc_l[pc] : -1;
   const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
-  const int P = gridDim.y;
-  if (l < 0 || i0 >= n_r) {
-    for (int i = i0; i < i1; ++i) Mbar[(long long)i * K_pad + pc] = 0.0;
-    for (int k = 0; k < 4; ++k) summ[((long long)k * P + p) * K_pad + pc] = (k == 1 || k == 3) ? 1.0 : 0.0;
-    return;
-  }
+  const bool live = l >= 0 && p < P && i0 < n_r;
   const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
-  const double* fin = rad + 2 * rs + (long long)l * n_r;
-  const double* fout = rad + 3 * rs + (long long)l * n_r;
-  double Z = 0.0, FZ = 1.0;
-  for (int i = i0; i < i1; ++i) {
-    float h = 0.f, lo = 0.f;
-    const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
-    for (int z = 0; z < S; ++z) {
-      float2 v = part[z * plane + (long long)i * K_pad + pc];
-      if (efi) {
-        const int es = -(efi[z] + ew[pc]);
-        v.x = tc::mul_pow2f(v.x, es);
-        v.y = tc::mul_pow2f(v.y, es);
+  const int lq = l < 0 ? 0 : l;
+  const double* at = rad + (long long)lq * n_r;
+  const double* bt = rad + rs + (long long)lq * n_r;
+  const double* fin = rad + 2 * rs + (long long)lq * n_r;
+  const double* fout = rad + 3 * rs + (long long)lq * n_r;
+  // ---- phase 1: Mbar from the partials, chains with zero carry, summaries
+  {
+    double Z = 0.0, FZ = 1.0, X = 0.0, FX = 1.0;
+    if (live) {
+      for (int i = i0; i < i1; ++i) {
+        float h = 0.f, lo = 0.f;
+        const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
+        for (int z = 0; z < S; ++z) {
+          float2 v = part[z * plane + (long long)i * K_pad + pc];
+          if (efi) {
+            const int es = -(efi[z] + ew[pc]);
+            v.x = tc::mul_pow2f(v.x, es);
+            v.y = tc::mul_pow2f(v.y, es);
+          }
+          float s2, e;
+          tc::two_sum(h, v.x, s2, e);
+          h = s2;
+          lo += e + v.y;
+        }
+        const double m = ff_to_f64(h, lo);
+        Mbar[(long long)i * K_pad + pc] = m;
+        const double hz = (i > 0) ? fout[i - 1] : 0.0;
+        Z = fma(hz, Z, m);
+        FZ *= hz;
       }
-      float s, e;
-      tc::two_sum(h, v.x, s, e);
-      h = s;
-      lo += e + v.y;
+      for (int i = i1 - 1; i >= i0; --i) {
+        const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
+        X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
+        FX *= gx;
+      }
+    } else if (pc < K_pad && l < 0) {
+      for (int i = i0; i < i1; ++i) Mbar[(long long)i * K_pad + pc] = 0.0;
     }
-    const double m = ff_to_f64(h, lo);
-    Mbar[(long long)i * K_pad + pc] = m;
-    const double hz = (i > 0) ? fout[i - 1] : 0.0;
-    Z = fma(hz, Z, m);
-    FZ *= hz;
+    if (p < kScanMaxP) {
+      sm[0][p][c] = Z;
+      sm[1][p][c] = FZ;
+      sm[2][p][c] = X;
+      sm[3][p][c] = FX;
+    }
   }
-  double X = 0.0, FX = 1.0;
-  for (int i = i1 - 1; i >= i0; --i) {
-    const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
-    X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
-    FX *= gx;
+  __syncthreads();
+  // ---- phase 2: carries (Z upward, X downward)
+  {
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (w < 2 * kScanCols) {
+      const int cc = w >> 1, dir = w & 1;
+      const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
+      const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
+      double F = 1.0, sv = 0.0;
+      for (int t = t0; t < t1; ++t) {
+        const int pp = dir ? P - 1 - t : t;
+        sv = fma(sm[kF][pp][cc], sv, sm[ks][pp][cc]);
+        F = sm[kF][pp][cc] * F;
+      }
+      affine_scan_up(F, sv, lane);
+      double cin = __shfl_up_sync(0xffffffffu, sv, 1);
+      if (lane == 0) cin = 0.0;
+      for (int t = t0; t < t1; ++t) {
+        const int pp = dir ? P - 1 - t : t;
+        cr[dir][pp][cc] = cin;
+        cin = fma(sm[kF][pp][cc], cin, sm[ks][pp][cc]);
+      }
+    }
   }
-  summ[((long long)0 * P + p) * K_pad + pc] = Z;
-  summ[((long long)1 * P + p) * K_pad + pc] = FZ;
-  summ[((long long)2 * P + p) * K_pad + pc] = X;
-  summ[((long long)3 * P + p) * K_pad + pc] = FX;
-}
-
-// Phase 3: the transposed recurrences with the carries; Bbar in FP64 and, for
-// BF16 operands, its slices (the B operand of the adjoint synthesis).
-__global__ void scan_adj_final_kernel(int n_r, int K_pad, int L, int nsl, int chunk, const int* __restrict__ pc_l,
-                                      const double* __restrict__ Mbar, const double* __restrict__ rad,
-                                      const double* __restrict__ carry, double* __restrict__ Bbar,
-                                      __nv_bfloat16* __restrict__ Bs, int write_slices) {
-  const int pc = blockIdx.x * blockDim.x + threadIdx.x;
-  const int p = blockIdx.y;
-  const int P = gridDim.y;
-  if (pc >= K_pad) return;
-  const int l = pc_l[pc];
-  const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
-  const long long splane = (long long)n_r * K_pad;
+  __syncthreads();
+  // ---- phase 3: Bbar_i = a_i X_i + b_i Z_{i-1} with the carries, and its BF16 slices
+  if (pc >= K_pad || p >= P || i0 >= n_r) return;
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
       Bbar[(long long)i * K_pad + pc] = 0.0;
       if (write_slices)
-        for (int k = 0; k < nsl; ++k) Bs[k * splane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
+        for (int k = 0; k < nsl; ++k) Bs[k * plane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
     }
     return;
   }
-  const long long rs = (long long)(L + 1) * n_r;
-  const double* at = rad + (long long)l * n_r;
-  const double* bt = rad + rs + (long long)l * n_r;
-  const double* fin = rad + 2 * rs + (long long)l * n_r;
-  const double* fout = rad + 3 * rs + (long long)l * n_r;
-  double X = carry[((long long)1 * P + p) * K_pad + pc];  // X_{i1}
+  double X = cr[1][p][c];  // X_{i1}
   for (int i = i1 - 1; i >= i0; --i) {
     const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
     X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
     Bbar[(long long)i * K_pad + pc] = at[i] * X;
   }
-  double Z = carry[((long long)0 * P + p) * K_pad + pc];  // Z_{i0-1}
+  double Z = cr[0][p][c];  // Z_{i0-1}
   for (int i = i0; i < i1; ++i) {
     const double b = fma(bt[i], Z, Bbar[(long long)i * K_pad + pc]);
     Bbar[(long long)i * K_pad + pc] = b;
@@ -753,7 +745,7 @@ __global__ void scan_adj_final_kernel(int n_r, int K_pad, int L, int nsl, int ch
     if (write_slices) {
       __nv_bfloat16 sl[3];
       slices_of(b, nsl, sl);
-      for (int k = 0; k < nsl; ++k) Bs[k * splane + (long long)i * K_pad + pc] = sl[k];
+      for (int k = 0; k < nsl; ++k) Bs[k * plane + (long long)i * K_pad + pc] = sl[k];
     }
   }
 }
@@ -1162,17 +1154,10 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if ((e = project_with(p, p->tc_map_qt, s)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
-  const int P = p->tc_scan_P;
-  dim3 g1((p->tc_k_pad + 127) / 128, P);
-  scan_adj_local_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_pc_l,
-                                           p->tc_part, p->rad, p->tc_Mbar, p->tc_summ, p->tc_ef, p->tc_eqt,
-                                           p->symmetric ? p->tc_k_even : p->tc_k_pad);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  scan_carry_kernel<<<(p->tc_k_pad * 2 + 3) / 4, 128, 0, s>>>(p->tc_k_pad, P, p->tc_summ, p->tc_carry);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  scan_adj_final_kernel<<<g1, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_nsl, p->tc_scan_chunk, p->tc_pc_l,
-                                           p->tc_Mbar, p->rad, p->tc_carry, p->tc_Bbar, p->tc_ms,
-                                           p->tc_fp16 ? 0 : 1);
+  scan_adj_fused_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
+      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part, p->rad,
+      p->tc_Mbar, p->tc_Bbar, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->tc_ef, p->tc_eqt,
+      p->symmetric ? p->tc_k_even : p->tc_k_pad);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p->tc_fp16) {
     slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_Bbar, 1,
