@@ -33,6 +33,7 @@ METRIC = "Φ solves/s & Gcell/s at l_max; split-prec vs FP64 GPU at ≤1e-6 rel 
 def workload_name(n_r: int) -> str:
     return f"yinyang-1deg-92x272x2-Nr{n_r}-lmax32-ellipsoid+3blobs"
 NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), profiling recipe table
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # derived from the SM count, FP32 lanes and max clock
 
 
 def parse():
@@ -488,18 +489,20 @@ def main():
     info = plan.info
     sym = info["symmetric"] == 1
     nang_eff = grid.nang(0) if sym else grid.nang_total
-    nprod = {"fp64": 1, "fp64tc": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}[precision]
+    nprod = {"fp64": 1, "fp64tc": 1, "fp32": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}[precision]
     # algorithmic FLOPs of one contraction: one FMA per (shell, stored cell, column) and slice product
     flops_gemm = 2.0 * nprod * grid.n_r * nang_eff * grid.K
     per = [x / max(ncalls, 1) for x in phase_ms]
     names = ["field_slices", "projection", "radial_scan", "synthesis"]
     dom = int(np.argmax(per))
-    if precision in ("fp64", "fp64tc"):
+    if precision in ("fp64", "fp64tc", "fp32"):
         flops = [0.0, flops_gemm, 0.0, flops_gemm][dom]
         achieved = flops / (per[dom] / 1e3) / 1e12
-        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 rate of the profiling recipe (no measured FP64 peak)",
+        pk = NOMINAL_FP32_TFLOPS if precision == "fp32" else NOMINAL_FP64_TFLOPS
+        src = ("FP32 lanes: 152 SMs x 128 x 2 FLOP x 2.07 GHz (recipe's unit counts and clock)"
+               if precision == "fp32" else "nominal FP64 rate of the profiling recipe (no measured FP64 peak)")
+        roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None, "peak_source": src,
                 "phase_ms": dict(zip(names, per))}
     else:
         if dom in (1, 3):
@@ -543,7 +546,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if precision in ("fp64", "fp64tc") else precision, "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp64tc": "f64", "fp32": "f32"}.get(precision, precision), "data": "synthetic",
             "gcell_per_s": value * grid.n_cells / 1e9,
             "config": {"workload": workload_name(grid.n_r), "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
                        "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"], "autotune": args.autotune,

@@ -81,8 +81,11 @@ typedef enum {
   YGS_FP16X3 = 3, /* tcgen05 FP16 tensor cores, 2-slice operands (22 significant bits), 3 products;
                      every operand row is scaled by a power of two into FP16's range (U per
                      column, the field and M per shell, Q as a whole) and unscaled exactly */
-  YGS_FP64_TC = 4 /* the FP64 path with its contractions on the FP64 tensor cores (DMMA 8x8x4):
+  YGS_FP64_TC = 4, /* the FP64 path with its contractions on the FP64 tensor cores (DMMA 8x8x4):
                      FP64 products and sums, another order of additions */
+  YGS_FP32 = 5     /* FP32 contractions on the CUDA cores (FP32 copies of U and Q, the field
+                     truncated to FP32, FP32 accumulation), FP64 radial scans; the adjoint of
+                     such a plan runs on its FP64 weights */
 } ygs_precision;
 
 typedef enum {

@@ -67,7 +67,8 @@ void free_plan(ygs_plan* p) {
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
   tc_free(p);
   void* bufs[] = {p->U, p->Q, p->rad, p->col_l, p->col_nat, p->chunks, p->part, p->B, p->M,
-                  p->Mbar, p->Bbar, p->d_err, p->h2d_rho, p->h2d_phi};
+                  p->Mbar, p->Bbar, p->d_err, p->h2d_rho, p->h2d_phi, p->U32, p->Q32, p->f32_field,
+                  p->part32, p->M32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -142,7 +143,7 @@ ygs_status validate_desc(const ygs_desc* d) {
     return fail(YGS_ERR_INVALID_ARG, "l_max must be in [0, " + std::to_string(kMaxLmax) + "]");
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
-  if (d->precision < YGS_FP64 || d->precision > YGS_FP64_TC) return fail(YGS_ERR_INVALID_ARG, "bad precision");
+  if (d->precision < YGS_FP64 || d->precision > YGS_FP32) return fail(YGS_ERR_INVALID_ARG, "bad precision");
   if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;
@@ -358,6 +359,21 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
     st = tc_setup(p, sms);
     if (st != YGS_OK) return fail_free(st);
   }
+  if (p->precision == YGS_FP32) {
+    const size_t wn = (size_t)p->nang_wtotal * p->K, kn = (size_t)p->n_r * p->K;
+    if ((e = al((void**)&p->U32, wn * sizeof(float))) != cudaSuccess ||
+        (e = al((void**)&p->Q32, wn * sizeof(float))) != cudaSuccess ||
+        (e = al((void**)&p->f32_field, (size_t)p->n_cells * sizeof(float))) != cudaSuccess ||
+        (e = al((void**)&p->part32, (size_t)p->S * kn * sizeof(float))) != cudaSuccess ||
+        (e = al((void**)&p->M32, kn * sizeof(float))) != cudaSuccess)
+      return fail_free(cuda_fail(e, "cudaMalloc FP32 operands"));
+    if ((e = launch_to_f32(p->U, p->U32, (long long)wn, false, 0)) != cudaSuccess ||
+        (e = launch_to_f32(p->Q, p->Q32, (long long)wn, false, 0)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess)
+      return fail_free(cuda_fail(e, "FP32 weights"));
+    p->weight_bytes += (long long)(2 * wn * sizeof(float));
+    p->work_bytes += (long long)(((size_t)p->n_cells + (size_t)(p->S + 1) * kn) * sizeof(float));
+  }
   *out = p;
   return YGS_OK;
 }
@@ -404,12 +420,16 @@ ygs_status ygs_solve(ygs_plan* p, const double* d_rho, double* d_phi, void* stre
     if (ev) API_TRY(cudaEventRecord(ev[3], s));
     API_TRY(tc_synthesize(p, d_phi, s));
   } else {
-    if (ev) API_TRY(cudaEventRecord(ev[1], s));
-    API_TRY(launch_project_fp64(p, d_rho, p->U, p->part, s));
-    if (ev) API_TRY(cudaEventRecord(ev[2], s));
-    API_TRY(launch_scan_fwd(p, p->part, p->S, p->B, p->M, s));
-    if (ev) API_TRY(cudaEventRecord(ev[3], s));
-    API_TRY(launch_synth_fp64(p, p->M, p->Q, d_phi, s));
+    if (p->precision == YGS_FP32) {
+      API_TRY(solve_fp32(p, d_rho, d_phi, s, ev));
+    } else {
+      if (ev) API_TRY(cudaEventRecord(ev[1], s));
+      API_TRY(launch_project_fp64(p, d_rho, p->U, p->part, s));
+      if (ev) API_TRY(cudaEventRecord(ev[2], s));
+      API_TRY(launch_scan_fwd(p, p->part, p->S, p->B, p->M, s));
+      if (ev) API_TRY(cudaEventRecord(ev[3], s));
+      API_TRY(launch_synth_fp64(p, p->M, p->Q, d_phi, s));
+    }
   }
   if (ev) API_TRY(cudaEventRecord(ev[4], s));
   return YGS_OK;
@@ -656,7 +676,9 @@ ygs_status ygs_debug_wait_timeout(ygs_plan* p, int spins, void* stream) {
   return YGS_OK;
 }
 
-int ygs_launches_per_solve(const ygs_plan* p) { return p ? (p->tc_nsl ? (p->tc_fp16 ? 5 : 4) : 3) : 0; }
+int ygs_launches_per_solve(const ygs_plan* p) {
+  return p ? (p->tc_nsl ? (p->tc_fp16 ? 5 : 4) : (p->precision == YGS_FP32 ? 5 : 3)) : 0;
+}
 
 ygs_status ygs_get_status(ygs_plan* p) {
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");

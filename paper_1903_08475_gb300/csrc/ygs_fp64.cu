@@ -1,4 +1,4 @@
-// FP64 contractions and FP64 radial scans (steps 2-5 of Sect. 4.3).
+// FP64 (and FP32 CUDA-core) contractions and FP64 radial scans (steps 2-5 of Sect. 4.3).
 //
 // Projection  part[z][i][c] = sum_{a in chunk z} field(g_z, i, a) * W[a][c]
 //   (Eq. B_CS; the split-K chunks z are the GPU image of the paper's
@@ -14,6 +14,8 @@
 // even-m first, the projection contracts (rho_Yin +- rho_Yang) against the
 // even / odd column blocks, and the synthesis writes Phi_Yin = E + O and
 // Phi_Yang = E - O from the even and odd partial sums: half the arithmetic.
+#include <type_traits>
+
 #include "ygs_internal.h"
 
 namespace ygs {
@@ -35,16 +37,15 @@ __device__ __forceinline__ void dmma_8x8x4(double& d0, double& d1, double a, dou
 // block of 2 x 4 DMMA tiles; acc[2 mb + i][nb] is element i of the lane's pair
 // in tile (mb, nb) (tile_out gives the position).  Both keep FP64 products and
 // FP64 accumulation; only the order of the additions differs.
-template <bool TC>
-__device__ __forceinline__ void tile_step(const double (&As)[BK][BM + 1], const double (&Bs)[BK][BN + 1],
-                                          double (&acc)[4][4]) {
+template <typename T, bool TC>
+__device__ __forceinline__ void tile_step(const T (&As)[BK][BM + 1], const T (&Bs)[BK][BN + 1], T (&acc)[4][4]) {
   const int tid = threadIdx.x;
-  if (TC) {
+  if constexpr (TC) {
     const int lane = tid % 32, w = tid / 32, g = lane >> 2, t4 = lane & 3;
     const int wr = (w >> 1) * 16, wc = (w & 1) * 32;
 #pragma unroll
     for (int k0 = 0; k0 < BK; k0 += 4) {
-      double av[2], bv[4];
+      T av[2], bv[4];
 #pragma unroll
       for (int mb = 0; mb < 2; ++mb) av[mb] = As[k0 + t4][wr + mb * 8 + g];
 #pragma unroll
@@ -58,7 +59,7 @@ __device__ __forceinline__ void tile_step(const double (&As)[BK][BM + 1], const 
     const int tx = tid % 16, ty = tid / 16;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double av[4], bv[4];
+      T av[4], bv[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
 #pragma unroll
@@ -85,50 +86,51 @@ __device__ __forceinline__ void tile_out(int r, int q, int& row, int& col) {
   }
 }
 
+template <typename T>
 struct ProjArgs {
   int n_r, K, K_even, tiles_e, symmetric;
-  const double* field;
-  const double* W;
-  double* part;
+  const T* field;
+  const T* W;
+  T* part;
   const Chunk* chunks;
   PatchTable pt;
 };
 
-template <bool TC>
-__global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+template <typename T, bool TC>
+__global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs<T> a) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
   int c0, c1;
-  double sgn;
+  T sgn;
   if (tn < a.tiles_e) {
     c0 = tn * BN;
     c1 = min(a.K_even, c0 + BN);
-    sgn = 1.0;
+    sgn = T(1);
   } else {
     c0 = a.K_even + (tn - a.tiles_e) * BN;
     c1 = min(a.K, c0 + BN);
-    sgn = -1.0;
+    sgn = T(-1);
   }
   const int i0 = tm * BM;
   const Chunk ch = a.chunks[z];
   const long long lda = a.pt.nang[ch.g];
-  const double* A0 = a.field + a.pt.fld_off[ch.g];
-  const double* A1 = a.symmetric ? a.field + a.pt.fld_off[1] : nullptr;
-  const double* Wg = a.W + a.pt.ang_off[ch.g] * (long long)a.K;
-  double acc[4][4];
+  const T* A0 = a.field + a.pt.fld_off[ch.g];
+  const T* A1 = a.symmetric ? a.field + a.pt.fld_off[1] : nullptr;
+  const T* Wg = a.W + a.pt.ang_off[ch.g] * (long long)a.K;
+  T acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
+    for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
 
   for (int k0 = ch.a0; k0 < ch.a1; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, row = e / BK, kk = e % BK;
       int i = i0 + row, k = k0 + kk;
-      double v = 0.0;
+      T v = T(0);
       if (i < a.n_r && k < ch.a1) {
         v = A0[i * lda + k];
         if (A1) v += sgn * A1[i * lda + k];
@@ -139,13 +141,13 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, kk = e / BN, col = e % BN;
       int k = k0 + kk, c = c0 + col;
-      Bs[kk][col] = (k < ch.a1 && c < c1) ? Wg[(long long)k * a.K + c] : 0.0;
+      Bs[kk][col] = (k < ch.a1 && c < c1) ? Wg[(long long)k * a.K + c] : T(0);
     }
     __syncthreads();
-    tile_step<TC>(As, Bs, acc);
+    tile_step<T, TC>(As, Bs, acc);
     __syncthreads();
   }
-  double* out = a.part + (long long)z * a.n_r * a.K;
+  T* out = a.part + (long long)z * a.n_r * a.K;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -157,55 +159,56 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs a) {
     }
 }
 
+template <typename T>
 struct SynthArgs {
   int n_r, K, K_even, symmetric;
-  const double* X;
-  const double* W;
+  const T* X;
+  const T* W;
   double* out;
   PatchTable pt;
 };
 
-template <bool TC>
-__device__ inline void synth_range(const SynthArgs& s, const double* Wg, long long nang, int i0, int a0, int k_lo,
-                                   int k_hi, double (&As)[BK][BM + 1], double (&Bs)[BK][BN + 1], double (&acc)[4][4]) {
+template <typename T, bool TC>
+__device__ inline void synth_range(const SynthArgs<T>& s, const T* Wg, long long nang, int i0, int a0, int k_lo,
+                                   int k_hi, T (&As)[BK][BM + 1], T (&Bs)[BK][BN + 1], T (&acc)[4][4]) {
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int k0 = k_lo; k0 < k_hi; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, row = e / BK, kk = e % BK;
       int i = i0 + row, k = k0 + kk;
-      As[kk][row] = (i < s.n_r && k < k_hi) ? s.X[(long long)i * s.K + k] : 0.0;
+      As[kk][row] = (i < s.n_r && k < k_hi) ? s.X[(long long)i * s.K + k] : T(0);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, n = e / BK, kk = e % BK;
       int a = a0 + n, k = k0 + kk;
-      Bs[kk][n] = (a < nang && k < k_hi) ? Wg[(long long)a * s.K + k] : 0.0;
+      Bs[kk][n] = (a < nang && k < k_hi) ? Wg[(long long)a * s.K + k] : T(0);
     }
     __syncthreads();
-    tile_step<TC>(As, Bs, acc);
+    tile_step<T, TC>(As, Bs, acc);
     __syncthreads();
   }
 }
 
-template <bool TC>
-__global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs s) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+template <typename T, bool TC>
+__global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs<T> s) {
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
   const int g = blockIdx.z;
   const long long nang = s.pt.nang[g];
   const int a0 = blockIdx.x * BN;
   if (a0 >= nang) return;
   const int i0 = blockIdx.y * BM;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const double* Wg = s.W + s.pt.ang_off[g] * (long long)s.K;
-  double ae[4][4], ao[4][4];
+  const T* Wg = s.W + s.pt.ang_off[g] * (long long)s.K;
+  T ae[4][4], ao[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) ae[r][q] = ao[r][q] = 0.0;
-  synth_range<TC>(s, Wg, nang, i0, a0, 0, s.K_even, As, Bs, ae);
-  if (s.K_even < s.K) synth_range<TC>(s, Wg, nang, i0, a0, s.K_even, s.K, As, Bs, ao);
+    for (int q = 0; q < 4; ++q) ae[r][q] = ao[r][q] = T(0);
+  synth_range<T, TC>(s, Wg, nang, i0, a0, 0, s.K_even, As, Bs, ae);
+  if (s.K_even < s.K) synth_range<T, TC>(s, Wg, nang, i0, a0, s.K_even, s.K, As, Bs, ao);
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -216,15 +219,16 @@ __global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs s) {
       long long a = a0 + col;
       if (i >= s.n_r || a >= nang) continue;
       if (s.symmetric) {
-        s.out[s.pt.fld_off[0] + i * nang + a] = ae[r][q] + ao[r][q];
-        s.out[s.pt.fld_off[1] + i * nang + a] = ae[r][q] - ao[r][q];
+        s.out[s.pt.fld_off[0] + i * nang + a] = (double)(ae[r][q] + ao[r][q]);
+        s.out[s.pt.fld_off[1] + i * nang + a] = (double)(ae[r][q] - ao[r][q]);
       } else {
-        s.out[s.pt.fld_off[g] + i * nang + a] = ae[r][q] + ao[r][q];
+        s.out[s.pt.fld_off[g] + i * nang + a] = (double)(ae[r][q] + ao[r][q]);
       }
     }
 }
 
-__global__ void scan_fwd_kernel(int n_r, int K, int L, const int* __restrict__ col_l, const double* __restrict__ part,
+template <typename T>
+__global__ void scan_fwd_kernel(int n_r, int K, int L, const int* __restrict__ col_l, const T* __restrict__ part,
                                 int S, const double* __restrict__ rad, double* __restrict__ B, double* __restrict__ M) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= K) return;
@@ -236,7 +240,7 @@ __global__ void scan_fwd_kernel(int n_r, int K, int L, const int* __restrict__ c
   const double* fout = rad + 3 * rs + (long long)l * n_r;
   for (int i = 0; i < n_r; ++i) {
     double b = 0.0;
-    for (int z = 0; z < S; ++z) b += part[z * plane + (long long)i * K + c];
+    for (int z = 0; z < S; ++z) b += (double)part[z * plane + (long long)i * K + c];
     B[(long long)i * K + c] = b;
   }
   double O = 0.0;
@@ -294,9 +298,11 @@ __global__ void unpermute_kernel(int n_r, int K, const int* __restrict__ col_nat
 
 }  // namespace
 
-cudaError_t launch_project_fp64(const ygs_plan* p, const double* field, const double* W, double* part,
-                                cudaStream_t s) {
-  ProjArgs a;
+namespace {
+
+template <typename T>
+cudaError_t project_t(const ygs_plan* p, const T* field, const T* W, T* part, bool tc, cudaStream_t s) {
+  ProjArgs<T> a;
   a.n_r = p->n_r;
   a.K = p->K;
   a.K_even = p->K_even;
@@ -309,15 +315,19 @@ cudaError_t launch_project_fp64(const ygs_plan* p, const double* field, const do
   a.pt = p->pt;
   int tiles_o = (p->K - p->K_even + BN - 1) / BN;
   dim3 grid(a.tiles_e + tiles_o, (p->n_r + BM - 1) / BM, p->S);
-  if (p->precision == YGS_FP64_TC)
-    proj_fp64_kernel<true><<<grid, NT, 0, s>>>(a);
-  else
-    proj_fp64_kernel<false><<<grid, NT, 0, s>>>(a);
+  if constexpr (std::is_same<T, double>::value) {
+    if (tc) {
+      proj_fp64_kernel<T, true><<<grid, NT, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  proj_fp64_kernel<T, false><<<grid, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* W, double* out, cudaStream_t s) {
-  SynthArgs a;
+template <typename T>
+cudaError_t synth_t(const ygs_plan* p, const T* X, const T* W, double* out, bool tc, cudaStream_t s) {
+  SynthArgs<T> a;
   a.n_r = p->n_r;
   a.K = p->K;
   a.K_even = p->K_even;
@@ -329,16 +339,69 @@ cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* 
   long long nmax = 0;
   for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
   dim3 grid((unsigned)((nmax + BN - 1) / BN), (p->n_r + BM - 1) / BM, p->n_wpatch);
-  if (p->precision == YGS_FP64_TC)
-    synth_fp64_kernel<true><<<grid, NT, 0, s>>>(a);
-  else
-    synth_fp64_kernel<false><<<grid, NT, 0, s>>>(a);
+  if constexpr (std::is_same<T, double>::value) {
+    if (tc) {
+      synth_fp64_kernel<T, true><<<grid, NT, 0, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  synth_fp64_kernel<T, false><<<grid, NT, 0, s>>>(a);
   return cudaGetLastError();
 }
 
+// FP64 -> FP32: round to nearest for the weights (once per plan), truncation
+// by integer operations for per-solve data (GB300 converts FP64 on its narrow
+// FP64 pipe); exponents outside FP32's normal range flush to zero / infinity.
+__global__ void to_f32_kernel(const double* __restrict__ in, float* __restrict__ out, long long n, int trunc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double x = in[e];
+    if (!trunc) {
+      out[e] = __double2float_rn(x);
+      continue;
+    }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 63) << 31;
+    const int ex = (int)((b >> 52) & 0x7FF) - 1023;
+    out[e] = ex < -126 ? __int_as_float((int)sign)
+                       : ex > 127 ? __int_as_float((int)(sign | 0x7F800000u))
+                                  : __int_as_float((int)(sign | ((unsigned int)(ex + 127) << 23) |
+                                                         (unsigned int)((b >> 29) & 0x7FFFFFu)));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_project_fp64(const ygs_plan* p, const double* field, const double* W, double* part,
+                                cudaStream_t s) {
+  return project_t<double>(p, field, W, part, p->precision == YGS_FP64_TC, s);
+}
+
+cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* W, double* out, cudaStream_t s) {
+  return synth_t<double>(p, X, W, out, p->precision == YGS_FP64_TC, s);
+}
+
 cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double* B, double* M, cudaStream_t s) {
-  scan_fwd_kernel<<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, part, S, p->rad, B, M);
+  scan_fwd_kernel<double><<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, part, S, p->rad, B, M);
   return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(const double* in, float* out, long long n, bool trunc, cudaStream_t s) {
+  to_f32_kernel<<<(int)std::min<long long>(4096, (n + 255) / 256), 256, 0, s>>>(in, out, n, trunc ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t solve_fp32(const ygs_plan* p, const double* rho, double* phi, cudaStream_t s, cudaEvent_t* ev) {
+  cudaError_t e;
+  if ((e = launch_to_f32(rho, p->f32_field, p->n_cells, true, s)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
+  if ((e = project_t<float>(p, p->f32_field, p->U32, p->part32, false, s)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+  scan_fwd_kernel<float><<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, p->part32, p->S, p->rad,
+                                                         p->B, p->M);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_to_f32(p->M, p->M32, (long long)p->n_r * p->K, false, s)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+  return synth_t<float>(p, p->M32, p->Q32, phi, false, s);
 }
 
 cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s) {

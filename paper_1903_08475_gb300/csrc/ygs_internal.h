@@ -57,6 +57,8 @@ struct ygs_plan {
   double* part = nullptr;   // [S][n_r][K] projection partials
   double* B = nullptr;      // [n_r][K]
   double* M = nullptr;      // [n_r][K]
+  // FP32 CUDA-core path (YGS_FP32): FP32 copies of the weights, the field, partials and M
+  float *U32 = nullptr, *Q32 = nullptr, *f32_field = nullptr, *part32 = nullptr, *M32 = nullptr;
   double* Mbar = nullptr;   // [n_r][K] adjoint workspace
   double* Bbar = nullptr;   // [n_r][K] adjoint workspace
   double* h2d_rho = nullptr;  // device staging for ygs_solve_host
@@ -135,6 +137,10 @@ cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double
 cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s);
 // out[i][col_nat[c]] = in[i][c]
 cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// FP64 -> FP32 (rounded, or truncated by integer operations)
+cudaError_t launch_to_f32(const double* in, float* out, long long n, bool trunc, cudaStream_t s);
+// The FP32 CUDA-core solve (YGS_FP32): FP32 contractions, FP64 scans; ev optional phase events 1..3
+cudaError_t solve_fp32(const ygs_plan* p, const double* rho, double* phi, cudaStream_t s, cudaEvent_t* ev);
 
 // ---- split-precision tensor-core path (ygs_tc.cu) --------------------------
 ygs_status tc_setup(ygs_plan* p, int sms);     // slices, tensor maps, workspaces (at create)

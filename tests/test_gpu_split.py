@@ -123,3 +123,19 @@ def test_autotuned_split_k(cuda, precision):
             phi = ygs_solve(p, torch.from_numpy(rho).cuda())
             torch.cuda.synchronize()
             assert rel_max(phi.cpu().numpy(), ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("name", ["yy_ragged", "three_patch", "many_shells"])
+def test_fp32_cuda_core_variant(cuda, name):
+    """YGS_FP32: FP32 contractions on the CUDA cores with FP64 scans; its error
+    against the oracle is that of FP32 accumulation (stated, held to 1e-4)."""
+    import torch
+    grid = CASES[name]()
+    rho = W.random_density(grid, 17)
+    ref = oracle.solve(grid, rho)
+    with Plan(grid, "fp32") as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        torch.cuda.synchronize()
+        err = rel_max(phi.cpu().numpy(), ref)
+    print(f"fp32 {name}: {err:.2e}")
+    assert err <= 1e-4
