@@ -1059,6 +1059,15 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   return cudaGetLastError();
 }
 
+// The synthesis flushes its accumulators every 128 k-elements: its terms change
+// sign (the monopole, the one coherent sum, is added exactly in the epilogue),
+// so the FP32 accumulation drifts less than in the projection, whose
+// monopole column sums positive terms and keeps 64.  (Measured on config 1:
+// 2.1e-7 -> 3.4e-7 against FP64 at 128, 5.4e-7 at 256.)
+#ifndef YGS_SYNTH_FLUSH_K
+#define YGS_SYNTH_FLUSH_K 128
+#endif
+
 static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.err = p->d_err;
   a.ab_fmt = p->tc_fp16 ? 0 : 1;
@@ -1110,6 +1119,7 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
 static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono, int q_exp) {
   a = TcArgs{};
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
+  a.flush_kb = std::max(1, YGS_SYNTH_FLUSH_K / tc::BK);
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;
