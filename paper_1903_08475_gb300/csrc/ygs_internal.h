@@ -157,7 +157,7 @@ namespace tc {
 struct TcProblem;
 }
 struct TcBatchGroup {
-  int nsl = 0, flush = 1, sms = 0, total_p = 0, total_s = 0;
+  int nsl = 0, flush = 1, flush_s = 1, sms = 0, total_p = 0, total_s = 0;  // flush: projection / synthesis k-blocks
   std::vector<ygs_plan*> members;
   tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
   int *d_start_p = nullptr, *d_start_s = nullptr;

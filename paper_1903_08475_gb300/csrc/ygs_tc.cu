@@ -1059,11 +1059,12 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   return cudaGetLastError();
 }
 
-// The synthesis flushes its accumulators every 128 k-elements: its terms change
-// sign (the monopole, the one coherent sum, is added exactly in the epilogue),
-// so the FP32 accumulation drifts less than in the projection, whose
-// monopole column sums positive terms and keeps 64.  (Measured on config 1:
-// 2.1e-7 -> 3.4e-7 against FP64 at 128, 5.4e-7 at 256.)
+// The forward synthesis flushes its accumulators every 128 k-elements: its
+// terms change sign (the monopole, the one coherent sum, is added exactly in
+// the epilogue), so the FP32 accumulation drifts less than in the projection
+// (and the adjoint's synthesis with U), whose monopole column sums positive
+// terms and keeps 64.  (Measured on config 1: 2.1e-7 -> 3.4e-7 against FP64 at
+// 128, 5.4e-7 at 256.)
 #ifndef YGS_SYNTH_FLUSH_K
 #define YGS_SYNTH_FLUSH_K 128
 #endif
@@ -1119,7 +1120,9 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
 static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono, int q_exp) {
   a = TcArgs{};
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
-  a.flush_kb = std::max(1, YGS_SYNTH_FLUSH_K / tc::BK);
+  // the forward synthesis excludes the monopole (added exactly) and may flush less
+  // often; the adjoint's U has a positive monopole column and keeps 64
+  a.flush_kb = std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / tc::BK);
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;
@@ -1209,6 +1212,7 @@ ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
       sp[k + 1] = sp[k] + proj[k].args.total_tiles;
       ss[k + 1] = ss[k] + syn[k].args.total_tiles;
       G.flush = proj[k].args.flush_kb;
+      G.flush_s = syn[k].args.flush_kb;
     }
     G.total_p = sp.back();
     G.total_s = ss.back();
@@ -1253,7 +1257,7 @@ cudaError_t tc_batch_synthesize(const TcBatchGroup& G, double* const* phi, cudaS
   tc::TcPhiList out{};
   for (size_t k = 0; k < G.members.size(); ++k) out.p[k] = phi[k];
   return dispatch_group<tc::kSynthesize>(G.nsl, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
-                                         (int)G.members.size(), G.total_s, G.flush, out, s);
+                                         (int)G.members.size(), G.total_s, G.flush_s, out, s);
 }
 
 namespace {
