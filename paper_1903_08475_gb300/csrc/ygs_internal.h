@@ -97,6 +97,8 @@ struct ygs_plan {
   int* tc_eu = nullptr;       // [K_pad] U^T row (column c)
   int* tc_ef = nullptr;       // [2][n_r][S] field row (plane, shell) per split-K chunk, written by every solve
   int* tc_em = nullptr;       // [n_r] M row (shell), written by every solve
+  float2* tc_u00 = nullptr;   // [n_wtotal] monopole weight of every stored cell (float-float)
+  float2* tc_mpart = nullptr; // [S][n_r] exact monopole moment per split-K chunk, written by every solve
   CUtensorMap tc_map_ut, tc_map_f, tc_map_f_tail, tc_map_q, tc_map_m, tc_map_m_tail;
   // adjoint on the tensor cores: Q^T slices in the projection layout, U slices
   // in the synthesis layout (monopole column kept), their FP16 exponents, and
@@ -157,7 +159,7 @@ namespace tc {
 struct TcProblem;
 }
 struct TcBatchGroup {
-  int nsl = 0, flush = 1, flush_s = 1, sms = 0, total_p = 0, total_s = 0;  // flush: projection / synthesis k-blocks
+  int nsl = 0, sms = 0, total_p = 0, total_s = 0;
   std::vector<ygs_plan*> members;
   tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
   int *d_start_p = nullptr, *d_start_s = nullptr;

@@ -222,9 +222,11 @@ __global__ void colexp_u_kernel(int K, const int* __restrict__ pc_int, long long
 }
 
 // Ut[s][pc][apad]: slices of U^T rows scaled by 2^eu[pc].
+// With zero_mono, padded column 0 (the monopole, whose moment the field pass
+// computes exactly) is left zero.
 __global__ void slice_ut16_kernel(int K, int K_pad, long long n_pad, const int* __restrict__ pc_int,
                                   const double* __restrict__ U, PatchTable pt, int nwp,
-                                  const long long* __restrict__ pad_off, const int* __restrict__ eu,
+                                  const long long* __restrict__ pad_off, const int* __restrict__ eu, int zero_mono,
                                   __half* __restrict__ Ut) {
   long long total = (long long)K_pad * n_pad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -235,11 +237,20 @@ __global__ void slice_ut16_kernel(int K, int K_pad, long long n_pad, const int* 
     long long a = ap - pad_off[g];
     double v = 0.0;
     int ci = pc_int[pc];
-    if (ci >= 0 && a < pt.nang[g]) v = ldexp(U[(pt.ang_off[g] + a) * K + ci], eu[pc]);
+    if (ci >= 0 && a < pt.nang[g] && !(zero_mono && pc == 0)) v = ldexp(U[(pt.ang_off[g] + a) * K + ci], eu[pc]);
     __half s0, s1;
     half2_slices(v, s0, s1);
     Ut[e] = s0;
     Ut[total + e] = s1;
+  }
+}
+
+// u00[row] = U[row][ci0] (the monopole weight of every stored cell) as a float-float pair.
+__global__ void u00_kernel(int K, int ci0, long long rows, const double* __restrict__ U, float2* __restrict__ u00) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
+    float h, l;
+    tc::f64_to_ff(U[r * K + ci0], h, l);
+    u00[r] = make_float2(h, l);
   }
 }
 
@@ -327,14 +338,29 @@ __device__ __forceinline__ void f16_group_max(const double (&x0)[8], const doubl
 }
 
 // Scaled FP16 slices of 8 cells written as 16-byte stores (fewer at a ragged end).
+// With u (the monopole weights of these cells), plane 0's sigma * u is also
+// added to the float-float sum (mh, ml): the exact monopole moment.
 __device__ __forceinline__ void f16_group_store(const double (&x0)[8], const double (&x1)[8], int symmetric,
                                                 const float (&f)[2][2], __half* __restrict__ out, long long plane,
-                                                long long j, long long n) {
+                                                long long j, long long n, const float2* __restrict__ u, float& mh,
+                                                float& ml) {
   uint32_t w[2][2][4];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     float hi[2], lo[2];
     sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi, lo);
+    if (u && j + c < n) {
+      // sigma's head times the weight's head, the product's rounding error
+      // recovered by an FMA; the running sum by FastTwoSum (exact while it
+      // dominates, as it does for a positive density); the heads' own
+      // truncations (2^-24) are left out
+      const float uh = u[j + c].x;
+      const float pr = hi[0] * uh;
+      const float pe = fmaf(hi[0], uh, -pr);
+      const float s2 = mh + pr;
+      ml += (pr - (s2 - mh)) + pe;
+      mh = s2;
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const float hs = (hi[h] * f[h][0]) * f[h][1], ls = (lo[h] * f[h][0]) * f[h][1];
@@ -379,7 +405,7 @@ constexpr int kF16Threads = 256;
 __global__ void __launch_bounds__(kF16Threads) field_slices16_kernel(
     int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
     const int2* __restrict__ chunks, int S, const double* __restrict__ rho, __half* __restrict__ F,
-    int* __restrict__ ef) {
+    int* __restrict__ ef, const float2* __restrict__ u00, float2* __restrict__ mpart) {
   __shared__ float red[32];
   const int z = blockIdx.x, i = blockIdx.y;
   const long long plane = (long long)n_r * n_pad;
@@ -414,6 +440,8 @@ __global__ void __launch_bounds__(kF16Threads) field_slices16_kernel(
   float f[2][2];
   tc::pow2_pair(e0, f[0][0], f[0][1]);
   tc::pow2_pair(e1, f[1][0], f[1][1]);
+  const float2* u = u00 ? u00 + pt.ang_off[g] + a0 : nullptr;  // this chunk's monopole weights
+  float mh = 0.0f, ml = 0.0f;
   for (long long j = 8LL * threadIdx.x; j < n; j += step) {
     double x0[8], x1[8];
     load8(x0p + j, n - j, vec, x0);
@@ -423,7 +451,34 @@ __global__ void __launch_bounds__(kF16Threads) field_slices16_kernel(
 #pragma unroll
       for (int c = 0; c < 8; ++c) x1[c] = 0.0;
     }
-    f16_group_store(x0, x1, symmetric, f, out, plane, j, n);
+    f16_group_store(x0, x1, symmetric, f, out, plane, j, n, u, mh, ml);
+  }
+  if (!mpart) return;
+  // block sum of the float-float monopole partials: warp TwoSum tree, then warp 0
+  __shared__ float rh[32], rl[32];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, mh, d), ol = __shfl_xor_sync(0xffffffffu, ml, d);
+    float s2, e2;
+    tc::two_sum(mh, oh, s2, e2);
+    mh = s2;
+    ml += ol + e2;
+  }
+  const int wid = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  if (lane == 0) {
+    rh[wid] = mh;
+    rl[wid] = ml;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float h = 0.0f, l = 0.0f;
+    for (int k = 0; k < nw; ++k) {
+      float s2, e2;
+      tc::two_sum(h, rh[k], s2, e2);
+      h = s2;
+      l += rl[k] + e2;
+    }
+    mpart[(long long)z * n_r + i] = make_float2(h, l);
   }
 }
 
@@ -513,7 +568,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
     const double* __restrict__ rad, const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ M,
     __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, double G, float2* __restrict__ mono,
-    const int* __restrict__ ef, const int* __restrict__ eu, int k_split) {
+    const int* __restrict__ ef, const int* __restrict__ eu, int k_split, const float2* __restrict__ mpart) {
   __shared__ double sm[4][kScanMaxP][kScanCols];
   __shared__ double cr[2][kScanMaxP][kScanCols];
   const int c = threadIdx.x % kScanCols, p = threadIdx.x / kScanCols;
@@ -523,6 +578,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
   const bool live = l >= 0 && p < P && i0 < n_r;
   const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
   const long long splane = plane;
+  const bool exact_mono = mpart && pc == 0;  // the monopole moment summed exactly by the field pass
   const int lq = l < 0 ? 0 : l;
   const double* at = rad + (long long)lq * n_r;
   const double* bt = rad + rs + (long long)lq * n_r;
@@ -536,11 +592,16 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
         float h = 0.f, lo = 0.f;
         const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
         for (int z = 0; z < S; ++z) {
-          float2 v = part[z * plane + (long long)i * K_pad + pc];
-          if (efi) {
-            const int es = -(efi[z] + eu[pc]);
-            v.x = tc::mul_pow2f(v.x, es);
-            v.y = tc::mul_pow2f(v.y, es);
+          float2 v;
+          if (exact_mono) {
+            v = mpart[(long long)z * n_r + i];
+          } else {
+            v = part[z * plane + (long long)i * K_pad + pc];
+            if (efi) {
+              const int es = -(efi[z] + eu[pc]);
+              v.x = tc::mul_pow2f(v.x, es);
+              v.y = tc::mul_pow2f(v.y, es);
+            }
           }
           float s, e;
           tc::two_sum(h, v.x, s, e);
@@ -787,12 +848,12 @@ cudaError_t dispatch_gemm(int nsl, int grid, const CUtensorMap& a, const CUtenso
 
 template <int MODE>
 cudaError_t dispatch_group(int nsl, int grid, const tc::TcProblem* probs, const int* start, int n, int total,
-                          int flush, const tc::TcPhiList& phis, cudaStream_t s) {
+                          const tc::TcPhiList& phis, cudaStream_t s) {
   constexpr int threads = tc::TileShape<MODE>::THREADS;
   if (nsl == 3) {
-    tc::tc_gemm_group_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(probs, start, n, total, flush, phis);
+    tc::tc_gemm_group_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(probs, start, n, total, phis);
   } else if (nsl == 2) {
-    tc::tc_gemm_group_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, flush, phis);
+    tc::tc_gemm_group_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -903,6 +964,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_ALLOC(p->tc_eqt, kp * sizeof(int));
     TC_ALLOC(p->tc_eu, kp * sizeof(int));
     TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * s_max * sizeof(int));
+    TC_ALLOC(p->tc_u00, (size_t)p->nang_wtotal * sizeof(float2));
+    TC_ALLOC(p->tc_mpart, s_max * p->n_r * sizeof(float2));
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
   }
 #undef TC_ALLOC
@@ -927,7 +990,9 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     colexp_u_kernel<<<p->tc_k_pad, 256>>>(K, p->tc_pc_int, p->nang_wtotal, p->U, p->tc_eu);
     TC_TRY(cudaGetLastError());
     slice_ut16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
-                                     p->tc_pad_off_d, p->tc_eu, reinterpret_cast<__half*>(p->tc_ut));
+                                     p->tc_pad_off_d, p->tc_eu, 1, reinterpret_cast<__half*>(p->tc_ut));
+    u00_kernel<<<256, 256>>>(K, pc_int[0], p->nang_wtotal, p->U, p->tc_u00);
+    TC_TRY(cudaGetLastError());
     TC_TRY(cudaGetLastError());
     // Q as a whole: its largest magnitude (through a scratch word in the M buffer) sets eq
     unsigned long long* qm = reinterpret_cast<unsigned long long*>(p->tc_M);
@@ -946,7 +1011,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     colexp_u_kernel<<<p->tc_k_pad, 256>>>(K, p->tc_pc_int, p->nang_wtotal, p->Q, p->tc_eqt);
     TC_TRY(cudaGetLastError());
     slice_ut16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->Q, p->pt, p->n_wpatch,
-                                     p->tc_pad_off_d, p->tc_eqt, reinterpret_cast<__half*>(p->tc_qt));
+                                     p->tc_pad_off_d, p->tc_eqt, 0, reinterpret_cast<__half*>(p->tc_qt));
     TC_TRY(cudaGetLastError());
     TC_TRY(cudaMemset(qm, 0, sizeof(unsigned long long)));
     qmax_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, 0, qm);
@@ -1037,16 +1102,17 @@ void tc_free(ygs_plan* p) {
   void* bufs[] = {p->tc_ut,    p->tc_qs,     p->tc_f,      p->tc_ms,     p->tc_part,      p->tc_B,
                   p->tc_M,     p->tc_summ,   p->tc_carry,  p->tc_chunks, p->tc_pc_int,    p->tc_pc_l,
                   p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_eu, p->tc_ef, p->tc_em,
-                  p->tc_qt,    p->tc_us,     p->tc_eqt,    p->tc_Mbar,   p->tc_Bbar};
+                  p->tc_qt,    p->tc_us,     p->tc_eqt,    p->tc_Mbar,   p->tc_Bbar,   p->tc_u00,
+                  p->tc_mpart};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
 
 cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
   if (p->tc_fp16) {
-    field_slices16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt,
-                                                                 p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, p->tc_S,
-                                                                 rho, reinterpret_cast<__half*>(p->tc_f), p->tc_ef);
+    field_slices16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(
+        p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, p->tc_S, rho,
+        reinterpret_cast<__half*>(p->tc_f), p->tc_ef, p->tc_u00, p->tc_mpart);
     return cudaGetLastError();
   }
   long long nmax = 0;
@@ -1065,6 +1131,9 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
 // (and the adjoint's synthesis with U), whose monopole column sums positive
 // terms and keeps 64.  (Measured on config 1: 2.1e-7 -> 3.4e-7 against FP64 at
 // 128, 5.4e-7 at 256.)
+#ifndef YGS_PROJ_FLUSH_K_EXACT_MONO
+#define YGS_PROJ_FLUSH_K_EXACT_MONO 128
+#endif
 #ifndef YGS_SYNTH_FLUSH_K
 #define YGS_SYNTH_FLUSH_K 128
 #endif
@@ -1080,9 +1149,13 @@ static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.n_tiles = n_full + (n_tail > 0 ? 1 : 0);
 }
 
-static void project_args(const ygs_plan* p, TcArgs& a) {
+// forward: FP16 plans take the monopole moment from the field pass (its U^T
+// column is zero), so the remaining columns, whose terms change sign, flush
+// every 128 k like the synthesis; BF16 plans and the adjoint keep 64
+static void project_args(const ygs_plan* p, TcArgs& a, bool forward = true) {
   a = TcArgs{};
   fill_tiles(p, a, p->tc_np_full, p->tc_np_tail);
+  if (forward && p->tc_fp16) a.flush_kb = std::max(1, YGS_PROJ_FLUSH_K_EXACT_MONO / tc::BK);
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
   a.a_row_odd = p->tc_k_even;
@@ -1095,9 +1168,9 @@ static void project_args(const ygs_plan* p, TcArgs& a) {
   a.total_tiles = a.tiles_m * a.n_chunks * a.n_tiles;
 }
 
-static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cudaStream_t s) {
+static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cudaStream_t s, bool forward = true) {
   TcArgs a;
-  project_args(p, a);
+  project_args(p, a, forward);
   const int grid = std::min(a.total_tiles, p->tc_sms);
   return dispatch_gemm<tc::kProject>(p->tc_nsl, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
 }
@@ -1109,7 +1182,7 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   scan_fused_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
       p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, P, p->tc_pc_l, p->tc_part, p->rad, p->tc_cp, p->tc_B,
       p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->G, p->tc_mono, p->tc_ef, p->tc_eu,
-      p->symmetric ? p->tc_k_even : p->tc_k_pad);
+      p->symmetric ? p->tc_k_even : p->tc_k_pad, p->tc_fp16 ? p->tc_mpart : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !p->tc_fp16) return e;
   slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M, 0,
@@ -1165,7 +1238,7 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   cudaError_t e;
   if ((e = tc_field_slices(p, gphi, s)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
-  if ((e = project_with(p, p->tc_map_qt, s)) != cudaSuccess) return e;
+  if ((e = project_with(p, p->tc_map_qt, s, false)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
   scan_adj_fused_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
       p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part, p->rad,
@@ -1211,8 +1284,6 @@ ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
       synth_args(p, syn[k].args, nullptr, p->tc_mono, p->tc_eq);  // outputs come per call
       sp[k + 1] = sp[k] + proj[k].args.total_tiles;
       ss[k + 1] = ss[k] + syn[k].args.total_tiles;
-      G.flush = proj[k].args.flush_kb;
-      G.flush_s = syn[k].args.flush_kb;
     }
     G.total_p = sp.back();
     G.total_s = ss.back();
@@ -1250,14 +1321,14 @@ void tc_batch_free(TcBatch* b) {
 cudaError_t tc_batch_project(const TcBatchGroup& G, cudaStream_t s) {
   tc::TcPhiList none{};
   return dispatch_group<tc::kProject>(G.nsl, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
-                                      (int)G.members.size(), G.total_p, G.flush, none, s);
+                                      (int)G.members.size(), G.total_p, none, s);
 }
 
 cudaError_t tc_batch_synthesize(const TcBatchGroup& G, double* const* phi, cudaStream_t s) {
   tc::TcPhiList out{};
   for (size_t k = 0; k < G.members.size(); ++k) out.p[k] = phi[k];
   return dispatch_group<tc::kSynthesize>(G.nsl, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
-                                         (int)G.members.size(), G.total_s, G.flush_s, out, s);
+                                         (int)G.members.size(), G.total_s, out, s);
 }
 
 namespace {

@@ -237,7 +237,7 @@ struct GroupSrc {  // tiles of several problems concatenated: problem k owns [st
 };
 
 template <int NSL, int MODE, class Src>
-__device__ __forceinline__ void gemm_body(const Src& src, const int flush) {
+__device__ __forceinline__ void gemm_body(const Src& src) {
   using C = TcCfg<NSL, MODE>;
   constexpr int NMAX = TileShape<MODE>::NMAX;
   constexpr int NH = TileShape<MODE>::NH;
@@ -326,6 +326,7 @@ __device__ __forceinline__ void gemm_body(const Src& src, const int flush) {
         const Tile T = decode_tile<MODE>(*R.A, R.t);
         err = R.A->err;
         const uint32_t idesc = idesc_f16(BM, T.n_eff, R.A->ab_fmt);
+        const int flush = R.A->flush_kb;  // k-blocks per accumulator flush, per problem
         for (int seg = 0; seg < 2 && ok; ++seg) {
           const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
@@ -395,6 +396,7 @@ __device__ __forceinline__ void gemm_body(const Src& src, const int flush) {
       const TileRef R = src.locate(t);
       const Tile T = decode_tile<MODE>(*R.A, R.t);
       err = R.A->err;
+      const int flush = R.A->flush_kb;
       const bool active = col0 < T.n_eff;  // this warp's columns exist in the tile (warp-uniform)
       // float-float sums of column pairs (2j, 2j+1), packed for the f32x2 pipes
       uint64_t H[NH / 2], L[NH / 2];
@@ -552,7 +554,7 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     prefetch_tmap(&mapBt);
   }
   const SingleSrc src{&args, &mapA, &mapB, &mapBt};
-  gemm_body<NSL, MODE>(src, args.flush_kb);
+  gemm_body<NSL, MODE>(src);
 }
 
 // Several problems of one operand type in one persistent launch (a batch of
@@ -561,9 +563,9 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
 template <int NSL, int MODE>
 __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     tc_gemm_group_kernel(const TcProblem* __restrict__ probs, const int* __restrict__ start, int n, int total,
-                         int flush, const __grid_constant__ TcPhiList phis) {
+                         const __grid_constant__ TcPhiList phis) {
   const GroupSrc src{probs, start, n, total, &phis};
-  gemm_body<NSL, MODE>(src, flush);
+  gemm_body<NSL, MODE>(src);
 }
 
 }  // namespace tc
