@@ -147,7 +147,9 @@ cudaError_t solve_fp32(const ygs_plan* p, const double* rho, double* phi, cudaSt
 // ---- split-precision tensor-core path (ygs_tc.cu) --------------------------
 ygs_status tc_setup(ygs_plan* p, int sms);     // slices, tensor maps, workspaces (at create)
 void tc_free(ygs_plan* p);
-cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s);
+// forward: FP16 plans also sum the monopole moment's chunk partials (the
+// adjoint's input needs none)
+cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s, bool forward = true);
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s);

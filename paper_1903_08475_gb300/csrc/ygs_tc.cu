@@ -246,11 +246,17 @@ __global__ void slice_ut16_kernel(int K, int K_pad, long long n_pad, const int* 
 }
 
 // u00[row] = U[row][ci0] (the monopole weight of every stored cell) as a float-float pair.
-__global__ void u00_kernel(int K, int ci0, long long rows, const double* __restrict__ U, float2* __restrict__ u00) {
-  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows; r += (long long)gridDim.x * blockDim.x) {
-    float h, l;
-    tc::f64_to_ff(U[r * K + ci0], h, l);
-    u00[r] = make_float2(h, l);
+__global__ void u00_kernel(int K, int ci0, long long n_pad, PatchTable pt, int nwp,
+                           const long long* __restrict__ pad_off, const double* __restrict__ U,
+                           float2* __restrict__ u00) {
+  for (long long ap = blockIdx.x * (long long)blockDim.x + threadIdx.x; ap < n_pad;
+       ap += (long long)gridDim.x * blockDim.x) {
+    int g = 0;
+    while (g + 1 < nwp && pad_off[g + 1] <= ap) ++g;
+    const long long a = ap - pad_off[g];
+    float h = 0.0f, l = 0.0f;
+    if (a < pt.nang[g]) tc::f64_to_ff(U[(pt.ang_off[g] + a) * K + ci0], h, l);
+    u00[ap] = make_float2(h, l);
   }
 }
 
@@ -288,92 +294,112 @@ __global__ void slice_q16_kernel(int K, int K_pad, long long rows, const int* __
   }
 }
 
-// sigma+- (or rho) of one cell as float-float pairs.
+// sigma+- (or rho) of one cell as float-float pairs: the exact sum and
+// difference of the two values rounded to FP32 (TwoSum), so each is within
+// 2^-24 (|rho_Yin| + |rho_Yang|) of the FP64 value, below the 2^-22 of the
+// two FP16 slices it becomes.
 __device__ __forceinline__ void sigma_ff(double r0, double r1, int symmetric, float (&hi)[2], float (&lo)[2]) {
-  float h0, l0;
-  tc::f64_to_ff_fast(r0, h0, l0);
+  const float h0 = tc::f64_round_f32(r0);
   if (!symmetric) {
     hi[0] = h0;
-    lo[0] = l0;
-    hi[1] = lo[1] = 0.0f;
+    lo[0] = hi[1] = lo[1] = 0.0f;
     return;
   }
-  float h1, l1;
-  tc::f64_to_ff_fast(r1, h1, l1);
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    float s, err;
-    tc::two_sum(h0, h ? -h1 : h1, s, err);
-    float l = err + (h ? (l0 - l1) : (l0 + l1));
-    hi[h] = s + l;
-    lo[h] = l - (hi[h] - s);
-  }
+  const float h1 = tc::f64_round_f32(r1);
+  tc::two_sum(h0, h1, hi[0], lo[0]);
+  tc::two_sum(h0, -h1, hi[1], lo[1]);
 }
 
-// 8 consecutive values of a row (two 16-byte loads per pair when aligned), zero past n.
-__device__ __forceinline__ void load8(const double* __restrict__ p, long long n, bool vec, double (&x)[8]) {
-  if (vec && n >= 8) {
+// A thread's 8 cells of one pass step: the pairs q_u = base + u * T + t
+// (u = 0..3, T threads), cells 2 q_u and 2 q_u + 1 -> x[2u], x[2u + 1];
+// cells at or past n read as zero.  Interleaved pairs keep every warp access
+// contiguous and the threads' shares of a chunk within one pair of each other.
+__device__ __forceinline__ void load_pairs(const double* __restrict__ p, int n, int base, int T, bool vec,
+                                           double (&x)[8]) {
 #pragma unroll
-    for (int c = 0; c < 8; c += 2) {
+  for (int u = 0; u < 4; ++u) {
+    const int c = 2 * (base + u * T + (int)threadIdx.x);
+    if (vec && c + 2 <= n) {
       const double2 v = *reinterpret_cast<const double2*>(p + c);
-      x[c] = v.x;
-      x[c + 1] = v.y;
+      x[2 * u] = v.x;
+      x[2 * u + 1] = v.y;
+    } else {
+      x[2 * u] = c < n ? p[c] : 0.0;
+      x[2 * u + 1] = c + 1 < n ? p[c + 1] : 0.0;
     }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) x[c] = (c < n) ? p[c] : 0.0;
   }
 }
 
 // Largest |sigma+-| of 8 cells from truncated FP32 values (a few ulp from the
 // float-float heads used for the slices; the caller raises the maxima by 2^-16).
+// Upper bounds of |sigma+-| over 8 cells from the truncated heads t (each
+// within 2^-23 |x| of x): |t0 +- t1| + 2^-22 (|t0| + |t1|) bounds the rounded
+// sums sigma_ff forms, up to second-order terms that the (1 + 2^-16) applied
+// to the maximum covers.
 __device__ __forceinline__ void f16_group_max(const double (&x0)[8], const double (&x1)[8], int symmetric,
                                               float& mx0, float& mx1) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const float f0 = tc::f64_trunc_f32(x0[c]), f1 = symmetric ? tc::f64_trunc_f32(x1[c]) : 0.0f;
-    mx0 = fmaxf(mx0, fabsf(f0 + f1));
-    mx1 = fmaxf(mx1, fabsf(f0 - f1));
+    const float slack = 0x1p-22f * (fabsf(f0) + fabsf(f1));
+    mx0 = fmaxf(mx0, fabsf(f0 + f1) + slack);
+    mx1 = fmaxf(mx1, fabsf(f0 - f1) + slack);
   }
 }
 
 // Scaled FP16 slices of 8 cells written as 16-byte stores (fewer at a ragged end).
 // With u (the monopole weights of these cells), plane 0's sigma * u is also
 // added to the float-float sum (mh, ml): the exact monopole moment.
+// the monopole weights (head, tail) of the same 8 cells, one 16-byte pair
+// each; pairs that start before n (the padded layout keeps their second cell
+// in bounds, and them 16-byte aligned), zero past it
+__device__ __forceinline__ void load_u_pairs(const float2* __restrict__ u, int n, int base, int T, float4 (&uu)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = 2 * (base + k * T + (int)threadIdx.x);
+    uu[k] = (u && c < n) ? *reinterpret_cast<const float4*>(u + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) {
+  uint32_t r;
+  memcpy(&r, &v, sizeof(r));
+  return r;
+}
 __device__ __forceinline__ void f16_group_store(const double (&x0)[8], const double (&x1)[8], int symmetric,
                                                 const float (&f)[2][2], __half* __restrict__ out, long long plane,
-                                                long long j, long long n, const float2* __restrict__ u, float& mh,
-                                                float& ml) {
+                                                int n, int base, int T, bool mono, const float4 (&uu)[4],
+                                                float& mh, float& ml) {
   uint32_t w[2][2][4];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    float hi[2], lo[2];
-    sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi, lo);
-    if (u && j + c < n) {
-      // sigma's head times the weight's head, the product's rounding error
-      // recovered by an FMA; the running sum by FastTwoSum (exact while it
-      // dominates, as it does for a positive density); the heads' own
-      // truncations (2^-24) are left out
-      const float uh = u[j + c].x;
-      const float pr = hi[0] * uh;
-      const float pe = fmaf(hi[0], uh, -pr);
-      const float s2 = mh + pr;
-      ml += (pr - (s2 - mh)) + pe;
-      mh = s2;
+  for (int u = 0; u < 4; ++u) {
+    float hi[2][2], lo[2][2];  // [cell of the pair][plane]
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const int c = 2 * u + d;
+      sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi[d], lo[d]);
+      if (mono) {
+        // sigma+ times the weight in float-float (cells past the chunk carry
+        // sigma = 0): the heads' product with its rounding error from an FMA,
+        // the cross terms of the tails, the running sum by FastTwoSum (exact
+        // while the sum dominates, as it does for a positive density)
+        const float uh = d ? uu[u].z : uu[u].x, ul = d ? uu[u].w : uu[u].y;
+        const float pr = hi[d][0] * uh;
+        const float pe = fmaf(hi[d][0], ul, fmaf(lo[d][0], uh, fmaf(hi[d][0], uh, -pr)));
+        const float s2 = mh + pr;
+        ml += (pr - (s2 - mh)) + pe;
+        mh = s2;
+      }
     }
+    // both cells' slices at once: s0 = fp16(hs), s1 = fp16((hs - s0) + ls)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const float hs = (hi[h] * f[h][0]) * f[h][1], ls = (lo[h] * f[h][0]) * f[h][1];
-      const __half s0 = __float2half_rn(hs);
-      const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
-      const uint32_t b0 = __half_as_ushort(s0), b1 = __half_as_ushort(s1);
-      if (c & 1) {
-        w[h][0][c / 2] |= b0 << 16;
-        w[h][1][c / 2] |= b1 << 16;
-      } else {
-        w[h][0][c / 2] = b0;
-        w[h][1][c / 2] = b1;
-      }
+      const float a0 = (hi[0][h] * f[h][0]) * f[h][1], a1 = (hi[1][h] * f[h][0]) * f[h][1];
+      const float b0 = (lo[0][h] * f[h][0]) * f[h][1], b1 = (lo[1][h] * f[h][0]) * f[h][1];
+      const __half2 s0 = __floats2half2_rn(a0, a1);  // a0 in the low half
+      const float2 back = __half22float2(s0);
+      const __half2 s1 = __floats2half2_rn((a0 - back.x) + b0, (a1 - back.y) + b1);
+      w[h][0][u] = h2_bits(s0);
+      w[h][1][u] = h2_bits(s1);
     }
   }
 #pragma unroll
@@ -381,17 +407,24 @@ __device__ __forceinline__ void f16_group_store(const double (&x0)[8], const dou
     if (h == 1 && !symmetric) break;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      __half* dst = out + (long long)(h * 2 + k) * plane + j;
-      if (n - j >= 8) {
-        *reinterpret_cast<uint4*>(dst) = make_uint4(w[h][k][0], w[h][k][1], w[h][k][2], w[h][k][3]);
-      } else {
-        for (int c = 0; c < n - j; ++c) dst[c] = __ushort_as_half((unsigned short)(w[h][k][c / 2] >> (16 * (c & 1))));
+      __half* dst = out + (long long)(h * 2 + k) * plane;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = 2 * (base + u * T + (int)threadIdx.x);
+        if (c + 2 <= n) {
+          *reinterpret_cast<uint32_t*>(dst + c) = w[h][k][u];
+        } else if (c < n) {
+          dst[c] = __ushort_as_half((unsigned short)(w[h][k][u] & 0xFFFFu));
+        }
       }
     }
   }
 }
 
 constexpr int kF16Threads = 256;
+#ifndef YGS_F16_MINB
+#define YGS_F16_MINB 3  // resident CTAs per SM the field pass's register budget is set for
+#endif
 
 // Field slices in FP16, one CTA per (split-K chunk z, shell i), 8 cells per
 // thread and step: pass 1 finds the largest |sigma| of each plane over the
@@ -402,59 +435,9 @@ constexpr int kF16Threads = 256;
 // could not hide the loads.)  Symmetric: planes sigma+ (h = 0) and sigma-
 // (h = 1) of the Yin/Yang rows; otherwise plane 0, each chunk lying inside one
 // stored patch.
-__global__ void __launch_bounds__(kF16Threads) field_slices16_kernel(
-    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
-    const int2* __restrict__ chunks, int S, const double* __restrict__ rho, __half* __restrict__ F,
-    int* __restrict__ ef, const float2* __restrict__ u00, float2* __restrict__ mpart) {
-  __shared__ float red[32];
-  const int z = blockIdx.x, i = blockIdx.y;
-  const long long plane = (long long)n_r * n_pad;
-  const int2 ch = chunks[z];
-  int g = 0;
-  while (g + 1 < nwp && pad_off[g + 1] <= ch.x) ++g;
-  const long long na = pt.nang[g];
-  const long long a0 = ch.x - pad_off[g], n = min((long long)ch.y - pad_off[g], na) - a0;  // real cells of the chunk
-  const double* x0p = rho + pt.fld_off[g] + i * na + a0;
-  const double* x1p = symmetric ? rho + pt.fld_off[1] + i * na + a0 : x0p;
-  const bool vec = ((reinterpret_cast<uintptr_t>(x0p) | reinterpret_cast<uintptr_t>(x1p)) & 15) == 0;
-  __half* out = F + (long long)i * n_pad + pad_off[g] + a0;  // 16-byte aligned: every offset is a multiple of 8
-  const long long step = 8LL * blockDim.x;
-  float mx0 = 0.0f, mx1 = 0.0f;
-  for (long long j = 8LL * threadIdx.x; j < n; j += step) {
-    double x0[8], x1[8];
-    load8(x0p + j, n - j, vec, x0);
-    if (symmetric) {
-      load8(x1p + j, n - j, vec, x1);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
-    }
-    f16_group_max(x0, x1, symmetric, mx0, mx1);
-  }
-  const int e0 = tc::fp16_row_exp((double)block_max(mx0, red) * (1.0 + 0x1p-16));
-  const int e1 = symmetric ? tc::fp16_row_exp((double)block_max(mx1, red) * (1.0 + 0x1p-16)) : 0;
-  if (threadIdx.x == 0) {
-    ef[(long long)i * S + z] = e0;
-    ef[((long long)n_r + i) * S + z] = e1;
-  }
-  float f[2][2];
-  tc::pow2_pair(e0, f[0][0], f[0][1]);
-  tc::pow2_pair(e1, f[1][0], f[1][1]);
-  const float2* u = u00 ? u00 + pt.ang_off[g] + a0 : nullptr;  // this chunk's monopole weights
-  float mh = 0.0f, ml = 0.0f;
-  for (long long j = 8LL * threadIdx.x; j < n; j += step) {
-    double x0[8], x1[8];
-    load8(x0p + j, n - j, vec, x0);
-    if (symmetric) {
-      load8(x1p + j, n - j, vec, x1);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
-    }
-    f16_group_store(x0, x1, symmetric, f, out, plane, j, n, u, mh, ml);
-  }
-  if (!mpart) return;
-  // block sum of the float-float monopole partials: warp TwoSum tree, then warp 0
+// Block sum of float-float partials (warp TwoSum tree, then warp 0's lane 0
+// over the warps); the result is valid in thread 0.
+__device__ __forceinline__ float2 block_ff_sum(float mh, float ml) {
   __shared__ float rh[32], rl[32];
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
@@ -470,17 +453,76 @@ __global__ void __launch_bounds__(kF16Threads) field_slices16_kernel(
     rl[wid] = ml;
   }
   __syncthreads();
+  float h = 0.0f, l = 0.0f;
   if (threadIdx.x == 0) {
-    float h = 0.0f, l = 0.0f;
     for (int k = 0; k < nw; ++k) {
       float s2, e2;
       tc::two_sum(h, rh[k], s2, e2);
       h = s2;
       l += rl[k] + e2;
     }
-    mpart[(long long)z * n_r + i] = make_float2(h, l);
   }
+  return make_float2(h, l);
 }
+
+__global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kernel(
+    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
+    const int2* __restrict__ chunks, int S, const double* __restrict__ rho, __half* __restrict__ F,
+    int* __restrict__ ef, const float2* __restrict__ u00, float2* __restrict__ mpart) {
+  __shared__ float red[32];
+  const int z = blockIdx.x, i = blockIdx.y;
+  const long long plane = (long long)n_r * n_pad;
+  const int2 ch = chunks[z];
+  int g = 0;
+  while (g + 1 < nwp && pad_off[g + 1] <= ch.x) ++g;
+  const long long na = pt.nang[g];
+  const long long a0 = ch.x - pad_off[g], n = min((long long)ch.y - pad_off[g], na) - a0;  // real cells of the chunk
+  const double* x0p = rho + pt.fld_off[g] + i * na + a0;
+  const double* x1p = symmetric ? rho + pt.fld_off[1] + i * na + a0 : x0p;
+  const bool vec = ((reinterpret_cast<uintptr_t>(x0p) | reinterpret_cast<uintptr_t>(x1p)) & 15) == 0;
+  __half* out = F + (long long)i * n_pad + pad_off[g] + a0;  // 4-byte aligned: every offset is even
+  const int nc = (int)n, T = blockDim.x, npair = (nc + 1) / 2;
+  float mx0 = 0.0f, mx1 = 0.0f;
+  for (int base = 0; base < npair; base += 4 * T) {
+    double x0[8], x1[8];
+    load_pairs(x0p, nc, base, T, vec, x0);
+    if (symmetric) {
+      load_pairs(x1p, nc, base, T, vec, x1);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
+    }
+    f16_group_max(x0, x1, symmetric, mx0, mx1);
+  }
+  const int e0 = tc::fp16_row_exp((double)block_max(mx0, red) * (1.0 + 0x1p-16));
+  const int e1 = symmetric ? tc::fp16_row_exp((double)block_max(mx1, red) * (1.0 + 0x1p-16)) : 0;
+  if (threadIdx.x == 0) {
+    ef[(long long)i * S + z] = e0;
+    ef[((long long)n_r + i) * S + z] = e1;
+  }
+  float f[2][2];
+  tc::pow2_pair(e0, f[0][0], f[0][1]);
+  tc::pow2_pair(e1, f[1][0], f[1][1]);
+  const float2* u = u00 ? u00 + pad_off[g] + a0 : nullptr;  // this chunk's monopole weights (padded layout)
+  float mh = 0.0f, ml = 0.0f;
+  for (int base = 0; base < npair; base += 4 * T) {
+    double x0[8], x1[8];
+    load_pairs(x0p, nc, base, T, vec, x0);
+    if (symmetric) {
+      load_pairs(x1p, nc, base, T, vec, x1);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
+    }
+    float4 uu[4];
+    load_u_pairs(u, nc, base, T, uu);
+    f16_group_store(x0, x1, symmetric, f, out, plane, nc, base, T, u != nullptr, uu, mh, ml);
+  }
+  if (!mpart) return;
+  const float2 m = block_ff_sum(mh, ml);
+  if (threadIdx.x == 0) mpart[(long long)z * n_r + i] = m;
+}
+
 
 // Ms[s][i][pc]: FP16 slices of M's row i scaled by 2^em[i] (largest |M| over the
 // real columns; without keep_mono the monopole, whose Q column is zero, is
@@ -964,7 +1006,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_ALLOC(p->tc_eqt, kp * sizeof(int));
     TC_ALLOC(p->tc_eu, kp * sizeof(int));
     TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * s_max * sizeof(int));
-    TC_ALLOC(p->tc_u00, (size_t)p->nang_wtotal * sizeof(float2));
+    TC_ALLOC(p->tc_u00, (size_t)p->tc_n_pad * sizeof(float2));
     TC_ALLOC(p->tc_mpart, s_max * p->n_r * sizeof(float2));
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
   }
@@ -991,7 +1033,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_TRY(cudaGetLastError());
     slice_ut16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
                                      p->tc_pad_off_d, p->tc_eu, 1, reinterpret_cast<__half*>(p->tc_ut));
-    u00_kernel<<<256, 256>>>(K, pc_int[0], p->nang_wtotal, p->U, p->tc_u00);
+    u00_kernel<<<256, 256>>>(K, pc_int[0], p->tc_n_pad, p->pt, p->n_wpatch, p->tc_pad_off_d, p->U, p->tc_u00);
     TC_TRY(cudaGetLastError());
     TC_TRY(cudaGetLastError());
     // Q as a whole: its largest magnitude (through a scratch word in the M buffer) sets eq
@@ -1094,6 +1136,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_TRY(cudaMemcpy(p->tc_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
     TC_TRY(cudaDeviceSynchronize());
   }
+
 #undef TC_TRY
   return YGS_OK;
 }
@@ -1108,11 +1151,13 @@ void tc_free(ygs_plan* p) {
     if (b) cudaFree(b);
 }
 
-cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
+cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s, bool forward) {
   if (p->tc_fp16) {
+    const float2* u00 = forward ? p->tc_u00 : nullptr;
+    float2* mpart = forward ? p->tc_mpart : nullptr;
     field_slices16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(
         p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, p->tc_S, rho,
-        reinterpret_cast<__half*>(p->tc_f), p->tc_ef, p->tc_u00, p->tc_mpart);
+        reinterpret_cast<__half*>(p->tc_f), p->tc_ef, u00, mpart);
     return cudaGetLastError();
   }
   long long nmax = 0;
@@ -1236,7 +1281,7 @@ cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
 // ev (optional) receives the phase events 1..4 after each phase.
 cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cudaStream_t s, cudaEvent_t* ev) {
   cudaError_t e;
-  if ((e = tc_field_slices(p, gphi, s)) != cudaSuccess) return e;
+  if ((e = tc_field_slices(p, gphi, s, false)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if ((e = project_with(p, p->tc_map_qt, s, false)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;

@@ -215,11 +215,25 @@ __device__ __forceinline__ void fast_two_sum2(uint64_t a, uint64_t b, uint64_t& 
 // conversions on its narrow FP64 pipe): the head of f64_to_ff.
 __device__ __forceinline__ float f64_trunc_f32(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(b >> 63) << 31;
-  const int e = (int)((b >> 52) & 0x7FF) - 1023;
-  if (e < -126) return __int_as_float((int)sign);
-  if (e > 127) return __int_as_float((int)(sign | 0x7F800000u));
-  return __int_as_float((int)(sign | ((unsigned int)(e + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu)));
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const unsigned int E = (hw >> 20) & 0x7FFu;  // biased FP64 exponent; FP32's normal range is 897..1150
+  unsigned int m = ((E - 896u) << 23) | (((hw << 3) | (lw >> 29)) & 0x7FFFFFu);
+  m = E < 897u ? 0u : (E > 1150u ? 0x7F800000u : m);  // selects, no branches
+  return __uint_as_float((hw & 0x80000000u) | m);
+}
+
+// FP64 -> FP32 rounded to nearest (ties away from zero) with integer
+// operations: the exponent and the top 23 mantissa bits, plus the first
+// dropped bit (a carry into the exponent is the correct rounding, and 2^128
+// gives infinity).  Exponents below FP32's normal range give a signed zero,
+// above it an infinity, as the truncating conversions here.
+__device__ __forceinline__ float f64_round_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const unsigned int E = (hw >> 20) & 0x7FFu;
+  unsigned int m = (((E - 896u) << 23) | (((hw << 3) | (lw >> 29)) & 0x7FFFFFu)) + ((lw >> 28) & 1u);
+  m = E < 897u ? 0u : (E > 1150u ? 0x7F800000u : m);
+  return __uint_as_float((hw & 0x80000000u) | m);
 }
 
 // FP64 -> (hi, lo) FP32 pair with integer operations and one exact FP32
