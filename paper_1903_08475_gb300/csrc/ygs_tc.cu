@@ -528,7 +528,8 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kern
 // real columns; without keep_mono the monopole, whose Q column is zero, is
 // left out and written as 0).  One CTA per shell; FP64 values enter as float-float pairs.
 __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_nat, const double* __restrict__ M,
-                                 int keep_mono, __half* __restrict__ Ms, int* __restrict__ em) {
+                                 int keep_mono, __half* __restrict__ Ms, int* __restrict__ em, int q_exp,
+                                 const float2* __restrict__ mono, float4* __restrict__ sc) {
   __shared__ float red[32];
   const int i = blockIdx.x;
   const long long splane = (long long)n_r * K_pad;
@@ -542,7 +543,14 @@ __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_
   }
   // the truncated maximum is every float-float head's bound below (same truncation)
   const int e = tc::fp16_row_exp((double)block_max(m, red));
-  if (threadIdx.x == 0) em[i] = e;
+  if (threadIdx.x == 0) {
+    em[i] = e;
+    // the synthesis epilogue's per-shell constants: its unscaling factors and the monopole pair
+    float f1, f2;
+    tc::pow2_pair(-(q_exp + e), f1, f2);
+    const float2 mm = mono ? mono[i] : make_float2(0.0f, 0.0f);
+    sc[i] = make_float4(f1, f2, mm.x, mm.y);
+  }
 #pragma unroll 4
   for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {
     const double v = row[pc];
@@ -1009,6 +1017,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_ALLOC(p->tc_u00, (size_t)p->tc_n_pad * sizeof(float2));
     TC_ALLOC(p->tc_mpart, s_max * p->n_r * sizeof(float2));
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
+    TC_ALLOC(p->tc_sc, (size_t)p->n_r * sizeof(float4));
   }
 #undef TC_ALLOC
   p->weight_bytes += (long long)(2 * (bytes_ut + bytes_q));
@@ -1146,7 +1155,7 @@ void tc_free(ygs_plan* p) {
                   p->tc_M,     p->tc_summ,   p->tc_carry,  p->tc_chunks, p->tc_pc_int,    p->tc_pc_l,
                   p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_eu, p->tc_ef, p->tc_em,
                   p->tc_qt,    p->tc_us,     p->tc_eqt,    p->tc_Mbar,   p->tc_Bbar,   p->tc_u00,
-                  p->tc_mpart};
+                  p->tc_mpart, p->tc_sc};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
@@ -1231,11 +1240,12 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !p->tc_fp16) return e;
   slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M, 0,
-                                          reinterpret_cast<__half*>(p->tc_ms), p->tc_em);
+                                          reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eq, p->tc_mono,
+                                          p->tc_sc);
   return cudaGetLastError();
 }
 
-static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono, int q_exp) {
+static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono) {
   a = TcArgs{};
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   // the forward synthesis excludes the monopole (added exactly) and may flush less
@@ -1258,20 +1268,19 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
   a.total_tiles = t;
   a.phi = phi;
   a.mono = mono;
-  a.m_exp = p->tc_fp16 ? p->tc_em : nullptr;
-  a.q_exp = q_exp;
+  a.sc = p->tc_fp16 ? p->tc_sc : nullptr;
 }
 
 static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, double* phi, const float2* mono,
-                                   int q_exp, cudaStream_t s) {
+                                   cudaStream_t s) {
   TcArgs a;
-  synth_args(p, a, phi, mono, q_exp);
+  synth_args(p, a, phi, mono);
   const int grid = std::min(a.total_tiles, p->tc_sms);
   return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
 }
 
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
-  return synthesize_with(p, p->tc_map_q, phi, p->tc_mono, p->tc_eq, s);
+  return synthesize_with(p, p->tc_map_q, phi, p->tc_mono, s);
 }
 
 // The adjoint: grad_phi's slices (sigma+- of the Yin/Yang rows, as the
@@ -1292,11 +1301,12 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p->tc_fp16) {
     slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_Bbar, 1,
-                                            reinterpret_cast<__half*>(p->tc_ms), p->tc_em);
+                                            reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eus, nullptr,
+                                            p->tc_sc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
-  return synthesize_with(p, p->tc_map_us, grho, nullptr, p->tc_eus, s);
+  return synthesize_with(p, p->tc_map_us, grho, nullptr, s);
 }
 
 // ---- batches: the contractions of many plans in one persistent launch each ----
@@ -1326,7 +1336,7 @@ ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
       syn[k].a = p->tc_map_q;
       syn[k].b = p->tc_map_m;
       syn[k].bt = p->tc_map_m_tail;
-      synth_args(p, syn[k].args, nullptr, p->tc_mono, p->tc_eq);  // outputs come per call
+      synth_args(p, syn[k].args, nullptr, p->tc_mono);  // outputs come per call
       sp[k + 1] = sp[k] + proj[k].args.total_tiles;
       ss[k + 1] = ss[k] + syn[k].args.total_tiles;
     }

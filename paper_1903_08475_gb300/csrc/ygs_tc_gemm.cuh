@@ -95,10 +95,11 @@ struct TcArgs {
   // slices).  nullptr disables it.
   const float2* mono;
   int ab_fmt;           // operand type of the slices: 1 = BF16, 0 = FP16
-  // FP16 slices are scaled rows: the synthesis result of shell n is multiplied
-  // by 2^-(q_exp + m_exp[n]).  nullptr: unscaled (BF16).
-  const int* m_exp;
-  int q_exp;
+  // FP16 slices are scaled rows: sc[n] = {f1, f2, monopole head, tail}, the
+  // synthesis result of shell n multiplied by f1 f2 = 2^-(q_exp + m_exp[n])
+  // (two power-of-two factors), and the monopole pair read from here instead
+  // of mono (which then only says whether to add it).  nullptr: unscaled (BF16).
+  const float4* sc;
 };
 
 template <int NSL, int MODE>
@@ -125,12 +126,11 @@ __device__ __forceinline__ int prod_s(int p) { return (p == 2 || p == 4) ? 1 : (
 __device__ __forceinline__ int prod_t(int p) { return (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0); }
 
 __device__ __forceinline__ double f32_to_f64(float f) {
-  unsigned int u = __float_as_uint(f);
-  unsigned int e = (u >> 23) & 0xFFu;
-  if (e == 0) return 0.0;
-  unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-  unsigned int lo = u << 29;
-  return __hiloint2double((int)hi, (int)lo);
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  // selects, no branches: FP32 zeros and subnormals give +-0
+  return __hiloint2double((int)(e == 0 ? (u & 0x80000000u) : hi), (int)(e == 0 ? 0u : u << 29));
 }
 
 __device__ __forceinline__ void set_err(int* err, int code) {
@@ -459,9 +459,9 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       }
       if (!ok || !active) continue;
       // this tile's output arguments in registers (the stores below cannot alias them)
-      const int n_b = R.A->n_b, ldp = R.A->ldp, q_exp = R.A->q_exp, symmetric = R.A->symmetric;
+      const int n_b = R.A->n_b, ldp = R.A->ldp, symmetric = R.A->symmetric;
       float2* const part = R.A->part;
-      const int* const m_exp = R.A->m_exp;
+      const float4* const sc = R.A->sc;
       const float2* const mono = R.A->mono;
       double* const phi = R.phi;
       const long long nang = MODE == kSynthesize ? R.A->pt.nang[T.g_patch] : 0;
@@ -499,17 +499,19 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             const long long a_loc = (long long)T.m_loc * BM + r;
             if (a_loc >= nang) continue;
             float hs = hj, ls = lj, e0 = ev[jj];
-            if (m_exp) {  // exact unscaling of FP16-slice results: two power-of-two factors per shell
-              float f1, f2;
-              pow2_pair(-(q_exp + m_exp[n]), f1, f2);
-              hs = (hs * f1) * f2;
-              ls = (ls * f1) * f2;
-              e0 = (e0 * f1) * f2;
+            float2 mm = make_float2(0.0f, 0.0f);
+            if (sc) {  // exact unscaling of FP16-slice results: two power-of-two factors per shell
+              const float4 t4 = sc[n];
+              hs = (hs * t4.x) * t4.y;
+              ls = (ls * t4.x) * t4.y;
+              e0 = (e0 * t4.x) * t4.y;
+              mm = make_float2(t4.z, t4.w);
+            } else if (mono) {
+              mm = mono[n];
             }
             float v = hs + ls;
             if (mono) {
               // the monopole belongs to the even block (E) or, without the symmetry, to the only block
-              const float2 mm = mono[n];
               float s, e;
               if (nseg == 2) {
                 two_sum(e0, mm.x, s, e);
