@@ -494,8 +494,10 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kern
     }
     f16_group_max(x0, x1, symmetric, mx0, mx1);
   }
-  const int e0 = tc::fp16_row_exp((double)block_max(mx0, red) * (1.0 + 0x1p-16));
-  const int e1 = symmetric ? tc::fp16_row_exp((double)block_max(mx1, red) * (1.0 + 0x1p-16)) : 0;
+  // (1 + 2^-16) covers the bound's second-order terms; FP32 rounding of the
+  // product is monotonic, so it never falls below the maximum
+  const int e0 = tc::fp16_row_exp_f(block_max(mx0, red) * (1.0f + 0x1p-16f));
+  const int e1 = symmetric ? tc::fp16_row_exp_f(block_max(mx1, red) * (1.0f + 0x1p-16f)) : 0;
   if (threadIdx.x == 0) {
     ef[(long long)i * S + z] = e0;
     ef[((long long)n_r + i) * S + z] = e1;
@@ -542,14 +544,15 @@ __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_
     m = fmaxf(m, nat > (keep_mono ? -1 : 0) ? fabsf(tc::f64_trunc_f32(v)) : 0.0f);
   }
   // the truncated maximum is every float-float head's bound below (same truncation)
-  const int e = tc::fp16_row_exp((double)block_max(m, red));
+  const int e = tc::fp16_row_exp_f(block_max(m, red));
   if (threadIdx.x == 0) {
     em[i] = e;
-    // the synthesis epilogue's per-shell constants: its unscaling factors and the monopole pair
+    // the synthesis epilogue's per-shell constants: the power of two that
+    // unscales its results, and the monopole pair brought into the scaled units
     float f1, f2;
-    tc::pow2_pair(-(q_exp + e), f1, f2);
+    tc::pow2_pair(q_exp + e, f1, f2);
     const float2 mm = mono ? mono[i] : make_float2(0.0f, 0.0f);
-    sc[i] = make_float4(f1, f2, mm.x, mm.y);
+    sc[i] = make_float4(__int_as_float(-(q_exp + e)), 0.0f, (mm.x * f1) * f2, (mm.y * f1) * f2);
   }
 #pragma unroll 4
   for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {

@@ -204,6 +204,18 @@ __host__ __device__ __forceinline__ int fp16_row_exp(double m) {
   return r < -200 ? -200 : (r > 200 ? 200 : r);
 }
 
+// The same exponent for an FP32 m >= 0, from its bits (no FP64 instruction:
+// GB300 runs those on a narrow pipe): frexp's exponent is the biased
+// exponent - 126 for normal m, and -117 - clz(mantissa) for subnormal m.
+__device__ __forceinline__ int fp16_row_exp_f(float m) {
+  const unsigned int u = __float_as_uint(m);
+  if (!(m > 0.0f)) return 0;
+  const int be = (int)(u >> 23);
+  const int e = be > 0 ? be - 126 : -117 - __clz(u & 0x7FFFFFu);
+  const int r = 15 - e;
+  return r < -200 ? -200 : (r > 200 ? 200 : r);
+}
+
 // Lane-wise FastTwoSum: s = fl(a + b), e = b - (s - a); exact (a + b = s + e)
 // when |a| >= |b| or a = 0, otherwise within one rounding of b.
 __device__ __forceinline__ void fast_two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e) {

@@ -95,10 +95,11 @@ struct TcArgs {
   // slices).  nullptr disables it.
   const float2* mono;
   int ab_fmt;           // operand type of the slices: 1 = BF16, 0 = FP16
-  // FP16 slices are scaled rows: sc[n] = {f1, f2, monopole head, tail}, the
-  // synthesis result of shell n multiplied by f1 f2 = 2^-(q_exp + m_exp[n])
-  // (two power-of-two factors), and the monopole pair read from here instead
-  // of mono (which then only says whether to add it).  nullptr: unscaled (BF16).
+  // FP16 slices are scaled rows: sc[n] = {d, 0, monopole head, tail}, with
+  // d = -(q_exp + m_exp[n]) (an int's bits) the power of two that unscales
+  // the synthesis result of shell n, applied as it is widened to FP64, and the
+  // monopole pair in the scaled units, read from here instead of mono (which
+  // then only says whether to add it).  nullptr: unscaled (BF16).
   const float4* sc;
 };
 
@@ -130,6 +131,15 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   const unsigned int e = (u >> 23) & 0xFFu;
   const unsigned int hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
   // selects, no branches: FP32 zeros and subnormals give +-0
+  return __hiloint2double((int)(e == 0 ? (u & 0x80000000u) : hi), (int)(e == 0 ? 0u : u << 29));
+}
+// f * 2^d exactly, for a normal result: d is added to the double's exponent
+// field (d20 = d << 20) while the value is widened, so the power-of-two
+// unscaling costs no arithmetic and cannot overflow FP32.
+__device__ __forceinline__ double f32_to_f64_pow2(float f, unsigned int d20) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  const unsigned int hi = (u & 0x80000000u) | (((e + 896u) << 20) + d20) | ((u & 0x7FFFFFu) >> 3);
   return __hiloint2double((int)(e == 0 ? (u & 0x80000000u) : hi), (int)(e == 0 ? 0u : u << 29));
 }
 
@@ -500,11 +510,10 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             if (a_loc >= nang) continue;
             float hs = hj, ls = lj, e0 = ev[jj];
             float2 mm = make_float2(0.0f, 0.0f);
-            if (sc) {  // exact unscaling of FP16-slice results: two power-of-two factors per shell
+            unsigned int d20 = 0u;  // FP16 slices: the exact unscaling, applied when widening to FP64
+            if (sc) {
               const float4 t4 = sc[n];
-              hs = (hs * t4.x) * t4.y;
-              ls = (ls * t4.x) * t4.y;
-              e0 = (e0 * t4.x) * t4.y;
+              d20 = (unsigned int)__float_as_int(t4.x) << 20;
               mm = make_float2(t4.z, t4.w);
             } else if (mono) {
               mm = mono[n];
@@ -524,10 +533,10 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             if (symmetric) {
               // Yin-Yang: Phi_Yin = E + O, Phi_Yang = E - O (O = 0 when there are no odd columns)
               const float ee = (nseg == 2) ? e0 : v, oo = (nseg == 2) ? v : 0.0f;
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64(ee + oo);
-              phi[off1 + (long long)n * nang + a_loc] = f32_to_f64(ee - oo);
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee + oo, d20);
+              phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee - oo, d20);
             } else {
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64(v);
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v, d20);
             }
           }
         }
