@@ -527,21 +527,24 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kern
 
 
 // Ms[s][i][pc]: FP16 slices of M's row i scaled by 2^em[i] (largest |M| over the
-// real columns; without keep_mono the monopole, whose Q column is zero, is
-// left out and written as 0).  One CTA per shell; FP64 values enter as float-float pairs.
-__global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_nat, const double* __restrict__ M,
-                                 int keep_mono, __half* __restrict__ Ms, int* __restrict__ em, int q_exp,
-                                 const float2* __restrict__ mono, float4* __restrict__ sc) {
+// row; without keep_mono the monopole, padded column 0, whose Q column is
+// zero, is left out and written as 0; padded columns hold zeros).  One CTA per
+// shell, a pair of adjacent columns per thread step (16-byte loads, 4-byte
+// stores); FP64 values enter as float-float pairs.  Also writes the synthesis
+// epilogue's per-shell constants sc[i].
+constexpr int kSliceM16Threads = 256;
+__global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
+    int n_r, int K_pad, const double* __restrict__ M, int keep_mono, __half* __restrict__ Ms, int* __restrict__ em,
+    int q_exp, const float2* __restrict__ mono, float4* __restrict__ sc) {
   __shared__ float red[32];
-  const int i = blockIdx.x;
+  const int i = blockIdx.x, npair = K_pad / 2;  // K_pad is a multiple of 64
   const long long splane = (long long)n_r * K_pad;
-  const double* row = M + (long long)i * K_pad;
+  const double2* row = reinterpret_cast<const double2*>(M + (long long)i * K_pad);
   float m = 0.0f;
-#pragma unroll 4
-  for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {
-    const double v = row[pc];
-    const int nat = pc_nat[pc];
-    m = fmaxf(m, nat > (keep_mono ? -1 : 0) ? fabsf(tc::f64_trunc_f32(v)) : 0.0f);
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    const double2 v = row[q];
+    const float a = (q == 0 && !keep_mono) ? 0.0f : fabsf(tc::f64_trunc_f32(v.x));
+    m = fmaxf(m, fmaxf(a, fabsf(tc::f64_trunc_f32(v.y))));
   }
   // the truncated maximum is every float-float head's bound below (same truncation)
   const int e = tc::fp16_row_exp_f(block_max(m, red));
@@ -554,17 +557,21 @@ __global__ void slice_m16_kernel(int n_r, int K_pad, const int* __restrict__ pc_
     const float2 mm = mono ? mono[i] : make_float2(0.0f, 0.0f);
     sc[i] = make_float4(__int_as_float(-(q_exp + e)), 0.0f, (mm.x * f1) * f2, (mm.y * f1) * f2);
   }
-#pragma unroll 4
-  for (int pc = threadIdx.x; pc < K_pad; pc += blockDim.x) {
-    const double v = row[pc];
-    const int nat = pc_nat[pc];
-    float hi = 0.0f, lo = 0.0f;
-    if (nat > (keep_mono ? -1 : 0)) tc::f64_to_ff_fast(v, hi, lo);
-    const float hs = tc::mul_pow2f(hi, e), ls = tc::mul_pow2f(lo, e);
-    const __half s0 = __float2half_rn(hs);
-    const __half s1 = __float2half_rn((hs - __half2float(s0)) + ls);
-    Ms[(long long)i * K_pad + pc] = s0;
-    Ms[splane + (long long)i * K_pad + pc] = s1;
+  float f1, f2;
+  tc::pow2_pair(e, f1, f2);
+  uint32_t* out0 = reinterpret_cast<uint32_t*>(Ms + (long long)i * K_pad);
+  uint32_t* out1 = reinterpret_cast<uint32_t*>(Ms + splane + (long long)i * K_pad);
+  for (int q = threadIdx.x; q < npair; q += blockDim.x) {
+    const double2 v = row[q];
+    float h0 = 0.0f, l0 = 0.0f, h1, l1;
+    if (!(q == 0 && !keep_mono)) tc::f64_to_ff_fast(v.x, h0, l0);
+    tc::f64_to_ff_fast(v.y, h1, l1);
+    const float a0 = (h0 * f1) * f2, a1 = (h1 * f1) * f2, b0 = (l0 * f1) * f2, b1 = (l1 * f1) * f2;
+    const __half2 s0 = __floats2half2_rn(a0, a1);  // the pair's first column in the low half
+    const float2 back = __half22float2(s0);
+    const __half2 s1 = __floats2half2_rn((a0 - back.x) + b0, (a1 - back.y) + b1);
+    out0[q] = h2_bits(s0);
+    out1[q] = h2_bits(s1);
   }
 }
 
@@ -616,6 +623,7 @@ __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
 // block barriers (no CTA waits on another).  Same arithmetic, in the same
 // order, as scan_local / scan_carry / scan_final.
 constexpr int kScanCols = 8, kScanMaxP = 128, kScanThreads = kScanCols * kScanMaxP;
+constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
 
 __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
@@ -641,33 +649,65 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
   if (p < kScanMaxP) {
     double I = 0.0, Pv = 0.0, FI = 1.0, FP = 1.0;
     if (live) {
-      for (int i = i0; i < i1; ++i) {
-        float h = 0.f, lo = 0.f;
-        const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
+      // shells in groups of kScanGroup: each chunk partial's loads for the
+      // whole group are issued together (the sum over chunks z stays in z
+      // order per shell); a chunk of at most one group keeps B in registers
+      const int* efc = ef ? ef + (long long)(pc >= k_split ? n_r : 0) * S : nullptr;
+      const int eup = (ef && !exact_mono) ? eu[pc] : 0;
+      double bb[kScanGroup];
+      for (int ib = i0; ib < i1; ib += kScanGroup) {
+        const int nb = min(kScanGroup, i1 - ib);
+        float hh[kScanGroup], ll[kScanGroup];
+#pragma unroll
+        for (int k = 0; k < kScanGroup; ++k) hh[k] = ll[k] = 0.f;
         for (int z = 0; z < S; ++z) {
-          float2 v;
-          if (exact_mono) {
-            v = mpart[(long long)z * n_r + i];
-          } else {
-            v = part[z * plane + (long long)i * K_pad + pc];
-            if (efi) {
-              const int es = -(efi[z] + eu[pc]);
-              v.x = tc::mul_pow2f(v.x, es);
-              v.y = tc::mul_pow2f(v.y, es);
+#pragma unroll
+          for (int k = 0; k < kScanGroup; ++k) {
+            if (k < nb) {
+              const int i = ib + k;
+              float2 v;
+              if (exact_mono) {
+                v = mpart[(long long)z * n_r + i];
+              } else {
+                v = part[z * plane + (long long)i * K_pad + pc];
+                if (efc) {
+                  const int es = -(efc[(long long)i * S + z] + eup);
+                  v.x = tc::mul_pow2f(v.x, es);
+                  v.y = tc::mul_pow2f(v.y, es);
+                }
+              }
+              float s, e;
+              tc::two_sum(hh[k], v.x, s, e);
+              hh[k] = s;
+              ll[k] += e + v.y;
             }
           }
-          float s, e;
-          tc::two_sum(h, v.x, s, e);
-          h = s;
-          lo += e + v.y;
         }
-        const double b = ff_to_f64(h, lo);
-        B[(long long)i * K_pad + pc] = b;
-        I = fma(at[i], b, fin[i] * I);
+#pragma unroll
+        for (int k = 0; k < kScanGroup; ++k) {
+          if (k < nb) {
+            const int i = ib + k;
+            const double b = ff_to_f64(hh[k], ll[k]);
+            B[(long long)i * K_pad + pc] = b;
+            bb[k] = b;
+            I = fma(at[i], b, fin[i] * I);
+          }
+        }
       }
-      for (int i = i1 - 1; i >= i0; --i) {
-        const double fo = (i > 0) ? fout[i - 1] : 0.0;
-        Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+      if (i1 - i0 <= kScanGroup) {
+#pragma unroll
+        for (int k = kScanGroup - 1; k >= 0; --k) {
+          if (k < i1 - i0) {
+            const int i = i0 + k;
+            const double fo = (i > 0) ? fout[i - 1] : 0.0;
+            Pv = fma(bt[i], bb[k], fo * Pv);
+          }
+        }
+      } else {
+        for (int i = i1 - 1; i >= i0; --i) {
+          const double fo = (i > 0) ? fout[i - 1] : 0.0;
+          Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+        }
       }
       FI = cp[(long long)l * P + p];
       FP = cp[(long long)(L + 1) * P + (long long)l * P + p];
@@ -714,16 +754,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
     }
     return;
   }
-  double Pv = cr[1][p][c];
-  for (int i = i1 - 1; i >= i0; --i) {
-    M[(long long)i * K_pad + pc] = Pv;
-    const double fo = (i > 0) ? fout[i - 1] : 0.0;
-    Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
-  }
-  double I = cr[0][p][c];
-  for (int i = i0; i < i1; ++i) {
-    I = fma(at[i], B[(long long)i * K_pad + pc], fin[i] * I);
-    const double m = M[(long long)i * K_pad + pc] + I;
+  auto emit = [&](int i, double m) {
     M[(long long)i * K_pad + pc] = m;
     if (pc == 0) {  // natural column 0 (l = 0) is padded column 0: the monopole
       float h, lo;
@@ -733,8 +764,45 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
     if (write_slices) {
       __nv_bfloat16 sl[3];
       slices_of(m, nsl, sl);
-      for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)  // constant indices keep sl in registers
+        if (k < nsl) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
     }
+  };
+  double Pv = cr[1][p][c];
+  double I = cr[0][p][c];
+  if (i1 - i0 <= kScanGroup) {
+    // the chunk's B and outer sums in registers; M written once
+    double bb[kScanGroup], pv[kScanGroup];
+#pragma unroll
+    for (int k = 0; k < kScanGroup; ++k) bb[k] = k < i1 - i0 ? B[(long long)(i0 + k) * K_pad + pc] : 0.0;
+#pragma unroll
+    for (int k = kScanGroup - 1; k >= 0; --k) {
+      pv[k] = Pv;
+      if (k < i1 - i0) {
+        const int i = i0 + k;
+        const double fo = (i > 0) ? fout[i - 1] : 0.0;
+        Pv = fma(bt[i], bb[k], fo * Pv);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kScanGroup; ++k) {
+      if (k < i1 - i0) {
+        const int i = i0 + k;
+        I = fma(at[i], bb[k], fin[i] * I);
+        emit(i, pv[k] + I);
+      }
+    }
+    return;
+  }
+  for (int i = i1 - 1; i >= i0; --i) {
+    M[(long long)i * K_pad + pc] = Pv;
+    const double fo = (i > 0) ? fout[i - 1] : 0.0;
+    Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+  }
+  for (int i = i0; i < i1; ++i) {
+    I = fma(at[i], B[(long long)i * K_pad + pc], fin[i] * I);
+    emit(i, M[(long long)i * K_pad + pc] + I);
   }
 }
 
@@ -1242,9 +1310,9 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
       p->symmetric ? p->tc_k_even : p->tc_k_pad, p->tc_fp16 ? p->tc_mpart : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !p->tc_fp16) return e;
-  slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_M, 0,
-                                          reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eq, p->tc_mono,
-                                          p->tc_sc);
+  slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_M, 0,
+                                                       reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eq,
+                                                       p->tc_mono, p->tc_sc);
   return cudaGetLastError();
 }
 
@@ -1303,9 +1371,9 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
       p->symmetric ? p->tc_k_even : p->tc_k_pad);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p->tc_fp16) {
-    slice_m16_kernel<<<p->n_r, 128, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_pc_nat, p->tc_Bbar, 1,
-                                            reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eus, nullptr,
-                                            p->tc_sc);
+    slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_Bbar, 1,
+                                                         reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eus,
+                                                         nullptr, p->tc_sc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
