@@ -550,12 +550,13 @@ __global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
   const int e = tc::fp16_row_exp_f(block_max(m, red));
   if (threadIdx.x == 0) {
     em[i] = e;
-    // the synthesis epilogue's per-shell constants: the power of two that
-    // unscales its results, and the monopole pair brought into the scaled units
+    // the synthesis epilogue's per-shell constants: the exponent rebase that
+    // unscales its results as they are widened to FP64, and the monopole pair
+    // brought into the scaled units
     float f1, f2;
     tc::pow2_pair(q_exp + e, f1, f2);
     const float2 mm = mono ? mono[i] : make_float2(0.0f, 0.0f);
-    sc[i] = make_float4(__int_as_float(-(q_exp + e)), 0.0f, (mm.x * f1) * f2, (mm.y * f1) * f2);
+    sc[i] = make_float4(__int_as_float((896 - (q_exp + e)) * (1 << 20)), 0.0f, (mm.x * f1) * f2, (mm.y * f1) * f2);
   }
   float f1, f2;
   tc::pow2_pair(e, f1, f2);

@@ -95,11 +95,12 @@ struct TcArgs {
   // slices).  nullptr disables it.
   const float2* mono;
   int ab_fmt;           // operand type of the slices: 1 = BF16, 0 = FP16
-  // FP16 slices are scaled rows: sc[n] = {d, 0, monopole head, tail}, with
-  // d = -(q_exp + m_exp[n]) (an int's bits) the power of two that unscales
-  // the synthesis result of shell n, applied as it is widened to FP64, and the
-  // monopole pair in the scaled units, read from here instead of mono (which
-  // then only says whether to add it).  nullptr: unscaled (BF16).
+  // FP16 slices are scaled rows: sc[n] = {c20, 0, monopole head, tail}, with
+  // c20 = (896 + d) << 20 (an int's bits) for d = -(q_exp + m_exp[n]), the
+  // power of two that unscales the synthesis result of shell n, applied as it
+  // is widened to FP64, and the monopole pair in the scaled units, read from
+  // here instead of mono (which then only says whether to add it).
+  // nullptr: unscaled (BF16).
   const float4* sc;
 };
 
@@ -133,14 +134,15 @@ __device__ __forceinline__ double f32_to_f64(float f) {
   // selects, no branches: FP32 zeros and subnormals give +-0
   return __hiloint2double((int)(e == 0 ? (u & 0x80000000u) : hi), (int)(e == 0 ? 0u : u << 29));
 }
-// f * 2^d exactly, for a normal result: d is added to the double's exponent
-// field (d20 = d << 20) while the value is widened, so the power-of-two
-// unscaling costs no arithmetic and cannot overflow FP32.
-__device__ __forceinline__ double f32_to_f64_pow2(float f, unsigned int d20) {
-  const unsigned int u = __float_as_uint(f);
-  const unsigned int e = (u >> 23) & 0xFFu;
-  const unsigned int hi = (u & 0x80000000u) | (((e + 896u) << 20) + d20) | ((u & 0x7FFFFFu) >> 3);
-  return __hiloint2double((int)(e == 0 ? (u & 0x80000000u) : hi), (int)(e == 0 ? 0u : u << 29));
+// f * 2^d exactly for a normal FP32 f: the magnitude bits shifted into the
+// double's layout and the exponent rebased by c20 = (896 + d) << 20 (896 =
+// 1023 - 127), so the power-of-two unscaling costs no arithmetic and cannot
+// overflow FP32.  Zeros stay exact; an FP32 subnormal (which the scaled
+// sums never produce) widens to a double subnormal.
+__device__ __forceinline__ double f32_to_f64_pow2(float f, unsigned int c20) {
+  const unsigned int u = __float_as_uint(f), mag = u & 0x7FFFFFFFu, sign = u & 0x80000000u;
+  const unsigned int hi = mag < 0x00800000u ? sign : (((mag >> 3) + c20) | sign);
+  return __hiloint2double((int)hi, (int)(u << 29));
 }
 
 __device__ __forceinline__ void set_err(int* err, int code) {
@@ -450,14 +452,35 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
         }
         if (!ok) break;
         if (MODE == kSynthesize && seg == 0 && nseg == 2 && active) {
-          // even block done: park E = hi + lo in TMEM, restart the sums for the odd block
+          // even block done: park E = hi + lo (+ the monopole, which belongs to
+          // E: its float-float pair is added before the one rounding to FP32)
+          // in TMEM, restart the sums for the odd block
+          const float4* const sce = R.A->sc;
+          const float2* const monoe = R.A->mono;
+          const int n_be = R.A->n_b;
 #pragma unroll
           for (int c0 = 0; c0 < NH; c0 += 8) {
             uint32_t ve[8];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
+              uint64_t hh = H[c0 / 2 + j], ll = L[c0 / 2 + j];
+              if (monoe) {
+                const int n0 = T.b_row0 + col0 + c0 + 2 * j;
+                float2 m0 = make_float2(0.0f, 0.0f), m1 = m0;
+                if (sce) {
+                  if (n0 < n_be) m0 = make_float2(sce[n0].z, sce[n0].w);
+                  if (n0 + 1 < n_be) m1 = make_float2(sce[n0 + 1].z, sce[n0 + 1].w);
+                } else {
+                  if (n0 < n_be) m0 = monoe[n0];
+                  if (n0 + 1 < n_be) m1 = monoe[n0 + 1];
+                }
+                uint64_t sm, em;
+                two_sum2(hh, pk2(m0.x, m1.x), sm, em);
+                hh = sm;
+                ll = add2(ll, add2(em, pk2(m0.y, m1.y)));
+              }
               float e0, e1;
-              upk2(add2(H[c0 / 2 + j], L[c0 / 2 + j]), e0, e1);
+              upk2(add2(hh, ll), e0, e1);
               ve[2 * j] = __float_as_uint(e0);
               ve[2 * j + 1] = __float_as_uint(e1);
               H[c0 / 2 + j] = L[c0 / 2 + j] = 0ull;
@@ -508,35 +531,25 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           } else {
             const long long a_loc = (long long)T.m_loc * BM + r;
             if (a_loc >= nang) continue;
-            float hs = hj, ls = lj, e0 = ev[jj];
-            float2 mm = make_float2(0.0f, 0.0f);
-            unsigned int d20 = 0u;  // FP16 slices: the exact unscaling, applied when widening to FP64
-            if (sc) {
-              const float4 t4 = sc[n];
-              d20 = (unsigned int)__float_as_int(t4.x) << 20;
-              mm = make_float2(t4.z, t4.w);
-            } else if (mono) {
-              mm = mono[n];
-            }
+            const float hs = hj, ls = lj, e0 = ev[jj];
+            // FP16 slices: the exact unscaling, applied when widening to FP64
+            const unsigned int c20 = sc ? (unsigned int)__float_as_int(sc[n].x) : (896u << 20);
             float v = hs + ls;
-            if (mono) {
-              // the monopole belongs to the even block (E) or, without the symmetry, to the only block
+            if (mono && nseg == 1) {
+              // without two column blocks the monopole belongs to the only one
+              // (with them, to E, where it was added when E was parked)
+              const float2 mm = sc ? make_float2(sc[n].z, sc[n].w) : mono[n];
               float s, e;
-              if (nseg == 2) {
-                two_sum(e0, mm.x, s, e);
-                e0 = s + (e + mm.y);
-              } else {
-                two_sum(hs, mm.x, s, e);
-                v = s + (e + mm.y + ls);
-              }
+              two_sum(hs, mm.x, s, e);
+              v = s + (e + mm.y + ls);
             }
             if (symmetric) {
               // Yin-Yang: Phi_Yin = E + O, Phi_Yang = E - O (O = 0 when there are no odd columns)
               const float ee = (nseg == 2) ? e0 : v, oo = (nseg == 2) ? v : 0.0f;
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee + oo, d20);
-              phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee - oo, d20);
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee + oo, c20);
+              phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee - oo, c20);
             } else {
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v, d20);
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v, c20);
             }
           }
         }
