@@ -63,9 +63,9 @@ def dist_env():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
 # pass on this workload at Nr = 400) of the current kernels, by precision and
 # phase; absent entries report null.  Source: profiles/tc_gemm_yinyang1deg_fp16x3.md.
-MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119396352 + 101581056,
-                    ("fp16x3", "projection", 400): 196937728 + 1191168,
-                    ("fp16x3", "field_slices", 400): 160508672 + 49695744}
+MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119340544 + 101447168,
+                    ("fp16x3", "projection", 400): 196942848 + 1384704,
+                    ("fp16x3", "field_slices", 400): 160486912 + 49733376}
 
 
 def load_peaks():
