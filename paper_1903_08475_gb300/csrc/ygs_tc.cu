@@ -842,31 +842,64 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
   {
     double Z = 0.0, FZ = 1.0, X = 0.0, FX = 1.0;
     if (live) {
-      for (int i = i0; i < i1; ++i) {
-        float h = 0.f, lo = 0.f;
-        const int* efi = ef ? ef + ((long long)(pc >= k_split ? n_r : 0) + i) * S : nullptr;
+      // as in the forward scan: the chunk-partial loads of a group of shells
+      // issued together (the sum over z in z order per shell), Mbar kept in
+      // registers for a chunk of at most one group
+      const int* efc = ef ? ef + (long long)(pc >= k_split ? n_r : 0) * S : nullptr;
+      const int ewp = ef ? ew[pc] : 0;
+      double mg[kScanGroup];
+      for (int ib = i0; ib < i1; ib += kScanGroup) {
+        const int nb = min(kScanGroup, i1 - ib);
+        float hh[kScanGroup], ll[kScanGroup];
+#pragma unroll
+        for (int k = 0; k < kScanGroup; ++k) hh[k] = ll[k] = 0.f;
         for (int z = 0; z < S; ++z) {
-          float2 v = part[z * plane + (long long)i * K_pad + pc];
-          if (efi) {
-            const int es = -(efi[z] + ew[pc]);
-            v.x = tc::mul_pow2f(v.x, es);
-            v.y = tc::mul_pow2f(v.y, es);
+#pragma unroll
+          for (int k = 0; k < kScanGroup; ++k) {
+            if (k < nb) {
+              const int i = ib + k;
+              float2 v = part[z * plane + (long long)i * K_pad + pc];
+              if (efc) {
+                const int es = -(efc[(long long)i * S + z] + ewp);
+                v.x = tc::mul_pow2f(v.x, es);
+                v.y = tc::mul_pow2f(v.y, es);
+              }
+              float s2, e;
+              tc::two_sum(hh[k], v.x, s2, e);
+              hh[k] = s2;
+              ll[k] += e + v.y;
+            }
           }
-          float s2, e;
-          tc::two_sum(h, v.x, s2, e);
-          h = s2;
-          lo += e + v.y;
         }
-        const double m = ff_to_f64(h, lo);
-        Mbar[(long long)i * K_pad + pc] = m;
-        const double hz = (i > 0) ? fout[i - 1] : 0.0;
-        Z = fma(hz, Z, m);
-        FZ *= hz;
+#pragma unroll
+        for (int k = 0; k < kScanGroup; ++k) {
+          if (k < nb) {
+            const int i = ib + k;
+            const double m = ff_to_f64(hh[k], ll[k]);
+            Mbar[(long long)i * K_pad + pc] = m;
+            mg[k] = m;
+            const double hz = (i > 0) ? fout[i - 1] : 0.0;
+            Z = fma(hz, Z, m);
+            FZ *= hz;
+          }
+        }
       }
-      for (int i = i1 - 1; i >= i0; --i) {
-        const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
-        X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
-        FX *= gx;
+      if (i1 - i0 <= kScanGroup) {
+#pragma unroll
+        for (int k = kScanGroup - 1; k >= 0; --k) {
+          if (k < i1 - i0) {
+            const int i = i0 + k;
+            const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
+            X = fma(gx, X, mg[k]);
+            FX *= gx;
+          }
+        }
+      } else {
+        for (int i = i1 - 1; i >= i0; --i) {
+          const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
+          X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
+          FX *= gx;
+        }
       }
     } else if (pc < K_pad && l < 0) {
       for (int i = i0; i < i1; ++i) Mbar[(long long)i * K_pad + pc] = 0.0;
@@ -913,23 +946,53 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
     }
     return;
   }
+  auto emit = [&](int i, double b) {
+    Bbar[(long long)i * K_pad + pc] = b;
+    if (write_slices) {
+      __nv_bfloat16 sl[3];
+      slices_of(b, nsl, sl);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)  // constant indices keep sl in registers
+        if (k < nsl) Bs[k * plane + (long long)i * K_pad + pc] = sl[k];
+    }
+  };
   double X = cr[1][p][c];  // X_{i1}
+  double Z = cr[0][p][c];  // Z_{i0-1}
+  if (i1 - i0 <= kScanGroup) {
+    // the chunk's Mbar and a_i X_i in registers; Bbar written once
+    double mg[kScanGroup], ax[kScanGroup];
+#pragma unroll
+    for (int k = 0; k < kScanGroup; ++k) mg[k] = k < i1 - i0 ? Mbar[(long long)(i0 + k) * K_pad + pc] : 0.0;
+#pragma unroll
+    for (int k = kScanGroup - 1; k >= 0; --k) {
+      ax[k] = 0.0;
+      if (k < i1 - i0) {
+        const int i = i0 + k;
+        const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
+        X = fma(gx, X, mg[k]);
+        ax[k] = at[i] * X;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kScanGroup; ++k) {
+      if (k < i1 - i0) {
+        const int i = i0 + k;
+        emit(i, fma(bt[i], Z, ax[k]));
+        const double hz = (i > 0) ? fout[i - 1] : 0.0;
+        Z = fma(hz, Z, mg[k]);
+      }
+    }
+    return;
+  }
   for (int i = i1 - 1; i >= i0; --i) {
     const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
     X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
     Bbar[(long long)i * K_pad + pc] = at[i] * X;
   }
-  double Z = cr[0][p][c];  // Z_{i0-1}
   for (int i = i0; i < i1; ++i) {
-    const double b = fma(bt[i], Z, Bbar[(long long)i * K_pad + pc]);
-    Bbar[(long long)i * K_pad + pc] = b;
+    emit(i, fma(bt[i], Z, Bbar[(long long)i * K_pad + pc]));
     const double hz = (i > 0) ? fout[i - 1] : 0.0;
     Z = fma(hz, Z, Mbar[(long long)i * K_pad + pc]);
-    if (write_slices) {
-      __nv_bfloat16 sl[3];
-      slices_of(b, nsl, sl);
-      for (int k = 0; k < nsl; ++k) Bs[k * plane + (long long)i * K_pad + pc] = sl[k];
-    }
   }
 }
 

@@ -139,3 +139,63 @@ def test_fp32_cuda_core_variant(cuda, name):
         err = rel_max(phi.cpu().numpy(), ref)
     print(f"fp32 {name}: {err:.2e}")
     assert err <= 1e-4
+
+
+def _rel_to_max(got, ref):
+    """Largest error relative to the largest |ref| (for fields that cross zero)."""
+    return float(np.max(np.abs(np.asarray(got) - ref)) / np.max(np.abs(ref)))
+
+
+def _special_density(grid, kind):
+    rng = np.random.default_rng(8)
+    n0 = grid.n_r * grid.nang(0)
+    if kind == "zero":
+        return np.zeros(grid.n_cells)
+    if kind == "signed":  # sums that change sign: the monopole's partials do not dominate
+        return rng.standard_normal(grid.n_cells)
+    yin = rng.uniform(0.5, 1.5, n0)
+    if kind == "yin_equals_yang":  # sigma- = 0 in every chunk
+        return np.concatenate([yin, yin])
+    if kind == "yang_zero":  # sigma+ = sigma- = rho_Yin
+        return np.concatenate([yin, np.zeros(grid.n_cells - n0)])
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("kind", ["zero", "signed", "yin_equals_yang", "yang_zero"])
+def test_special_densities(cuda, precision, kind):
+    """Densities that reach the degenerate branches of the split path: all zero
+    (every scale exponent from a zero maximum, Phi exactly zero), signed
+    (monopole partials of both signs), equal Yin and Yang values (a zero
+    sigma- plane) and an empty Yang patch."""
+    import torch
+    grid = small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9)
+    rho = _special_density(grid, kind)
+    with Plan(grid, precision) as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        torch.cuda.synchronize()
+        got = phi.cpu().numpy()
+    if kind == "zero":
+        assert np.all(got == 0.0)
+        return
+    ref = oracle.solve(grid, rho)
+    assert _rel_to_max(got, ref) <= TOL[precision], f"{kind} {precision}"
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+def test_signed_density_large_chunks(cuda, precision):
+    """Signed density on a 2-degree grid with config-1 shells and degree
+    (Nr = 400, l_max = 32), whose split-K chunks hold about 2000 cells: the
+    field pass's monopole sums (FastTwoSum) run over long chunks of terms of
+    both signs.  Zero-mean noise cancels: max |Phi(|rho|)| is ~400 x
+    max |Phi(rho)| here, so the error is bounded normwise, as any rounded sum
+    is, relative to the magnitudes summed (Phi of |rho|)."""
+    import torch
+    grid = small_yinyang(W, n_theta=46, n_phi=136, deg=2.0, n_r=400, l_max=32)
+    rho = np.random.default_rng(9).standard_normal(grid.n_cells)
+    ref = oracle.solve(grid, rho)
+    scale = np.max(np.abs(oracle.solve(grid, np.abs(rho))))
+    with Plan(grid, precision) as plan:
+        phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
+        torch.cuda.synchronize()
+        assert np.max(np.abs(phi.cpu().numpy() - ref)) <= TOL[precision] * scale
