@@ -310,14 +310,19 @@ __device__ __forceinline__ void sigma_ff(double r0, double r1, int symmetric, fl
   tc::two_sum(h0, -h1, hi[1], lo[1]);
 }
 
-// A thread's 8 cells of one pass step: the pairs q_u = base + u * T + t
-// (u = 0..3, T threads), cells 2 q_u and 2 q_u + 1 -> x[2u], x[2u + 1];
+#ifndef YGS_F16_PAIRS
+#define YGS_F16_PAIRS 2
+#endif
+constexpr int kF16Pairs = YGS_F16_PAIRS;  // cell pairs a thread takes per pass step
+
+// A thread's 2 kF16Pairs cells of one pass step: the pairs q_u = base + u * T + t
+// (u < kF16Pairs, T threads), cells 2 q_u and 2 q_u + 1 -> x[2u], x[2u + 1];
 // cells at or past n read as zero.  Interleaved pairs keep every warp access
 // contiguous and the threads' shares of a chunk within one pair of each other.
 __device__ __forceinline__ void load_pairs(const double* __restrict__ p, int n, int base, int T, bool vec,
-                                           double (&x)[8]) {
+                                           double (&x)[2 * kF16Pairs]) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < kF16Pairs; ++u) {
     const int c = 2 * (base + u * T + (int)threadIdx.x);
     if (vec && c + 2 <= n) {
       const double2 v = *reinterpret_cast<const double2*>(p + c);
@@ -336,10 +341,11 @@ __device__ __forceinline__ void load_pairs(const double* __restrict__ p, int n, 
 // within 2^-23 |x| of x): |t0 +- t1| + 2^-22 (|t0| + |t1|) bounds the rounded
 // sums sigma_ff forms, up to second-order terms that the (1 + 2^-16) applied
 // to the maximum covers.
-__device__ __forceinline__ void f16_group_max(const double (&x0)[8], const double (&x1)[8], int symmetric,
+__device__ __forceinline__ void f16_group_max(const double (&x0)[2 * kF16Pairs], const double (&x1)[2 * kF16Pairs],
+                                              int symmetric,
                                               float& mx0, float& mx1) {
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
+  for (int c = 0; c < 2 * kF16Pairs; ++c) {
     const float f0 = tc::f64_trunc_f32(x0[c]), f1 = symmetric ? tc::f64_trunc_f32(x1[c]) : 0.0f;
     const float slack = 0x1p-22f * (fabsf(f0) + fabsf(f1));
     mx0 = fmaxf(mx0, fabsf(f0 + f1) + slack);
@@ -353,9 +359,10 @@ __device__ __forceinline__ void f16_group_max(const double (&x0)[8], const doubl
 // the monopole weights (head, tail) of the same 8 cells, one 16-byte pair
 // each; pairs that start before n (the padded layout keeps their second cell
 // in bounds, and them 16-byte aligned), zero past it
-__device__ __forceinline__ void load_u_pairs(const float2* __restrict__ u, int n, int base, int T, float4 (&uu)[4]) {
+__device__ __forceinline__ void load_u_pairs(const float2* __restrict__ u, int n, int base, int T,
+                                             float4 (&uu)[kF16Pairs]) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kF16Pairs; ++k) {
     const int c = 2 * (base + k * T + (int)threadIdx.x);
     uu[k] = (u && c < n) ? *reinterpret_cast<const float4*>(u + c) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
@@ -365,13 +372,14 @@ __device__ __forceinline__ uint32_t h2_bits(__half2 v) {
   memcpy(&r, &v, sizeof(r));
   return r;
 }
-__device__ __forceinline__ void f16_group_store(const double (&x0)[8], const double (&x1)[8], int symmetric,
+__device__ __forceinline__ void f16_group_store(const double (&x0)[2 * kF16Pairs], const double (&x1)[2 * kF16Pairs],
+                                                int symmetric,
                                                 const float (&f)[2][2], __half* __restrict__ out, long long plane,
-                                                int n, int base, int T, bool mono, const float4 (&uu)[4],
+                                                int n, int base, int T, bool mono, const float4 (&uu)[kF16Pairs],
                                                 float& mh, float& ml) {
-  uint32_t w[2][2][4];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
+  uint32_t w[2][2][kF16Pairs];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < kF16Pairs; ++u) {
     float hi[2][2], lo[2][2];  // [cell of the pair][plane]
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
@@ -409,7 +417,7 @@ __device__ __forceinline__ void f16_group_store(const double (&x0)[8], const dou
     for (int k = 0; k < 2; ++k) {
       __half* dst = out + (long long)(h * 2 + k) * plane;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kF16Pairs; ++u) {
         const int c = 2 * (base + u * T + (int)threadIdx.x);
         if (c + 2 <= n) {
           *reinterpret_cast<uint32_t*>(dst + c) = w[h][k][u];
@@ -423,7 +431,7 @@ __device__ __forceinline__ void f16_group_store(const double (&x0)[8], const dou
 
 constexpr int kF16Threads = 256;
 #ifndef YGS_F16_MINB
-#define YGS_F16_MINB 3  // resident CTAs per SM the field pass's register budget is set for
+#define YGS_F16_MINB 4  // resident CTAs per SM the field pass's register budget is set for
 #endif
 
 // Field slices in FP16, one CTA per (split-K chunk z, shell i), 8 cells per
@@ -483,14 +491,14 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kern
   __half* out = F + (long long)i * n_pad + pad_off[g] + a0;  // 4-byte aligned: every offset is even
   const int nc = (int)n, T = blockDim.x, npair = (nc + 1) / 2;
   float mx0 = 0.0f, mx1 = 0.0f;
-  for (int base = 0; base < npair; base += 4 * T) {
-    double x0[8], x1[8];
+  for (int base = 0; base < npair; base += kF16Pairs * T) {
+    double x0[2 * kF16Pairs], x1[2 * kF16Pairs];
     load_pairs(x0p, nc, base, T, vec, x0);
     if (symmetric) {
       load_pairs(x1p, nc, base, T, vec, x1);
     } else {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
+      for (int c = 0; c < 2 * kF16Pairs; ++c) x1[c] = 0.0;
     }
     f16_group_max(x0, x1, symmetric, mx0, mx1);
   }
@@ -507,16 +515,16 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kern
   tc::pow2_pair(e1, f[1][0], f[1][1]);
   const float2* u = u00 ? u00 + pad_off[g] + a0 : nullptr;  // this chunk's monopole weights (padded layout)
   float mh = 0.0f, ml = 0.0f;
-  for (int base = 0; base < npair; base += 4 * T) {
-    double x0[8], x1[8];
+  for (int base = 0; base < npair; base += kF16Pairs * T) {
+    double x0[2 * kF16Pairs], x1[2 * kF16Pairs];
     load_pairs(x0p, nc, base, T, vec, x0);
     if (symmetric) {
       load_pairs(x1p, nc, base, T, vec, x1);
     } else {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) x1[c] = 0.0;
+      for (int c = 0; c < 2 * kF16Pairs; ++c) x1[c] = 0.0;
     }
-    float4 uu[4];
+    float4 uu[kF16Pairs];
     load_u_pairs(u, nc, base, T, uu);
     f16_group_store(x0, x1, symmetric, f, out, plane, nc, base, T, u != nullptr, uu, mh, ml);
   }
