@@ -160,6 +160,18 @@ ygs_status ygs_solve(ygs_plan* plan, const double* d_rho, double* d_phi, void* s
  * buffers should be page-locked for full copy bandwidth. */
 ygs_status ygs_solve_host(ygs_plan* plan, const double* h_rho, double* h_phi, void* stream);
 
+/* n solves of one plan from and to HOST buffers, pipelined: field k + 1 is
+ * copied host->device and Phi_{k-1} device->host (on two copy streams of the
+ * plan, made on first use) while field k is solved on `stream`, through two
+ * device staging pairs (4 * n_cells doubles, allocated on first use and kept
+ * with the plan).  h_rho[k] and h_phi[k] (HOST arrays of n host pointers)
+ * each hold n_cells doubles and should be page-locked, or the copies do not
+ * overlap.  Returns after the last Phi is in h_phi[n - 1] (synchronises
+ * `stream`; not capturable into a CUDA graph).  n = 0 does nothing.
+ * Errors: INVALID_ARG (NULL plan or pointer, n < 0), OOM, CUDA. */
+ygs_status ygs_solve_host_many(ygs_plan* plan, int n, const double* const* h_rho, double* const* h_phi,
+                               void* stream);
+
 /* n independent solves (plans may differ in every size) as one unit of work
  * on `stream`: the fields are forked onto a pool of internal worker streams
  * (fields of the same plan stay in order on one worker, since they share its

@@ -25,7 +25,8 @@ EVAL = {"upper_vertex": 0, "cell_centre": 1}
 FLAG_NO_SYMMETRY = 1
 FLAG_AUTOTUNE = 2
 
-EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_batched",
+EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_host_many",
+           "ygs_solve_batched",
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
            "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
            "ygs_debug_wait_timeout", "ygs_solve_static", "ygs_batch_create", "ygs_batch_solve",
@@ -80,6 +81,7 @@ def load_library(path: Optional[str] = None):
         L.ygs_solve.argtypes = [vp, vp, vp, vp]
         L.ygs_solve_host.argtypes = [vp, vp, vp, vp]
         L.ygs_solve_batched.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        L.ygs_solve_host_many.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.ygs_backward.argtypes = [vp, vp, vp, vp]
         L.ygs_get_moments.argtypes = [vp, vp, vp, vp]
         L.ygs_get_weights.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
@@ -254,6 +256,19 @@ def ygs_solve_host(plan: Plan, h_rho, h_phi, stream=None):
     """Host buffers in and out (copies inside the call); synchronous."""
     _check(load_library().ygs_solve_host(plan.handle, _ptr(h_rho), _ptr(h_phi), _stream_handle(stream)))
     return h_phi
+
+
+def ygs_solve_host_many(plan: Plan, h_rhos, h_phis, stream=None):
+    """n solves from and to host buffers with the copies overlapped (pinned
+    CPU tensors or arrays); returns h_phis after the last result is in."""
+    n = len(h_rhos)
+    if len(h_phis) != n:
+        raise ValueError("h_rhos and h_phis differ in length")
+    VA = ctypes.c_void_p * max(n, 1)
+    rp = VA(*[_ptr(r) for r in h_rhos])
+    pp = VA(*[_ptr(p) for p in h_phis])
+    _check(load_library().ygs_solve_host_many(plan.handle, n, rp, pp, _stream_handle(stream)))
+    return h_phis
 
 
 def ygs_solve_batched(plans: Sequence[Plan], rhos, phis, stream=None):

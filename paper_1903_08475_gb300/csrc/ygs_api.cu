@@ -65,10 +65,17 @@ bool finite(double x) { return std::isfinite(x); }
 void free_plan(ygs_plan* p) {
   if (!p) return;
   for (cudaEvent_t e : p->prof_events) cudaEventDestroy(e);
+  for (cudaStream_t st : {p->hm_in, p->hm_out})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t e : p->hm_ev)
+    if (e) cudaEventDestroy(e);
   tc_free(p);
   void* bufs[] = {p->U, p->Q, p->rad, p->col_l, p->col_nat, p->chunks, p->part, p->B, p->M,
-                  p->Mbar, p->Bbar, p->d_err, p->h2d_rho, p->h2d_phi, p->U32, p->Q32, p->f32_field,
-                  p->part32, p->M32};
+                  p->Mbar, p->Bbar, p->d_err, p->h2d_rho, p->h2d_phi, p->h2d_rho2, p->h2d_phi2,
+                  p->U32, p->Q32, p->f32_field, p->part32, p->M32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete p;
@@ -446,6 +453,53 @@ ygs_status ygs_solve_host(ygs_plan* p, const double* h_rho, double* h_phi, void*
   ygs_status st = ygs_solve(p, p->h2d_rho, p->h2d_phi, stream);
   if (st != YGS_OK) return st;
   API_TRY(cudaMemcpyAsync(h_phi, p->h2d_phi, bytes, cudaMemcpyDeviceToHost, s));
+  API_TRY(cudaStreamSynchronize(s));
+  return YGS_OK;
+}
+
+ygs_status ygs_solve_host_many(ygs_plan* p, int n, const double* const* h_rho, double* const* h_phi,
+                               void* stream) {
+  if (!p || n < 0 || (n > 0 && (!h_rho || !h_phi))) return fail(YGS_ERR_INVALID_ARG, "NULL argument or n < 0");
+  for (int k = 0; k < n; ++k)
+    if (!h_rho[k] || !h_phi[k]) return fail(YGS_ERR_INVALID_ARG, "NULL host buffer");
+  if (n == 0) return YGS_OK;
+  DeviceGuard guard(p->device);
+  const size_t bytes = (size_t)p->n_cells * sizeof(double);
+  double** rho[2] = {&p->h2d_rho, &p->h2d_rho2};
+  double** phi[2] = {&p->h2d_phi, &p->h2d_phi2};
+  for (int b = 0; b < 2; ++b) {
+    if (!*rho[b]) API_TRY(dev_malloc((void**)rho[b], bytes));
+    if (!*phi[b]) API_TRY(dev_malloc((void**)phi[b], bytes));
+  }
+  if (!p->hm_in) API_TRY(cudaStreamCreateWithFlags(&p->hm_in, cudaStreamNonBlocking));
+  if (!p->hm_out) API_TRY(cudaStreamCreateWithFlags(&p->hm_out, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : p->hm_ev)
+    if (!e) API_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaEvent_t start = p->hm_ev[0], *ev_in = p->hm_ev + 1, *ev_comp = p->hm_ev + 3, *ev_out = p->hm_ev + 5;
+  cudaStream_t s = (cudaStream_t)stream, in = p->hm_in, out = p->hm_out;
+  // the copy streams start after the work already queued on `stream`
+  API_TRY(cudaEventRecord(start, s));
+  API_TRY(cudaStreamWaitEvent(in, start, 0));
+  API_TRY(cudaStreamWaitEvent(out, start, 0));
+  for (int k = 0; k < n; ++k) {
+    const int b = k & 1;
+    // upload field k into staging pair b once solve k - 2 has read it
+    if (k >= 2) API_TRY(cudaStreamWaitEvent(in, ev_comp[b], 0));
+    API_TRY(cudaMemcpyAsync(*rho[b], h_rho[k], bytes, cudaMemcpyHostToDevice, in));
+    API_TRY(cudaEventRecord(ev_in[b], in));
+    // solve k once its input is in and the read-back of solve k - 2 has left pair b
+    API_TRY(cudaStreamWaitEvent(s, ev_in[b], 0));
+    if (k >= 2) API_TRY(cudaStreamWaitEvent(s, ev_out[b], 0));
+    ygs_status st = ygs_solve(p, *rho[b], *phi[b], stream);
+    if (st != YGS_OK) return st;
+    API_TRY(cudaEventRecord(ev_comp[b], s));
+    // read Phi_k back while solve k + 1 runs
+    API_TRY(cudaStreamWaitEvent(out, ev_comp[b], 0));
+    API_TRY(cudaMemcpyAsync(h_phi[k], *phi[b], bytes, cudaMemcpyDeviceToHost, out));
+    API_TRY(cudaEventRecord(ev_out[b], out));
+  }
+  // the read-back stream is in order: its last copy ends the batch
+  API_TRY(cudaStreamWaitEvent(s, ev_out[(n - 1) & 1], 0));
   API_TRY(cudaStreamSynchronize(s));
   return YGS_OK;
 }

@@ -63,6 +63,12 @@ struct ygs_plan {
   double* Bbar = nullptr;   // [n_r][K] adjoint workspace
   double* h2d_rho = nullptr;  // device staging for ygs_solve_host
   double* h2d_phi = nullptr;
+  // ygs_solve_host_many: the second staging pair, the copy streams and their
+  // events (start, in[2], comp[2], out[2]), made on first use
+  double* h2d_rho2 = nullptr;
+  double* h2d_phi2 = nullptr;
+  cudaStream_t hm_in = nullptr, hm_out = nullptr;
+  cudaEvent_t hm_ev[7] = {};
   int* d_err = nullptr;     // device error word
   cudaStream_t last_stream = nullptr;
   // phase profiling: 4 events per recorded call

@@ -77,6 +77,7 @@ def test_null_arguments_rejected():
     assert L.ygs_create(None, 0, None) == 1
     assert L.ygs_solve(None, None, None, None) == 1
     assert L.ygs_backward(None, None, None, None) == 1
+    assert L.ygs_solve_host_many(None, 1, None, None, None) == 1
     assert L.ygs_get_info(None, None) == 1
     assert L.ygs_destroy(None) == 0
 

@@ -138,3 +138,26 @@ def test_batch_rejects_repeated_plan(cuda):
         Batch([plans[0], plans[1], plans[0]])
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("precision", ["fp16x3", "fp64"])
+def test_solve_host_many_equals_device_solves(cuda, precision):
+    """The pipelined host-buffer entry point (uploads, solves and read-backs
+    of consecutive fields overlapped through two staging pairs) gives, field
+    by field, the same bits as ygs_solve on device buffers; n = 0 and n = 1
+    included."""
+    import torch
+    from paper_1903_08475_gb300 import ygs_solve_host_many
+    grid = small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9)
+    fields = [W.random_density(grid, 60 + k) * (1.0 + k) for k in range(5)]
+    with Plan(grid, precision) as plan:
+        ref = [ygs_solve(plan, torch.from_numpy(f).cuda()).cpu() for f in fields]
+        torch.cuda.synchronize()
+        for n in (0, 1, 5):
+            h_rho = [torch.from_numpy(f).pin_memory() for f in fields[:n]]
+            h_phi = [torch.empty_like(r).pin_memory() for r in h_rho]
+            ygs_solve_host_many(plan, h_rho, h_phi)
+            for k in range(n):
+                assert torch.equal(h_phi[k], ref[k]), (n, k)
+        with pytest.raises(ValueError):
+            ygs_solve_host_many(plan, [torch.zeros(1)], [])
