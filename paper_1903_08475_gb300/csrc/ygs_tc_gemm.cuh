@@ -44,7 +44,13 @@ constexpr int BM = 128;        // output rows per tile (TMEM lanes)
 // keep the tensor core compute-bound (a 128 x 80 x 16 MMA is bound by reading
 // its operands from shared memory) and cut the operand bytes per flop.
 constexpr int kNmaxProject = 144, kNhProject = 48;
-constexpr int kNmaxSynth = 144, kNhSynth = 48;
+#ifndef YGS_SYNTH_N
+#define YGS_SYNTH_N 144  // shells per synthesis tile
+#endif
+#ifndef YGS_SYNTH_NH
+#define YGS_SYNTH_NH 48  // of them per epilogue warp
+#endif
+constexpr int kNmaxSynth = YGS_SYNTH_N, kNhSynth = YGS_SYNTH_NH;
 
 template <int MODE>
 struct TileShape {
