@@ -245,7 +245,8 @@ __global__ void slice_ut16_kernel(int K, int K_pad, long long n_pad, const int* 
   }
 }
 
-// u00[row] = U[row][ci0] (the monopole weight of every stored cell) as a float-float pair.
+// u00[ap] = U[row][ci0] (the monopole weight of the stored cell at padded
+// angular index ap) as a float-float pair; zero in the padding.
 __global__ void u00_kernel(int K, int ci0, long long n_pad, PatchTable pt, int nwp,
                            const long long* __restrict__ pad_off, const double* __restrict__ U,
                            float2* __restrict__ u00) {
@@ -335,10 +336,8 @@ __device__ __forceinline__ void load_pairs(const double* __restrict__ p, int n, 
   }
 }
 
-// Largest |sigma+-| of 8 cells from truncated FP32 values (a few ulp from the
-// float-float heads used for the slices; the caller raises the maxima by 2^-16).
-// Upper bounds of |sigma+-| over 8 cells from the truncated heads t (each
-// within 2^-23 |x| of x): |t0 +- t1| + 2^-22 (|t0| + |t1|) bounds the rounded
+// Upper bounds of |sigma+-| over a thread's cells of one step from the
+// truncated heads t (each within 2^-23 |x| of x): |t0 +- t1| + 2^-22 (|t0| + |t1|) bounds the rounded
 // sums sigma_ff forms, up to second-order terms that the (1 + 2^-16) applied
 // to the maximum covers.
 __device__ __forceinline__ void f16_group_max(const double (&x0)[2 * kF16Pairs], const double (&x1)[2 * kF16Pairs],
@@ -353,10 +352,7 @@ __device__ __forceinline__ void f16_group_max(const double (&x0)[2 * kF16Pairs],
   }
 }
 
-// Scaled FP16 slices of 8 cells written as 16-byte stores (fewer at a ragged end).
-// With u (the monopole weights of these cells), plane 0's sigma * u is also
-// added to the float-float sum (mh, ml): the exact monopole moment.
-// the monopole weights (head, tail) of the same 8 cells, one 16-byte pair
+// the monopole weights (head, tail) of the same cells, one 16-byte pair
 // each; pairs that start before n (the padded layout keeps their second cell
 // in bounds, and them 16-byte aligned), zero past it
 __device__ __forceinline__ void load_u_pairs(const float2* __restrict__ u, int n, int base, int T,
@@ -372,6 +368,10 @@ __device__ __forceinline__ uint32_t h2_bits(__half2 v) {
   memcpy(&r, &v, sizeof(r));
   return r;
 }
+// Scaled FP16 slices of a thread's cells of one step, one 4-byte store per
+// cell pair, plane and slice (a 2-byte store at a ragged end).  With mono
+// (uu: the monopole weights of these cells), plane 0's sigma * u is also added
+// to the float-float sum (mh, ml): the exact monopole moment.
 __device__ __forceinline__ void f16_group_store(const double (&x0)[2 * kF16Pairs], const double (&x1)[2 * kF16Pairs],
                                                 int symmetric,
                                                 const float (&f)[2][2], __half* __restrict__ out, long long plane,
@@ -434,15 +434,6 @@ constexpr int kF16Threads = 256;
 #define YGS_F16_MINB 4  // resident CTAs per SM the field pass's register budget is set for
 #endif
 
-// Field slices in FP16, one CTA per (split-K chunk z, shell i), 8 cells per
-// thread and step: pass 1 finds the largest |sigma| of each plane over the
-// chunk's cells (ef[h][i][z]), pass 2 (the chunk now in L2) writes the scaled
-// slices F[h*2+s][i][apad], 16 bytes per store.  Every projection partial of
-// chunk z then carries one power of two per shell.  (Keeping a chunk in
-// registers between the passes instead ran at half the speed: one CTA per SM
-// could not hide the loads.)  Symmetric: planes sigma+ (h = 0) and sigma-
-// (h = 1) of the Yin/Yang rows; otherwise plane 0, each chunk lying inside one
-// stored patch.
 // Block sum of float-float partials (warp TwoSum tree, then warp 0's lane 0
 // over the warps); the result is valid in thread 0.
 __device__ __forceinline__ float2 block_ff_sum(float mh, float ml) {
@@ -473,6 +464,16 @@ __device__ __forceinline__ float2 block_ff_sum(float mh, float ml) {
   return make_float2(h, l);
 }
 
+// Field slices in FP16, one CTA per (split-K chunk z, shell i), kF16Pairs
+// interleaved cell pairs per thread and step: pass 1 bounds the largest |sigma|
+// of each plane over the chunk's cells (ef[h][i][z]), pass 2 (the chunk now in
+// L2) writes the scaled slices F[h*2+s][i][apad].  Every projection partial of
+// chunk z then carries one power of two per shell.  (Holding the chunk in
+// registers or shared memory between the passes, in clusters of CTAs that
+// exchange their maxima, measured slower: each CTA then waits through load,
+// reduction, cluster barrier and compute in turn.)  Symmetric: planes sigma+
+// (h = 0) and sigma- (h = 1) of the Yin/Yang rows; otherwise plane 0, each
+// chunk lying inside one stored patch.
 __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kernel(
     int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
     const int2* __restrict__ chunks, int S, const double* __restrict__ rho, __half* __restrict__ F,
