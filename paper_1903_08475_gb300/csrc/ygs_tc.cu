@@ -632,7 +632,10 @@ __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
 // chunk summaries and carries in shared memory and separates the phases with
 // block barriers (no CTA waits on another).  Same arithmetic, in the same
 // order, as scan_local / scan_carry / scan_final.
-constexpr int kScanCols = 8, kScanMaxP = 128, kScanThreads = kScanCols * kScanMaxP;
+#ifndef YGS_SCAN_COLS
+#define YGS_SCAN_COLS 2  // columns per scan CTA (256 threads: several CTAs share an SM and overlap their phases)
+#endif
+constexpr int kScanCols = YGS_SCAN_COLS, kScanMaxP = 128, kScanThreads = kScanCols * kScanMaxP;
 constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
 
 __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
