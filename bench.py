@@ -65,9 +65,9 @@ def dist_env():
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
 # pass on this workload at Nr = 400) of the current kernels, by precision and
 # phase; absent entries report null.  Source: profiles/tc_gemm_yinyang1deg_fp16x3.md.
-MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119340544 + 101447168,
-                    ("fp16x3", "projection", 400): 196942848 + 1384704,
-                    ("fp16x3", "field_slices", 400): 160486912 + 49733376}
+MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119222784 + 101773824,
+                    ("fp16x3", "projection", 400): 196941312 + 1273856,
+                    ("fp16x3", "field_slices", 400): 163332608 + 50309376}
 
 
 def load_peaks():
