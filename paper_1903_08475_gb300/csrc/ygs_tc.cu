@@ -630,8 +630,9 @@ __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
 // All three phases in one launch: a CTA owns kScanCols columns and up to
 // kScanMaxP chunks of shells (thread = column + kScanCols * chunk), keeps the
 // chunk summaries and carries in shared memory and separates the phases with
-// block barriers (no CTA waits on another).  Same arithmetic, in the same
-// order, as scan_local / scan_carry / scan_final.
+// block barriers (no CTA waits on another).  Phase 1: each chunk's
+// recurrences with zero carry and its summary (an affine map); phase 2: the
+// carries, a scan of those maps; phase 3: the recurrences with the carries.
 #ifndef YGS_SCAN_COLS
 #define YGS_SCAN_COLS 2  // columns per scan CTA (256 threads: several CTAs share an SM and overlap their phases)
 #endif
