@@ -1,14 +1,16 @@
 // Split-precision tensor-core contraction for sm_103a (tcgen05 + TMEM + TMA).
 //
-//   D[r][n] = sum_k A[r][k] * B[n][k],  A and B given as NSL BF16 slices each
-//   (A ~ A_0 + A_1 + A_2, likewise B), of which the products A_s B_t with
-//   s + t <= NSL - 1 are formed (3 for two slices, 6 for three).
+//   D[r][n] = sum_k A[r][k] * B[n][k],  A and B given as NSL BF16 slices, or
+//   NSL FP16 slices of power-of-two-scaled rows, each (A ~ A_0 + A_1 + A_2,
+//   likewise B), of which the products A_s B_t with s + t <= NSL - 1 are
+//   formed (3 for two slices, 6 for three).
 //
 // Persistent kernel: one CTA per SM walks a static list of 128 x n_eff output
-// tiles (n_eff = 128, or the tail width for the last shell tile).  Warp 0
-// streams A/B slice tiles of BK k-elements (128-byte rows, 128-byte swizzle)
-// through a ring of shared-memory stages with TMA; warp 1 issues tcgen05.mma
-// into FP32 TMEM accumulators; warps 2-17 drain them with tcgen05.ld.  The
+// tiles (n_eff = NMAX shells, 144 by default, or the tail width for the last
+// shell tile).  Warp 0 streams A/B slice tiles of BK k-elements (128-byte
+// rows, 128-byte swizzle) through a ring of shared-memory stages with TMA;
+// warp 1 issues tcgen05.mma into FP32 TMEM accumulators; the epilogue warps
+// (2 onwards, 4 per group of NH columns) drain them with tcgen05.ld.  The
 // tensor core's FP32 accumulation loses about one unit in the last place per
 // accumulation step, always in the same direction, so every product is
 // accumulated only over a short "group" of k-blocks in one of NBUF rotating
@@ -21,9 +23,9 @@
 //                moments: part[z][n][r].
 //   kSynthesize: tile = (cell tile m of patch g, shell tile n); segment 0 is
 //                the even-m column block, segment 1 (Yin-Yang symmetry) the
-//                odd block; the epilogue writes Phi_Yin = E + O and
-//                Phi_Yang = E - O (or Phi_g = E) in FP64, adding the monopole
-//                term exactly.
+//                odd block; E (with the monopole term, added in float-float)
+//                is parked in TMEM, and the epilogue writes Phi_Yin = E + O
+//                and Phi_Yang = E - O (or Phi_g = E + monopole) in FP64.
 #pragma once
 
 #include "ygs_internal.h"

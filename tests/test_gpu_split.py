@@ -3,9 +3,10 @@ tcgen05) against the CPU FP64 oracle, through the C ABI.
 
 BF16x6 (three slices, six products) and FP16x3 (two power-of-two-scaled FP16
 slices, three products) are held to 1e-6 relative error in Phi; BF16x3 (two
-slices, three products) to 5e-4.  The FP32 accumulation of the
-tensor cores is flushed into float-float sums every 64 k-elements, which keeps
-its bias far below these bounds."""
+slices, three products) to 5e-4.  The FP32 accumulation of the tensor cores
+is flushed into float-float sums every 64 or 128 k-elements (128 where the
+summed terms change sign and the monopole is summed exactly elsewhere), which
+keeps its bias far below these bounds."""
 import math
 
 import numpy as np
