@@ -166,7 +166,9 @@ ygs_status ygs_solve_host(ygs_plan* plan, const double* h_rho, double* h_phi, vo
  * device staging pairs (4 * n_cells doubles, allocated on first use and kept
  * with the plan).  h_rho[k] and h_phi[k] (HOST arrays of n host pointers)
  * each hold n_cells doubles and should be page-locked, or the copies do not
- * overlap.  Returns after the last Phi is in h_phi[n - 1] (synchronises
+ * overlap; an h_phi[k] must not overlap any h_rho[j] with j > k (those are
+ * still being read while Phi_k is written).  The same h_rho or h_phi buffer
+ * may appear several times.  Returns after the last Phi is in h_phi[n - 1] (synchronises
  * `stream`; not capturable into a CUDA graph).  n = 0 does nothing.
  * Errors: INVALID_ARG (NULL plan or pointer, n < 0), OOM, CUDA. */
 ygs_status ygs_solve_host_many(ygs_plan* plan, int n, const double* const* h_rho, double* const* h_phi,
