@@ -103,7 +103,7 @@ struct ygs_plan {
   int* tc_eu = nullptr;       // [K_pad] U^T row (column c)
   int* tc_ef = nullptr;       // [2][n_r][S] field row (plane, shell) per split-K chunk, written by every solve
   int* tc_em = nullptr;       // [n_r] M row (shell), written by every solve
-  float4* tc_sc = nullptr;    // [n_r] the synthesis epilogue's per-shell {f1, f2, monopole pair}, per solve
+  float4* tc_sc = nullptr;    // [n_r] the synthesis epilogue's per-shell {exponent rebase, 0, scaled monopole pair}, per solve
   float2* tc_u00 = nullptr;   // [n_wtotal] monopole weight of every stored cell (float-float)
   float2* tc_mpart = nullptr; // [S][n_r] exact monopole moment per split-K chunk, written by every solve
   CUtensorMap tc_map_ut, tc_map_f, tc_map_f_tail, tc_map_q, tc_map_m, tc_map_m_tail;
