@@ -78,7 +78,7 @@ struct ygs_plan {
   long long weight_bytes = 0, work_bytes = 0;
 
   // ---- split-precision (tcgen05) path
-  int tc_nsl = 0;            // BF16 slices per operand (0: FP64 path)
+  int tc_nsl = 0;            // BF16 or FP16 slices per operand (0: FP64 path)
   int tc_N = 0;              // shells per full tile
   int tc_np_full = 0;        // full shell tiles of the projection
   int tc_np_tail = 0;        // width of the projection's tail shell tile (0: none)
@@ -104,7 +104,7 @@ struct ygs_plan {
   int* tc_ef = nullptr;       // [2][n_r][S] field row (plane, shell) per split-K chunk, written by every solve
   int* tc_em = nullptr;       // [n_r] M row (shell), written by every solve
   float4* tc_sc = nullptr;    // [n_r] the synthesis epilogue's per-shell {exponent rebase, 0, scaled monopole pair}, per solve
-  float2* tc_u00 = nullptr;   // [n_wtotal] monopole weight of every stored cell (float-float)
+  float2* tc_u00 = nullptr;   // [n_pad] monopole weight of every stored cell (float-float), padded layout
   float2* tc_mpart = nullptr; // [S][n_r] exact monopole moment per split-K chunk, written by every solve
   CUtensorMap tc_map_ut, tc_map_f, tc_map_f_tail, tc_map_q, tc_map_m, tc_map_m_tail;
   // adjoint on the tensor cores: Q^T slices in the projection layout, U slices
