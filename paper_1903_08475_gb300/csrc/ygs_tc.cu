@@ -315,6 +315,7 @@ __device__ __forceinline__ void sigma_ff(double r0, double r1, int symmetric, fl
 #define YGS_F16_PAIRS 2
 #endif
 constexpr int kF16Pairs = YGS_F16_PAIRS;  // cell pairs a thread takes per pass step
+static_assert(kF16Pairs >= 1 && kF16Pairs <= 8, "field pass: 1 to 8 cell pairs per thread step");
 
 // A thread's 2 kF16Pairs cells of one pass step: the pairs q_u = base + u * T + t
 // (u < kF16Pairs, T threads), cells 2 q_u and 2 q_u + 1 -> x[2u], x[2u + 1];
@@ -638,6 +639,8 @@ __device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
 #endif
 constexpr int kScanCols = YGS_SCAN_COLS, kScanMaxP = 128, kScanThreads = kScanCols * kScanMaxP;
 constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
+static_assert(kScanCols >= 1 && kScanThreads <= 1024 && 2 * kScanCols <= kScanThreads / 32,
+              "scan: a CTA of at most 1024 threads with a warp per column and direction for the carries");
 
 __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
