@@ -91,17 +91,19 @@ struct ygs_plan {
   int tc_S = 0, tc_scan_chunk = 0, tc_scan_P = 0;
   __nv_bfloat16 *tc_ut = nullptr, *tc_qs = nullptr, *tc_f = nullptr, *tc_ms = nullptr;
   float2* tc_part = nullptr;
-  double *tc_B = nullptr, *tc_M = nullptr, *tc_summ = nullptr, *tc_carry = nullptr;
+  float2 *tc_B = nullptr, *tc_M = nullptr;  // [n_r][K_pad] float-float moments of the last solve
+  double *tc_summ = nullptr, *tc_carry = nullptr;
   int2* tc_chunks = nullptr;
   int *tc_pc_int = nullptr, *tc_pc_l = nullptr, *tc_pc_nat = nullptr;
   long long* tc_pad_off_d = nullptr;
   float2* tc_mono = nullptr;  // -G M[i][0] per shell as (hi, lo)
-  double* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells
+  float2* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells (float-float)
+  float2* tc_radff = nullptr; // [4][l_max+1][n_r] the radial tables a, b, f_in, f_out as float-float
   // FP16 slices (YGS_FP16X3): power-of-two exponents that scale each operand row into FP16's range
   int tc_fp16 = 0;
   int tc_eq = 0;              // Q (all rows)
   int* tc_eu = nullptr;       // [K_pad] U^T row (column c)
-  int* tc_ef = nullptr;       // [2][n_r][S] field row (plane, shell) per split-K chunk, written by every solve
+  float* tc_fac = nullptr;    // [2][n_pad / 128][n_r] 2^-e of the field row (plane, exponent group, shell), per solve
   int* tc_em = nullptr;       // [n_r] M row (shell), written by every solve
   float4* tc_sc = nullptr;    // [n_r] the synthesis epilogue's per-shell {exponent rebase, 0, scaled monopole pair}, per solve
   float2* tc_u00 = nullptr;   // [n_pad] monopole weight of every stored cell (float-float), padded layout
@@ -114,7 +116,7 @@ struct ygs_plan {
   __nv_bfloat16 *tc_qt = nullptr, *tc_us = nullptr;
   int* tc_eqt = nullptr;      // [K_pad] Q^T row (column c)
   int tc_eus = 0;             // U (all rows)
-  double *tc_Mbar = nullptr, *tc_Bbar = nullptr;
+  float2 *tc_Mbar = nullptr, *tc_Bbar = nullptr;  // float-float
   CUtensorMap tc_map_qt, tc_map_us;
 };
 
@@ -144,6 +146,15 @@ cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* 
 cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double* B, double* M, cudaStream_t s);
 // Mbar = sum_z part[z]; Bbar = transposed scans of Mbar.
 cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s);
+// Loads the FP64 kernels' module on the current device (they are loaded
+// lazily otherwise, at their first launch, which may allocate device memory).
+cudaError_t preload_fp64_kernels();
+// Makes the static scratch array of ygs_solve_static resident on the current
+// device (ygs_noalloc.cu): its module is loaded, and its array allocated, here
+// rather than at the first ygs_solve_static.
+cudaError_t prepare_static_scratch();
+// Scratch bytes ygs_solve_static needs for plan p: (S + 2) n_r K doubles.
+long long static_scratch_bytes(const ygs_plan* p);
 // out[i][col_nat[c]] = in[i][c]
 cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
 // FP64 -> FP32 (rounded, or truncated by integer operations)
@@ -160,15 +171,15 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s);
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s);
-cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
-// Batches: the split-precision plans of a batch grouped by slice count; each
+cudaError_t tc_unpermute(const ygs_plan* p, const float2* in, double* out, cudaStream_t s);
+// Batches: the split-precision plans of a batch grouped by operand kind; each
 // group's projection and synthesis tiles run in one persistent launch, with
 // the problems' tensor maps and arguments in device memory.
 namespace tc {
 struct TcProblem;
 }
 struct TcBatchGroup {
-  int nsl = 0, sms = 0, total_p = 0, total_s = 0;
+  int nsl = 0, fp16 = 0, sms = 0, total_p = 0, total_s = 0;
   std::vector<ygs_plan*> members;
   tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
   int *d_start_p = nullptr, *d_start_s = nullptr;

@@ -311,129 +311,18 @@ __device__ __forceinline__ void sigma_ff(double r0, double r1, int symmetric, fl
   tc::two_sum(h0, -h1, hi[1], lo[1]);
 }
 
-#ifndef YGS_F16_PAIRS
-#define YGS_F16_PAIRS 2
-#endif
-constexpr int kF16Pairs = YGS_F16_PAIRS;  // cell pairs a thread takes per pass step
-static_assert(kF16Pairs >= 1 && kF16Pairs <= 8, "field pass: 1 to 8 cell pairs per thread step");
-
-// A thread's 2 kF16Pairs cells of one pass step: the pairs q_u = base + u * T + t
-// (u < kF16Pairs, T threads), cells 2 q_u and 2 q_u + 1 -> x[2u], x[2u + 1];
-// cells at or past n read as zero.  Interleaved pairs keep every warp access
-// contiguous and the threads' shares of a chunk within one pair of each other.
-__device__ __forceinline__ void load_pairs(const double* __restrict__ p, int n, int base, int T, bool vec,
-                                           double (&x)[2 * kF16Pairs]) {
-#pragma unroll
-  for (int u = 0; u < kF16Pairs; ++u) {
-    const int c = 2 * (base + u * T + (int)threadIdx.x);
-    if (vec && c + 2 <= n) {
-      const double2 v = *reinterpret_cast<const double2*>(p + c);
-      x[2 * u] = v.x;
-      x[2 * u + 1] = v.y;
-    } else {
-      x[2 * u] = c < n ? p[c] : 0.0;
-      x[2 * u + 1] = c + 1 < n ? p[c + 1] : 0.0;
-    }
-  }
-}
-
-// Upper bounds of |sigma+-| over a thread's cells of one step from the
-// truncated heads t (each within 2^-23 |x| of x): |t0 +- t1| + 2^-22 (|t0| + |t1|) bounds the rounded
-// sums sigma_ff forms, up to second-order terms that the (1 + 2^-16) applied
-// to the maximum covers.
-__device__ __forceinline__ void f16_group_max(const double (&x0)[2 * kF16Pairs], const double (&x1)[2 * kF16Pairs],
-                                              int symmetric,
-                                              float& mx0, float& mx1) {
-#pragma unroll
-  for (int c = 0; c < 2 * kF16Pairs; ++c) {
-    const float f0 = tc::f64_trunc_f32(x0[c]), f1 = symmetric ? tc::f64_trunc_f32(x1[c]) : 0.0f;
-    const float slack = 0x1p-22f * (fabsf(f0) + fabsf(f1));
-    mx0 = fmaxf(mx0, fabsf(f0 + f1) + slack);
-    mx1 = fmaxf(mx1, fabsf(f0 - f1) + slack);
-  }
-}
-
-// the monopole weights (head, tail) of the same cells, one 16-byte pair
-// each; pairs that start before n (the padded layout keeps their second cell
-// in bounds, and them 16-byte aligned), zero past it
-__device__ __forceinline__ void load_u_pairs(const float2* __restrict__ u, int n, int base, int T,
-                                             float4 (&uu)[kF16Pairs]) {
-#pragma unroll
-  for (int k = 0; k < kF16Pairs; ++k) {
-    const int c = 2 * (base + k * T + (int)threadIdx.x);
-    uu[k] = (u && c < n) ? *reinterpret_cast<const float4*>(u + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-__device__ __forceinline__ uint32_t h2_bits(__half2 v) {
-  uint32_t r;
-  memcpy(&r, &v, sizeof(r));
-  return r;
-}
-// Scaled FP16 slices of a thread's cells of one step, one 4-byte store per
-// cell pair, plane and slice (a 2-byte store at a ragged end).  With mono
-// (uu: the monopole weights of these cells), plane 0's sigma * u is also added
-// to the float-float sum (mh, ml): the exact monopole moment.
-__device__ __forceinline__ void f16_group_store(const double (&x0)[2 * kF16Pairs], const double (&x1)[2 * kF16Pairs],
-                                                int symmetric,
-                                                const float (&f)[2][2], __half* __restrict__ out, long long plane,
-                                                int n, int base, int T, bool mono, const float4 (&uu)[kF16Pairs],
-                                                float& mh, float& ml) {
-  uint32_t w[2][2][kF16Pairs];  // [plane][slice][cell pair]: two FP16 values per word, lower cell first
-#pragma unroll
-  for (int u = 0; u < kF16Pairs; ++u) {
-    float hi[2][2], lo[2][2];  // [cell of the pair][plane]
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      const int c = 2 * u + d;
-      sigma_ff(x0[c], symmetric ? x1[c] : 0.0, symmetric, hi[d], lo[d]);
-      if (mono) {
-        // sigma+ times the weight in float-float (cells past the chunk carry
-        // sigma = 0): the heads' product with its rounding error from an FMA,
-        // the cross terms of the tails, the running sum by FastTwoSum (exact
-        // while the sum dominates, as it does for a positive density)
-        const float uh = d ? uu[u].z : uu[u].x, ul = d ? uu[u].w : uu[u].y;
-        const float pr = hi[d][0] * uh;
-        const float pe = fmaf(hi[d][0], ul, fmaf(lo[d][0], uh, fmaf(hi[d][0], uh, -pr)));
-        const float s2 = mh + pr;
-        ml += (pr - (s2 - mh)) + pe;
-        mh = s2;
-      }
-    }
-    // both cells' slices at once: s0 = fp16(hs), s1 = fp16((hs - s0) + ls)
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float a0 = (hi[0][h] * f[h][0]) * f[h][1], a1 = (hi[1][h] * f[h][0]) * f[h][1];
-      const float b0 = (lo[0][h] * f[h][0]) * f[h][1], b1 = (lo[1][h] * f[h][0]) * f[h][1];
-      const __half2 s0 = __floats2half2_rn(a0, a1);  // a0 in the low half
-      const float2 back = __half22float2(s0);
-      const __half2 s1 = __floats2half2_rn((a0 - back.x) + b0, (a1 - back.y) + b1);
-      w[h][0][u] = h2_bits(s0);
-      w[h][1][u] = h2_bits(s1);
-    }
-  }
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    if (h == 1 && !symmetric) break;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      __half* dst = out + (long long)(h * 2 + k) * plane;
-#pragma unroll
-      for (int u = 0; u < kF16Pairs; ++u) {
-        const int c = 2 * (base + u * T + (int)threadIdx.x);
-        if (c + 2 <= n) {
-          *reinterpret_cast<uint32_t*>(dst + c) = w[h][k][u];
-        } else if (c < n) {
-          dst[c] = __ushort_as_half((unsigned short)(w[h][k][u] & 0xFFFFu));
-        }
-      }
-    }
-  }
-}
-
+// The FP16 field pass works on exponent groups of kGroup = 128 angular cells
+// (two k-blocks, aligned to the padded layout, so never straddling a chunk or
+// a patch): every (plane, group, shell) row of a group is scaled by its own
+// power of two, and the projection applies the inverse at the flush that
+// closes the group (its accumulator holds exactly one group's products).
+constexpr int kGroup = 128;
 constexpr int kF16Threads = 256;
-#ifndef YGS_F16_MINB
-#define YGS_F16_MINB 4  // resident CTAs per SM the field pass's register budget is set for
+#ifndef YGS_FIELD_BATCH
+#define YGS_FIELD_BATCH 1
 #endif
+constexpr int kFieldBatch = YGS_FIELD_BATCH;  // exponent groups a warp loads at once
+static_assert(kFieldBatch >= 1 && kFieldBatch <= 4, "field pass: 1 to 4 groups per warp step");
 
 // Block sum of float-float partials (warp TwoSum tree, then warp 0's lane 0
 // over the warps); the result is valid in thread 0.
@@ -465,70 +354,145 @@ __device__ __forceinline__ float2 block_ff_sum(float mh, float ml) {
   return make_float2(h, l);
 }
 
-// Field slices in FP16, one CTA per (split-K chunk z, shell i), kF16Pairs
-// interleaved cell pairs per thread and step: pass 1 bounds the largest |sigma|
-// of each plane over the chunk's cells (ef[h][i][z]), pass 2 (the chunk now in
-// L2) writes the scaled slices F[h*2+s][i][apad].  Every projection partial of
-// chunk z then carries one power of two per shell.  (Holding the chunk in
-// registers or shared memory between the passes, in clusters of CTAs that
-// exchange their maxima, measured slower: each CTA then waits through load,
-// reduction, cluster barrier and compute in turn.)  Symmetric: planes sigma+
-// (h = 0) and sigma- (h = 1) of the Yin/Yang rows; otherwise plane 0, each
-// chunk lying inside one stored patch.
-__global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kernel(
+__device__ __forceinline__ uint32_t h2_bits(__half2 v) {
+  uint32_t r;
+  memcpy(&r, &v, sizeof(r));
+  return r;
+}
+
+// Four consecutive values of a row (cells c .. c + 3 of n; zero past n), by
+// two 16-byte loads where the row allows.
+__device__ __forceinline__ void load4(const double* __restrict__ p, long long c, long long n, bool vec,
+                                      double (&x)[4]) {
+  if (vec && c + 4 <= n) {
+    const double2 v0 = *reinterpret_cast<const double2*>(p + c);
+    const double2 v1 = *reinterpret_cast<const double2*>(p + c + 2);
+    x[0] = v0.x; x[1] = v0.y; x[2] = v1.x; x[3] = v1.y;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 4; ++d) x[d] = c + d < n ? p[c + d] : 0.0;
+  }
+}
+
+// The exponent e that puts a group's largest |head| m into [2^14, 2^15),
+// kept within FP32's normal range so that 2^e and 2^-e are single FP32
+// factors (groups whose largest value is below 2^-111 keep fewer bits).
+__device__ __forceinline__ int group_exp(float m) {
+  const int e = tc::fp16_row_exp_f(m);
+  return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+// Row length of the factor table: whole projection shell tiles, so that the
+// contraction's TMA warp copies a tile's row (kNmaxProject floats) in bounds.
+int fac_ld(const ygs_plan* p) { return (p->tc_np_full + (p->tc_np_tail > 0 ? 1 : 0)) * tc::kNmaxProject; }
+
+// Field slices in FP16 in one pass over rho.  One CTA per (split-K chunk z,
+// shell i); each warp takes whole exponent groups of the chunk, lane l the
+// cells 4l .. 4l + 3 of a group.  Per group and plane: sigma+- (or rho) in
+// float-float from the FP32-rounded values (sigma_ff), the largest |head| by a
+// warp max, its exponent e, the two FP16 slices of sigma * 2^e (one 8-byte
+// store per lane, plane and slice) and the factor 2^-e for the projection's
+// flush in fac[h][G][i] (G: the group's index in the padded angular layout;
+// rows of fac_ld floats).
+// With u00 (forward solves), plane 0's sigma * u (the monopole weight) is
+// summed in float-float per thread and reduced over the CTA into
+// mpart[z][i]: the monopole moment of the chunk, exactly to float-float
+// rounding.  Cells past the patch read as zero, so a group's padding is
+// written as zero slices.
+#ifndef YGS_F16_MINB
+#define YGS_F16_MINB 4  // resident CTAs per SM the field pass's register budget is set for
+#endif
+__global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field16_kernel(
     int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
-    const int2* __restrict__ chunks, int S, const double* __restrict__ rho, __half* __restrict__ F,
-    int* __restrict__ ef, const float2* __restrict__ u00, float2* __restrict__ mpart) {
-  __shared__ float red[32];
+    const int2* __restrict__ chunks, const double* __restrict__ rho, __half* __restrict__ F,
+    float* __restrict__ fac, int fac_ld, const float2* __restrict__ u00, float2* __restrict__ mpart) {
   const int z = blockIdx.x, i = blockIdx.y;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const long long plane = (long long)n_r * n_pad;
+  const long long ngroups_all = n_pad / kGroup;
   const int2 ch = chunks[z];
   int g = 0;
   while (g + 1 < nwp && pad_off[g + 1] <= ch.x) ++g;
   const long long na = pt.nang[g];
-  const long long a0 = ch.x - pad_off[g], n = min((long long)ch.y - pad_off[g], na) - a0;  // real cells of the chunk
-  const double* x0p = rho + pt.fld_off[g] + i * na + a0;
-  const double* x1p = symmetric ? rho + pt.fld_off[1] + i * na + a0 : x0p;
+  const double* x0p = rho + pt.fld_off[g] + (long long)i * na;
+  const double* x1p = symmetric ? rho + pt.fld_off[1] + (long long)i * na : x0p;
   const bool vec = ((reinterpret_cast<uintptr_t>(x0p) | reinterpret_cast<uintptr_t>(x1p)) & 15) == 0;
-  __half* out = F + (long long)i * n_pad + pad_off[g] + a0;  // 4-byte aligned: every offset is even
-  const int nc = (int)n, T = blockDim.x, npair = (nc + 1) / 2;
-  float mx0 = 0.0f, mx1 = 0.0f;
-  for (int base = 0; base < npair; base += kF16Pairs * T) {
-    double x0[2 * kF16Pairs], x1[2 * kF16Pairs];
-    load_pairs(x0p, nc, base, T, vec, x0);
-    if (symmetric) {
-      load_pairs(x1p, nc, base, T, vec, x1);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 2 * kF16Pairs; ++c) x1[c] = 0.0;
-    }
-    f16_group_max(x0, x1, symmetric, mx0, mx1);
-  }
-  // (1 + 2^-16) covers the bound's second-order terms; FP32 rounding of the
-  // product is monotonic, so it never falls below the maximum
-  const int e0 = tc::fp16_row_exp_f(block_max(mx0, red) * (1.0f + 0x1p-16f));
-  const int e1 = symmetric ? tc::fp16_row_exp_f(block_max(mx1, red) * (1.0f + 0x1p-16f)) : 0;
-  if (threadIdx.x == 0) {
-    ef[(long long)i * S + z] = e0;
-    ef[((long long)n_r + i) * S + z] = e1;
-  }
-  float f[2][2];
-  tc::pow2_pair(e0, f[0][0], f[0][1]);
-  tc::pow2_pair(e1, f[1][0], f[1][1]);
-  const float2* u = u00 ? u00 + pad_off[g] + a0 : nullptr;  // this chunk's monopole weights (padded layout)
+  const long long c_chunk = ch.x - pad_off[g];  // first cell of the chunk within patch g (a multiple of kGroup)
+  const int ngroups = (ch.y - ch.x) / kGroup;
+  const float2* const uz = u00 ? u00 + pad_off[g] : nullptr;
   float mh = 0.0f, ml = 0.0f;
-  for (int base = 0; base < npair; base += kF16Pairs * T) {
-    double x0[2 * kF16Pairs], x1[2 * kF16Pairs];
-    load_pairs(x0p, nc, base, T, vec, x0);
-    if (symmetric) {
-      load_pairs(x1p, nc, base, T, vec, x1);
-    } else {
+  // kFieldBatch groups per warp step, their loads issued together (more bytes
+  // in flight per warp: the pass is bound by memory latency, not issue)
+  for (int q0 = warp; q0 < ngroups; q0 += kFieldBatch * nw) {
+    double x0[kFieldBatch][4], x1[kFieldBatch][4];
+    float4 ua[kFieldBatch], ub[kFieldBatch];
 #pragma unroll
-      for (int c = 0; c < 2 * kF16Pairs; ++c) x1[c] = 0.0;
+    for (int b = 0; b < kFieldBatch; ++b) {
+      const int q = q0 + b * nw;
+      const long long c = c_chunk + (long long)q * kGroup + 4 * lane;  // this lane's first cell in patch g
+      const bool live = q < ngroups;
+      load4(x0p, c, live ? na : 0, vec, x0[b]);
+      load4(x1p, c, (live && symmetric) ? na : 0, vec, x1[b]);
+      // the monopole weights of the same cells (padded layout, zero in the padding)
+      ua[b] = (uz && live) ? *reinterpret_cast<const float4*>(uz + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ub[b] = (uz && live) ? *reinterpret_cast<const float4*>(uz + c + 2) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float4 uu[kF16Pairs];
-    load_u_pairs(u, nc, base, T, uu);
-    f16_group_store(x0, x1, symmetric, f, out, plane, nc, base, T, u != nullptr, uu, mh, ml);
+#pragma unroll
+    for (int b = 0; b < kFieldBatch; ++b) {
+      const int q = q0 + b * nw;
+      if (q >= ngroups) break;  // warp-uniform
+      const long long c = c_chunk + (long long)q * kGroup + 4 * lane;
+      float hi[4][2], lo[4][2];
+      float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        sigma_ff(x0[b][d], x1[b][d], symmetric, hi[d], lo[d]);
+        m0 = fmaxf(m0, fabsf(hi[d][0]));
+        m1 = fmaxf(m1, fabsf(hi[d][1]));
+      }
+      // non-negative floats order like their bit patterns
+      m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
+      m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
+      const int e[2] = {group_exp(m0), symmetric ? group_exp(m1) : 0};
+      const long long G = (ch.x / kGroup) + q;
+      if (lane < 2 && (lane == 0 || symmetric)) fac[((long long)lane * ngroups_all + G) * fac_ld + i] = pow2f(-e[lane]);
+      if (uz) {
+        // sigma+ times the weight in float-float (padding cells carry sigma = 0):
+        // the heads' product with its rounding error from an FMA, the tails'
+        // cross terms, the running sum by FastTwoSum (exact while the sum
+        // dominates, as it does for a positive density)
+        const float uh[4] = {ua[b].x, ua[b].z, ub[b].x, ub[b].z}, ul[4] = {ua[b].y, ua[b].w, ub[b].y, ub[b].w};
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const float pr = hi[d][0] * uh[d];
+          const float pe = fmaf(hi[d][0], ul[d], fmaf(lo[d][0], uh[d], fmaf(hi[d][0], uh[d], -pr)));
+          const float s2 = mh + pr;
+          ml += (pr - (s2 - mh)) + pe;
+          mh = s2;
+        }
+      }
+      __half* out = F + (long long)i * n_pad + pad_off[g] + c;  // 8-byte aligned: pad_off, c multiples of 4
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !symmetric) break;
+        const float f = pow2f(e[h]);
+        uint32_t w0[2], w1[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          // both cells of a pair at once: s0 = fp16(a), s1 = fp16((a - s0) + b)
+          const float a0 = hi[2 * u][h] * f, a1 = hi[2 * u + 1][h] * f;
+          const float b0 = lo[2 * u][h] * f, b1 = lo[2 * u + 1][h] * f;
+          const __half2 s0 = __floats2half2_rn(a0, a1);  // a0 in the low half
+          const float2 back = __half22float2(s0);
+          const __half2 s1 = __floats2half2_rn((a0 - back.x) + b0, (a1 - back.y) + b1);
+          w0[u] = h2_bits(s0);
+          w1[u] = h2_bits(s1);
+        }
+        *reinterpret_cast<uint2*>(out + (long long)(2 * h) * plane) = make_uint2(w0[0], w0[1]);
+        *reinterpret_cast<uint2*>(out + (long long)(2 * h + 1) * plane) = make_uint2(w1[0], w1[1]);
+      }
+    }
   }
   if (!mpart) return;
   const float2 m = block_ff_sum(mh, ml);
@@ -544,19 +508,19 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field_slices16_kern
 // epilogue's per-shell constants sc[i].
 constexpr int kSliceM16Threads = 256;
 __global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
-    int n_r, int K_pad, const double* __restrict__ M, int keep_mono, __half* __restrict__ Ms, int* __restrict__ em,
+    int n_r, int K_pad, const float2* __restrict__ M, int keep_mono, __half* __restrict__ Ms, int* __restrict__ em,
     int q_exp, const float2* __restrict__ mono, float4* __restrict__ sc) {
   __shared__ float red[32];
   const int i = blockIdx.x, npair = K_pad / 2;  // K_pad is a multiple of 64
   const long long splane = (long long)n_r * K_pad;
-  const double2* row = reinterpret_cast<const double2*>(M + (long long)i * K_pad);
+  const float4* row = reinterpret_cast<const float4*>(M + (long long)i * K_pad);  // two float-float columns each
   float m = 0.0f;
   for (int q = threadIdx.x; q < npair; q += blockDim.x) {
-    const double2 v = row[q];
-    const float a = (q == 0 && !keep_mono) ? 0.0f : fabsf(tc::f64_trunc_f32(v.x));
-    m = fmaxf(m, fmaxf(a, fabsf(tc::f64_trunc_f32(v.y))));
+    const float4 v = row[q];
+    const float a = (q == 0 && !keep_mono) ? 0.0f : fabsf(v.x);
+    m = fmaxf(m, fmaxf(a, fabsf(v.z)));
   }
-  // the truncated maximum is every float-float head's bound below (same truncation)
+  // the largest head bounds every head below
   const int e = tc::fp16_row_exp_f(block_max(m, red));
   if (threadIdx.x == 0) {
     em[i] = e;
@@ -573,10 +537,9 @@ __global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
   uint32_t* out0 = reinterpret_cast<uint32_t*>(Ms + (long long)i * K_pad);
   uint32_t* out1 = reinterpret_cast<uint32_t*>(Ms + splane + (long long)i * K_pad);
   for (int q = threadIdx.x; q < npair; q += blockDim.x) {
-    const double2 v = row[q];
-    float h0 = 0.0f, l0 = 0.0f, h1, l1;
-    if (!(q == 0 && !keep_mono)) tc::f64_to_ff_fast(v.x, h0, l0);
-    tc::f64_to_ff_fast(v.y, h1, l1);
+    const float4 v = row[q];
+    const bool skip = q == 0 && !keep_mono;
+    const float h0 = skip ? 0.0f : v.x, l0 = skip ? 0.0f : v.y, h1 = v.z, l1 = v.w;
     const float a0 = (h0 * f1) * f2, a1 = (h1 * f1) * f2, b0 = (l0 * f1) * f2, b1 = (l1 * f1) * f2;
     const __half2 s0 = __floats2half2_rn(a0, a1);  // the pair's first column in the low half
     const float2 back = __half22float2(s0);
@@ -586,11 +549,12 @@ __global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
   }
 }
 
-// Products of the radial ratios over every chunk of shells (per degree l):
+// Products of the radial ratios over every chunk of shells (per degree l),
+// as float-float:
 // cp[0][l][p] = prod_{i in chunk p} (r_{i-1}^+/r_i^+)^(l+1),
 // cp[1][l][p] = prod_{i in chunk p} (r_{i-1}^+/r_i^+)^l   (0 for chunks that contain shell 0).
 __global__ void chunk_prod_kernel(int n_r, int L, int chunk, int P, const double* __restrict__ rad,
-                                  double* __restrict__ cp) {
+                                  float2* __restrict__ cp) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (L + 1) * P) return;
   int l = t / P, p = t % P;
@@ -602,38 +566,103 @@ __global__ void chunk_prod_kernel(int n_r, int L, int chunk, int P, const double
     a *= fin[i];
     b *= (i > 0) ? fout[i - 1] : 0.0;
   }
-  cp[(long long)l * P + p] = a;
-  cp[(long long)(L + 1) * P + (long long)l * P + p] = b;
+  cp[(long long)l * P + p] = tc::ff_from_f64(a);
+  cp[(long long)(L + 1) * P + (long long)l * P + p] = tc::ff_from_f64(b);
 }
 
-__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-  return tc::f32_to_f64(hi) + tc::f32_to_f64(lo);
+// The radial tables a, b, f_in, f_out ([4][L + 1][n_r]) as float-float.
+__global__ void rad_ff_kernel(long long n, const double* __restrict__ rad, float2* __restrict__ radff) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    radff[e] = tc::ff_from_f64(rad[e]);
 }
 
 // Carries between chunks.  The chunk summaries define affine maps c -> F c + s;
 // one warp per column and direction composes them: each lane folds up to 32
 // consecutive chunks, this shuffle scan joins the lanes (inner recurrence
 // upward, outer downward), and each lane walks its chunks again.
-__device__ __forceinline__ void affine_scan_up(double& F, double& s, int lane) {
+__device__ __forceinline__ float2 shfl_up_ff(float2 v, int d) {
+  return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ void affine_scan_up(float2& F, float2& s, int lane) {
   // inclusive scan: after it lane p holds the composition of chunks 0..p
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const double Fo = __shfl_up_sync(0xffffffffu, F, d);
-    const double so = __shfl_up_sync(0xffffffffu, s, d);
+    const float2 Fo = shfl_up_ff(F, d), so = shfl_up_ff(s, d);
     if (lane >= d) {
-      s = fma(F, so, s);
-      F = F * Fo;
+      s = tc::ff_fma(F, so, s);
+      F = tc::ff_mul(F, Fo);
     }
   }
 }
 
+// Phase 2 of both scans: warp w < 2 kScanCols composes column w / 2's chunk
+// summaries upward (dir 0: sm[1] the factor, sm[0] the offset) or downward
+// (dir 1: sm[3], sm[2]) and writes each chunk's incoming carry to cr[dir].
+template <int kCols, int kMaxP>
+__device__ __forceinline__ void carry_scan(const float2 (&sm)[4][kMaxP][kCols], float2 (&cr)[2][kMaxP][kCols],
+                                           int P) {
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (w >= 2 * kCols) return;
+  const int cc = w >> 1, dir = w & 1;
+  const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
+  const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
+  float2 F = make_float2(1.0f, 0.0f), sv = make_float2(0.0f, 0.0f);
+  for (int t = t0; t < t1; ++t) {
+    const int pp = dir ? P - 1 - t : t;
+    sv = tc::ff_fma(sm[kF][pp][cc], sv, sm[ks][pp][cc]);
+    F = tc::ff_mul(sm[kF][pp][cc], F);
+  }
+  affine_scan_up(F, sv, lane);
+  float2 cin = shfl_up_ff(sv, 1);
+  if (lane == 0) cin = make_float2(0.0f, 0.0f);
+  for (int t = t0; t < t1; ++t) {
+    const int pp = dir ? P - 1 - t : t;
+    cr[dir][pp][cc] = cin;
+    cin = tc::ff_fma(sm[kF][pp][cc], cin, sm[ks][pp][cc]);
+  }
+}
 
-// All three phases in one launch: a CTA owns kScanCols columns and up to
+// The chunk partials of shell i, column pc summed over the chunks z in z
+// order (TwoSum), as float-float; FP16 plans' partials are unscaled by the
+// column's exponent first, and the monopole column of a forward FP16 solve
+// takes the field pass's exact chunk sums instead.
+__device__ __forceinline__ float2 sum_chunks(const float2* __restrict__ part, long long plane, int S, int i, int K_pad,
+                                             int pc, int escale, const float2* __restrict__ mp, int n_r) {
+  float hh = 0.0f, ll = 0.0f;
+  for (int z = 0; z < S; ++z) {
+    float2 v;
+    if (mp) {
+      v = mp[(long long)z * n_r + i];
+    } else {
+      v = part[z * plane + (long long)i * K_pad + pc];
+      if (escale) {
+        v.x = tc::mul_pow2f(v.x, -escale);
+        v.y = tc::mul_pow2f(v.y, -escale);
+      }
+    }
+    float s, e;
+    tc::two_sum(hh, v.x, s, e);
+    hh = s;
+    ll += e + v.y;
+  }
+  return tc::ff_renorm(hh, ll);
+}
+
+__device__ __forceinline__ void ff_slices(float2 v, int nsl, __nv_bfloat16 (&sl)[3]) {
+  tc::ff_to_bf16x3(v.x, v.y, sl[0], sl[1], sl[2]);
+  if (nsl == 2) sl[1] = __float2bfloat16_rn((v.x - __bfloat162float(sl[0])) + v.y);
+}
+
+// All three phases of the forward radial sums (Eq. M_C, step 4 of Sect. 4.3)
+// in one launch, in float-float: a CTA owns kScanCols columns and up to
 // kScanMaxP chunks of shells (thread = column + kScanCols * chunk), keeps the
 // chunk summaries and carries in shared memory and separates the phases with
-// block barriers (no CTA waits on another).  Phase 1: each chunk's
-// recurrences with zero carry and its summary (an affine map); phase 2: the
-// carries, a scan of those maps; phase 3: the recurrences with the carries.
+// block barriers (no CTA waits on another).  Phase 1: B from the projection's
+// chunk partials (step 3), each chunk's recurrences with zero carry
+//   I_i = a_i B_i + f_in,i I_{i-1},   O_i = b_i B_i + f_out,i-1 O_{i+1},
+// and its summary (an affine map); phase 2: the carries, a scan of those
+// maps; phase 3: the recurrences with the carries, M_i = I_i + O_{i+1}, its
+// BF16 slices (BF16 plans) and the monopole -G M[i][0].
 #ifndef YGS_SCAN_COLS
 #define YGS_SCAN_COLS 2  // columns per scan CTA (256 threads: several CTAs share an SM and overlap their phases)
 #endif
@@ -642,73 +671,46 @@ constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
 static_assert(kScanCols >= 1 && kScanThreads <= 1024 && 2 * kScanCols <= kScanThreads / 32,
               "scan: a CTA of at most 1024 threads with a warp per column and direction for the carries");
 
-__global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
+__global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
-    const double* __restrict__ rad, const double* __restrict__ cp, double* __restrict__ B, double* __restrict__ M,
-    __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, double G, float2* __restrict__ mono,
-    const int* __restrict__ ef, const int* __restrict__ eu, int k_split, const float2* __restrict__ mpart) {
-  __shared__ double sm[4][kScanMaxP][kScanCols];
-  __shared__ double cr[2][kScanMaxP][kScanCols];
+    const float2* __restrict__ rad, const float2* __restrict__ cp, float2* __restrict__ B, float2* __restrict__ M,
+    __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, float2 neg_G, float2* __restrict__ mono,
+    const int* __restrict__ eu, const float2* __restrict__ mpart) {
+  __shared__ float2 sm[4][kScanMaxP][kScanCols];
+  __shared__ float2 cr[2][kScanMaxP][kScanCols];
+  const float2 zero = make_float2(0.0f, 0.0f), one = make_float2(1.0f, 0.0f);
   const int c = threadIdx.x % kScanCols, p = threadIdx.x / kScanCols;
   const int pc = blockIdx.x * kScanCols + c;
   const int l = pc < K_pad ? pc_l[pc] : -1;
   const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
   const bool live = l >= 0 && p < P && i0 < n_r;
   const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
-  const long long splane = plane;
   const bool exact_mono = mpart && pc == 0;  // the monopole moment summed exactly by the field pass
   const int lq = l < 0 ? 0 : l;
-  const double* at = rad + (long long)lq * n_r;
-  const double* bt = rad + rs + (long long)lq * n_r;
-  const double* fin = rad + 2 * rs + (long long)lq * n_r;
-  const double* fout = rad + 3 * rs + (long long)lq * n_r;
+  const float2* at = rad + (long long)lq * n_r;
+  const float2* bt = rad + rs + (long long)lq * n_r;
+  const float2* fin = rad + 2 * rs + (long long)lq * n_r;
+  const float2* fout = rad + 3 * rs + (long long)lq * n_r;
   // ---- phase 1: B from the partials, local recurrences with zero carry, summaries
-  if (p < kScanMaxP) {
-    double I = 0.0, Pv = 0.0, FI = 1.0, FP = 1.0;
+  float2 bb[kScanGroup];  // the chunk's B, kept for phase 3 when it is one group
+  {
+    float2 I = zero, Pv = zero, FI = one, FP = one;
     if (live) {
-      // shells in groups of kScanGroup: each chunk partial's loads for the
-      // whole group are issued together (the sum over chunks z stays in z
-      // order per shell); a chunk of at most one group keeps B in registers
-      const int* efc = ef ? ef + (long long)(pc >= k_split ? n_r : 0) * S : nullptr;
-      const int eup = (ef && !exact_mono) ? eu[pc] : 0;
-      double bb[kScanGroup];
+      const int escale = (eu && !exact_mono) ? eu[pc] : 0;
       for (int ib = i0; ib < i1; ib += kScanGroup) {
-        const int nb = min(kScanGroup, i1 - ib);
-        float hh[kScanGroup], ll[kScanGroup];
+        float2 bg[kScanGroup];
 #pragma unroll
-        for (int k = 0; k < kScanGroup; ++k) hh[k] = ll[k] = 0.f;
-        for (int z = 0; z < S; ++z) {
-#pragma unroll
-          for (int k = 0; k < kScanGroup; ++k) {
-            if (k < nb) {
-              const int i = ib + k;
-              float2 v;
-              if (exact_mono) {
-                v = mpart[(long long)z * n_r + i];
-              } else {
-                v = part[z * plane + (long long)i * K_pad + pc];
-                if (efc) {
-                  const int es = -(efc[(long long)i * S + z] + eup);
-                  v.x = tc::mul_pow2f(v.x, es);
-                  v.y = tc::mul_pow2f(v.y, es);
-                }
-              }
-              float s, e;
-              tc::two_sum(hh[k], v.x, s, e);
-              hh[k] = s;
-              ll[k] += e + v.y;
-            }
-          }
-        }
+        for (int k = 0; k < kScanGroup; ++k)
+          bg[k] = ib + k < i1 ? sum_chunks(part, plane, S, ib + k, K_pad, pc, escale, exact_mono ? mpart : nullptr, n_r)
+                              : zero;
 #pragma unroll
         for (int k = 0; k < kScanGroup; ++k) {
-          if (k < nb) {
+          if (ib + k < i1) {
             const int i = ib + k;
-            const double b = ff_to_f64(hh[k], ll[k]);
-            B[(long long)i * K_pad + pc] = b;
-            bb[k] = b;
-            I = fma(at[i], b, fin[i] * I);
+            B[(long long)i * K_pad + pc] = bg[k];
+            I = tc::ff_add(tc::ff_mul(at[i], bg[k]), tc::ff_mul(fin[i], I));
           }
+          if (ib == i0) bb[k] = bg[k];
         }
       }
       if (i1 - i0 <= kScanGroup) {
@@ -716,110 +718,85 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
         for (int k = kScanGroup - 1; k >= 0; --k) {
           if (k < i1 - i0) {
             const int i = i0 + k;
-            const double fo = (i > 0) ? fout[i - 1] : 0.0;
-            Pv = fma(bt[i], bb[k], fo * Pv);
+            const float2 fo = (i > 0) ? fout[i - 1] : zero;
+            Pv = tc::ff_add(tc::ff_mul(bt[i], bb[k]), tc::ff_mul(fo, Pv));
           }
         }
       } else {
         for (int i = i1 - 1; i >= i0; --i) {
-          const double fo = (i > 0) ? fout[i - 1] : 0.0;
-          Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+          const float2 fo = (i > 0) ? fout[i - 1] : zero;
+          Pv = tc::ff_add(tc::ff_mul(bt[i], B[(long long)i * K_pad + pc]), tc::ff_mul(fo, Pv));
         }
       }
       FI = cp[(long long)l * P + p];
       FP = cp[(long long)(L + 1) * P + (long long)l * P + p];
     } else if (pc < K_pad && l < 0) {
-      for (int i = i0; i < i1; ++i) B[(long long)i * K_pad + pc] = 0.0;
+      for (int i = i0; i < i1; ++i) B[(long long)i * K_pad + pc] = zero;
     }
-    sm[0][p][c] = I;
-    sm[1][p][c] = FI;
-    sm[2][p][c] = Pv;
-    sm[3][p][c] = FP;
-  }
-  __syncthreads();
-  // ---- phase 2: carries; warp w < 2 kScanCols scans column w/2 upward (inner) or downward (outer)
-  {
-    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (w < 2 * kScanCols) {
-      const int cc = w >> 1, dir = w & 1;
-      const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
-      const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
-      double F = 1.0, sv = 0.0;
-      for (int t = t0; t < t1; ++t) {
-        const int pp = dir ? P - 1 - t : t;
-        sv = fma(sm[kF][pp][cc], sv, sm[ks][pp][cc]);
-        F = sm[kF][pp][cc] * F;
-      }
-      affine_scan_up(F, sv, lane);
-      double cin = __shfl_up_sync(0xffffffffu, sv, 1);
-      if (lane == 0) cin = 0.0;
-      for (int t = t0; t < t1; ++t) {
-        const int pp = dir ? P - 1 - t : t;
-        cr[dir][pp][cc] = cin;
-        cin = fma(sm[kF][pp][cc], cin, sm[ks][pp][cc]);
-      }
+    if (p < kScanMaxP) {
+      sm[0][p][c] = I;
+      sm[1][p][c] = FI;
+      sm[2][p][c] = Pv;
+      sm[3][p][c] = FP;
     }
   }
   __syncthreads();
-  // ---- phase 3: the recurrences with the carries; M (FP64), its BF16 slices, the monopole
+  // ---- phase 2: carries
+  carry_scan<kScanCols, kScanMaxP>(sm, cr, P);
+  __syncthreads();
+  // ---- phase 3: the recurrences with the carries; M, its BF16 slices, the monopole
   if (pc >= K_pad || p >= P || i0 >= n_r) return;
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
-      M[(long long)i * K_pad + pc] = 0.0;
+      M[(long long)i * K_pad + pc] = zero;
       if (write_slices)
-        for (int k = 0; k < nsl; ++k) Ms[k * splane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
+        for (int k = 0; k < nsl; ++k) Ms[k * plane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
     }
     return;
   }
-  auto emit = [&](int i, double m) {
+  auto emit = [&](int i, float2 m) {
     M[(long long)i * K_pad + pc] = m;
-    if (pc == 0) {  // natural column 0 (l = 0) is padded column 0: the monopole
-      float h, lo;
-      tc::f64_to_ff(-G * m, h, lo);
-      mono[i] = make_float2(h, lo);
-    }
+    if (pc == 0) mono[i] = tc::ff_mul(neg_G, m);  // natural column 0 (l = 0) is padded column 0: the monopole
     if (write_slices) {
       __nv_bfloat16 sl[3];
-      slices_of(m, nsl, sl);
+      ff_slices(m, nsl, sl);
 #pragma unroll
       for (int k = 0; k < 3; ++k)  // constant indices keep sl in registers
-        if (k < nsl) Ms[k * splane + (long long)i * K_pad + pc] = sl[k];
+        if (k < nsl) Ms[k * plane + (long long)i * K_pad + pc] = sl[k];
     }
   };
-  double Pv = cr[1][p][c];
-  double I = cr[0][p][c];
+  float2 Pv = cr[1][p][c];
+  float2 I = cr[0][p][c];
   if (i1 - i0 <= kScanGroup) {
     // the chunk's B and outer sums in registers; M written once
-    double bb[kScanGroup], pv[kScanGroup];
-#pragma unroll
-    for (int k = 0; k < kScanGroup; ++k) bb[k] = k < i1 - i0 ? B[(long long)(i0 + k) * K_pad + pc] : 0.0;
+    float2 pv[kScanGroup];
 #pragma unroll
     for (int k = kScanGroup - 1; k >= 0; --k) {
       pv[k] = Pv;
       if (k < i1 - i0) {
         const int i = i0 + k;
-        const double fo = (i > 0) ? fout[i - 1] : 0.0;
-        Pv = fma(bt[i], bb[k], fo * Pv);
+        const float2 fo = (i > 0) ? fout[i - 1] : zero;
+        Pv = tc::ff_add(tc::ff_mul(bt[i], bb[k]), tc::ff_mul(fo, Pv));
       }
     }
 #pragma unroll
     for (int k = 0; k < kScanGroup; ++k) {
       if (k < i1 - i0) {
         const int i = i0 + k;
-        I = fma(at[i], bb[k], fin[i] * I);
-        emit(i, pv[k] + I);
+        I = tc::ff_add(tc::ff_mul(at[i], bb[k]), tc::ff_mul(fin[i], I));
+        emit(i, tc::ff_add(pv[k], I));
       }
     }
     return;
   }
   for (int i = i1 - 1; i >= i0; --i) {
     M[(long long)i * K_pad + pc] = Pv;
-    const double fo = (i > 0) ? fout[i - 1] : 0.0;
-    Pv = fma(bt[i], B[(long long)i * K_pad + pc], fo * Pv);
+    const float2 fo = (i > 0) ? fout[i - 1] : zero;
+    Pv = tc::ff_add(tc::ff_mul(bt[i], B[(long long)i * K_pad + pc]), tc::ff_mul(fo, Pv));
   }
   for (int i = i0; i < i1; ++i) {
-    I = fma(at[i], B[(long long)i * K_pad + pc], fin[i] * I);
-    emit(i, M[(long long)i * K_pad + pc] + I);
+    I = tc::ff_add(tc::ff_mul(at[i], B[(long long)i * K_pad + pc]), tc::ff_mul(fin[i], I));
+    emit(i, tc::ff_add(M[(long long)i * K_pad + pc], I));
   }
 }
 
@@ -831,18 +808,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_fused_kernel(
 // chunked like the forward scans: the summaries [0] Z at the chunk's end and
 // [1] the product of its fout factors (upward), [2] X at its start and [3] the
 // product of its fin factors (downward), all with zero carry, are composed by
-// the same carry scan (scan_adj_fused_kernel).
-
-
-
-// The transposed scans in one launch, organised like scan_fused_kernel.
-__global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
+// the same carry scan, in float-float like the forward scan.
+__global__ void __launch_bounds__(kScanThreads) scan_adj_ff_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
-    const double* __restrict__ rad, double* __restrict__ Mbar, double* __restrict__ Bbar,
-    __nv_bfloat16* __restrict__ Bs, int nsl, int write_slices, const int* __restrict__ ef,
-    const int* __restrict__ ew, int k_split) {
-  __shared__ double sm[4][kScanMaxP][kScanCols];
-  __shared__ double cr[2][kScanMaxP][kScanCols];
+    const float2* __restrict__ rad, float2* __restrict__ Mbar, float2* __restrict__ Bbar,
+    __nv_bfloat16* __restrict__ Bs, int nsl, int write_slices, const int* __restrict__ ew) {
+  __shared__ float2 sm[4][kScanMaxP][kScanCols];
+  __shared__ float2 cr[2][kScanMaxP][kScanCols];
+  const float2 zero = make_float2(0.0f, 0.0f), one = make_float2(1.0f, 0.0f);
   const int c = threadIdx.x % kScanCols, p = threadIdx.x / kScanCols;
   const int pc = blockIdx.x * kScanCols + c;
   const int l = pc < K_pad ? pc_l[pc] : -1;
@@ -850,54 +823,31 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
   const bool live = l >= 0 && p < P && i0 < n_r;
   const long long plane = (long long)n_r * K_pad, rs = (long long)(L + 1) * n_r;
   const int lq = l < 0 ? 0 : l;
-  const double* at = rad + (long long)lq * n_r;
-  const double* bt = rad + rs + (long long)lq * n_r;
-  const double* fin = rad + 2 * rs + (long long)lq * n_r;
-  const double* fout = rad + 3 * rs + (long long)lq * n_r;
+  const float2* at = rad + (long long)lq * n_r;
+  const float2* bt = rad + rs + (long long)lq * n_r;
+  const float2* fin = rad + 2 * rs + (long long)lq * n_r;
+  const float2* fout = rad + 3 * rs + (long long)lq * n_r;
   // ---- phase 1: Mbar from the partials, chains with zero carry, summaries
+  float2 mg[kScanGroup];  // the chunk's Mbar, kept for phase 3 when it is one group
   {
-    double Z = 0.0, FZ = 1.0, X = 0.0, FX = 1.0;
+    float2 Z = zero, FZ = one, X = zero, FX = one;
     if (live) {
-      // as in the forward scan: the chunk-partial loads of a group of shells
-      // issued together (the sum over z in z order per shell), Mbar kept in
-      // registers for a chunk of at most one group
-      const int* efc = ef ? ef + (long long)(pc >= k_split ? n_r : 0) * S : nullptr;
-      const int ewp = ef ? ew[pc] : 0;
-      double mg[kScanGroup];
+      const int escale = ew ? ew[pc] : 0;  // FP16 plans: Q^T's row scale
       for (int ib = i0; ib < i1; ib += kScanGroup) {
-        const int nb = min(kScanGroup, i1 - ib);
-        float hh[kScanGroup], ll[kScanGroup];
+        float2 gg[kScanGroup];
 #pragma unroll
-        for (int k = 0; k < kScanGroup; ++k) hh[k] = ll[k] = 0.f;
-        for (int z = 0; z < S; ++z) {
-#pragma unroll
-          for (int k = 0; k < kScanGroup; ++k) {
-            if (k < nb) {
-              const int i = ib + k;
-              float2 v = part[z * plane + (long long)i * K_pad + pc];
-              if (efc) {
-                const int es = -(efc[(long long)i * S + z] + ewp);
-                v.x = tc::mul_pow2f(v.x, es);
-                v.y = tc::mul_pow2f(v.y, es);
-              }
-              float s2, e;
-              tc::two_sum(hh[k], v.x, s2, e);
-              hh[k] = s2;
-              ll[k] += e + v.y;
-            }
-          }
-        }
+        for (int k = 0; k < kScanGroup; ++k)
+          gg[k] = ib + k < i1 ? sum_chunks(part, plane, S, ib + k, K_pad, pc, escale, nullptr, n_r) : zero;
 #pragma unroll
         for (int k = 0; k < kScanGroup; ++k) {
-          if (k < nb) {
+          if (ib + k < i1) {
             const int i = ib + k;
-            const double m = ff_to_f64(hh[k], ll[k]);
-            Mbar[(long long)i * K_pad + pc] = m;
-            mg[k] = m;
-            const double hz = (i > 0) ? fout[i - 1] : 0.0;
-            Z = fma(hz, Z, m);
-            FZ *= hz;
+            Mbar[(long long)i * K_pad + pc] = gg[k];
+            const float2 hz = (i > 0) ? fout[i - 1] : zero;
+            Z = tc::ff_fma(hz, Z, gg[k]);
+            FZ = tc::ff_mul(FZ, hz);
           }
+          if (ib == i0) mg[k] = gg[k];
         }
       }
       if (i1 - i0 <= kScanGroup) {
@@ -905,20 +855,20 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
         for (int k = kScanGroup - 1; k >= 0; --k) {
           if (k < i1 - i0) {
             const int i = i0 + k;
-            const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
-            X = fma(gx, X, mg[k]);
-            FX *= gx;
+            const float2 gx = (i + 1 < n_r) ? fin[i + 1] : zero;
+            X = tc::ff_fma(gx, X, mg[k]);
+            FX = tc::ff_mul(FX, gx);
           }
         }
       } else {
         for (int i = i1 - 1; i >= i0; --i) {
-          const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
-          X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
-          FX *= gx;
+          const float2 gx = (i + 1 < n_r) ? fin[i + 1] : zero;
+          X = tc::ff_fma(gx, X, Mbar[(long long)i * K_pad + pc]);
+          FX = tc::ff_mul(FX, gx);
         }
       }
     } else if (pc < K_pad && l < 0) {
-      for (int i = i0; i < i1; ++i) Mbar[(long long)i * K_pad + pc] = 0.0;
+      for (int i = i0; i < i1; ++i) Mbar[(long long)i * K_pad + pc] = zero;
     }
     if (p < kScanMaxP) {
       sm[0][p][c] = Z;
@@ -929,118 +879,99 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_fused_kernel(
   }
   __syncthreads();
   // ---- phase 2: carries (Z upward, X downward)
-  {
-    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-    if (w < 2 * kScanCols) {
-      const int cc = w >> 1, dir = w & 1;
-      const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
-      const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
-      double F = 1.0, sv = 0.0;
-      for (int t = t0; t < t1; ++t) {
-        const int pp = dir ? P - 1 - t : t;
-        sv = fma(sm[kF][pp][cc], sv, sm[ks][pp][cc]);
-        F = sm[kF][pp][cc] * F;
-      }
-      affine_scan_up(F, sv, lane);
-      double cin = __shfl_up_sync(0xffffffffu, sv, 1);
-      if (lane == 0) cin = 0.0;
-      for (int t = t0; t < t1; ++t) {
-        const int pp = dir ? P - 1 - t : t;
-        cr[dir][pp][cc] = cin;
-        cin = fma(sm[kF][pp][cc], cin, sm[ks][pp][cc]);
-      }
-    }
-  }
+  carry_scan<kScanCols, kScanMaxP>(sm, cr, P);
   __syncthreads();
   // ---- phase 3: Bbar_i = a_i X_i + b_i Z_{i-1} with the carries, and its BF16 slices
   if (pc >= K_pad || p >= P || i0 >= n_r) return;
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
-      Bbar[(long long)i * K_pad + pc] = 0.0;
+      Bbar[(long long)i * K_pad + pc] = zero;
       if (write_slices)
         for (int k = 0; k < nsl; ++k) Bs[k * plane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
     }
     return;
   }
-  auto emit = [&](int i, double b) {
+  auto emit = [&](int i, float2 b) {
     Bbar[(long long)i * K_pad + pc] = b;
     if (write_slices) {
       __nv_bfloat16 sl[3];
-      slices_of(b, nsl, sl);
+      ff_slices(b, nsl, sl);
 #pragma unroll
       for (int k = 0; k < 3; ++k)  // constant indices keep sl in registers
         if (k < nsl) Bs[k * plane + (long long)i * K_pad + pc] = sl[k];
     }
   };
-  double X = cr[1][p][c];  // X_{i1}
-  double Z = cr[0][p][c];  // Z_{i0-1}
+  float2 X = cr[1][p][c];  // X_{i1}
+  float2 Z = cr[0][p][c];  // Z_{i0-1}
   if (i1 - i0 <= kScanGroup) {
     // the chunk's Mbar and a_i X_i in registers; Bbar written once
-    double mg[kScanGroup], ax[kScanGroup];
-#pragma unroll
-    for (int k = 0; k < kScanGroup; ++k) mg[k] = k < i1 - i0 ? Mbar[(long long)(i0 + k) * K_pad + pc] : 0.0;
+    float2 ax[kScanGroup];
 #pragma unroll
     for (int k = kScanGroup - 1; k >= 0; --k) {
-      ax[k] = 0.0;
+      ax[k] = zero;
       if (k < i1 - i0) {
         const int i = i0 + k;
-        const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
-        X = fma(gx, X, mg[k]);
-        ax[k] = at[i] * X;
+        const float2 gx = (i + 1 < n_r) ? fin[i + 1] : zero;
+        X = tc::ff_fma(gx, X, mg[k]);
+        ax[k] = tc::ff_mul(at[i], X);
       }
     }
 #pragma unroll
     for (int k = 0; k < kScanGroup; ++k) {
       if (k < i1 - i0) {
         const int i = i0 + k;
-        emit(i, fma(bt[i], Z, ax[k]));
-        const double hz = (i > 0) ? fout[i - 1] : 0.0;
-        Z = fma(hz, Z, mg[k]);
+        emit(i, tc::ff_fma(bt[i], Z, ax[k]));
+        const float2 hz = (i > 0) ? fout[i - 1] : zero;
+        Z = tc::ff_fma(hz, Z, mg[k]);
       }
     }
     return;
   }
   for (int i = i1 - 1; i >= i0; --i) {
-    const double gx = (i + 1 < n_r) ? fin[i + 1] : 0.0;
-    X = fma(gx, X, Mbar[(long long)i * K_pad + pc]);
-    Bbar[(long long)i * K_pad + pc] = at[i] * X;
+    const float2 gx = (i + 1 < n_r) ? fin[i + 1] : zero;
+    X = tc::ff_fma(gx, X, Mbar[(long long)i * K_pad + pc]);
+    Bbar[(long long)i * K_pad + pc] = tc::ff_mul(at[i], X);
   }
   for (int i = i0; i < i1; ++i) {
-    emit(i, fma(bt[i], Z, Bbar[(long long)i * K_pad + pc]));
-    const double hz = (i > 0) ? fout[i - 1] : 0.0;
-    Z = fma(hz, Z, Mbar[(long long)i * K_pad + pc]);
+    emit(i, tc::ff_fma(bt[i], Z, Bbar[(long long)i * K_pad + pc]));
+    const float2 hz = (i > 0) ? fout[i - 1] : zero;
+    Z = tc::ff_fma(hz, Z, Mbar[(long long)i * K_pad + pc]);
   }
 }
 
-// out[i][nat] = in[i][pc] for every real padded column.
+// out[i][nat] = in[i][pc] (float-float, widened to FP64) for every real padded column.
 __global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __restrict__ pc_nat,
-                                    const double* __restrict__ in, double* __restrict__ out) {
+                                    const float2* __restrict__ in, double* __restrict__ out) {
   long long total = (long long)n_r * K_pad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     long long i = e / K_pad;
     int pc = (int)(e % K_pad);
     int c = pc_nat[pc];
-    if (c >= 0) out[i * K + c] = in[e];
+    if (c >= 0) out[i * K + c] = (double)in[e].x + (double)in[e].y;
   }
 }
 
-template <int NSL, int MODE>
+template <int NSL, int MODE, bool SCALE>
 cudaError_t set_smem_attr() {
-  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       TcCfg<NSL, MODE>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE, SCALE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<NSL, MODE>::SMEM);
+  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE, SCALE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
 }
 
+// scale: the projection of FP16 field slices (group factors applied at the
+// flushes); two slices only
 template <int MODE>
-cudaError_t dispatch_gemm(int nsl, int grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& bt,
-                          const TcArgs& args, cudaStream_t s) {
+cudaError_t dispatch_gemm(int nsl, bool scale, int grid, const CUtensorMap& a, const CUtensorMap& b,
+                          const CUtensorMap& bt, const TcArgs& args, cudaStream_t s) {
   constexpr int threads = tc::TileShape<MODE>::THREADS;
-  if (nsl == 3) {
-    tc::tc_gemm_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(a, b, bt, args);
-  } else if (nsl == 2) {
-    tc::tc_gemm_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
+  if (nsl == 3 && !scale) {
+    tc::tc_gemm_kernel<3, MODE, false><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(a, b, bt, args);
+  } else if (nsl == 2 && !scale) {
+    tc::tc_gemm_kernel<2, MODE, false><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
+  } else if (nsl == 2 && MODE == tc::kProject) {
+    tc::tc_gemm_kernel<2, MODE, MODE == tc::kProject><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1048,13 +979,16 @@ cudaError_t dispatch_gemm(int nsl, int grid, const CUtensorMap& a, const CUtenso
 }
 
 template <int MODE>
-cudaError_t dispatch_group(int nsl, int grid, const tc::TcProblem* probs, const int* start, int n, int total,
-                          const tc::TcPhiList& phis, cudaStream_t s) {
+cudaError_t dispatch_group(int nsl, bool scale, int grid, const tc::TcProblem* probs, const int* start, int n,
+                           int total, const tc::TcPhiList& phis, cudaStream_t s) {
   constexpr int threads = tc::TileShape<MODE>::THREADS;
-  if (nsl == 3) {
-    tc::tc_gemm_group_kernel<3, MODE><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(probs, start, n, total, phis);
-  } else if (nsl == 2) {
-    tc::tc_gemm_group_kernel<2, MODE><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
+  if (nsl == 3 && !scale) {
+    tc::tc_gemm_group_kernel<3, MODE, false><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(probs, start, n, total, phis);
+  } else if (nsl == 2 && !scale) {
+    tc::tc_gemm_group_kernel<2, MODE, false><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
+  } else if (nsl == 2 && MODE == tc::kProject) {
+    tc::tc_gemm_group_kernel<2, MODE, MODE == tc::kProject>
+        <<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -1067,7 +1001,10 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   const int nsl = p->tc_nsl;
   const int K = p->K;
   auto r64 = [](long long x) { return (x + 63) / 64 * 64; };
-  auto r32 = [](long long x) { return (x + tc::BK - 1) / tc::BK * tc::BK; };  // angular padding to whole k-blocks
+  // angular padding to whole exponent groups (two k-blocks): chunk and
+  // patch starts then fall on group boundaries
+  auto r32 = [](long long x) { return (x + kGroup - 1) / kGroup * kGroup; };
+  static_assert(kGroup == 2 * tc::BK, "an exponent group is two k-blocks");
   // padded column layout: [even block | pad | odd block | pad]
   const int Ke = p->K_even, Ko = K - p->K_even;
   p->tc_k_even = (int)r64(Ke);
@@ -1112,7 +1049,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
       const long long kb_g = r32(p->nang[g]) / tc::BK;
       long long sg = std::max(1LL, (wv * p->nang[g] + p->nang_wtotal - 1) / p->nang_wtotal);
       sg = std::min(sg, std::max(1LL, kb_g / 4));
-      const long long per = (kb_g + sg - 1) / sg;
+      const long long per = ((kb_g + sg - 1) / sg + 1) / 2 * 2;  // whole exponent groups per chunk
       for (long long k0 = 0; k0 < kb_g; k0 += per)
         chunks.push_back(make_int2((int)((p->tc_pad_off[g] + k0 * tc::BK)),
                                    (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
@@ -1160,11 +1097,12 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_ALLOC(p->tc_pc_nat, kp * sizeof(int));
   TC_ALLOC(p->tc_pad_off_d, (p->n_wpatch + 1) * sizeof(long long));
   TC_ALLOC(p->tc_mono, (size_t)p->n_r * sizeof(float2));
-  TC_ALLOC(p->tc_cp, (size_t)2 * (p->l_max + 1) * p->tc_scan_P * sizeof(double));
+  TC_ALLOC(p->tc_cp, (size_t)2 * (p->l_max + 1) * p->tc_scan_P * sizeof(float2));
+  TC_ALLOC(p->tc_radff, (size_t)4 * (p->l_max + 1) * p->n_r * sizeof(float2));
   if (p->tc_fp16) {
     TC_ALLOC(p->tc_eqt, kp * sizeof(int));
     TC_ALLOC(p->tc_eu, kp * sizeof(int));
-    TC_ALLOC(p->tc_ef, (size_t)2 * p->n_r * s_max * sizeof(int));
+    TC_ALLOC(p->tc_fac, (size_t)2 * (p->tc_n_pad / kGroup) * fac_ld(p) * sizeof(float));
     TC_ALLOC(p->tc_u00, (size_t)p->tc_n_pad * sizeof(float2));
     TC_ALLOC(p->tc_mpart, s_max * p->n_r * sizeof(float2));
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
@@ -1185,8 +1123,12 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_TRY(cudaMemcpy(p->tc_pad_off_d, p->tc_pad_off.data(), (p->n_wpatch + 1) * sizeof(long long),
                     cudaMemcpyHostToDevice));
   TC_TRY(cudaMemset(p->tc_f, 0, bytes_f));  // padding columns stay zero
+  if (p->tc_fp16)  // factors of the shells past n_r (read with a tile's row, never written) stay zero
+    TC_TRY(cudaMemset(p->tc_fac, 0, (size_t)2 * (p->tc_n_pad / kGroup) * fac_ld(p) * sizeof(float)));
   chunk_prod_kernel<<<((p->l_max + 1) * p->tc_scan_P + 127) / 128, 128>>>(p->n_r, p->l_max, p->tc_scan_chunk,
                                                                           p->tc_scan_P, p->rad, p->tc_cp);
+  TC_TRY(cudaGetLastError());
+  rad_ff_kernel<<<256, 256>>>((long long)4 * (p->l_max + 1) * p->n_r, p->rad, p->tc_radff);
   TC_TRY(cudaGetLastError());
   if (p->tc_fp16) {
     colexp_u_kernel<<<p->tc_k_pad, 256>>>(K, p->tc_pc_int, p->nang_wtotal, p->U, p->tc_eu);
@@ -1258,11 +1200,11 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   {
     cudaError_t a1 = cudaSuccess, a2 = cudaSuccess;
     if (nsl == 3) {
-      a1 = set_smem_attr<3, tc::kProject>();
-      a2 = set_smem_attr<3, tc::kSynthesize>();
+      a1 = set_smem_attr<3, tc::kProject, false>();
+      a2 = set_smem_attr<3, tc::kSynthesize, false>();
     } else {
-      a1 = set_smem_attr<2, tc::kProject>();
-      a2 = set_smem_attr<2, tc::kSynthesize>();
+      a1 = p->tc_fp16 ? set_smem_attr<2, tc::kProject, true>() : set_smem_attr<2, tc::kProject, false>();
+      a2 = set_smem_attr<2, tc::kSynthesize, false>();
     }
     TC_TRY(a1);
     TC_TRY(a2);
@@ -1304,7 +1246,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
 void tc_free(ygs_plan* p) {
   void* bufs[] = {p->tc_ut,    p->tc_qs,     p->tc_f,      p->tc_ms,     p->tc_part,      p->tc_B,
                   p->tc_M,     p->tc_summ,   p->tc_carry,  p->tc_chunks, p->tc_pc_int,    p->tc_pc_l,
-                  p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_eu, p->tc_ef, p->tc_em,
+                  p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_radff, p->tc_eu, p->tc_fac, p->tc_em,
                   p->tc_qt,    p->tc_us,     p->tc_eqt,    p->tc_Mbar,   p->tc_Bbar,   p->tc_u00,
                   p->tc_mpart, p->tc_sc};
   for (void* b : bufs)
@@ -1315,9 +1257,9 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   if (p->tc_fp16) {
     const float2* u00 = forward ? p->tc_u00 : nullptr;
     float2* mpart = forward ? p->tc_mpart : nullptr;
-    field_slices16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(
-        p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, p->tc_S, rho,
-        reinterpret_cast<__half*>(p->tc_f), p->tc_ef, u00, mpart);
+    field16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(
+        p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, rho,
+        reinterpret_cast<__half*>(p->tc_f), p->tc_fac, fac_ld(p), u00, mpart);
     return cudaGetLastError();
   }
   long long nmax = 0;
@@ -1370,6 +1312,9 @@ static void project_args(const ygs_plan* p, TcArgs& a, bool forward = true) {
   a.chunks = p->tc_chunks;
   a.part = p->tc_part;
   a.ldp = p->tc_k_pad;
+  a.fac = p->tc_fp16 ? p->tc_fac : nullptr;
+  a.fac_ld = fac_ld(p);
+  a.fac_plane = (p->tc_n_pad / kGroup) * (long long)a.fac_ld;
   a.total_tiles = a.tiles_m * a.n_chunks * a.n_tiles;
 }
 
@@ -1377,17 +1322,19 @@ static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cuda
   TcArgs a;
   project_args(p, a, forward);
   const int grid = std::min(a.total_tiles, p->tc_sms);
-  return dispatch_gemm<tc::kProject>(p->tc_nsl, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
+  return dispatch_gemm<tc::kProject>(p->tc_nsl, a.fac != nullptr, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
 }
 
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) { return project_with(p, p->tc_map_ut, s); }
 
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   const int P = p->tc_scan_P;
-  scan_fused_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
-      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, P, p->tc_pc_l, p->tc_part, p->rad, p->tc_cp, p->tc_B,
-      p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->G, p->tc_mono, p->tc_ef, p->tc_eu,
-      p->symmetric ? p->tc_k_even : p->tc_k_pad, p->tc_fp16 ? p->tc_mpart : nullptr);
+  const float neg_gh = (float)(-p->G);
+  const float2 neg_g = make_float2(neg_gh, (float)(-p->G - (double)neg_gh));
+  scan_ff_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
+      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, P, p->tc_pc_l, p->tc_part, p->tc_radff, p->tc_cp,
+      p->tc_B, p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, neg_g, p->tc_mono, p->tc_fp16 ? p->tc_eu : nullptr,
+      p->tc_fp16 ? p->tc_mpart : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !p->tc_fp16) return e;
   slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_M, 0,
@@ -1427,7 +1374,7 @@ static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, d
   TcArgs a;
   synth_args(p, a, phi, mono);
   const int grid = std::min(a.total_tiles, p->tc_sms);
-  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
+  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, false, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
 }
 
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
@@ -1445,10 +1392,9 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if ((e = project_with(p, p->tc_map_qt, s, false)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
-  scan_adj_fused_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
-      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part, p->rad,
-      p->tc_Mbar, p->tc_Bbar, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->tc_ef, p->tc_eqt,
-      p->symmetric ? p->tc_k_even : p->tc_k_pad);
+  scan_adj_ff_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
+      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part, p->tc_radff,
+      p->tc_Mbar, p->tc_Bbar, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->tc_fp16 ? p->tc_eqt : nullptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p->tc_fp16) {
     slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_Bbar, 1,
@@ -1464,17 +1410,21 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
 
 ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
   b->groups.clear();
-  for (int nsl = 2; nsl <= 3; ++nsl) {
+  // one group per operand kind: BF16 two-slice, FP16 two-slice (whose
+  // projection applies the field's group factors), BF16 three-slice
+  for (int kind = 0; kind < 3; ++kind) {
+    const int nsl = kind == 2 ? 3 : 2, fp16 = kind == 1 ? 1 : 0;
     std::vector<ygs_plan*> mem;
     for (ygs_plan* p : plans)
-      if (p->tc_nsl == nsl) mem.push_back(p);
+      if (p->tc_nsl == nsl && p->tc_fp16 == fp16) mem.push_back(p);
     if (mem.empty()) continue;
     if ((int)mem.size() > tc::kMaxGroup) {
-      set_error("a batch holds at most 128 split-precision plans of one slice count");
+      set_error("a batch holds at most 128 split-precision plans of one operand kind");
       return YGS_ERR_UNSUPPORTED;
     }
     TcBatchGroup G;
     G.nsl = nsl;
+    G.fp16 = fp16;
     G.members = mem;
     std::vector<tc::TcProblem> proj(mem.size()), syn(mem.size());
     std::vector<int> sp(mem.size() + 1, 0), ss(mem.size() + 1, 0);
@@ -1526,14 +1476,14 @@ void tc_batch_free(TcBatch* b) {
 
 cudaError_t tc_batch_project(const TcBatchGroup& G, cudaStream_t s) {
   tc::TcPhiList none{};
-  return dispatch_group<tc::kProject>(G.nsl, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
+  return dispatch_group<tc::kProject>(G.nsl, G.fp16 != 0, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
                                       (int)G.members.size(), G.total_p, none, s);
 }
 
 cudaError_t tc_batch_synthesize(const TcBatchGroup& G, double* const* phi, cudaStream_t s) {
   tc::TcPhiList out{};
   for (size_t k = 0; k < G.members.size(); ++k) out.p[k] = phi[k];
-  return dispatch_group<tc::kSynthesize>(G.nsl, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
+  return dispatch_group<tc::kSynthesize>(G.nsl, false, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
                                          (int)G.members.size(), G.total_s, out, s);
 }
 
@@ -1557,7 +1507,7 @@ cudaError_t debug_wait_timeout(const ygs_plan* p, int spins, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t tc_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s) {
+cudaError_t tc_unpermute(const ygs_plan* p, const float2* in, double* out, cudaStream_t s) {
   tc_unpermute_kernel<<<256, 256, 0, s>>>(p->n_r, p->K, p->tc_k_pad, p->tc_pc_nat, in, out);
   return cudaGetLastError();
 }

@@ -62,6 +62,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Plain bulk copy global -> shared (no tensor map): `bytes` a multiple of 16,
+// both addresses 16-byte aligned; completion counted on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
 }
@@ -179,11 +188,41 @@ __device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 // Lane-wise TwoSum: s = fl(a + b) and e with a + b = s + e exactly.
 __device__ __forceinline__ void two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e) {
   s = add2(a, b);
   const uint64_t bb = sub2(s, a);
   e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
+// ---- float-float arithmetic (value = x + y, |y| <= ulp(x) / 2) -------------
+// The split path's radial scans run on these: GB300 issues FP64 at about two
+// FMAs per clock per SM, FP32 at 128, and the scans' results feed FP16 or
+// BF16 slices, so 2^-44 (normwise) accuracy is ample.  Sums are the
+// "sloppy" float-float addition: error <= 2^-44 (|a| + |b|).
+__device__ __forceinline__ float2 ff_renorm(float s, float e) {  // FastTwoSum, |s| >= |e|
+  const float h = s + e;
+  return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  return ff_renorm(s, e + (a.y + b.y));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  return ff_renorm(p, fmaf(a.x, b.y, fmaf(a.y, b.x, fmaf(a.x, b.x, -p))));
+}
+__device__ __forceinline__ float2 ff_fma(float2 a, float2 b, float2 c) { return ff_add(ff_mul(a, b), c); }
+// FP64 -> float-float (rounded head, rounded remainder): for tables made once
+__device__ __forceinline__ float2 ff_from_f64(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
 }
 
 // x * 2^e for |e| <= 252, as two exact multiplications by representable powers of two.
@@ -221,6 +260,27 @@ __device__ __forceinline__ int fp16_row_exp_f(float m) {
 __device__ __forceinline__ void fast_two_sum2(uint64_t a, uint64_t b, uint64_t& s, uint64_t& e) {
   s = add2(a, b);
   e = sub2(b, sub2(s, a));
+}
+
+// Lane-wise FastTwoSum of a + v * f for a power-of-two f (v * f exact):
+// s = fl(a + v f), e = v f - (s - a).
+// Two floats from shared memory, kept in program order (volatile): a load
+// the compiler may not hoist ahead of the TMEM loads it belongs with, so a
+// fully unrolled flush does not hold every pair's factors at once.
+__device__ __forceinline__ uint64_t lds_pair(const float* p) {
+  uint64_t r;
+  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(r) : "r"(smem_u32(p)));
+  return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ void fast_two_sum_scaled2(uint64_t a, uint64_t v, uint64_t f, uint64_t& s, uint64_t& e) {
+  const uint64_t vf = mul2(v, f);  // exact: f is a power of two
+  s = add2(a, vf);
+  e = sub2(vf, sub2(s, a));
 }
 
 // FP64 -> FP32 by truncation with integer operations only (GB300 runs FP64

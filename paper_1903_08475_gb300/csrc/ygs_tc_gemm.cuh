@@ -40,6 +40,9 @@ namespace tc {
 #ifndef YGS_EPI_CHUNK
 #define YGS_EPI_CHUNK 24  // TMEM columns an epilogue warp loads per wait (multiple of 8)
 #endif
+#ifndef YGS_EPI_CHUNK_SCALED
+#define YGS_EPI_CHUNK_SCALED 8  // the same for the flushes that apply the field's group factors
+#endif
 constexpr int BK = YGS_TC_BK;  // k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
 constexpr int BM = 128;        // output rows per tile (TMEM lanes)
 // Tile shapes (shells per tile, columns per epilogue warp).  144-shell tiles
@@ -69,6 +72,7 @@ struct TileShape {
 };
 
 enum Mode { kProject = 0, kSynthesize = 1 };
+constexpr int kGroupKb = 2;  // k-blocks per exponent group of the FP16 field slices
 
 struct TcArgs {
   int* err;
@@ -88,6 +92,14 @@ struct TcArgs {
   const int2* chunks;   // k range [x, y) of chunk z, in elements (multiples of BK)
   float2* part;         // [z][n_b][ldp] (hi, lo)
   int ldp;
+  // FP16 field slices: fac[h][G][n] = 2^-e of the field row (plane h, exponent
+  // group G of kGroupKb k-blocks, shell n), applied at each flush (a flush
+  // covers one group, or half of one).  Rows of fac_ld >= n_tiles * NMAX
+  // floats (zero past n_b), so that a tile's row is one 16-byte-aligned
+  // bulk copy; fac_plane = the offset of plane 1.  nullptr: unscaled.
+  const float* fac;
+  long long fac_plane;
+  int fac_ld;
   // ---- synthesis: tile = (patch g, m-tile, n-tile), n fastest
   int k_even;           // length of the even column block (elements, multiple of BK)
   int k_total;          // total padded columns
@@ -124,10 +136,22 @@ struct TcCfg {
 #else
   static constexpr int STAGES = (220 * 1024) / STAGE > 8 ? 8 : (220 * 1024) / STAGE;
 #endif
-  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+  // stages, alignment slack, barriers, and (projection) a ring of FAC_RING
+  // slots for the field's group factors of a tile's NMAX shells, filled by
+  // the TMA warp with each group's first k-block.  The ring cannot be lapped:
+  // the TMA warp writes the slot of group g after the MMAs of the k-block
+  // STAGES earlier have finished, i.e. after the epilogue has released group
+  // g - ceil(STAGES / flush) - 1 - NBUF or later, which is more than
+  // FAC_RING groups back for STAGES <= 3, NBUF <= 3, any flush >= 1.
+  static constexpr int FAC_OFF = 512;
+  static constexpr int FAC_RING = 8;
+  static constexpr int FAC_BYTES = MODE == 0 ? FAC_RING * NMAX * 4 : 0;
+  static_assert(MODE != 0 || FAC_RING > 3 + 1 + 3, "factor ring deeper than the pipeline's lead");
+  static constexpr int SMEM = STAGES * STAGE + 1024 + FAC_OFF + FAC_BYTES;
   static constexpr int NBUF = TileShape<MODE>::NBUF;
   static constexpr int E_COL0 = NBUF * NMAX;  // first TMEM column of the parked E (synthesis)
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
+  static_assert(MODE != 0 || (STAGES <= 3 && NBUF <= 3), "the factor ring's depth assumes STAGES, NBUF <= 3");
 };
 
 // (s, t) slice pairs in issue order; pair 0 is the leading product.
@@ -256,8 +280,13 @@ struct GroupSrc {  // tiles of several problems concatenated: problem k owns [st
   }
 };
 
-template <int NSL, int MODE, class Src>
+// SCALE (projection of FP16 field slices only): undo the field's group
+// factors at every flush.  A compile-time switch: each instance then holds
+// only its own flush code, and the epilogue's float-float sums stay in
+// registers.
+template <int NSL, int MODE, bool SCALE, class Src>
 __device__ __forceinline__ void gemm_body(const Src& src) {
+  static_assert(!SCALE || MODE == kProject, "only the projection scales its flushes");
   using C = TcCfg<NSL, MODE>;
   constexpr int NMAX = TileShape<MODE>::NMAX;
   constexpr int NH = TileShape<MODE>::NH;
@@ -271,6 +300,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   uint64_t* mma_done = tempty + C::NBUF;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  float* fac_ring = (float*)(smem + C::STAGES * C::STAGE + C::FAC_OFF);  // [FAC_RING][NMAX] (projection)
+  static_assert((2 * C::STAGES + 2 * C::NBUF + 2) * 8 + 8 <= C::FAC_OFF, "barriers fit below the factor slots");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -299,7 +330,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   if (warp == 0) {
     // ================= TMA producer =================
     if (lane == 0) {
-      int issued = 0;
+      int issued = 0, fgroups = 0;  // k-blocks issued; factor rows issued (the ring's position)
       bool ok = true;
       int* err = nullptr;
       for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
@@ -309,6 +340,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
         const CUtensorMap* mb = T.use_tail ? R.mbt : R.mb;
         const uint32_t bytes = NSL * (C::A_SLICE + T.n_eff * BK * 2);
         const int nkb = T.seg_kb0 + T.seg_kb1;
+        const float* const fac = SCALE ? R.A->fac : nullptr;
+        const int flush = R.A->flush_kb;
         for (int kb = 0; kb < nkb; ++kb) {
           const int stage = issued % C::STAGES;
           const uint32_t ph = (issued / C::STAGES) & 1;
@@ -318,7 +351,14 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           }
           uint8_t* sA = smem + stage * C::STAGE;
           uint8_t* sB = sA + NSL * C::A_SLICE;
-          mbar_arrive_expect_tx(&full[stage], bytes);
+          const bool fac_now = SCALE && kb % flush == 0;  // first k-block of a flush group
+          mbar_arrive_expect_tx(&full[stage], bytes + (fac_now ? NMAX * 4 : 0));
+          if (fac_now) {
+            const int G = (T.kstart / BK + kb) / kGroupKb;
+            const float* src = fac + (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
+            bulk_load(fac_ring + (fgroups % C::FAC_RING) * NMAX, src, NMAX * 4, &full[stage]);
+            ++fgroups;
+          }
           const int kx = T.kstart + kb * BK;
 #pragma unroll
           for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, R.ma, &full[stage], kx, T.a_row0, s);
@@ -423,6 +463,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
 #pragma unroll
       for (int j = 0; j < NH / 2; ++j) H[j] = L[j] = 0ull;
       const int nseg = T.seg_kb1 > 0 ? 2 : 1;
+      // FP16 projection: the field's group factors of the tile's shells, in
+      // the ring slot the TMA warp filled with the group's first k-block
       for (int seg = 0; seg < nseg && ok; ++seg) {
         const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
         for (int kg = 0; kg < nkb; kg += flush, ++gglob) {
@@ -433,8 +475,11 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           }
           tc_fence_after();
           if (active) {
-            // CH columns in flight per wait
-            constexpr int CH = YGS_EPI_CHUNK < NH ? YGS_EPI_CHUNK : NH;
+            const float* const fslot = SCALE ? fac_ring + (gglob % C::FAC_RING) * NMAX + col0 : nullptr;
+            // CH columns in flight per wait (fewer when scaling: each pair's
+            // factors are live beside its values)
+            constexpr int CH0 = SCALE ? YGS_EPI_CHUNK_SCALED : YGS_EPI_CHUNK;
+            constexpr int CH = CH0 < NH ? CH0 : NH;
 #pragma unroll
             for (int c0 = 0; c0 < NH; c0 += CH) {
               uint32_t vm[CH];
@@ -448,7 +493,12 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
                 // (always for same-sign terms); where it does not, the pair still
                 // holds the sum within one rounding of that flush
                 uint64_t s, e;
-                fast_two_sum2(H[c0 / 2 + j], pk2(__uint_as_float(vm[2 * j]), __uint_as_float(vm[2 * j + 1])), s, e);
+                const uint64_t v = pk2(__uint_as_float(vm[2 * j]), __uint_as_float(vm[2 * j + 1]));
+                if (SCALE) {
+                  fast_two_sum_scaled2(H[c0 / 2 + j], v, lds_pair(fslot + c0 + 2 * j), s, e);
+                } else {
+                  fast_two_sum2(H[c0 / 2 + j], v, s, e);
+                }
                 H[c0 / 2 + j] = s;
                 L[c0 / 2 + j] = add2(L[c0 / 2 + j], e);
               }
@@ -575,8 +625,11 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// Registers: 14 warps (448 threads), at most 128 each: a CTA's warps are
+// spread over the SM's four sub-partitions (16,384 registers each), four
+// warps on two of them, so 4 x 32 x 128 is the ceiling for one CTA per SM.
 // One problem: maps and arguments in kernel parameters.
-template <int NSL, int MODE>
+template <int NSL, int MODE, bool SCALE>
 __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ TcArgs args) {
@@ -586,18 +639,18 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     prefetch_tmap(&mapBt);
   }
   const SingleSrc src{&args, &mapA, &mapB, &mapBt};
-  gemm_body<NSL, MODE>(src);
+  gemm_body<NSL, MODE, SCALE>(src);
 }
 
 // Several problems of one operand type in one persistent launch (a batch of
 // fields): every CTA walks the concatenated tile list; TMEM accumulators and
 // shared-memory stages carry over from one problem to the next.
-template <int NSL, int MODE>
+template <int NSL, int MODE, bool SCALE>
 __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     tc_gemm_group_kernel(const TcProblem* __restrict__ probs, const int* __restrict__ start, int n, int total,
                          const __grid_constant__ TcPhiList phis) {
   const GroupSrc src{probs, start, n, total, &phis};
-  gemm_body<NSL, MODE>(src);
+  gemm_body<NSL, MODE, SCALE>(src);
 }
 
 }  // namespace tc

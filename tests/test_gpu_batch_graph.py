@@ -87,15 +87,16 @@ def _uneven_fields(cuda):
 
 
 def test_grouped_batch_equals_per_field(cuda):
-    """One persistent launch per slice count for the contractions of every
+    """One persistent launch per operand kind for the contractions of every
     field gives bit-identical results to the per-field solves."""
     import torch
     plans, rhos = _uneven_fields(cuda)
     ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
     with Batch(plans) as b:
         # 6 fields: field slices + one scan (+ M slicing for FP16) per split field,
-        # 2 grouped launches for each of the two slice counts, 3 for the FP64 field
-        assert b.launches == 3 * 3 + 2 + 2 + 2 * 2 + 3
+        # 2 grouped launches for each of the three operand kinds (FP16 two-slice,
+        # BF16 two-slice, BF16 three-slice), 3 for the FP64 field
+        assert b.launches == 3 * 3 + 2 + 2 + 2 * 3 + 3
         for _ in range(2):
             outs = b.solve(rhos)
             torch.cuda.synchronize()

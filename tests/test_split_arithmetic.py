@@ -1,8 +1,9 @@
 """Bit-level claims behind the FP16 split path, checked on the CPU with NumPy
 restatements of the integer conversions (FP64 -> FP32 truncated and rounded
 heads, FP32 -> FP64 widening with an exponent rebase, the FP16 scale exponent
-from FP32 bits).  Each is compared with NumPy's own IEEE operations, and the
-field pass's pass-1 bound is checked to cover the values pass 2 forms."""
+from FP32 bits).  Each is compared with NumPy's own IEEE operations; the
+field pass's per-group scaling is checked to fit FP16 and keep 22 bits, and
+scaled flushes to sum like unscaled ones."""
 import numpy as np
 import pytest
 
@@ -82,25 +83,79 @@ def test_out_of_range_flushes():
         assert np.all(np.isinf(r[4:])) and r[5] < 0
 
 
-@pytest.mark.parametrize("kind", ["random", "cancel", "same_sign"])
-def test_pass1_bound_covers_pass2_sums(kind):
-    """|t0 +- t1| + 2^-22 (|t0| + |t1|), times (1 + 2^-16), bounds the rounded
-    TwoSum head fl(h0 +- h1) that pass 2 scales, for every cell."""
+def group_exp(m):
+    """The field pass's exponent of a group whose largest |head| is m (FP32):
+    m 2^e in [2^14, 2^15), kept within [-126, 126]."""
+    return np.clip(15 - fp16_exp_from_bits(np.atleast_1d(np.float32(m)))[0], -126, 126)
+
+
+def fp16_slices(hi, lo, e):
+    """Two FP16 slices of (hi + lo) 2^e as the field pass forms them."""
+    f = np.float32(2.0 ** e)
+    a, b = (hi * f).astype(np.float32), (lo * f).astype(np.float32)
+    s0 = a.astype(np.float16)
+    s1 = ((a - s0.astype(np.float32)) + b).astype(np.float16)
+    return s0, s1
+
+
+@pytest.mark.parametrize("kind", ["random", "cancel", "wide"])
+def test_group_exponent_fits_fp16_and_keeps_22_bits(kind):
+    """Per 128-cell group: sigma+- from the FP32-rounded values by TwoSum,
+    scaled by 2^e from the group's largest head, split into two FP16 slices:
+    no slice overflows and the slices hold sigma to 2^-22 of the group max."""
     rng = np.random.default_rng(3)
-    x0 = _doubles(rng, 100000, -5, 5)
-    if kind == "random":
-        x1 = _doubles(rng, 100000, -5, 5)
-    elif kind == "cancel":  # rho_Yang within a few ulp of rho_Yin: sigma- cancels
-        x1 = x0 * (1.0 + rng.integers(-8, 9, 100000) * 2.0 ** -52)
-    else:
-        x1 = np.abs(x0) * rng.uniform(0.5, 2.0, 100000) * np.sign(x0)
-    t0, t1 = trunc_head(x0), trunc_head(x1)
-    h0, h1 = round_head(x0), round_head(x1)
-    slack = np.float32(2.0 ** -22) * (np.abs(t0) + np.abs(t1))
-    for sgn in (1, -1):
-        bound = (np.abs(t0 + np.float32(sgn) * t1) + slack).astype(np.float64) * (1.0 + 2.0 ** -16)
-        s = (h0 + np.float32(sgn) * h1).astype(np.float64)  # fl(h0 +- h1) in FP32
-        assert np.all(np.abs(s) <= bound)
+    for _ in range(200):
+        x0 = _doubles(rng, 128, -3, 3)
+        if kind == "random":
+            x1 = _doubles(rng, 128, -3, 3)
+        elif kind == "cancel":  # rho_Yang within a few ulp of rho_Yin: sigma- cancels
+            x1 = x0 * (1.0 + rng.integers(-8, 9, 128) * 2.0 ** -52)
+        else:  # one group spanning many decades
+            x1 = _doubles(rng, 128, -20, 20)
+        h0, h1 = round_head(x0), round_head(x1)
+        for sgn in (1.0, -1.0):
+            hi = (h0 + np.float32(sgn) * h1).astype(np.float32)  # TwoSum head
+            lo = ((h0.astype(np.float64) + sgn * h1.astype(np.float64)) - hi.astype(np.float64)).astype(np.float32)
+            m = np.max(np.abs(hi))
+            if m == 0:
+                continue
+            e = int(group_exp(np.float32(m)))
+            assert 2.0 ** 14 <= m * 2.0 ** e < 2.0 ** 15
+            s0, s1 = fp16_slices(hi, lo, e)
+            assert np.all(np.isfinite(s0)) and np.all(np.abs(s0.astype(np.float64)) <= 2.0 ** 15)
+            back = (s0.astype(np.float64) + s1.astype(np.float64)) * 2.0 ** -e
+            sig = h0.astype(np.float64) + sgn * h1.astype(np.float64)
+            assert np.max(np.abs(back - sig)) <= 2.0 ** -22 * m * 1.01
+
+
+def test_scaled_flushes_sum_like_unscaled():
+    """A float-float running sum of accumulator flushes, each in its own
+    group's units 2^e and brought back by the exact factor 2^-e before
+    FastTwoSum, carries the same error as flushes that were never scaled."""
+    rng = np.random.default_rng(7)
+    f32 = np.float32
+
+    def ff_sum(vals, scales):
+        H = np.zeros(vals.shape[1], np.float32)
+        L = np.zeros_like(H)
+        for v, sc in zip(vals, scales):
+            b = (v * f32(sc)).astype(np.float32)  # exact: a power of two
+            s = (H + b).astype(np.float32)
+            e = (b - (s - H)).astype(np.float32)
+            H, L = s, (L + e).astype(np.float32)
+        return H.astype(np.float64) + L.astype(np.float64)
+
+    # same-sign flushes of one order of magnitude: FastTwoSum is exact once
+    # the running sum dominates, and within one rounding of a flush before
+    true = rng.uniform(0.5, 2.0, (60, 4096)).astype(np.float32).astype(np.float64)
+    exps = rng.integers(-40, 40, 60)
+    scaled = (true * 2.0 ** exps[:, None]).astype(np.float32)  # exact scaling of FP32 values
+    got = ff_sum(scaled, 2.0 ** -exps.astype(np.float64))
+    ref = ff_sum(true.astype(np.float32), np.ones(60))
+    assert np.array_equal(got, ref)
+    exact = true.sum(axis=0)
+    assert np.all(np.abs(got - exact) <= 2.0 ** -23 * true.max(axis=0))
+    assert np.median(np.abs(got - exact) / exact) < 2.0 ** -40
 
 
 def test_widening_matches_ieee_and_scales_exactly():
