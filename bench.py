@@ -34,7 +34,6 @@ METRIC = "Φ solves/s & Gcell/s at l_max; split-prec vs FP64 GPU at ≤1e-6 rel 
 
 def workload_name(n_r: int) -> str:
     return f"yinyang-1deg-92x272x2-Nr{n_r}-lmax32-ellipsoid+3blobs"
-NOMINAL_FP64_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), profiling recipe table
 NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # derived from the SM count, FP32 lanes and max clock
 
 
@@ -47,6 +46,8 @@ def parse():
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="skip the config-2 leg (0.5 degree, Nr 800, l_max 64) of the default run")
     ap.add_argument("--n-r", type=int, default=400)
     ap.add_argument("--autotune", action="store_true",
                     help="plans pick their split-K count by timing candidates at create")
@@ -62,12 +63,24 @@ def dist_env():
     return dist.env()
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
-# pass on this workload at Nr = 400) of the current kernels, by precision and
-# phase; absent entries report null.  Source: profiles/tc_gemm_yinyang1deg_fp16x3.md.
-MEASURED_TRAFFIC = {("fp16x3", "synthesis", 400): 119222784 + 101773824,
-                    ("fp16x3", "projection", 400): 196941312 + 1273856,
-                    ("fp16x3", "field_slices", 400): 163332608 + 50309376}
+def measure_fp64_peak(dev) -> float:
+    """FP64 TFLOP/s of a cuBLAS DGEMM (torch.matmul, 4096^3, best of 5 after a
+    warm-up; CUDA events), the same kind of measurement as the driver's BF16
+    peak: the denominator of the FP64 paths' roofline."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
 def load_peaks():
@@ -271,47 +284,46 @@ def run_config3(args, ws, rank, local):
         torch.distributed.destroy_process_group()
 
 
-def run_config2(args, ws, rank, local):
+def config2_leg(precision, steps, warmup, local, fp64_cuda_core=True):
     """0.5-degree Yin-Yang, Nr = 800, l_max = 64 (1.6e8 cells, 4225 columns): the
-    split path timed against the FP64 tensor-core and FP64 CUDA-core paths on
-    the same field, with the error of Phi and of B and M per degree band."""
+    split path timed against the FP64 tensor-core (and FP64 CUDA-core) paths on
+    the same field, with the error of Phi and of B and M per degree band
+    (relative 2-norm of each degree's columns).  Returns a dict."""
     import torch
 
     from paper_1903_08475_gb300 import Plan, ygs_get_moments, ygs_solve, workloads as W
     from paper_1903_08475_gb300 import dist as D
 
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    precision = args.precision or "fp16x3"
     grid = W.config2_grid()
     rho = W.lognormal_density_torch(grid, device=dev)
     stream = torch.cuda.Stream(device=dev)
 
-    def timed(plan, steps, out):
+    def timed(plan, n, out, warm):
         with torch.cuda.stream(stream):
-            for _ in range(max(1, min(3, args.warmup))):
+            for _ in range(warm):
                 ygs_solve(plan, rho, out, stream=stream)
         stream.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         with torch.cuda.stream(stream):
-            for _ in range(steps):
+            for _ in range(n):
                 ygs_solve(plan, rho, out, stream=stream)
         e1.record(stream)
         stream.synchronize()
-        return D.max_over_ranks(e0.elapsed_time(e1) / steps, dev)
+        return D.max_over_ranks(e0.elapsed_time(e1) / n, dev)
 
-    res = {}
-    outs = {}
-    moments = {}
+    res, outs, moments = {}, {}, {}
     clocks = ClockSampler(local)
-    for prec, steps in ((precision, args.steps), ("fp64tc", 2), ("fp64", 2)):
+    clk = None
+    legs = [(precision, steps), ("fp64tc", 1)] + ([("fp64", 1)] if fp64_cuda_core else [])
+    for prec, n in legs:
         with Plan(grid, prec, device=local) as plan:
             out = torch.empty_like(rho)
             if prec == precision:
                 clocks.start()
                 time.sleep(0.3)
-            res[prec] = timed(plan, steps, out)
+            res[prec] = timed(plan, n, out, max(1, min(3, warmup)) if prec == precision else 1)
             if prec == precision:
                 clk = clocks.stop()
             ygs_solve(plan, rho, out, stream=stream)
@@ -320,7 +332,6 @@ def run_config2(args, ws, rank, local):
             outs[prec], moments[prec] = out, (B, M)
     ref, got = outs["fp64tc"], outs[precision]
     rel = float(((got - ref).abs() / ref.abs()).max().item())
-    same = bool(torch.equal(outs["fp64"], outs["fp64tc"]))
 
     def bands(X, Y):
         errs = []
@@ -332,18 +343,37 @@ def run_config2(args, ws, rank, local):
     eB = bands(moments[precision][0], moments["fp64tc"][0])
     eM = bands(moments[precision][1], moments["fp64tc"][1])
     ms = res[precision]
+    out = {"workload": "yinyang-0.5deg-184x544x2-Nr800-lmax64-lognormal", "cells": grid.n_cells, "K": grid.K,
+           "precision": precision, "steps": steps, "ms_per_step": ms, "solves_per_s": 1e3 / ms,
+           "gcell_per_s": grid.n_cells / (ms / 1e3) / 1e9,
+           "fp64_tensor_solves_per_s": 1e3 / res["fp64tc"], "speedup_vs_fp64_tensor": res["fp64tc"] / ms,
+           "max_rel_err_phi_vs_fp64_tensor": rel,
+           "B_rel_err_per_l_band": {l: eB[l] for l in range(0, grid.l_max + 1, 8)},
+           "M_rel_err_per_l_band": {l: eM[l] for l in range(0, grid.l_max + 1, 8)},
+           "B_rel_err_max_over_l": max(eB), "M_rel_err_max_over_l": max(eM), "clocks": clk}
+    if "fp64" in res:
+        out["fp64_cuda_core_solves_per_s"] = 1e3 / res["fp64"]
+        out["fp64_tensor_equals_cuda_core_bitwise"] = bool(torch.equal(outs["fp64"], outs["fp64tc"]))
+    del outs, moments, rho
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_config2(args, ws, rank, local):
+    """Config 2 on its own line (``--workload config2``)."""
+    import torch
+
+    torch.cuda.set_device(local)
+    precision = args.precision or "fp16x3"
+    c2 = config2_leg(precision, args.steps, args.warmup, local)
+    ms = c2["ms_per_step"]
     line = {"metric": "Phi solves/s, 0.5-degree Yin-Yang Nr 800 l_max 64 (config 2)", "value": ws * 1e3 / ms,
             "unit": "solves/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": precision,
-            "data": "synthetic", "gcell_per_s": ws * grid.n_cells / (ms / 1e3) / 1e9,
-            "config": {"workload": "yinyang-0.5deg-184x544x2-Nr800-lmax64-lognormal", "cells": grid.n_cells,
-                       "K": grid.K, "precision": precision, "l2": "inputs larger than L2 (rho 1.3 GB)"},
-            "fp64_tensor_solves_per_s": 1e3 / res["fp64tc"], "fp64_cuda_core_solves_per_s": 1e3 / res["fp64"],
-            "speedup_vs_fp64_tensor": res["fp64tc"] / ms, "max_rel_err_phi_vs_fp64_tensor": rel,
-            "fp64_tensor_equals_cuda_core_bitwise": same,
-            "B_rel_err_per_l_band": {l: eB[l] for l in range(0, grid.l_max + 1, 8)},
-            "M_rel_err_per_l_band": {l: eM[l] for l in range(0, grid.l_max + 1, 8)},
-            "clocks": clk}
+            "data": "synthetic", "gcell_per_s": ws * c2["gcell_per_s"],
+            "config": {"workload": c2["workload"], "cells": c2["cells"], "K": c2["K"], "precision": precision,
+                       "l2": "inputs larger than L2 (rho 1.3 GB)"},
+            **{k: v for k, v in c2.items() if k not in ("workload", "cells", "K", "precision", "steps", "ms_per_step")}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -499,6 +529,7 @@ def main():
     e2e_single_s = D.max_over_ranks((time.perf_counter() - t0) / n_single, dev)
 
     # roofline of the dominant kernel
+    from paper_1903_08475_gb300.profiling import load_traffic
     peaks, peak_src = load_peaks()
     info = plan.info
     sym = info["symmetric"] == 1
@@ -512,9 +543,12 @@ def main():
     if precision in ("fp64", "fp64tc", "fp32"):
         flops = [0.0, flops_gemm, 0.0, flops_gemm][dom]
         achieved = flops / (per[dom] / 1e3) / 1e12
-        pk = NOMINAL_FP32_TFLOPS if precision == "fp32" else NOMINAL_FP64_TFLOPS
-        src = ("FP32 lanes: 152 SMs x 128 x 2 FLOP x 2.07 GHz (recipe's unit counts and clock)"
-               if precision == "fp32" else "nominal FP64 rate of the profiling recipe (no measured FP64 peak)")
+        if precision == "fp32":
+            pk = NOMINAL_FP32_TFLOPS
+            src = "FP32 lanes: 152 SMs x 128 x 2 FLOP x 2.07 GHz (recipe's unit counts and clock)"
+        else:
+            pk = measure_fp64_peak(dev)
+            src = "cuBLAS DGEMM 4096^3 measured in this run (torch.matmul, best of 5)"
         roof = {"kernel": names[dom], "bound": "alu", "achieved": achieved, "peak": pk,
                 "unit": "TFLOP/s", "frac": achieved / pk, "traffic": None, "peak_source": src,
                 "phase_ms": dict(zip(names, per))}
@@ -524,7 +558,7 @@ def main():
             peak = float(peaks["bf16_tflops"])
             roof = {"kernel": names[dom], "bound": "tensor", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": MEASURED_TRAFFIC.get((precision, names[dom], grid.n_r)),
+                    "traffic": load_traffic(precision, grid.n_r, names[dom]),
                     "peak_source": f"bf16_tflops ({peak_src}, burst)" + (
                         "; FP16 dense rate = BF16's (nominal ratio 1)" if precision == "fp16x3" else ""),
                     "phase_ms": dict(zip(names, per))}
@@ -535,7 +569,7 @@ def main():
             achieved = byts / (per[dom] / 1e3) / 1e9
             peak = float(peaks["hbm_gbs"])
             roof = {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": None, "peak_source": f"hbm_gbs ({peak_src})",
+                    "frac": achieved / peak, "traffic": load_traffic(precision, grid.n_r, names[dom]), "peak_source": f"hbm_gbs ({peak_src})",
                     "phase_ms": dict(zip(names, per))}
 
     # the plain FP64 GPU path on the same input: speed-up and accuracy of the split path against it
@@ -557,6 +591,15 @@ def main():
             rel = float(((phi_d - phi64).abs() / phi64.abs()).max().item())
         extra = {"fp64_gpu_solves_per_s": 1e3 / ms64, "speedup_vs_fp64_gpu": ms64 / ms_step,
                  "max_rel_err_vs_fp64_gpu": rel}
+
+    # the largest single-GPU configuration beside it (config 2: 0.5 degree,
+    # Nr 800, l_max 64), a short leg of the same precision
+    if not args.no_config2:
+        try:
+            extra["config2"] = config2_leg(precision, max(3, min(20, args.steps)), args.warmup, local,
+                                           fp64_cuda_core=False)
+        except Exception as e:  # context; never lose the headline line over it
+            extra["config2"] = {"error": repr(e)}
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -58,6 +58,8 @@
 #ifndef YGS_H
 #define YGS_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -80,7 +82,8 @@ typedef enum {
   YGS_BF16X6 = 2, /* tcgen05 BF16 tensor cores, 3-slice operands, 6 products */
   YGS_FP16X3 = 3, /* tcgen05 FP16 tensor cores, 2-slice operands (22 significant bits), 3 products;
                      every operand row is scaled by a power of two into FP16's range (U per
-                     column, the field and M per shell, Q as a whole) and unscaled exactly */
+                     column, the field per shell and group of 128 angular cells, M per
+                     shell, Q as a whole) and unscaled exactly */
   YGS_FP64_TC = 4, /* the FP64 path with its contractions on the FP64 tensor cores (DMMA 8x8x4):
                      FP64 products and sums, another order of additions */
   YGS_FP32 = 5     /* FP32 contractions on the CUDA cores (FP32 copies of U and Q, the field
@@ -132,6 +135,10 @@ typedef struct {
   int split_k;            /* number of angular chunks the projection is split into */
   long long weight_bytes; /* device bytes held for U, Q and their split copies */
   long long work_bytes;   /* device bytes of per-solve workspace */
+  int fp64_split_k;       /* angular chunks of the FP64 kernels' projection (= split_k on FP64
+                             plans; ygs_solve_static always runs those kernels) */
+  long long static_scratch_bytes; /* scratch ygs_solve_static needs for this plan:
+                                     (fp64_split_k + 2) * n_r * K * 8 */
 } ygs_info;
 
 /* Builds the plan: validates the descriptor, allocates device memory on
@@ -187,12 +194,12 @@ ygs_status ygs_solve_batched(int n, ygs_plan* const* plans, const double* const*
 /* A fixed set of plans whose solves run together (the paper solves one field;
  * batching many independent fields of uneven sizes is this library's).
  * ygs_batch_create prepares, once, device descriptors of every split-precision
- * plan's contractions; plans are grouped by slice count (BF16x6 apart from the
- * two-slice precisions) and each group's projection and synthesis tiles then run
+ * plan's contractions; plans are grouped by operand kind (BF16 two-slice, FP16
+ * two-slice, BF16 three-slice) and each group's projection and synthesis tiles then run
  * in ONE persistent launch each per ygs_batch_solve, instead of one launch per
  * field.  FP64 plans of the batch run their ordinary solves.  All plans must
  * live on one device and appear once; they must outlive the batch.  At most
- * 128 split plans per slice count, 1024 plans in all.  Errors: INVALID_ARG,
+ * 128 split plans per operand kind, 1024 plans in all.  Errors: INVALID_ARG,
  * OOM, CUDA, UNSUPPORTED. */
 typedef struct ygs_batch ygs_batch;
 ygs_status ygs_batch_create(int n, ygs_plan* const* plans, ygs_batch** out);
@@ -256,15 +263,21 @@ ygs_status ygs_debug_wait_timeout(ygs_plan* plan, int spins, void* stream);
  * given all free device memory to its own pool, a running time-step loop that
  * forbids allocator calls).
  * Limit: the plan must need at most YGS_STATIC_SCRATCH_BYTES of scratch,
- * (split_k + 2) * n_r * K * 8 bytes (split_k from ygs_get_info); a larger plan
- * returns UNSUPPORTED with the sizes in ygs_last_error() and enqueues nothing.
- * The first call on a device resolves the array's device address (module
- * set-up); make that first call before any stream capture.
+ * ygs_info.static_scratch_bytes = (fp64_split_k + 2) * n_r * K * 8 bytes
+ * (fp64_split_k, not split_k: a split-precision plan's tensor-core path chunks
+ * its projection differently); a larger plan returns UNSUPPORTED with the
+ * sizes in ygs_last_error() and enqueues nothing.
+ * ygs_create loads the module that holds the array (allocating it, once per
+ * device and process) and the FP64 kernels, so no call of this function
+ * allocates; each call looks the array's address up on the current device.
  * The array is shared by all calls on a device in the process: calls whose GPU
  * work overlaps (unordered streams, concurrent host threads) race on it.  No
  * part of it has to start at zero.  The plan's own moments (ygs_get_moments)
  * are not updated.  Errors: as ygs_solve, plus UNSUPPORTED for the limit. */
 ygs_status ygs_solve_static(ygs_plan* plan, const double* d_rho, double* d_phi, void* stream);
+
+/* YGS_STATIC_SCRATCH_BYTES, for bindings that cannot read this header. */
+size_t ygs_static_scratch_capacity(void);
 
 /* Number of kernel launches one ygs_solve (or ygs_backward) enqueues. */
 int ygs_launches_per_solve(const ygs_plan* plan);

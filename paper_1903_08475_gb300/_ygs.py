@@ -30,7 +30,7 @@ EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
            "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
            "ygs_debug_wait_timeout", "ygs_solve_static", "ygs_batch_create", "ygs_batch_solve",
-           "ygs_batch_destroy", "ygs_batch_launches")
+           "ygs_batch_destroy", "ygs_batch_launches", "ygs_static_scratch_capacity")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -53,7 +53,8 @@ class Info(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("n_patch", ctypes.c_int), ("l_max", ctypes.c_int), ("K", ctypes.c_int),
                 ("n_ang", ctypes.c_longlong), ("n_cells", ctypes.c_longlong), ("precision", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("split_k", ctypes.c_int), ("weight_bytes", ctypes.c_longlong),
-                ("work_bytes", ctypes.c_longlong)]
+                ("work_bytes", ctypes.c_longlong), ("fp64_split_k", ctypes.c_int),
+                ("static_scratch_bytes", ctypes.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -64,12 +65,13 @@ _lock = threading.Lock()
 
 
 def load_library(path: Optional[str] = None):
-    """Loads libygs.so (building it first if it is absent)."""
+    """Loads libygs.so (building it first if it is absent).  The environment
+    variable YGS_LIB, when set, names another build of the library to load."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or os.environ.get("YGS_LIB") or LIB_PATH
         if not os.path.exists(p):
             from . import build as _build
             _build.build()
@@ -98,9 +100,11 @@ def load_library(path: Optional[str] = None):
         L.ygs_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.ygs_batch_destroy.argtypes = [vp]
         L.ygs_batch_launches.argtypes = [vp]
+        L.ygs_static_scratch_capacity.argtypes = []
         for f in EXPORTS:
-            if f not in ("ygs_status_string", "ygs_last_error"):
+            if f not in ("ygs_status_string", "ygs_last_error", "ygs_static_scratch_capacity"):
                 getattr(L, f).restype = ctypes.c_int
+        L.ygs_static_scratch_capacity.restype = ctypes.c_size_t
         _lib = L
         return L
 
@@ -239,10 +243,16 @@ class Batch:
 
 def ygs_solve_static(plan: Plan, rho, phi=None, stream=None):
     """Phi = A rho in FP64 with the library's static device scratch (no device
-    allocation inside the call; the plan must fit its 32 MiB limit)."""
+    allocation inside the call; the plan's info["static_scratch_bytes"] must
+    be at most ygs_static_scratch_capacity())."""
     phi = _field_out(plan, rho) if phi is None else phi
     _check(load_library().ygs_solve_static(plan.handle, _ptr(rho), _ptr(phi), _stream_handle(stream)))
     return phi
+
+
+def ygs_static_scratch_capacity() -> int:
+    """Bytes of the device array behind ygs_solve_static (YGS_STATIC_SCRATCH_BYTES)."""
+    return int(load_library().ygs_static_scratch_capacity())
 
 
 def ygs_backward(plan: Plan, grad_phi, grad_rho=None, stream=None):

@@ -359,6 +359,10 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
 
   st = build_weights(p);
   if (st != YGS_OK) return fail_free(st);
+  // load what ygs_solve_static runs, so that its first call allocates nothing
+  if ((e = preload_fp64_kernels()) != cudaSuccess) return fail_free(cuda_fail(e, "loading the FP64 kernels"));
+  if ((e = prepare_static_scratch()) != cudaSuccess)
+    return fail_free(cuda_fail(e, "making the static scratch array resident"));
   if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3 || p->precision == YGS_FP16X3) {
     if (p->n_r > 65535) return fail_free(fail(YGS_ERR_UNSUPPORTED, "split precision supports n_r <= 65535"));
     p->tc_nsl = (p->precision == YGS_BF16X6) ? 3 : 2;
@@ -406,6 +410,8 @@ ygs_status ygs_get_info(const ygs_plan* p, ygs_info* info) {
   info->split_k = p->tc_nsl ? p->tc_S : p->S;
   info->weight_bytes = p->weight_bytes;
   info->work_bytes = p->work_bytes;
+  info->fp64_split_k = p->S;
+  info->static_scratch_bytes = static_scratch_bytes(p);
   return YGS_OK;
 }
 

@@ -380,6 +380,17 @@ cudaError_t launch_synth_fp64(const ygs_plan* p, const double* X, const double* 
   return synth_t<double>(p, X, W, out, p->precision == YGS_FP64_TC, s);
 }
 
+cudaError_t preload_fp64_kernels() {
+  // cudaFuncGetAttributes loads a lazily loaded kernel (and its module) now
+  cudaFuncAttributes fa;
+  cudaError_t e;
+  if ((e = cudaFuncGetAttributes(&fa, proj_fp64_kernel<double, false>)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fa, proj_fp64_kernel<double, true>)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fa, synth_fp64_kernel<double, false>)) != cudaSuccess) return e;
+  if ((e = cudaFuncGetAttributes(&fa, synth_fp64_kernel<double, true>)) != cudaSuccess) return e;
+  return cudaFuncGetAttributes(&fa, scan_fwd_kernel<double>);
+}
+
 cudaError_t launch_scan_fwd(const ygs_plan* p, const double* part, int S, double* B, double* M, cudaStream_t s) {
   scan_fwd_kernel<double><<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, part, S, p->rad, B, M);
   return cudaGetLastError();

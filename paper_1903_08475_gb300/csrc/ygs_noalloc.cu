@@ -15,7 +15,7 @@
 // needs to start at zero: every element a kernel reads was written earlier in
 // the same call (each split-K chunk writes its whole [n_r][K] plane, the
 // scan writes all of B and M).
-#include <mutex>
+#include <string>
 
 #include "ygs_internal.h"
 
@@ -27,21 +27,15 @@ constexpr size_t kScratchDoubles = (size_t)YGS_STATIC_SCRATCH_BYTES / sizeof(dou
 // Layout of one call: S split-K planes of [n_r][K], then B [n_r][K], then M [n_r][K].
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_scratch on the current device, resolved once per device.
-cudaError_t scratch_address(int dev, double** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_ptr[dev] = (double*)p;
-  }
-  *out = g_ptr[dev];
-  return cudaSuccess;
+// Device address of g_scratch on the current device.  Looked up on every
+// call rather than cached: a cached address would outlive a reset of the
+// device or a new primary context, and cudaGetSymbolAddress costs little once
+// the module is loaded (ygs_create loads it, see prepare_static_scratch).
+cudaError_t scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  *out = (double*)p;
+  return e;
 }
 
 struct CurrentDevice {
@@ -62,13 +56,21 @@ ygs_status fail(ygs_status s, const std::string& msg) {
 }
 
 }  // namespace
+
+cudaError_t prepare_static_scratch() {
+  double* base = nullptr;
+  return scratch_address(&base);
+}
+
+long long static_scratch_bytes(const ygs_plan* p) {
+  return (long long)(p->S + 2) * p->n_r * (long long)p->K * (long long)sizeof(double);
+}
+
 }  // namespace ygs
 
 using namespace ygs;
 
-static size_t scratch_needed(const ygs_plan* p) {
-  return (size_t)(p->S + 2) * (size_t)p->n_r * (size_t)p->K * sizeof(double);
-}
+extern "C" size_t ygs_static_scratch_capacity(void) { return (size_t)YGS_STATIC_SCRATCH_BYTES; }
 
 extern "C" ygs_status ygs_solve_static(ygs_plan* p, const double* d_rho, double* d_phi, void* stream) {
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
@@ -79,19 +81,18 @@ extern "C" ygs_status ygs_solve_static(ygs_plan* p, const double* d_rho, double*
   const char* ca = (const char*)d_rho;
   const char* cb = (const char*)d_phi;
   if (ca < cb + bytes && cb < ca + bytes) return fail(YGS_ERR_INVALID_ARG, "input and output fields overlap");
-  const size_t need = scratch_needed(p);
+  const size_t need = (size_t)static_scratch_bytes(p);
   if (need > (size_t)YGS_STATIC_SCRATCH_BYTES)
     return fail(YGS_ERR_UNSUPPORTED, "ygs_solve_static: this plan needs " + std::to_string(need) +
-                                         " bytes of scratch ((split_k + 2) * n_r * K doubles = (" +
+                                         " bytes of scratch ((fp64_split_k + 2) * n_r * K doubles = (" +
                                          std::to_string(p->S) + " + 2) * " + std::to_string(p->n_r) + " * " +
                                          std::to_string(p->K) + "), more than the static " +
                                          std::to_string((size_t)YGS_STATIC_SCRATCH_BYTES) +
                                          " bytes; use ygs_solve");
-  if (p->device < 0 || p->device >= kMaxDevices) return fail(YGS_ERR_UNSUPPORTED, "device ordinal too large");
   CurrentDevice cur(p->device);
   if (!cur.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
   double* base = nullptr;
-  cudaError_t e = scratch_address(p->device, &base);
+  cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return fail(YGS_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   const size_t plane = (size_t)p->n_r * p->K;
   double* part = base;

@@ -22,6 +22,8 @@
 //               (Eqs. R_in/R_out, step 4 of Sect. 4.3).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "ygs_internal.h"
@@ -390,6 +392,92 @@ void euler_matrix(double a, double b, double g, double* R) {
   R[8] = cb;
 }
 
+// ---- create-time self-check of the rotation (Eqs. ylm_transform, wigner-D) ----
+// At kCheckDirs fixed local directions xi of every stored patch g, the real
+// harmonics of the global frame evaluated directly at x = R^(g) xi must equal
+// the rotation of the local ones, Y_l(x) = W^l Y_l(xi), degree by degree.
+// The directions: a Fibonacci spiral over the sphere (cos theta uniform in
+// steps, phi advancing by the golden angle).
+constexpr int kCheckDirs = 32;
+constexpr double kCheckTol = 1e-10;  // |Y| <= 1 in this normalisation; the builder's error is ~1e-15
+
+__device__ inline void check_dir(int s, double& th, double& ph) {
+  th = acos(1.0 - 2.0 * (s + 0.5) / kCheckDirs);
+  ph = fmod(s * 2.39996322972865332, 6.283185307179586);
+}
+
+// Y[(g * kCheckDirs + s)][l*l + r] (real harmonics, the columns' order) at
+// direction s of patch g, in the local frame (global = 0) or at R^(g) xi.
+__global__ void check_ylm_kernel(int L, int K, int nwp, PatchGeo geo, int global, double* Y) {
+  const int s = blockIdx.x, g = blockIdx.y;
+  double th, ph;
+  check_dir(s, th, ph);
+  double st, ct, sp, cp;
+  sincos(th, &st, &ct);
+  sincos(ph, &sp, &cp);
+  double v0 = st * cp, v1 = st * sp, v2 = ct;
+  if (global) {
+    const double* R = geo.R[g];
+    const double x0 = R[0] * v0 + R[1] * v1 + R[2] * v2;
+    const double x1 = R[3] * v0 + R[4] * v1 + R[5] * v2;
+    const double x2 = R[6] * v0 + R[7] * v1 + R[8] * v2;
+    v0 = x0;
+    v1 = x1;
+    v2 = x2;
+  }
+  const double sn = sqrt(v0 * v0 + v1 * v1), x = fmax(-1.0, fmin(1.0, v2)), phi = atan2(v1, v0);
+  double* Yr = Y + ((long long)g * kCheckDirs + s) * K;
+  for (int m = threadIdx.x; m <= L; m += blockDim.x) {
+    double smp, cmp;
+    sincos(m * phi, &smp, &cmp);
+    double pmm = 1.0;
+    for (int kk = 1; kk <= m; ++kk) pmm *= sqrt((2.0 * kk - 1.0) / (2.0 * kk)) * sn;
+    double p2 = 0.0, p1 = 0.0;
+    for (int l = m; l <= L; ++l) {
+      double pv;
+      if (l == m) pv = pmm;
+      else if (l == m + 1) pv = sqrt(2.0 * m + 1.0) * x * pmm;
+      else
+        pv = ((2.0 * l - 1.0) * x * p1 - sqrt((double)(l - 1 - m) * (double)(l - 1 + m)) * p2) /
+             sqrt((double)(l - m) * (double)(l + m));
+      p2 = p1;
+      p1 = pv;
+      if (m == 0) {
+        Yr[l * l] = pv;
+      } else {
+        Yr[l * l + 2 * m - 1] = pv * cmp;
+        Yr[l * l + 2 * m] = pv * smp;
+      }
+    }
+  }
+}
+
+// Largest |Y_glob - W Y_loc| over rows, degrees, directions and patches, as
+// the bits of a non-negative double (atomicMax orders them like the values).
+__global__ void check_rot_kernel(int L, int K, const double* W, const double* Yl, const double* Yg,
+                                 unsigned long long* worst) {
+  const int s = blockIdx.x, g = blockIdx.y;
+  const double* yl = Yl + ((long long)g * kCheckDirs + s) * K;
+  const double* yg = Yg + ((long long)g * kCheckDirs + s) * K;
+  double m = 0.0;
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const int l = isqrt_col(c);
+    const int n = 2 * l + 1, r = c - l * l;
+    const double* Wr = W + (long long)g * blk(L + 1) + blk(l) + (long long)r * n;
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q) acc = fma(Wr[q], yl[l * l + q], acc);
+    m = fmax(m, fabs(acc - yg[c]));
+  }
+  if (!(m == m)) m = 1e300;  // a NaN fails the check
+  atomicMax(worst, (unsigned long long)__double_as_longlong(m));
+}
+
+// Testing hook: flips the sign of every W^1 block (a mis-signed rotation).
+__global__ void perturb_w_kernel(int L, int nwp, double* W) {
+  for (int g = 0; g < nwp; ++g)
+    for (int idx = threadIdx.x; idx < 9 && L >= 1; idx += blockDim.x) W[(long long)g * blk(L + 1) + blk(1) + idx] *= -1.0;
+}
+
 struct Scratch {
   std::vector<void*> ptrs;
   ~Scratch() {
@@ -504,6 +592,37 @@ ygs_status build_weights(ygs_plan* p) {
   YGS_TRY(cudaGetLastError());
   wreal_kernel<<<dim3(L + 1, nwp), 256>>>(L, d_db, d_alpha, d_gamma, d_W);
   YGS_TRY(cudaGetLastError());
+  {
+    // the rotation self-check: Y(R xi) = W Y(xi) at fixed directions
+    const char* hook = getenv("YGS_TEST_PERTURB_WIGNER");
+    if (hook && hook[0] == '1') {
+      perturb_w_kernel<<<1, 32>>>(L, nwp, d_W);
+      YGS_TRY(cudaGetLastError());
+    }
+    double *d_yl, *d_yg;
+    unsigned long long* d_worst;
+    YGS_TRY(s.alloc(&d_yl, (size_t)nwp * kCheckDirs * K));
+    YGS_TRY(s.alloc(&d_yg, (size_t)nwp * kCheckDirs * K));
+    YGS_TRY(s.alloc(&d_worst, 1));
+    YGS_TRY(cudaMemset(d_worst, 0, sizeof(unsigned long long)));
+    check_ylm_kernel<<<dim3(kCheckDirs, nwp), 64>>>(L, K, nwp, geo, 0, d_yl);
+    YGS_TRY(cudaGetLastError());
+    check_ylm_kernel<<<dim3(kCheckDirs, nwp), 64>>>(L, K, nwp, geo, 1, d_yg);
+    YGS_TRY(cudaGetLastError());
+    check_rot_kernel<<<dim3(kCheckDirs, nwp), 256>>>(L, K, d_W, d_yl, d_yg, d_worst);
+    YGS_TRY(cudaGetLastError());
+    unsigned long long bits = 0;
+    YGS_TRY(cudaMemcpy(&bits, d_worst, sizeof(bits), cudaMemcpyDeviceToHost));
+    double worst;
+    memcpy(&worst, &bits, sizeof(worst));
+    if (!(worst <= kCheckTol)) {
+      char msg[160];
+      snprintf(msg, sizeof msg, "weights: rotation self-check failed: |Y(R xi) - W Y(xi)| = %.3e > %.1e", worst,
+               kCheckTol);
+      set_error(msg);
+      return YGS_ERR_NUMERIC;
+    }
+  }
 
   // separable local integrals
   long long tstride = (long long)nth_max * (L + 1) * (L + 1);

@@ -53,3 +53,18 @@ def test_injected_allocation_failures(cuda, precision):
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert abs(free1 - free0) < 64 << 20  # nothing of the failed creates stays allocated
+
+
+def test_create_rejects_a_wrong_rotation(cuda, monkeypatch):
+    """ygs_create checks Y(R xi) = W Y(xi) (Eqs. ylm_transform, wigner-D) at
+    fixed directions; a rotation table with its degree-1 block negated (the
+    testing hook YGS_TEST_PERTURB_WIGNER) is caught as YGS_ERR_NUMERIC, and
+    the same grid builds normally without the hook."""
+    grid = small_yinyang(W)
+    monkeypatch.setenv("YGS_TEST_PERTURB_WIGNER", "1")
+    with pytest.raises(YgsError) as e:
+        Plan(grid, "fp64")
+    assert "YGS_ERR_NUMERIC" in str(e.value) and "self-check" in str(e.value)
+    monkeypatch.delenv("YGS_TEST_PERTURB_WIGNER")
+    with Plan(grid, "fp64") as plan:
+        assert plan.info["K"] == (grid.l_max + 1) ** 2
