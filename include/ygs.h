@@ -86,9 +86,14 @@ typedef enum {
                      shell, Q as a whole) and unscaled exactly */
   YGS_FP64_TC = 4, /* the FP64 path with its contractions on the FP64 tensor cores (DMMA 8x8x4):
                      FP64 products and sums, another order of additions */
-  YGS_FP32 = 5     /* FP32 contractions on the CUDA cores (FP32 copies of U and Q, the field
+  YGS_FP32 = 5,    /* FP32 contractions on the CUDA cores (FP32 copies of U and Q, the field
                      truncated to FP32, FP32 accumulation), FP64 radial scans; the adjoint of
                      such a plan runs on its FP64 weights */
+  YGS_TF32X3 = 6   /* tcgen05 TF32 tensor cores (kind::tf32), 2-slice operands (each value split
+                     into two TF32 values, 22 significant bits), 3 products; FP32's exponent range,
+                     so no row scaling; twice the operand bytes and half the tensor rate of FP16x3.
+                     Phi within 1e-6 of FP64 (as FP16x3); its adjoint within 2e-6 of the
+                     largest |A^T w| (1.4e-6 measured at l_max = 32) */
 } ygs_precision;
 
 typedef enum {

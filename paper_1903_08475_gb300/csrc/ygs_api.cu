@@ -150,7 +150,7 @@ ygs_status validate_desc(const ygs_desc* d) {
     return fail(YGS_ERR_INVALID_ARG, "l_max must be in [0, " + std::to_string(kMaxLmax) + "]");
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
-  if (d->precision < YGS_FP64 || d->precision > YGS_FP32) return fail(YGS_ERR_INVALID_ARG, "bad precision");
+  if (d->precision < YGS_FP64 || d->precision > YGS_TF32X3) return fail(YGS_ERR_INVALID_ARG, "bad precision");
   if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;
@@ -363,10 +363,12 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
   if ((e = preload_fp64_kernels()) != cudaSuccess) return fail_free(cuda_fail(e, "loading the FP64 kernels"));
   if ((e = prepare_static_scratch()) != cudaSuccess)
     return fail_free(cuda_fail(e, "making the static scratch array resident"));
-  if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3 || p->precision == YGS_FP16X3) {
+  if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3 || p->precision == YGS_FP16X3 ||
+      p->precision == YGS_TF32X3) {
     if (p->n_r > 65535) return fail_free(fail(YGS_ERR_UNSUPPORTED, "split precision supports n_r <= 65535"));
     p->tc_nsl = (p->precision == YGS_BF16X6) ? 3 : 2;
     p->tc_fp16 = (p->precision == YGS_FP16X3) ? 1 : 0;
+    p->tc_tf32 = (p->precision == YGS_TF32X3) ? 1 : 0;
     st = tc_setup(p, sms);
     if (st != YGS_OK) return fail_free(st);
   }

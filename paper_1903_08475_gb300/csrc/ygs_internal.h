@@ -99,6 +99,7 @@ struct ygs_plan {
   float2* tc_mono = nullptr;  // -G M[i][0] per shell as (hi, lo)
   float2* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells (float-float)
   float2* tc_radff = nullptr; // [4][l_max+1][n_r] the radial tables a, b, f_in, f_out as float-float
+  int tc_tf32 = 0;            // TF32 slices (YGS_TF32X3): 4-byte elements behind the slice pointers
   // FP16 slices (YGS_FP16X3): power-of-two exponents that scale each operand row into FP16's range
   int tc_fp16 = 0;
   int tc_eq = 0;              // Q (all rows)
@@ -179,7 +180,7 @@ namespace tc {
 struct TcProblem;
 }
 struct TcBatchGroup {
-  int nsl = 0, fp16 = 0, sms = 0, total_p = 0, total_s = 0;
+  int nsl = 0, fp16 = 0, tf32 = 0, sms = 0, total_p = 0, total_s = 0;
   std::vector<ygs_plan*> members;
   tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
   int *d_start_p = nullptr, *d_start_s = nullptr;

@@ -41,16 +41,26 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3-D BF16 tensor (kdim fastest, rows, planes) read in boxes of BK x box_rows x 1, swizzled to match
-// the UMMA shared-memory descriptors (128-byte swizzle for BK = 64).
-bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long long planes, int box_rows, bool fp16) {
+// Operand kind of a plan's slices: BF16, FP16 (scaled rows) or TF32 (FP32 storage).
+enum SliceKind { kSliceBF16 = 0, kSliceFP16 = 1, kSliceTF32 = 2 };
+int slice_kind(const ygs_plan* p) { return p->tc_tf32 ? kSliceTF32 : (p->tc_fp16 ? kSliceFP16 : kSliceBF16); }
+size_t slice_bytes(const ygs_plan* p) { return p->tc_tf32 ? 4 : 2; }
+
+// 3-D slice tensor (kdim fastest, rows, planes) read in boxes of one 128-byte
+// k-block row (BK 2-byte or BK / 2 TF32 elements) x box_rows x 1, swizzled to
+// match the UMMA shared-memory descriptors (128-byte swizzle for BK = 64).
+bool make_map(CUtensorMap* m, void* base, long long kdim, long long rows, long long planes, int box_rows, int kind) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
+  const cuuint64_t esz = kind == kSliceTF32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)kdim, (cuuint64_t)rows, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)kdim * 2, (cuuint64_t)kdim * 2 * rows};
-  cuuint32_t box[3] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)kdim * esz, (cuuint64_t)kdim * esz * rows};
+  cuuint32_t box[3] = {(cuuint32_t)(tc::BK * 2 / esz), (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  return enc(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  const CUtensorMapDataType dt = kind == kSliceTF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : kind == kSliceFP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  return enc(m, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              tc::BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -98,6 +108,53 @@ __global__ void slice_q_kernel(int nsl, int K, int K_pad, long long rows, const 
     int ci = pc_int[pc];
     if (ci >= 0 && (!zero_mono || pc_nat[pc] != 0)) slices_of(Q[row * K + ci], nsl, s);
     for (int k = 0; k < nsl; ++k) Qs[(long long)k * total + e] = s[k];
+  }
+}
+
+// ---- TF32 slices (two per value, 22 significant bits; FP32's exponent range, no scaling) ----
+// hi = tf32(head), lo = tf32((head - hi) + tail) of a float-float value.
+__device__ __forceinline__ void ff_tf32(float h, float l, float& s0, float& s1) {
+  s0 = tc::to_tf32(h);
+  s1 = tc::to_tf32((h - s0) + l);
+}
+__device__ __forceinline__ void tf32_slices_of(double x, float& s0, float& s1) {
+  float h, l;
+  tc::f64_to_ff_fast(x, h, l);
+  ff_tf32(h, l, s0, s1);
+}
+
+// Ut[s][pc][apad] (TF32) from U[row][ci] (FP64 internal order), as slice_ut_kernel.
+__global__ void slice_ut_tf32_kernel(int K, int K_pad, long long n_pad, const int* __restrict__ pc_int,
+                                     const double* __restrict__ U, PatchTable pt, int nwp,
+                                     const long long* __restrict__ pad_off, float* __restrict__ Ut) {
+  long long total = (long long)K_pad * n_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int pc = (int)(e / n_pad);
+    long long ap = e % n_pad;
+    int g = 0;
+    while (g + 1 < nwp && pad_off[g + 1] <= ap) ++g;
+    long long a = ap - pad_off[g];
+    float s0 = 0.0f, s1 = 0.0f;
+    int ci = pc_int[pc];
+    if (ci >= 0 && a < pt.nang[g]) tf32_slices_of(U[(pt.ang_off[g] + a) * K + ci], s0, s1);
+    Ut[e] = s0;
+    Ut[total + e] = s1;
+  }
+}
+
+// Qs[s][row][pc] (TF32) from W[row][ci], as slice_q_kernel (zero_mono: the monopole column stays zero).
+__global__ void slice_q_tf32_kernel(int K, int K_pad, long long rows, const int* __restrict__ pc_int,
+                                    const int* __restrict__ pc_nat, const double* __restrict__ Q, int zero_mono,
+                                    float* __restrict__ Qs) {
+  long long total = rows * K_pad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long row = e / K_pad;
+    int pc = (int)(e % K_pad);
+    float s0 = 0.0f, s1 = 0.0f;
+    int ci = pc_int[pc];
+    if (ci >= 0 && (!zero_mono || pc_nat[pc] != 0)) tf32_slices_of(Q[row * K + ci], s0, s1);
+    Qs[e] = s0;
+    Qs[total + e] = s1;
   }
 }
 
@@ -184,6 +241,81 @@ __global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable 
           *reinterpret_cast<uint2*>(dst) = w;
         } else {
           for (int c = 0; c < 4 && a + c < na; ++c) dst[c] = out[c][h][k];
+        }
+      }
+  }
+}
+
+// sigma+- (or rho) of one cell as float-float pairs from the two values'
+// float-float forms (TwoSum of the heads, renormalised), as sigma_slices.
+__device__ __forceinline__ void sigma_ff2(double r0, double r1, int symmetric, float (&hi)[2], float (&lo)[2]) {
+  float h0, l0;
+  tc::f64_to_ff_fast(r0, h0, l0);
+  if (!symmetric) {
+    hi[0] = h0;
+    lo[0] = l0;
+    hi[1] = lo[1] = 0.0f;
+    return;
+  }
+  float h1, l1;
+  tc::f64_to_ff_fast(r1, h1, l1);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float s, err;
+    tc::two_sum(h0, h ? -h1 : h1, s, err);
+    float l = err + (h ? (l0 - l1) : (l0 + l1));
+    float hh = s + l;  // renormalise
+    lo[h] = l - (hh - s);
+    hi[h] = hh;
+  }
+}
+
+// TF32 field slices, organised like field_slices_kernel: 4 cells per thread,
+// 16-byte loads where the rows allow, one 16-byte store per plane and slice.
+__global__ void field_slices_tf32_kernel(int n_r, int symmetric, PatchTable pt, const long long* __restrict__ pad_off,
+                                         long long n_pad, const double* __restrict__ rho, float* __restrict__ F) {
+  const long long plane = (long long)n_r * n_pad;
+  const int g = blockIdx.z;
+  const int i = blockIdx.y;
+  const int na = (int)pt.nang[g];
+  const long long row_in = pt.fld_off[g] + (long long)i * na;
+  const long long row_in1 = symmetric ? pt.fld_off[1] + (long long)i * na : row_in;
+  const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
+  const bool vec = ((row_in | row_in1) & 1) == 0;
+  for (int a = 4 * (blockIdx.x * blockDim.x + threadIdx.x); a < na; a += 4 * gridDim.x * blockDim.x) {
+    double v0[4], v1[4];
+    if (vec && a + 4 <= na) {
+      const double2 x0 = *reinterpret_cast<const double2*>(rho + row_in + a);
+      const double2 x1 = *reinterpret_cast<const double2*>(rho + row_in + a + 2);
+      v0[0] = x0.x; v0[1] = x0.y; v0[2] = x1.x; v0[3] = x1.y;
+      if (symmetric) {
+        const double2 y0 = *reinterpret_cast<const double2*>(rho + row_in1 + a);
+        const double2 y1 = *reinterpret_cast<const double2*>(rho + row_in1 + a + 2);
+        v1[0] = y0.x; v1[1] = y0.y; v1[2] = y1.x; v1[3] = y1.y;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        v0[c] = (a + c < na) ? rho[row_in + a + c] : 0.0;
+        v1[c] = (symmetric && a + c < na) ? rho[row_in1 + a + c] : 0.0;
+      }
+    }
+    float sl[2][2][4];  // [plane][slice][cell]
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float hi[2], lo[2];
+      sigma_ff2(v0[c], v1[c], symmetric, hi, lo);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) ff_tf32(hi[h], lo[h], sl[h][0][c], sl[h][1][c]);
+    }
+    const int nh = symmetric ? 2 : 1;
+    for (int h = 0; h < nh; ++h)
+      for (int k = 0; k < 2; ++k) {
+        float* dst = F + (long long)(h * 2 + k) * plane + row_out + a;
+        if (a + 4 <= na) {
+          *reinterpret_cast<float4*>(dst) = make_float4(sl[h][k][0], sl[h][k][1], sl[h][k][2], sl[h][k][3]);
+        } else {
+          for (int c = 0; c < 4 && a + c < na; ++c) dst[c] = sl[h][k][c];
         }
       }
   }
@@ -749,7 +881,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
       M[(long long)i * K_pad + pc] = zero;
-      if (write_slices)
+      if (write_slices == 2)
+        for (int k = 0; k < 2; ++k) reinterpret_cast<float*>(Ms)[k * plane + (long long)i * K_pad + pc] = 0.0f;
+      else if (write_slices)
         for (int k = 0; k < nsl; ++k) Ms[k * plane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
     }
     return;
@@ -757,7 +891,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
   auto emit = [&](int i, float2 m) {
     M[(long long)i * K_pad + pc] = m;
     if (pc == 0) mono[i] = tc::ff_mul(neg_G, m);  // natural column 0 (l = 0) is padded column 0: the monopole
-    if (write_slices) {
+    if (write_slices == 2) {  // TF32 slices (4-byte elements)
+      float s0, s1;
+      ff_tf32(m.x, m.y, s0, s1);
+      float* Mf = reinterpret_cast<float*>(Ms);
+      Mf[(long long)i * K_pad + pc] = s0;
+      Mf[plane + (long long)i * K_pad + pc] = s1;
+    } else if (write_slices) {
       __nv_bfloat16 sl[3];
       ff_slices(m, nsl, sl);
 #pragma unroll
@@ -886,14 +1026,22 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_ff_kernel(
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
       Bbar[(long long)i * K_pad + pc] = zero;
-      if (write_slices)
+      if (write_slices == 2)
+        for (int k = 0; k < 2; ++k) reinterpret_cast<float*>(Bs)[k * plane + (long long)i * K_pad + pc] = 0.0f;
+      else if (write_slices)
         for (int k = 0; k < nsl; ++k) Bs[k * plane + (long long)i * K_pad + pc] = __float2bfloat16_rn(0.f);
     }
     return;
   }
   auto emit = [&](int i, float2 b) {
     Bbar[(long long)i * K_pad + pc] = b;
-    if (write_slices) {
+    if (write_slices == 2) {  // TF32 slices (4-byte elements)
+      float s0, s1;
+      ff_tf32(b.x, b.y, s0, s1);
+      float* Bf = reinterpret_cast<float*>(Bs);
+      Bf[(long long)i * K_pad + pc] = s0;
+      Bf[plane + (long long)i * K_pad + pc] = s1;
+    } else if (write_slices) {
       __nv_bfloat16 sl[3];
       ff_slices(b, nsl, sl);
 #pragma unroll
@@ -951,26 +1099,28 @@ __global__ void tc_unpermute_kernel(int n_r, int K, int K_pad, const int* __rest
   }
 }
 
-template <int NSL, int MODE, bool SCALE>
+template <int NSL, int MODE, bool SCALE, bool TF = false>
 cudaError_t set_smem_attr() {
-  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE, SCALE>,
+  cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE, SCALE, TF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE, SCALE>,
+  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE, SCALE, TF>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
 }
 
 // scale: the projection of FP16 field slices (group factors applied at the
-// flushes); two slices only
+// flushes); tf: TF32 operands; both two slices only
 template <int MODE>
-cudaError_t dispatch_gemm(int nsl, bool scale, int grid, const CUtensorMap& a, const CUtensorMap& b,
+cudaError_t dispatch_gemm(int nsl, bool scale, bool tf, int grid, const CUtensorMap& a, const CUtensorMap& b,
                           const CUtensorMap& bt, const TcArgs& args, cudaStream_t s) {
   constexpr int threads = tc::TileShape<MODE>::THREADS;
-  if (nsl == 3 && !scale) {
+  if (nsl == 3 && !scale && !tf) {
     tc::tc_gemm_kernel<3, MODE, false><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(a, b, bt, args);
+  } else if (nsl == 2 && tf && !scale) {
+    tc::tc_gemm_kernel<2, MODE, false, true><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
   } else if (nsl == 2 && !scale) {
     tc::tc_gemm_kernel<2, MODE, false><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
-  } else if (nsl == 2 && MODE == tc::kProject) {
+  } else if (nsl == 2 && !tf && MODE == tc::kProject) {
     tc::tc_gemm_kernel<2, MODE, MODE == tc::kProject><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(a, b, bt, args);
   } else {
     return cudaErrorInvalidValue;
@@ -979,14 +1129,17 @@ cudaError_t dispatch_gemm(int nsl, bool scale, int grid, const CUtensorMap& a, c
 }
 
 template <int MODE>
-cudaError_t dispatch_group(int nsl, bool scale, int grid, const tc::TcProblem* probs, const int* start, int n,
-                           int total, const tc::TcPhiList& phis, cudaStream_t s) {
+cudaError_t dispatch_group(int nsl, bool scale, bool tf, int grid, const tc::TcProblem* probs, const int* start,
+                           int n, int total, const tc::TcPhiList& phis, cudaStream_t s) {
   constexpr int threads = tc::TileShape<MODE>::THREADS;
-  if (nsl == 3 && !scale) {
+  if (nsl == 3 && !scale && !tf) {
     tc::tc_gemm_group_kernel<3, MODE, false><<<grid, threads, TcCfg<3, MODE>::SMEM, s>>>(probs, start, n, total, phis);
+  } else if (nsl == 2 && tf && !scale) {
+    tc::tc_gemm_group_kernel<2, MODE, false, true>
+        <<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
   } else if (nsl == 2 && !scale) {
     tc::tc_gemm_group_kernel<2, MODE, false><<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
-  } else if (nsl == 2 && MODE == tc::kProject) {
+  } else if (nsl == 2 && !tf && MODE == tc::kProject) {
     tc::tc_gemm_group_kernel<2, MODE, MODE == tc::kProject>
         <<<grid, threads, TcCfg<2, MODE>::SMEM, s>>>(probs, start, n, total, phis);
   } else {
@@ -1065,10 +1218,11 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
 
   const size_t kp = (size_t)p->tc_k_pad;
-  size_t bytes_ut = (size_t)nsl * kp * p->tc_n_pad * 2;
-  size_t bytes_q = (size_t)nsl * p->nang_wtotal * kp * 2;
-  size_t bytes_f = (size_t)(p->symmetric ? 2 : 1) * nsl * p->n_r * p->tc_n_pad * 2;
-  size_t bytes_m = (size_t)nsl * p->n_r * kp * 2;
+  const size_t esz = slice_bytes(p);
+  size_t bytes_ut = (size_t)nsl * kp * p->tc_n_pad * esz;
+  size_t bytes_q = (size_t)nsl * p->nang_wtotal * kp * esz;
+  size_t bytes_f = (size_t)(p->symmetric ? 2 : 1) * nsl * p->n_r * p->tc_n_pad * esz;
+  size_t bytes_m = (size_t)nsl * p->n_r * kp * esz;
   size_t bytes_part = s_max * p->n_r * kp * sizeof(float2);
   size_t bytes_nk = (size_t)p->n_r * kp * sizeof(double);
   size_t bytes_sum = (size_t)4 * p->tc_scan_P * kp * sizeof(double);
@@ -1166,6 +1320,20 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     slice_q16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, p->tc_eus, 0,
                                     reinterpret_cast<__half*>(p->tc_us));
     TC_TRY(cudaGetLastError());
+  } else if (p->tc_tf32) {
+    slice_ut_tf32_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
+                                        p->tc_pad_off_d, reinterpret_cast<float*>(p->tc_ut));
+    TC_TRY(cudaGetLastError());
+    slice_q_tf32_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->Q, 1,
+                                       reinterpret_cast<float*>(p->tc_qs));
+    TC_TRY(cudaGetLastError());
+    // adjoint operands: Q^T in the projection layout, U in the synthesis layout (monopole kept)
+    slice_ut_tf32_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->Q, p->pt, p->n_wpatch,
+                                        p->tc_pad_off_d, reinterpret_cast<float*>(p->tc_qt));
+    TC_TRY(cudaGetLastError());
+    slice_q_tf32_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, 0,
+                                       reinterpret_cast<float*>(p->tc_us));
+    TC_TRY(cudaGetLastError());
   } else {
     slice_ut_kernel<<<1024, 256>>>(nsl, K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
                                    p->tc_pad_off_d, p->tc_ut);
@@ -1185,15 +1353,15 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   const int Nt = p->tc_n_tail > 0 ? p->tc_n_tail : N;
   const int Npt = p->tc_np_tail > 0 ? p->tc_np_tail : NP;
   const int fplanes = (p->symmetric ? 2 : 1) * nsl;
-  const bool h16 = p->tc_fp16 != 0;
-  if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM, h16) ||
-      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, NP, h16) ||
-      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Npt, h16) ||
-      !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, h16) ||
-      !make_map(&p->tc_map_qt, p->tc_qt, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM, h16) ||
-      !make_map(&p->tc_map_us, p->tc_us, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, h16) ||
-      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N, h16) ||
-      !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt, h16)) {
+  const int kind = slice_kind(p);
+  if (!make_map(&p->tc_map_ut, p->tc_ut, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM, kind) ||
+      !make_map(&p->tc_map_f, p->tc_f, p->tc_n_pad, p->n_r, fplanes, NP, kind) ||
+      !make_map(&p->tc_map_f_tail, p->tc_f, p->tc_n_pad, p->n_r, fplanes, Npt, kind) ||
+      !make_map(&p->tc_map_q, p->tc_qs, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, kind) ||
+      !make_map(&p->tc_map_qt, p->tc_qt, p->tc_n_pad, p->tc_k_pad, nsl, tc::BM, kind) ||
+      !make_map(&p->tc_map_us, p->tc_us, p->tc_k_pad, p->nang_wtotal, nsl, tc::BM, kind) ||
+      !make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N, kind) ||
+      !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt, kind)) {
     set_error("cuTensorMapEncodeTiled failed or is unavailable");
     return YGS_ERR_CUDA;
   }
@@ -1203,8 +1371,10 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
       a1 = set_smem_attr<3, tc::kProject, false>();
       a2 = set_smem_attr<3, tc::kSynthesize, false>();
     } else {
-      a1 = p->tc_fp16 ? set_smem_attr<2, tc::kProject, true>() : set_smem_attr<2, tc::kProject, false>();
-      a2 = set_smem_attr<2, tc::kSynthesize, false>();
+      a1 = p->tc_fp16   ? set_smem_attr<2, tc::kProject, true>()
+           : p->tc_tf32 ? set_smem_attr<2, tc::kProject, false, true>()
+                        : set_smem_attr<2, tc::kProject, false>();
+      a2 = p->tc_tf32 ? set_smem_attr<2, tc::kSynthesize, false, true>() : set_smem_attr<2, tc::kSynthesize, false>();
     }
     TC_TRY(a1);
     TC_TRY(a2);
@@ -1267,6 +1437,11 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   const int threads = 128;
   const int bx = (int)std::min<long long>(64, (nmax / 4 + threads - 1) / threads);
   dim3 grid(std::max(1, bx), p->n_r, p->n_wpatch);
+  if (p->tc_tf32) {
+    field_slices_tf32_kernel<<<grid, threads, 0, s>>>(p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d, p->tc_n_pad,
+                                                      rho, reinterpret_cast<float*>(p->tc_f));
+    return cudaGetLastError();
+  }
   field_slices_kernel<<<grid, threads, 0, s>>>(p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d,
                                                p->tc_n_pad, rho, p->tc_f);
   return cudaGetLastError();
@@ -1285,11 +1460,14 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
 #define YGS_SYNTH_FLUSH_K 128
 #endif
 
+// k elements of one stage of the contractions: 64 two-byte or 32 TF32 values
+static int kblock_elems(const ygs_plan* p) { return p->tc_tf32 ? tc::BK / 2 : tc::BK; }
+
 static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.err = p->d_err;
-  a.ab_fmt = p->tc_fp16 ? 0 : 1;
+  a.ab_fmt = p->tc_tf32 ? 2 : (p->tc_fp16 ? 0 : 1);
   // flush the FP32 accumulators into the float-float sums every 64 k-elements
-  a.flush_kb = std::max(1, 64 / tc::BK);
+  a.flush_kb = std::max(1, 64 / kblock_elems(p));
   a.n_b = p->n_r;
   a.n_full = n_full;
   a.n_tail = n_tail;
@@ -1302,7 +1480,7 @@ static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
 static void project_args(const ygs_plan* p, TcArgs& a, bool forward = true) {
   a = TcArgs{};
   fill_tiles(p, a, p->tc_np_full, p->tc_np_tail);
-  if (forward && p->tc_fp16) a.flush_kb = std::max(1, YGS_PROJ_FLUSH_K_EXACT_MONO / tc::BK);
+  if (forward && p->tc_fp16) a.flush_kb = std::max(1, YGS_PROJ_FLUSH_K_EXACT_MONO / kblock_elems(p));
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
   a.a_row_odd = p->tc_k_even;
@@ -1322,7 +1500,8 @@ static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cuda
   TcArgs a;
   project_args(p, a, forward);
   const int grid = std::min(a.total_tiles, p->tc_sms);
-  return dispatch_gemm<tc::kProject>(p->tc_nsl, a.fac != nullptr, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
+  return dispatch_gemm<tc::kProject>(p->tc_nsl, a.fac != nullptr, p->tc_tf32 != 0, grid, wmap, p->tc_map_f,
+                                     p->tc_map_f_tail, a, s);
 }
 
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) { return project_with(p, p->tc_map_ut, s); }
@@ -1333,7 +1512,8 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   const float2 neg_g = make_float2(neg_gh, (float)(-p->G - (double)neg_gh));
   scan_ff_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
       p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, P, p->tc_pc_l, p->tc_part, p->tc_radff, p->tc_cp,
-      p->tc_B, p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, neg_g, p->tc_mono, p->tc_fp16 ? p->tc_eu : nullptr,
+      p->tc_B, p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : (p->tc_tf32 ? 2 : 1), neg_g, p->tc_mono,
+      p->tc_fp16 ? p->tc_eu : nullptr,
       p->tc_fp16 ? p->tc_mpart : nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !p->tc_fp16) return e;
@@ -1348,7 +1528,7 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   // the forward synthesis excludes the monopole (added exactly) and may flush less
   // often; the adjoint's U has a positive monopole column and keeps 64
-  a.flush_kb = std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / tc::BK);
+  a.flush_kb = std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / kblock_elems(p));
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;
@@ -1374,7 +1554,8 @@ static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, d
   TcArgs a;
   synth_args(p, a, phi, mono);
   const int grid = std::min(a.total_tiles, p->tc_sms);
-  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, false, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
+  return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, false, p->tc_tf32 != 0, grid, wmap, p->tc_map_m,
+                                        p->tc_map_m_tail, a, s);
 }
 
 cudaError_t tc_synthesize(const ygs_plan* p, double* phi, cudaStream_t s) {
@@ -1394,7 +1575,8 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
   scan_adj_ff_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
       p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part, p->tc_radff,
-      p->tc_Mbar, p->tc_Bbar, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : 1, p->tc_fp16 ? p->tc_eqt : nullptr);
+      p->tc_Mbar, p->tc_Bbar, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : (p->tc_tf32 ? 2 : 1),
+      p->tc_fp16 ? p->tc_eqt : nullptr);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p->tc_fp16) {
     slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_Bbar, 1,
@@ -1411,12 +1593,12 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
 ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
   b->groups.clear();
   // one group per operand kind: BF16 two-slice, FP16 two-slice (whose
-  // projection applies the field's group factors), BF16 three-slice
-  for (int kind = 0; kind < 3; ++kind) {
-    const int nsl = kind == 2 ? 3 : 2, fp16 = kind == 1 ? 1 : 0;
+  // projection applies the field's group factors), BF16 three-slice, TF32 two-slice
+  for (int kind = 0; kind < 4; ++kind) {
+    const int nsl = kind == 2 ? 3 : 2, fp16 = kind == 1 ? 1 : 0, tf32 = kind == 3 ? 1 : 0;
     std::vector<ygs_plan*> mem;
     for (ygs_plan* p : plans)
-      if (p->tc_nsl == nsl && p->tc_fp16 == fp16) mem.push_back(p);
+      if (p->tc_nsl == nsl && p->tc_fp16 == fp16 && p->tc_tf32 == tf32) mem.push_back(p);
     if (mem.empty()) continue;
     if ((int)mem.size() > tc::kMaxGroup) {
       set_error("a batch holds at most 128 split-precision plans of one operand kind");
@@ -1425,6 +1607,7 @@ ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
     TcBatchGroup G;
     G.nsl = nsl;
     G.fp16 = fp16;
+    G.tf32 = tf32;
     G.members = mem;
     std::vector<tc::TcProblem> proj(mem.size()), syn(mem.size());
     std::vector<int> sp(mem.size() + 1, 0), ss(mem.size() + 1, 0);
@@ -1476,14 +1659,14 @@ void tc_batch_free(TcBatch* b) {
 
 cudaError_t tc_batch_project(const TcBatchGroup& G, cudaStream_t s) {
   tc::TcPhiList none{};
-  return dispatch_group<tc::kProject>(G.nsl, G.fp16 != 0, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
+  return dispatch_group<tc::kProject>(G.nsl, G.fp16 != 0, G.tf32 != 0, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
                                       (int)G.members.size(), G.total_p, none, s);
 }
 
 cudaError_t tc_batch_synthesize(const TcBatchGroup& G, double* const* phi, cudaStream_t s) {
   tc::TcPhiList out{};
   for (size_t k = 0; k < G.members.size(); ++k) out.p[k] = phi[k];
-  return dispatch_group<tc::kSynthesize>(G.nsl, false, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
+  return dispatch_group<tc::kSynthesize>(G.nsl, false, G.tf32 != 0, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
                                          (int)G.members.size(), G.total_s, out, s);
 }
 

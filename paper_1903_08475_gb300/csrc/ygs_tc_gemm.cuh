@@ -43,7 +43,14 @@ namespace tc {
 #ifndef YGS_EPI_CHUNK_SCALED
 #define YGS_EPI_CHUNK_SCALED 8  // the same for the flushes that apply the field's group factors
 #endif
-constexpr int BK = YGS_TC_BK;  // k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
+constexpr int BK = YGS_TC_BK;  // 2-byte k elements per stage: 64 (128-byte rows, 128-byte swizzle) or 32 (64-byte)
+// k elements per stage: BK for 2-byte operands, BK / 2 for TF32 (4-byte)
+// operands, so that a stage holds the same bytes (and the same descriptors
+// and k-steps: four of 32 bytes per product) for every operand type
+template <bool TF>
+struct KElems {
+  static constexpr int KE = TF ? BK / 2 : BK;
+};
 constexpr int BM = 128;        // output rows per tile (TMEM lanes)
 // Tile shapes (shells per tile, columns per epilogue warp).  144-shell tiles
 // keep the tensor core compute-bound (a 128 x 80 x 16 MMA is bound by reading
@@ -89,7 +96,7 @@ struct TcArgs {
   int a_rows_total;     // rows of A that hold data (even + odd blocks)
   int b_plane_odd;      // B plane of the odd block's field slices (sigma-) or 0
   int n_chunks;         // S
-  const int2* chunks;   // k range [x, y) of chunk z, in elements (multiples of BK)
+  const int2* chunks;   // k range [x, y) of chunk z, in elements (multiples of the k-block)
   float2* part;         // [z][n_b][ldp] (hi, lo)
   int ldp;
   // FP16 field slices: fac[h][G][n] = 2^-e of the field row (plane h, exponent
@@ -101,7 +108,7 @@ struct TcArgs {
   long long fac_plane;
   int fac_ld;
   // ---- synthesis: tile = (patch g, m-tile, n-tile), n fastest
-  int k_even;           // length of the even column block (elements, multiple of BK)
+  int k_even;           // length of the even column block (elements, multiple of the k-block)
   int k_total;          // total padded columns
   int symmetric;
   int n_wpatch;
@@ -114,7 +121,7 @@ struct TcArgs {
   // of being accumulated on the tensor cores (its column is zero in the Q
   // slices).  nullptr disables it.
   const float2* mono;
-  int ab_fmt;           // operand type of the slices: 1 = BF16, 0 = FP16
+  int ab_fmt;           // operand type of the slices: 1 = BF16, 0 = FP16, 2 = TF32 (then a TF32 kernel)
   // FP16 slices are scaled rows: sc[n] = {c20, 0, monopole head, tail}, with
   // c20 = (896 + d) << 20 (an int's bits) for d = -(q_exp + m_exp[n]), the
   // power of two that unscales the synthesis result of shell n, applied as it
@@ -193,7 +200,7 @@ struct Tile {
   int g_patch, m_loc, z;
 };
 
-template <int MODE>
+template <int MODE, int KE>
 __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
   constexpr int NMAX = TileShape<MODE>::NMAX;
   Tile T;
@@ -210,7 +217,7 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
     T.b_plane0 = odd ? a.b_plane_odd : 0;
     const int2 ch = a.chunks[T.z];
     T.kstart = ch.x;
-    T.seg_kb0 = (ch.y - ch.x) / BK;
+    T.seg_kb0 = (ch.y - ch.x) / KE;
     T.seg_kb1 = 0;
     T.g_patch = 0;
     T.m_loc = mt;
@@ -226,8 +233,8 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
     T.b_plane0 = 0;
     T.kstart = 0;
     const bool two = a.symmetric && a.k_even < a.k_total;
-    T.seg_kb0 = (two ? a.k_even : a.k_total) / BK;
-    T.seg_kb1 = two ? (a.k_total - a.k_even) / BK : 0;
+    T.seg_kb0 = (two ? a.k_even : a.k_total) / KE;
+    T.seg_kb1 = two ? (a.k_total - a.k_even) / KE : 0;
     T.z = 0;
   }
   T.use_tail = (n >= a.n_full);
@@ -284,9 +291,11 @@ struct GroupSrc {  // tiles of several problems concatenated: problem k owns [st
 // factors at every flush.  A compile-time switch: each instance then holds
 // only its own flush code, and the epilogue's float-float sums stay in
 // registers.
-template <int NSL, int MODE, bool SCALE, class Src>
+template <int NSL, int MODE, bool SCALE, bool TF, class Src>
 __device__ __forceinline__ void gemm_body(const Src& src) {
   static_assert(!SCALE || MODE == kProject, "only the projection scales its flushes");
+  static_assert(!(TF && SCALE), "TF32 operands need no scaling");
+  constexpr int KE = KElems<TF>::KE;
   using C = TcCfg<NSL, MODE>;
   constexpr int NMAX = TileShape<MODE>::NMAX;
   constexpr int NH = TileShape<MODE>::NH;
@@ -335,7 +344,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       int* err = nullptr;
       for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
         const TileRef R = src.locate(t);
-        const Tile T = decode_tile<MODE>(*R.A, R.t);
+        const Tile T = decode_tile<MODE, KE>(*R.A, R.t);
         err = R.A->err;
         const CUtensorMap* mb = T.use_tail ? R.mbt : R.mb;
         const uint32_t bytes = NSL * (C::A_SLICE + T.n_eff * BK * 2);
@@ -354,12 +363,12 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           const bool fac_now = SCALE && kb % flush == 0;  // first k-block of a flush group
           mbar_arrive_expect_tx(&full[stage], bytes + (fac_now ? NMAX * 4 : 0));
           if (fac_now) {
-            const int G = (T.kstart / BK + kb) / kGroupKb;
+            const int G = (T.kstart / KE + kb) / kGroupKb;
             const float* src = fac + (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
             bulk_load(fac_ring + (fgroups % C::FAC_RING) * NMAX, src, NMAX * 4, &full[stage]);
             ++fgroups;
           }
-          const int kx = T.kstart + kb * BK;
+          const int kx = T.kstart + kb * KE;
 #pragma unroll
           for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, R.ma, &full[stage], kx, T.a_row0, s);
 #pragma unroll
@@ -383,7 +392,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       int* err = nullptr;
       for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
         const TileRef R = src.locate(t);
-        const Tile T = decode_tile<MODE>(*R.A, R.t);
+        const Tile T = decode_tile<MODE, KE>(*R.A, R.t);
         err = R.A->err;
         const uint32_t idesc = idesc_f16(BM, T.n_eff, R.A->ab_fmt);
         const int flush = R.A->flush_kb;  // k-blocks per accumulator flush, per problem
@@ -423,7 +432,10 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
                 const int kk = (i < NC * (BK / 16)) ? i / NCd : i - NC * (BK / 16);
                 const uint64_t ad = a0 + (uint64_t)((prod_s(p) * C::A_SLICE + kk * 32) >> 4);
                 const uint64_t bd = b0 + (uint64_t)((prod_t(p) * C::B_SLICE + kk * 32) >> 4);
-                umma_f16(d, ad, bd, idesc, init ? 1u : 0u);
+                if (TF)
+                  umma_tf32(d, ad, bd, idesc, init ? 1u : 0u);
+                else
+                  umma_f16(d, ad, bd, idesc, init ? 1u : 0u);
                 init = true;
               }
               umma_commit(&empty[stage]);
@@ -454,7 +466,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
     int* err = nullptr;
     for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
       const TileRef R = src.locate(t);
-      const Tile T = decode_tile<MODE>(*R.A, R.t);
+      const Tile T = decode_tile<MODE, KE>(*R.A, R.t);
       err = R.A->err;
       const int flush = R.A->flush_kb;
       const bool active = col0 < T.n_eff;  // this warp's columns exist in the tile (warp-uniform)
@@ -629,7 +641,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
 // spread over the SM's four sub-partitions (16,384 registers each), four
 // warps on two of them, so 4 x 32 x 128 is the ceiling for one CTA per SM.
 // One problem: maps and arguments in kernel parameters.
-template <int NSL, int MODE, bool SCALE>
+template <int NSL, int MODE, bool SCALE, bool TF = false>
 __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ TcArgs args) {
@@ -639,18 +651,18 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     prefetch_tmap(&mapBt);
   }
   const SingleSrc src{&args, &mapA, &mapB, &mapBt};
-  gemm_body<NSL, MODE, SCALE>(src);
+  gemm_body<NSL, MODE, SCALE, TF>(src);
 }
 
 // Several problems of one operand type in one persistent launch (a batch of
 // fields): every CTA walks the concatenated tile list; TMEM accumulators and
 // shared-memory stages carry over from one problem to the next.
-template <int NSL, int MODE, bool SCALE>
+template <int NSL, int MODE, bool SCALE, bool TF = false>
 __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     tc_gemm_group_kernel(const TcProblem* __restrict__ probs, const int* __restrict__ start, int n, int total,
                          const __grid_constant__ TcPhiList phis) {
   const GroupSrc src{probs, start, n, total, &phis};
-  gemm_body<NSL, MODE, SCALE>(src);
+  gemm_body<NSL, MODE, SCALE, TF>(src);
 }
 
 }  // namespace tc

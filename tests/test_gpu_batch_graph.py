@@ -80,7 +80,7 @@ def _uneven_fields(cuda):
              W.polar_grid(7, 13, W.linear_edges(6, 0.1, 1.0), 5),
              small_yinyang(W, n_theta=10, n_phi=28, n_r=300, l_max=12),
              small_yinyang(W, n_theta=6, n_phi=18, n_r=9, l_max=0)]
-    precs = ["fp16x3", "bf16x6", "fp16x3", "fp64", "bf16x3", "fp16x3"]
+    precs = ["fp16x3", "bf16x6", "tf32x3", "fp64", "bf16x3", "fp16x3"]
     plans = [Plan(g, p) for g, p in zip(grids, precs)]
     rhos = [torch.from_numpy(W.random_density(g, 40 + i)).cuda() for i, g in enumerate(grids)]
     return plans, rhos
@@ -94,9 +94,9 @@ def test_grouped_batch_equals_per_field(cuda):
     ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
     with Batch(plans) as b:
         # 6 fields: field slices + one scan (+ M slicing for FP16) per split field,
-        # 2 grouped launches for each of the three operand kinds (FP16 two-slice,
-        # BF16 two-slice, BF16 three-slice), 3 for the FP64 field
-        assert b.launches == 3 * 3 + 2 + 2 + 2 * 3 + 3
+        # 2 grouped launches for each of the four operand kinds (FP16 two-slice,
+        # BF16 two-slice, BF16 three-slice, TF32 two-slice), 3 for the FP64 field
+        assert b.launches == 2 * 3 + 2 + 2 + 2 + 2 * 4 + 3
         for _ in range(2):
             outs = b.solve(rhos)
             torch.cuda.synchronize()

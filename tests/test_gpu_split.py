@@ -19,7 +19,7 @@ from tests.test_gpu_fp64 import three_patch_grid, hole_grid
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x6": 1e-6, "bf16x3": 5e-4, "fp16x3": 1e-6}
+TOL = {"bf16x6": 1e-6, "bf16x3": 5e-4, "fp16x3": 1e-6, "tf32x3": 1e-6}
 
 CASES = {
     "yy_small": lambda: small_yinyang(W),
@@ -42,7 +42,7 @@ def case(request, cuda):
     return request.param, grid, rho, phi_ref, B_ref, M_ref
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "bf16x3", "fp16x3", "tf32x3"])
 def test_phi_matches_oracle(case, precision):
     import torch
     name, grid, rho, phi_ref, B_ref, M_ref = case
@@ -57,7 +57,7 @@ def test_phi_matches_oracle(case, precision):
         assert rel_max(M.cpu().numpy()[:, 0], M_ref[:, 0]) <= TOL[precision]
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3", "tf32x3"])
 def test_config0(cuda, precision):
     import torch
     grid, rho = W.config0()
@@ -79,7 +79,7 @@ def test_split_deterministic(cuda):
         assert torch.equal(a, b)
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3", "tf32x3"])
 def test_large_dynamic_range(cuda, precision):
     """Density spanning 1e-30 .. 1e30 (BF16's exponent range covers it; FP16
     rows are scaled by powers of two, and cells far below a row's largest
@@ -110,7 +110,7 @@ def test_fp16_scaling_physical_units(cuda, scale):
         assert rel_max(phi.cpu().numpy(), ref) <= TOL["fp16x3"]
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3", "tf32x3"])
 def test_autotuned_split_k(cuda, precision):
     """A plan whose split-K count was picked by timing candidates at create
     (YGS_FLAG_AUTOTUNE) stays within the precision's bound of the oracle."""
@@ -162,7 +162,7 @@ def _special_density(grid, kind):
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3", "tf32x3"])
 @pytest.mark.parametrize("kind", ["zero", "signed", "yin_equals_yang", "yang_zero"])
 def test_special_densities(cuda, precision, kind):
     """Densities that reach the degenerate branches of the split path: all zero
@@ -183,7 +183,7 @@ def test_special_densities(cuda, precision, kind):
     assert _rel_to_max(got, ref) <= TOL[precision], f"{kind} {precision}"
 
 
-@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3"])
+@pytest.mark.parametrize("precision", ["bf16x6", "fp16x3", "tf32x3"])
 def test_signed_density_large_chunks(cuda, precision):
     """Signed density on a 2-degree grid with config-1 shells and degree
     (Nr = 400, l_max = 32), whose split-K chunks hold about 2000 cells: the
