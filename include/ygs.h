@@ -70,7 +70,8 @@ typedef enum {
   YGS_ERR_OOM = 2,         /* device allocation failed */
   YGS_ERR_CUDA = 3,        /* a CUDA runtime/driver call failed */
   YGS_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
-  YGS_ERR_NUMERIC = 5,     /* a weight self-check failed */
+  YGS_ERR_NUMERIC = 5,     /* a weight self-check failed, or (YGS_FP64_EMU) a field value at
+                              or above 2^127, beyond what the FP32 window sums can hold */
   YGS_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
 } ygs_status;
 
@@ -89,11 +90,18 @@ typedef enum {
   YGS_FP32 = 5,    /* FP32 contractions on the CUDA cores (FP32 copies of U and Q, the field
                      truncated to FP32, FP32 accumulation), FP64 radial scans; the adjoint of
                      such a plan runs on its FP64 weights */
-  YGS_TF32X3 = 6   /* tcgen05 TF32 tensor cores (kind::tf32), 2-slice operands (each value split
+  YGS_TF32X3 = 6,  /* tcgen05 TF32 tensor cores (kind::tf32), 2-slice operands (each value split
                      into two TF32 values, 22 significant bits), 3 products; FP32's exponent range,
                      so no row scaling; twice the operand bytes and half the tensor rate of FP16x3.
                      Phi within 1e-6 of FP64 (as FP16x3); its adjoint within 2e-6 of the
                      largest |A^T w| (1.4e-6 measured at l_max = 32) */
+  YGS_FP64_EMU = 7 /* FP64-accurate contractions on the BF16 tensor cores (Ozaki-type splitting):
+                     every FP64 value cut exactly into six 8-bit slices on a fixed grid (per
+                     weight row; per shell and window of 256 cells for the field; per shell
+                     for M), the 21 slice products with s + t <= 5 each summed exactly in FP32
+                     over windows of 256 k, the window sums added in float-float; FP64 radial
+                     scans.  Phi within 1e-12 of FP64.  The FP32 window sums bound the field:
+                     values (and their products with U) must stay well inside FP32's range */
 } ygs_precision;
 
 typedef enum {

@@ -20,7 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libygs.so")
 YGS_OK = 0
 STATUS = {0: "YGS_OK", 1: "YGS_ERR_INVALID_ARG", 2: "YGS_ERR_OOM", 3: "YGS_ERR_CUDA",
           4: "YGS_ERR_UNSUPPORTED", 5: "YGS_ERR_NUMERIC", 6: "YGS_ERR_TIMEOUT"}
-PRECISION = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp16x3": 3, "fp64tc": 4, "fp32": 5, "tf32x3": 6}
+PRECISION = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp16x3": 3, "fp64tc": 4, "fp32": 5, "tf32x3": 6,
+             "fp64emu": 7}
 EVAL = {"upper_vertex": 0, "cell_centre": 1}
 FLAG_NO_SYMMETRY = 1
 FLAG_AUTOTUNE = 2

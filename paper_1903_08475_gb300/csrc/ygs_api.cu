@@ -150,7 +150,7 @@ ygs_status validate_desc(const ygs_desc* d) {
     return fail(YGS_ERR_INVALID_ARG, "l_max must be in [0, " + std::to_string(kMaxLmax) + "]");
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
-  if (d->precision < YGS_FP64 || d->precision > YGS_TF32X3) return fail(YGS_ERR_INVALID_ARG, "bad precision");
+  if (d->precision < YGS_FP64 || d->precision > YGS_FP64_EMU) return fail(YGS_ERR_INVALID_ARG, "bad precision");
   if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;
@@ -364,11 +364,12 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
   if ((e = prepare_static_scratch()) != cudaSuccess)
     return fail_free(cuda_fail(e, "making the static scratch array resident"));
   if (p->precision == YGS_BF16X6 || p->precision == YGS_BF16X3 || p->precision == YGS_FP16X3 ||
-      p->precision == YGS_TF32X3) {
+      p->precision == YGS_TF32X3 || p->precision == YGS_FP64_EMU) {
     if (p->n_r > 65535) return fail_free(fail(YGS_ERR_UNSUPPORTED, "split precision supports n_r <= 65535"));
-    p->tc_nsl = (p->precision == YGS_BF16X6) ? 3 : 2;
+    p->tc_nsl = (p->precision == YGS_FP64_EMU) ? 6 : ((p->precision == YGS_BF16X6) ? 3 : 2);
     p->tc_fp16 = (p->precision == YGS_FP16X3) ? 1 : 0;
     p->tc_tf32 = (p->precision == YGS_TF32X3) ? 1 : 0;
+    p->tc_emu = (p->precision == YGS_FP64_EMU) ? 1 : 0;
     st = tc_setup(p, sms);
     if (st != YGS_OK) return fail_free(st);
   }
@@ -638,7 +639,7 @@ ygs_status ygs_batch_solve(ygs_batch* b, const double* const* d_rho, double* con
 int ygs_batch_launches(const ygs_batch* b) {
   if (!b) return 0;
   int n = 0;
-  for (int k : b->split) n += b->plans[k]->tc_fp16 ? 3 : 2;  // field slices, scan (+ M slicing)
+  for (int k : b->split) n += (b->plans[k]->tc_fp16 || b->plans[k]->tc_emu) ? 3 : 2;  // field slices, scan (+ M slicing)
   n += 2 * (int)b->tc.groups.size() + 3 * (int)b->fp64.size();
   return n;
 }
@@ -671,7 +672,10 @@ ygs_status ygs_get_moments(ygs_plan* p, double* d_B, double* d_M, void* stream) 
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
   DeviceGuard guard(p->device);
   cudaStream_t s = (cudaStream_t)stream;
-  if (p->tc_nsl) {
+  if (p->tc_emu) {
+    if (d_B) API_TRY(emu_unpermute(p, p->tc_Bd, d_B, s));
+    if (d_M) API_TRY(emu_unpermute(p, p->tc_Md, d_M, s));
+  } else if (p->tc_nsl) {
     if (d_B) API_TRY(tc_unpermute(p, p->tc_B, d_B, s));
     if (d_M) API_TRY(tc_unpermute(p, p->tc_M, d_M, s));
   } else {
@@ -739,7 +743,7 @@ ygs_status ygs_debug_wait_timeout(ygs_plan* p, int spins, void* stream) {
 }
 
 int ygs_launches_per_solve(const ygs_plan* p) {
-  return p ? (p->tc_nsl ? (p->tc_fp16 ? 5 : 4) : (p->precision == YGS_FP32 ? 5 : 3)) : 0;
+  return p ? (p->tc_nsl ? ((p->tc_fp16 || p->tc_emu) ? 5 : 4) : (p->precision == YGS_FP32 ? 5 : 3)) : 0;
 }
 
 ygs_status ygs_get_status(ygs_plan* p) {

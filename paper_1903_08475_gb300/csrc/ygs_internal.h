@@ -100,6 +100,11 @@ struct ygs_plan {
   float2* tc_cp = nullptr;    // [2][l_max+1][P] radial ratio products per chunk of shells (float-float)
   float2* tc_radff = nullptr; // [4][l_max+1][n_r] the radial tables a, b, f_in, f_out as float-float
   int tc_tf32 = 0;            // TF32 slices (YGS_TF32X3): 4-byte elements behind the slice pointers
+  // FP64-accurate slices (YGS_FP64_EMU): six exact 8-bit BF16 slices per
+  // value (tc_nsl = 6), the field on per-window grids (factors in tc_fac), M
+  // on per-shell grids (tc_sc); FP64 radial scans into tc_Bd / tc_Md
+  int tc_emu = 0;
+  double *tc_Bd = nullptr, *tc_Md = nullptr;  // [n_r][K_pad] FP64 B and M of the last solve
   // FP16 slices (YGS_FP16X3): power-of-two exponents that scale each operand row into FP16's range
   int tc_fp16 = 0;
   int tc_eq = 0;              // Q (all rows)
@@ -117,7 +122,7 @@ struct ygs_plan {
   __nv_bfloat16 *tc_qt = nullptr, *tc_us = nullptr;
   int* tc_eqt = nullptr;      // [K_pad] Q^T row (column c)
   int tc_eus = 0;             // U (all rows)
-  float2 *tc_Mbar = nullptr, *tc_Bbar = nullptr;  // float-float
+  float2 *tc_Mbar = nullptr, *tc_Bbar = nullptr;  // float-float (EMU: n_r K_pad doubles each)
   CUtensorMap tc_map_qt, tc_map_us;
 };
 
@@ -180,7 +185,7 @@ namespace tc {
 struct TcProblem;
 }
 struct TcBatchGroup {
-  int nsl = 0, fp16 = 0, tf32 = 0, sms = 0, total_p = 0, total_s = 0;
+  int nsl = 0, fp16 = 0, tf32 = 0, emu = 0, sms = 0, total_p = 0, total_s = 0;
   std::vector<ygs_plan*> members;
   tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
   int *d_start_p = nullptr, *d_start_s = nullptr;
@@ -198,5 +203,33 @@ cudaError_t tc_batch_synthesize(const TcBatchGroup& g, double* const* phi, cudaS
 // with Q, transposed scans, synthesis with U.
 cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t debug_wait_timeout(const ygs_plan* p, int spins, cudaStream_t s);
+
+// ---- FP64-accurate splitting on the BF16 tensor cores (ygs_emu.cu) ----------
+// Cells per exponent window of the field (the flush group of its contraction).
+constexpr int kEmuWindow = 1024;
+// The weights' slices of an EMU plan (tc_ut, tc_qs, tc_qt, tc_us: six each,
+// on per-row grids, monopole columns kept); synchronous, at create.
+cudaError_t emu_slice_weights(ygs_plan* p);
+// Shared-memory limits of the EMU contraction kernels (at create).
+cudaError_t emu_set_smem_attrs();
+// Field slices sigma+- (or rho) on per-(plane, window, shell) grids and their
+// factors 2^e in tc_fac.
+cudaError_t emu_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s);
+// Forward scans in FP64 (B, M into tc_Bd / tc_Md, float-float copies into
+// tc_B / tc_M), then M's slices and tc_sc.
+cudaError_t emu_scan(const ygs_plan* p, cudaStream_t s);
+// Adjoint scans in FP64 (Mbar, Bbar into tc_Mbar / tc_Bbar as doubles), then Bbar's slices.
+cudaError_t emu_scan_adj(const ygs_plan* p, cudaStream_t s);
+// out[i][natural column] = in[i][pc] for FP64 moments in the padded column order.
+cudaError_t emu_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// The EMU contraction kernels (one problem, or a group of problems).
+namespace tc {
+struct TcArgs;
+struct TcPhiList;
+}
+cudaError_t emu_dispatch_gemm(int mode, int grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& bt,
+                              const tc::TcArgs& args, cudaStream_t s);
+cudaError_t emu_dispatch_group(int mode, int grid, const tc::TcProblem* probs, const int* start, int n, int total,
+                               const tc::TcPhiList& phis, cudaStream_t s);
 
 }  // namespace ygs

@@ -1154,9 +1154,10 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   const int nsl = p->tc_nsl;
   const int K = p->K;
   auto r64 = [](long long x) { return (x + 63) / 64 * 64; };
-  // angular padding to whole exponent groups (two k-blocks): chunk and
-  // patch starts then fall on group boundaries
-  auto r32 = [](long long x) { return (x + kGroup - 1) / kGroup * kGroup; };
+  // angular padding to whole exponent groups (two k-blocks; EMU: windows of
+  // four): chunk and patch starts then fall on group boundaries
+  const long long grp = p->tc_emu ? kEmuWindow : kGroup;
+  auto r32 = [grp](long long x) { return (x + grp - 1) / grp * grp; };
   static_assert(kGroup == 2 * tc::BK, "an exponent group is two k-blocks");
   // padded column layout: [even block | pad | odd block | pad]
   const int Ke = p->K_even, Ko = K - p->K_even;
@@ -1175,7 +1176,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   p->tc_pad_off.assign(p->n_wpatch + 1, 0);
   for (int g = 0; g < p->n_wpatch; ++g) p->tc_pad_off[g + 1] = p->tc_pad_off[g] + r32(p->nang[g]);
   p->tc_n_pad = p->tc_pad_off[p->n_wpatch];
-  const int NP = tc::kNmaxProject, NS = tc::kNmaxSynth;
+  const int NP = tc::kNmaxProject, NS = p->tc_emu ? tc::kNmaxSynthEmu : tc::kNmaxSynth;
   p->tc_N = NS;
   p->tc_np_full = p->n_r / NP;
   p->tc_np_tail = ((p->n_r % NP) + 15) / 16 * 16;
@@ -1202,7 +1203,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
       const long long kb_g = r32(p->nang[g]) / tc::BK;
       long long sg = std::max(1LL, (wv * p->nang[g] + p->nang_wtotal - 1) / p->nang_wtotal);
       sg = std::min(sg, std::max(1LL, kb_g / 4));
-      const long long per = ((kb_g + sg - 1) / sg + 1) / 2 * 2;  // whole exponent groups per chunk
+      const long long gkb = grp / tc::BK;
+      const long long per = ((kb_g + sg - 1) / sg + gkb - 1) / gkb * gkb;  // whole exponent groups per chunk
       for (long long k0 = 0; k0 < kb_g; k0 += per)
         chunks.push_back(make_int2((int)((p->tc_pad_off[g] + k0 * tc::BK)),
                                    (int)(p->tc_pad_off[g] + std::min(kb_g, k0 + per) * tc::BK)));
@@ -1262,6 +1264,12 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_ALLOC(p->tc_em, (size_t)p->n_r * sizeof(int));
     TC_ALLOC(p->tc_sc, (size_t)p->n_r * sizeof(float4));
   }
+  if (p->tc_emu) {
+    TC_ALLOC(p->tc_fac, (size_t)2 * (p->tc_n_pad / kEmuWindow) * fac_ld(p) * sizeof(float));
+    TC_ALLOC(p->tc_sc, (size_t)p->n_r * sizeof(float4));
+    TC_ALLOC(p->tc_Bd, bytes_nk);
+    TC_ALLOC(p->tc_Md, bytes_nk);
+  }
 #undef TC_ALLOC
   p->weight_bytes += (long long)(2 * (bytes_ut + bytes_q));
   p->work_bytes += (long long)(bytes_f + bytes_m + bytes_part + 4 * bytes_nk + bytes_sum * 3 / 2);
@@ -1277,8 +1285,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   TC_TRY(cudaMemcpy(p->tc_pad_off_d, p->tc_pad_off.data(), (p->n_wpatch + 1) * sizeof(long long),
                     cudaMemcpyHostToDevice));
   TC_TRY(cudaMemset(p->tc_f, 0, bytes_f));  // padding columns stay zero
-  if (p->tc_fp16)  // factors of the shells past n_r (read with a tile's row, never written) stay zero
-    TC_TRY(cudaMemset(p->tc_fac, 0, (size_t)2 * (p->tc_n_pad / kGroup) * fac_ld(p) * sizeof(float)));
+  if (p->tc_fp16 || p->tc_emu)  // factors of the shells past n_r (read with a tile's row, never written) stay zero
+    TC_TRY(cudaMemset(p->tc_fac, 0, (size_t)2 * (p->tc_n_pad / grp) * fac_ld(p) * sizeof(float)));
   chunk_prod_kernel<<<((p->l_max + 1) * p->tc_scan_P + 127) / 128, 128>>>(p->n_r, p->l_max, p->tc_scan_chunk,
                                                                           p->tc_scan_P, p->rad, p->tc_cp);
   TC_TRY(cudaGetLastError());
@@ -1320,6 +1328,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     slice_q16_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->nang_wtotal, p->tc_pc_int, p->tc_pc_nat, p->U, p->tc_eus, 0,
                                     reinterpret_cast<__half*>(p->tc_us));
     TC_TRY(cudaGetLastError());
+  } else if (p->tc_emu) {
+    TC_TRY(emu_slice_weights(p));
   } else if (p->tc_tf32) {
     slice_ut_tf32_kernel<<<1024, 256>>>(K, p->tc_k_pad, p->tc_n_pad, p->tc_pc_int, p->U, p->pt, p->n_wpatch,
                                         p->tc_pad_off_d, reinterpret_cast<float*>(p->tc_ut));
@@ -1367,7 +1377,9 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   }
   {
     cudaError_t a1 = cudaSuccess, a2 = cudaSuccess;
-    if (nsl == 3) {
+    if (p->tc_emu) {
+      a1 = emu_set_smem_attrs();
+    } else if (nsl == 3) {
       a1 = set_smem_attr<3, tc::kProject, false>();
       a2 = set_smem_attr<3, tc::kSynthesize, false>();
     } else {
@@ -1418,12 +1430,13 @@ void tc_free(ygs_plan* p) {
                   p->tc_M,     p->tc_summ,   p->tc_carry,  p->tc_chunks, p->tc_pc_int,    p->tc_pc_l,
                   p->tc_pc_nat, p->tc_pad_off_d, p->tc_mono, p->tc_cp, p->tc_radff, p->tc_eu, p->tc_fac, p->tc_em,
                   p->tc_qt,    p->tc_us,     p->tc_eqt,    p->tc_Mbar,   p->tc_Bbar,   p->tc_u00,
-                  p->tc_mpart, p->tc_sc};
+                  p->tc_mpart, p->tc_sc, p->tc_Bd, p->tc_Md};
   for (void* b : bufs)
     if (b) cudaFree(b);
 }
 
 cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s, bool forward) {
+  if (p->tc_emu) return emu_field_slices(p, rho, s);
   if (p->tc_fp16) {
     const float2* u00 = forward ? p->tc_u00 : nullptr;
     float2* mpart = forward ? p->tc_mpart : nullptr;
@@ -1467,7 +1480,8 @@ static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
   a.err = p->d_err;
   a.ab_fmt = p->tc_tf32 ? 2 : (p->tc_fp16 ? 0 : 1);
   // flush the FP32 accumulators into the float-float sums every 64 k-elements
-  a.flush_kb = std::max(1, 64 / kblock_elems(p));
+  // (EMU: every window of four k-blocks, whose sums are exact)
+  a.flush_kb = p->tc_emu ? tc::kEmuWindowKb : std::max(1, 64 / kblock_elems(p));
   a.n_b = p->n_r;
   a.n_full = n_full;
   a.n_tail = n_tail;
@@ -1490,9 +1504,9 @@ static void project_args(const ygs_plan* p, TcArgs& a, bool forward = true) {
   a.chunks = p->tc_chunks;
   a.part = p->tc_part;
   a.ldp = p->tc_k_pad;
-  a.fac = p->tc_fp16 ? p->tc_fac : nullptr;
+  a.fac = (p->tc_fp16 || p->tc_emu) ? p->tc_fac : nullptr;
   a.fac_ld = fac_ld(p);
-  a.fac_plane = (p->tc_n_pad / kGroup) * (long long)a.fac_ld;
+  a.fac_plane = (p->tc_n_pad / (p->tc_emu ? kEmuWindow : kGroup)) * (long long)a.fac_ld;
   a.total_tiles = a.tiles_m * a.n_chunks * a.n_tiles;
 }
 
@@ -1500,6 +1514,7 @@ static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cuda
   TcArgs a;
   project_args(p, a, forward);
   const int grid = std::min(a.total_tiles, p->tc_sms);
+  if (p->tc_emu) return emu_dispatch_gemm(tc::kProject, grid, wmap, p->tc_map_f, p->tc_map_f_tail, a, s);
   return dispatch_gemm<tc::kProject>(p->tc_nsl, a.fac != nullptr, p->tc_tf32 != 0, grid, wmap, p->tc_map_f,
                                      p->tc_map_f_tail, a, s);
 }
@@ -1507,6 +1522,7 @@ static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cuda
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) { return project_with(p, p->tc_map_ut, s); }
 
 cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
+  if (p->tc_emu) return emu_scan(p, s);
   const int P = p->tc_scan_P;
   const float neg_gh = (float)(-p->G);
   const float2 neg_g = make_float2(neg_gh, (float)(-p->G - (double)neg_gh));
@@ -1528,7 +1544,7 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   // the forward synthesis excludes the monopole (added exactly) and may flush less
   // often; the adjoint's U has a positive monopole column and keeps 64
-  a.flush_kb = std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / kblock_elems(p));
+  a.flush_kb = p->tc_emu ? tc::kEmuWindowKb : std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / kblock_elems(p));
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;
@@ -1545,8 +1561,9 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
   a.tile0[p->n_wpatch] = t;
   a.total_tiles = t;
   a.phi = phi;
-  a.mono = mono;
-  a.sc = p->tc_fp16 ? p->tc_sc : nullptr;
+  // EMU: the monopole column is an ordinary one on the tensor cores
+  a.mono = p->tc_emu ? nullptr : mono;
+  a.sc = (p->tc_fp16 || p->tc_emu) ? p->tc_sc : nullptr;
 }
 
 static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, double* phi, const float2* mono,
@@ -1554,6 +1571,7 @@ static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, d
   TcArgs a;
   synth_args(p, a, phi, mono);
   const int grid = std::min(a.total_tiles, p->tc_sms);
+  if (p->tc_emu) return emu_dispatch_gemm(tc::kSynthesize, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
   return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, false, p->tc_tf32 != 0, grid, wmap, p->tc_map_m,
                                         p->tc_map_m_tail, a, s);
 }
@@ -1573,6 +1591,11 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
   if (ev && (e = cudaEventRecord(ev[1], s)) != cudaSuccess) return e;
   if ((e = project_with(p, p->tc_map_qt, s, false)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], s)) != cudaSuccess) return e;
+  if (p->tc_emu) {
+    if ((e = emu_scan_adj(p, s)) != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[3], s)) != cudaSuccess) return e;
+    return synthesize_with(p, p->tc_map_us, grho, nullptr, s);
+  }
   scan_adj_ff_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
       p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part, p->tc_radff,
       p->tc_Mbar, p->tc_Bbar, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : (p->tc_tf32 ? 2 : 1),
@@ -1593,12 +1616,14 @@ cudaError_t tc_backward(const ygs_plan* p, const double* gphi, double* grho, cud
 ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
   b->groups.clear();
   // one group per operand kind: BF16 two-slice, FP16 two-slice (whose
-  // projection applies the field's group factors), BF16 three-slice, TF32 two-slice
-  for (int kind = 0; kind < 4; ++kind) {
-    const int nsl = kind == 2 ? 3 : 2, fp16 = kind == 1 ? 1 : 0, tf32 = kind == 3 ? 1 : 0;
+  // projection applies the field's group factors), BF16 three-slice, TF32
+  // two-slice, EMU six-slice
+  for (int kind = 0; kind < 5; ++kind) {
+    const int nsl = kind == 4 ? tc::kEmuSlices : (kind == 2 ? 3 : 2), fp16 = kind == 1 ? 1 : 0,
+              tf32 = kind == 3 ? 1 : 0, emu = kind == 4 ? 1 : 0;
     std::vector<ygs_plan*> mem;
     for (ygs_plan* p : plans)
-      if (p->tc_nsl == nsl && p->tc_fp16 == fp16 && p->tc_tf32 == tf32) mem.push_back(p);
+      if (p->tc_nsl == nsl && p->tc_fp16 == fp16 && p->tc_tf32 == tf32 && p->tc_emu == emu) mem.push_back(p);
     if (mem.empty()) continue;
     if ((int)mem.size() > tc::kMaxGroup) {
       set_error("a batch holds at most 128 split-precision plans of one operand kind");
@@ -1608,6 +1633,7 @@ ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
     G.nsl = nsl;
     G.fp16 = fp16;
     G.tf32 = tf32;
+    G.emu = emu;
     G.members = mem;
     std::vector<tc::TcProblem> proj(mem.size()), syn(mem.size());
     std::vector<int> sp(mem.size() + 1, 0), ss(mem.size() + 1, 0);
@@ -1659,6 +1685,9 @@ void tc_batch_free(TcBatch* b) {
 
 cudaError_t tc_batch_project(const TcBatchGroup& G, cudaStream_t s) {
   tc::TcPhiList none{};
+  if (G.emu)
+    return emu_dispatch_group(tc::kProject, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p, (int)G.members.size(),
+                              G.total_p, none, s);
   return dispatch_group<tc::kProject>(G.nsl, G.fp16 != 0, G.tf32 != 0, std::min(G.total_p, G.sms), G.d_proj, G.d_start_p,
                                       (int)G.members.size(), G.total_p, none, s);
 }
@@ -1666,6 +1695,9 @@ cudaError_t tc_batch_project(const TcBatchGroup& G, cudaStream_t s) {
 cudaError_t tc_batch_synthesize(const TcBatchGroup& G, double* const* phi, cudaStream_t s) {
   tc::TcPhiList out{};
   for (size_t k = 0; k < G.members.size(); ++k) out.p[k] = phi[k];
+  if (G.emu)
+    return emu_dispatch_group(tc::kSynthesize, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
+                              (int)G.members.size(), G.total_s, out, s);
   return dispatch_group<tc::kSynthesize>(G.nsl, false, G.tf32 != 0, std::min(G.total_s, G.sms), G.d_synth, G.d_start_s,
                                          (int)G.members.size(), G.total_s, out, s);
 }

@@ -64,16 +64,53 @@ constexpr int kNmaxProject = 144, kNhProject = 48;
 #endif
 constexpr int kNmaxSynth = YGS_SYNTH_N, kNhSynth = YGS_SYNTH_NH;
 
-template <int MODE>
+// FP64-accurate mode (EMU, Ozaki-type splitting): every operand value is cut
+// into kEmuSlices balanced base-256 digits (each in [-128, 128], exact in
+// BF16) on a grid fixed per row (or per row and window of kEmuWindowKb
+// k-blocks), and the kEmuProducts products A_s B_t with s + t <= kEmuSlices
+// are accumulated one at a time over windows of kEmuWindowKb k-blocks.  A
+// window's sum of one product is a sum of 1024 integers of magnitude at most
+// 2^14 on a common grid, so the FP32 accumulator holds it exactly; only the
+// flushes into the float-float sums round.  The synthesis tile is 128 shells
+// wide so that E can be parked in TMEM as a (hi, lo) pair.
+constexpr int kEmuSlices = 6, kEmuProducts = 26, kEmuWindowKb = 16;
+// k-blocks per shared-memory stage in EMU mode: one slice of each operand is
+// 4 MMAs per k-block, and every barrier wait of the issuing thread drains its
+// queued MMAs, so a stage carries two k-blocks (8 MMAs per wait)
+constexpr int kEmuStageKb = 2;
+static_assert(kEmuWindowKb % kEmuStageKb == 0, "a flush window holds whole stages");
+constexpr int kNmaxSynthEmu = 128, kNhSynthEmu = 64;
+static_assert(kEmuProducts == kEmuSlices * (kEmuSlices + 1) / 2 + kEmuSlices - 1,
+              "products with s, t < kEmuSlices and s + t <= kEmuSlices");
+static_assert(kEmuWindowKb * 64 * 128 * 128 <= (1 << 24), "a window's products sum exactly in FP32");
+
+// Product p of the EMU order: by total order d = s + t ascending, s ascending
+// within d (s from max(0, d - kEmuSlices + 1) to min(d, kEmuSlices - 1)).
+__device__ __forceinline__ void emu_pair(int p, int& s, int& t) {
+  int d = 0, first = 0;
+  for (;; ++d) {
+    const int lo = d < kEmuSlices ? 0 : d - kEmuSlices + 1, hi = d < kEmuSlices ? d : kEmuSlices - 1;
+    if (p < first + hi - lo + 1) {
+      s = lo + (p - first);
+      break;
+    }
+    first += hi - lo + 1;
+  }
+  t = d - s;
+}
+
+template <int MODE, bool EMU = false>
 struct TileShape {
-  static constexpr int NMAX = MODE == 0 ? kNmaxProject : kNmaxSynth;  // shells per full tile
-  static constexpr int NH = MODE == 0 ? kNhProject : kNhSynth;        // columns per epilogue warp
+  // shells per full tile; columns per epilogue warp
+  static constexpr int NMAX = MODE == 0 ? kNmaxProject : (EMU ? kNmaxSynthEmu : kNmaxSynth);
+  static constexpr int NH = MODE == 0 ? kNhProject : (EMU ? kNhSynthEmu : kNhSynth);
   static constexpr int EPI_WARPS = 4 * (NMAX / NH);
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static_assert(NMAX % 16 == 0 && NMAX <= 256 && NMAX % NH == 0 && NH % 8 == 0, "tile shape");
   // TMEM (512 columns): NBUF rotating accumulators of NMAX columns, plus, in
-  // the synthesis, NMAX columns that hold the even-block result E of a tile.
-  static constexpr int E_COLS = MODE == 0 ? 0 : NMAX;
+  // the synthesis, NMAX columns that hold the even-block result E of a tile
+  // (2 NMAX in EMU mode: its head and tail).
+  static constexpr int E_COLS = MODE == 0 ? 0 : (EMU ? 2 : 1) * NMAX;
   static constexpr int NBUF = (512 - E_COLS) / NMAX > 4 ? 4 : (512 - E_COLS) / NMAX;
   static_assert(NBUF >= 2, "TMEM holds 512 columns: need two accumulators");
 };
@@ -131,13 +168,16 @@ struct TcArgs {
   const float4* sc;
 };
 
-template <int NSL, int MODE>
+template <int NSL, int MODE, bool EMU = false>
 struct TcCfg {
-  static constexpr int NMAX = TileShape<MODE>::NMAX;
+  static_assert(!EMU || NSL == 1, "EMU stages hold one slice of each operand");
+  static constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
   static constexpr int NPROD = (NSL == 3) ? 6 : (NSL == 2 ? 3 : 1);
-  static constexpr int A_SLICE = BM * BK * 2;
+  static constexpr int KBS = EMU ? kEmuStageKb : 1;  // k-blocks per stage
+  static constexpr int A_SLICE = BM * BK * 2;      // one k-block of one slice (a 128-byte-swizzled block)
   static constexpr int B_SLICE = NMAX * BK * 2;
-  static constexpr int STAGE = NSL * (A_SLICE + B_SLICE);
+  // [A: KBS k-blocks x NSL slices | B: the same]
+  static constexpr int STAGE = KBS * NSL * (A_SLICE + B_SLICE);
 #ifdef YGS_TC_STAGES
   static constexpr int STAGES = YGS_TC_STAGES;
 #else
@@ -150,15 +190,19 @@ struct TcCfg {
   // STAGES earlier have finished, i.e. after the epilogue has released group
   // g - ceil(STAGES / flush) - 1 - NBUF or later, which is more than
   // FAC_RING groups back for STAGES <= 3, NBUF <= 3, any flush >= 1.
+  // (EMU: flush groups of kEmuWindowKb k-blocks, so the lead is
+  // ceil(STAGES / kEmuWindowKb) + 1 + NBUF groups.)
   static constexpr int FAC_OFF = 512;
   static constexpr int FAC_RING = 8;
   static constexpr int FAC_BYTES = MODE == 0 ? FAC_RING * NMAX * 4 : 0;
   static_assert(MODE != 0 || FAC_RING > 3 + 1 + 3, "factor ring deeper than the pipeline's lead");
   static constexpr int SMEM = STAGES * STAGE + 1024 + FAC_OFF + FAC_BYTES;
-  static constexpr int NBUF = TileShape<MODE>::NBUF;
+  static constexpr int NBUF = TileShape<MODE, EMU>::NBUF;
   static constexpr int E_COL0 = NBUF * NMAX;  // first TMEM column of the parked E (synthesis)
   static_assert(STAGES >= 2, "not enough shared memory for two stages");
-  static_assert(MODE != 0 || (STAGES <= 3 && NBUF <= 3), "the factor ring's depth assumes STAGES, NBUF <= 3");
+  static_assert(MODE != 0 || (EMU ? (STAGES * KBS + kEmuWindowKb - 1) / kEmuWindowKb + 1 + NBUF < FAC_RING
+                                  : (STAGES <= 3 && NBUF <= 3)),
+                "the factor ring is deeper than the pipeline's lead");
 };
 
 // (s, t) slice pairs in issue order; pair 0 is the leading product.
@@ -200,9 +244,9 @@ struct Tile {
   int g_patch, m_loc, z;
 };
 
-template <int MODE, int KE>
+template <int MODE, int KE, bool EMU = false>
 __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
-  constexpr int NMAX = TileShape<MODE>::NMAX;
+  constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
   Tile T;
   int n;
   if (MODE == kProject) {
@@ -287,19 +331,24 @@ struct GroupSrc {  // tiles of several problems concatenated: problem k owns [st
   }
 };
 
-// SCALE (projection of FP16 field slices only): undo the field's group
-// factors at every flush.  A compile-time switch: each instance then holds
-// only its own flush code, and the epilogue's float-float sums stay in
-// registers.
-template <int NSL, int MODE, bool SCALE, bool TF, class Src>
+// SCALE (projection of FP16 or EMU field slices only): undo the field's
+// group factors at every flush.  A compile-time switch: each instance then
+// holds only its own flush code, and the epilogue's float-float sums stay in
+// registers.  EMU: one slice of each operand per stage, the kEmuProducts
+// products one after another over the whole k range of a segment (each
+// sweep its own flush groups), flushed by a renormalised float-float add.
+template <int NSL, int MODE, bool SCALE, bool TF, bool EMU, class Src>
 __device__ __forceinline__ void gemm_body(const Src& src) {
   static_assert(!SCALE || MODE == kProject, "only the projection scales its flushes");
   static_assert(!(TF && SCALE), "TF32 operands need no scaling");
+  static_assert(!(TF && EMU), "EMU slices are BF16");
   constexpr int KE = KElems<TF>::KE;
-  using C = TcCfg<NSL, MODE>;
-  constexpr int NMAX = TileShape<MODE>::NMAX;
-  constexpr int NH = TileShape<MODE>::NH;
-  constexpr int kEpiWarps = TileShape<MODE>::EPI_WARPS;
+  using C = TcCfg<NSL, MODE, EMU>;
+  constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
+  constexpr int NH = TileShape<MODE, EMU>::NH;
+  constexpr int kEpiWarps = TileShape<MODE, EMU>::EPI_WARPS;
+  constexpr int NPASS = EMU ? kEmuProducts : 1;        // sweeps over a segment's k-blocks
+  constexpr int GKB = EMU ? kEmuWindowKb : kGroupKb;   // k-blocks per exponent group of the field
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
@@ -344,36 +393,53 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       int* err = nullptr;
       for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
         const TileRef R = src.locate(t);
-        const Tile T = decode_tile<MODE, KE>(*R.A, R.t);
+        const Tile T = decode_tile<MODE, KE, EMU>(*R.A, R.t);
         err = R.A->err;
         const CUtensorMap* mb = T.use_tail ? R.mbt : R.mb;
         const uint32_t bytes = NSL * (C::A_SLICE + T.n_eff * BK * 2);
-        const int nkb = T.seg_kb0 + T.seg_kb1;
         const float* const fac = SCALE ? R.A->fac : nullptr;
         const int flush = R.A->flush_kb;
-        for (int kb = 0; kb < nkb; ++kb) {
-          const int stage = issued % C::STAGES;
-          const uint32_t ph = (issued / C::STAGES) & 1;
-          if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag)) {
-            ok = false;
-            break;
-          }
-          uint8_t* sA = smem + stage * C::STAGE;
-          uint8_t* sB = sA + NSL * C::A_SLICE;
-          const bool fac_now = SCALE && kb % flush == 0;  // first k-block of a flush group
-          mbar_arrive_expect_tx(&full[stage], bytes + (fac_now ? NMAX * 4 : 0));
-          if (fac_now) {
-            const int G = (T.kstart / KE + kb) / kGroupKb;
-            const float* src = fac + (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
-            bulk_load(fac_ring + (fgroups % C::FAC_RING) * NMAX, src, NMAX * 4, &full[stage]);
-            ++fgroups;
-          }
-          const int kx = T.kstart + kb * KE;
+        // segments (even and odd column blocks of the synthesis), then the
+        // products of an EMU tile, then the k-blocks of the segment
+        for (int seg = 0; seg < 2 && ok; ++seg) {
+          const int nkb = seg ? T.seg_kb1 : T.seg_kb0, kb0 = seg ? T.seg_kb0 : 0;
+          for (int pp = 0; pp < NPASS && ok; ++pp) {
+            int ps = 0, pt = 0;
+            if (EMU) emu_pair(pp, ps, pt);
+            for (int kb = 0; kb < nkb; kb += C::KBS) {
+              const int stage = issued % C::STAGES;
+              const uint32_t ph = (issued / C::STAGES) & 1;
+              if (!mbar_wait(&empty[stage], ph ^ 1, abort_flag)) {
+                ok = false;
+                break;
+              }
+              uint8_t* sA = smem + stage * C::STAGE;
+              uint8_t* sB = sA + C::KBS * NSL * C::A_SLICE;
+              const int nks = min(C::KBS, nkb - kb);          // k-blocks in this stage
+              const bool fac_now = SCALE && kb % flush == 0;  // first k-block of a flush group
+              mbar_arrive_expect_tx(&full[stage], nks * bytes + (fac_now ? NMAX * 4 : 0));
+              if (fac_now) {
+                const int G = (T.kstart / KE + kb0 + kb) / GKB;
+                const float* src = fac + (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
+                bulk_load(fac_ring + (fgroups % C::FAC_RING) * NMAX, src, NMAX * 4, &full[stage]);
+                ++fgroups;
+              }
+              const int kx = T.kstart + (kb0 + kb) * KE;
+              if (EMU) {
+                for (int j = 0; j < nks; ++j) {
+                  tma_load_3d(sA + j * C::A_SLICE, R.ma, &full[stage], kx + j * KE, T.a_row0, ps);
+                  tma_load_3d(sB + j * C::B_SLICE, mb, &full[stage], kx + j * KE, T.b_row0, T.b_plane0 + pt);
+                }
+              } else {
 #pragma unroll
-          for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, R.ma, &full[stage], kx, T.a_row0, s);
+                for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, R.ma, &full[stage], kx, T.a_row0, s);
 #pragma unroll
-          for (int s = 0; s < NSL; ++s) tma_load_3d(sB + s * C::B_SLICE, mb, &full[stage], kx, T.b_row0, T.b_plane0 + s);
-          ++issued;
+                for (int s = 0; s < NSL; ++s)
+                  tma_load_3d(sB + s * C::B_SLICE, mb, &full[stage], kx, T.b_row0, T.b_plane0 + s);
+              }
+              ++issued;
+            }
+          }
         }
       }
       if (!ok) {
@@ -392,11 +458,12 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       int* err = nullptr;
       for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
         const TileRef R = src.locate(t);
-        const Tile T = decode_tile<MODE, KE>(*R.A, R.t);
+        const Tile T = decode_tile<MODE, KE, EMU>(*R.A, R.t);
         err = R.A->err;
         const uint32_t idesc = idesc_f16(BM, T.n_eff, R.A->ab_fmt);
         const int flush = R.A->flush_kb;  // k-blocks per accumulator flush, per problem
-        for (int seg = 0; seg < 2 && ok; ++seg) {
+        for (int sp = 0; sp < 2 * NPASS && ok; ++sp) {
+          const int seg = sp / NPASS;
           const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
             const int buf = gglob % C::NBUF, use = gglob / C::NBUF;
@@ -408,7 +475,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             const uint32_t d = tmem + buf * NMAX;
             bool init = false;
             const int kg1 = min(nkb, kg + flush);
-            for (int kb = kg; kb < kg1; ++kb) {
+            for (int kb = kg; kb < kg1; kb += C::KBS) {
               const int stage = consumed % C::STAGES;
               const uint32_t ph = (consumed / C::STAGES) & 1;
               if (!mbar_wait(&full[stage], ph, abort_flag)) {
@@ -420,8 +487,24 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
               // offsets added to the start-address field (addresses stay below 256 KB)
               const uint32_t sA = smem_u32(smem + stage * C::STAGE);
               const uint64_t a0 = BK == 64 ? sdesc_kmajor_sw128(sA) : sdesc_kmajor_sw64(sA);
-              const uint64_t b0 = BK == 64 ? sdesc_kmajor_sw128(sA + NSL * C::A_SLICE)
-                                           : sdesc_kmajor_sw64(sA + NSL * C::A_SLICE);
+              const uint64_t b0 = BK == 64 ? sdesc_kmajor_sw128(sA + C::KBS * NSL * C::A_SLICE)
+                                           : sdesc_kmajor_sw64(sA + C::KBS * NSL * C::A_SLICE);
+              if (EMU) {
+                // one product, the stage's k-blocks one after another
+                const int nks = min(C::KBS, kg1 - kb);
+                for (int j = 0; j < nks; ++j) {
+#pragma unroll
+                  for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint64_t ad = a0 + (uint64_t)((j * C::A_SLICE + kk * 32) >> 4);
+                    const uint64_t bd = b0 + (uint64_t)((j * C::B_SLICE + kk * 32) >> 4);
+                    umma_f16(d, ad, bd, idesc, init ? 1u : 0u);
+                    init = true;
+                  }
+                }
+                umma_commit(&empty[stage]);
+                ++consumed;
+                continue;
+              }
               // correction products first, while the accumulator is still small (their
               // rounding then stays ~2^-8 below the leading product's), the leading
               // product A_0 B_0 last: one FP32 rounding per MMA at its own scale
@@ -466,7 +549,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
     int* err = nullptr;
     for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
       const TileRef R = src.locate(t);
-      const Tile T = decode_tile<MODE, KE>(*R.A, R.t);
+      const Tile T = decode_tile<MODE, KE, EMU>(*R.A, R.t);
       err = R.A->err;
       const int flush = R.A->flush_kb;
       const bool active = col0 < T.n_eff;  // this warp's columns exist in the tile (warp-uniform)
@@ -477,7 +560,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       const int nseg = T.seg_kb1 > 0 ? 2 : 1;
       // FP16 projection: the field's group factors of the tile's shells, in
       // the ring slot the TMA warp filled with the group's first k-block
-      for (int seg = 0; seg < nseg && ok; ++seg) {
+      for (int sp = 0; sp < nseg * NPASS && ok; ++sp) {
+        const int seg = sp / NPASS;
         const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
         for (int kg = 0; kg < nkb; kg += flush, ++gglob) {
           const int buf = gglob % C::NBUF, use = gglob / C::NBUF;
@@ -506,13 +590,21 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
                 // holds the sum within one rounding of that flush
                 uint64_t s, e;
                 const uint64_t v = pk2(__uint_as_float(vm[2 * j]), __uint_as_float(vm[2 * j + 1]));
-                if (SCALE) {
-                  fast_two_sum_scaled2(H[c0 / 2 + j], v, lds_pair(fslot + c0 + 2 * j), s, e);
+                if (EMU) {
+                  // the window sum is exact (times an exact power of two): TwoSum
+                  // into the head, the tail folded in, renormalised
+                  const uint64_t w = SCALE ? mul2(v, lds_pair(fslot + c0 + 2 * j)) : v;
+                  two_sum2(H[c0 / 2 + j], w, s, e);
+                  fast_two_sum2(s, add2(e, L[c0 / 2 + j]), H[c0 / 2 + j], L[c0 / 2 + j]);
                 } else {
-                  fast_two_sum2(H[c0 / 2 + j], v, s, e);
+                  if (SCALE) {
+                    fast_two_sum_scaled2(H[c0 / 2 + j], v, lds_pair(fslot + c0 + 2 * j), s, e);
+                  } else {
+                    fast_two_sum2(H[c0 / 2 + j], v, s, e);
+                  }
+                  H[c0 / 2 + j] = s;
+                  L[c0 / 2 + j] = add2(L[c0 / 2 + j], e);
                 }
-                H[c0 / 2 + j] = s;
-                L[c0 / 2 + j] = add2(L[c0 / 2 + j], e);
               }
             }
           }
@@ -521,7 +613,28 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         if (!ok) break;
-        if (MODE == kSynthesize && seg == 0 && nseg == 2 && active) {
+        if (EMU && MODE == kSynthesize && sp == NPASS - 1 && nseg == 2 && active) {
+          // even block done (all products): park E = (hi, lo) in TMEM, restart the sums
+#pragma unroll
+          for (int c0 = 0; c0 < NH; c0 += 8) {
+            uint32_t vh[8], vl[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float h0, h1, l0, l1;
+              upk2(H[c0 / 2 + j], h0, h1);
+              upk2(L[c0 / 2 + j], l0, l1);
+              vh[2 * j] = __float_as_uint(h0);
+              vh[2 * j + 1] = __float_as_uint(h1);
+              vl[2 * j] = __float_as_uint(l0);
+              vl[2 * j + 1] = __float_as_uint(l1);
+              H[c0 / 2 + j] = L[c0 / 2 + j] = 0ull;
+            }
+            tmem_st8(tmem + t_lane + C::E_COL0 + col0 + c0, vh);
+            tmem_st8(tmem + t_lane + C::E_COL0 + NMAX + col0 + c0, vl);
+          }
+          tmem_st_wait();
+        }
+        if (!EMU && MODE == kSynthesize && seg == 0 && nseg == 2 && active) {
           // even block done: park E = hi + lo (+ the monopole, which belongs to
           // E: its float-float pair is added before the one rounding to FP32)
           // in TMEM, restart the sums for the odd block
@@ -570,6 +683,51 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       const long long nang = MODE == kSynthesize ? R.A->pt.nang[T.g_patch] : 0;
       const long long off0 = MODE == kSynthesize ? R.A->pt.fld_off[symmetric ? 0 : T.g_patch] : 0;
       const long long off1 = MODE == kSynthesize && symmetric ? R.A->pt.fld_off[1] : 0;
+      if (EMU && MODE == kSynthesize) {
+        // output in float-float: Phi_Yin = E + O, Phi_Yang = E - O (or Phi_g),
+        // each widened to FP64 as head + tail with the shell's power of two
+        const long long a_loc = (long long)T.m_loc * BM + r;
+#pragma unroll
+        for (int c0 = 0; c0 < NH; c0 += 8) {
+          uint32_t eh[8], el[8];
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) eh[jj] = el[jj] = 0u;
+          if (nseg == 2) {
+            tmem_ld8(tmem + t_lane + C::E_COL0 + col0 + c0, eh);
+            tmem_ld8(tmem + t_lane + C::E_COL0 + NMAX + col0 + c0, el);
+            tmem_ld_wait();
+          }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = c0 + jj;
+            float h0, h1, l0, l1;
+            upk2(H[j / 2], h0, h1);
+            upk2(L[j / 2], l0, l1);
+            const float oh = (j & 1) ? h1 : h0, ol = (j & 1) ? l1 : l0;
+            const int n = T.b_row0 + col0 + j;
+            if (n >= n_b || a_loc >= nang) continue;
+            const unsigned int c20 = sc ? (unsigned int)__float_as_int(sc[n].x) : (896u << 20);
+            if (nseg == 2 || symmetric) {
+              // E from TMEM (zero without two column blocks: then the sums are E and O = 0)
+              const float e_h = nseg == 2 ? __uint_as_float(eh[jj]) : oh;
+              const float e_l = nseg == 2 ? __uint_as_float(el[jj]) : ol;
+              const float o_h = nseg == 2 ? oh : 0.0f, o_l = nseg == 2 ? ol : 0.0f;
+              float s, e;
+              two_sum(e_h, o_h, s, e);
+              float2 v = ff_renorm(s, e + (e_l + o_l));
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v.x, c20) + f32_to_f64_pow2(v.y, c20);
+              if (symmetric) {
+                two_sum(e_h, -o_h, s, e);
+                v = ff_renorm(s, e + (e_l - o_l));
+                phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v.x, c20) + f32_to_f64_pow2(v.y, c20);
+              }
+            } else {
+              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(oh, c20) + f32_to_f64_pow2(ol, c20);
+            }
+          }
+        }
+        continue;
+      }
       // output, 8 columns at a time (keeps the register footprint of the sums)
 #pragma unroll
       for (int c0 = 0; c0 < NH; c0 += 8) {
@@ -641,8 +799,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
 // spread over the SM's four sub-partitions (16,384 registers each), four
 // warps on two of them, so 4 x 32 x 128 is the ceiling for one CTA per SM.
 // One problem: maps and arguments in kernel parameters.
-template <int NSL, int MODE, bool SCALE, bool TF = false>
-__global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
+template <int NSL, int MODE, bool SCALE, bool TF = false, bool EMU = false>
+__global__ void __launch_bounds__(TileShape<MODE, EMU>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ TcArgs args) {
   if (threadIdx.x == 0) {
@@ -651,18 +809,18 @@ __global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
     prefetch_tmap(&mapBt);
   }
   const SingleSrc src{&args, &mapA, &mapB, &mapBt};
-  gemm_body<NSL, MODE, SCALE, TF>(src);
+  gemm_body<NSL, MODE, SCALE, TF, EMU>(src);
 }
 
 // Several problems of one operand type in one persistent launch (a batch of
 // fields): every CTA walks the concatenated tile list; TMEM accumulators and
 // shared-memory stages carry over from one problem to the next.
-template <int NSL, int MODE, bool SCALE, bool TF = false>
-__global__ void __launch_bounds__(TileShape<MODE>::THREADS, 1)
+template <int NSL, int MODE, bool SCALE, bool TF = false, bool EMU = false>
+__global__ void __launch_bounds__(TileShape<MODE, EMU>::THREADS, 1)
     tc_gemm_group_kernel(const TcProblem* __restrict__ probs, const int* __restrict__ start, int n, int total,
                          const __grid_constant__ TcPhiList phis) {
   const GroupSrc src{probs, start, n, total, &phis};
-  gemm_body<NSL, MODE, SCALE, TF>(src);
+  gemm_body<NSL, MODE, SCALE, TF, EMU>(src);
 }
 
 }  // namespace tc

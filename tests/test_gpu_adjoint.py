@@ -12,7 +12,8 @@ from tests._util import rel_norm, small_yinyang
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("bf16x6", 1e-6), ("fp16x3", 1e-6), ("tf32x3", 1e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp64emu", 1e-10), ("bf16x6", 1e-6), ("fp16x3", 1e-6),
+                                           ("tf32x3", 1e-6)])
 def test_central_differences_on_64_cells(cuda, precision, tol):
     """J(rho) = sum w Phi(rho) is linear: (J(rho + h e_k) - J(rho - h e_k)) / 2h
     equals (A^T w)_k.  Phi is differenced elementwise before the dot product,
@@ -59,7 +60,8 @@ def config4_transpose():
     return grid, rho, w, oracle.apply_T(grid, w, U=U, Q=Q)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6), ("tf32x3", 2e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp64emu", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6),
+                                           ("tf32x3", 2e-6)])
 def test_adjoint_full_size_vs_oracle_transpose(cuda, config4_transpose, precision, tol):
     """Yin-Yang 1 degree, Nr = 256, l_max = 32, w ~ N(0, 1): the plan's adjoint
     (FP64 kernels, or the tensor cores for split precisions) against the

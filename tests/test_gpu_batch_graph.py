@@ -79,8 +79,9 @@ def _uneven_fields(cuda):
              three_patch_grid(),
              W.polar_grid(7, 13, W.linear_edges(6, 0.1, 1.0), 5),
              small_yinyang(W, n_theta=10, n_phi=28, n_r=300, l_max=12),
-             small_yinyang(W, n_theta=6, n_phi=18, n_r=9, l_max=0)]
-    precs = ["fp16x3", "bf16x6", "tf32x3", "fp64", "bf16x3", "fp16x3"]
+             small_yinyang(W, n_theta=6, n_phi=18, n_r=9, l_max=0),
+             small_yinyang(W, n_theta=9, n_phi=25, n_r=40, l_max=8)]
+    precs = ["fp16x3", "bf16x6", "tf32x3", "fp64", "bf16x3", "fp16x3", "fp64emu"]
     plans = [Plan(g, p) for g, p in zip(grids, precs)]
     rhos = [torch.from_numpy(W.random_density(g, 40 + i)).cuda() for i, g in enumerate(grids)]
     return plans, rhos
@@ -93,10 +94,11 @@ def test_grouped_batch_equals_per_field(cuda):
     plans, rhos = _uneven_fields(cuda)
     ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
     with Batch(plans) as b:
-        # 6 fields: field slices + one scan (+ M slicing for FP16) per split field,
-        # 2 grouped launches for each of the four operand kinds (FP16 two-slice,
-        # BF16 two-slice, BF16 three-slice, TF32 two-slice), 3 for the FP64 field
-        assert b.launches == 2 * 3 + 2 + 2 + 2 + 2 * 4 + 3
+        # 7 fields: field slices + one scan (+ M slicing for FP16 and EMU) per
+        # split field, 2 grouped launches for each of the five operand kinds
+        # (FP16 two-slice, BF16 two-slice, BF16 three-slice, TF32 two-slice,
+        # EMU six-slice), 3 for the FP64 field
+        assert b.launches == 2 * 3 + 2 + 2 + 2 + 3 + 2 * 5 + 3
         for _ in range(2):
             outs = b.solve(rhos)
             torch.cuda.synchronize()

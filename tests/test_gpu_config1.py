@@ -29,7 +29,7 @@ def sample_phi(grid, M, Q, idx):
     return out
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp64tc", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6), ("tf32x3", 1e-6), ("fp32", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp64tc", 1e-12), ("fp64emu", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6), ("tf32x3", 1e-6), ("fp32", 1e-4)])
 def test_config1_sampled(cfg1, cuda, precision, tol):
     import torch
     grid, rho, B_ref, M_ref, Q = cfg1

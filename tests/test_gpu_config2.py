@@ -23,7 +23,7 @@ def cfg2_small():
     return grid, rho, phi, B, M
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp64tc", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6), ("fp32", 1e-4)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp64tc", 1e-12), ("fp64emu", 1e-12), ("bf16x6", 1e-6), ("fp16x3", 1e-6), ("fp32", 1e-4)])
 def test_config2_lmax64(cfg2_small, cuda, precision, tol):
     import torch
     grid, rho, phi_ref, B_ref, M_ref = cfg2_small

@@ -1,4 +1,6 @@
-"""GPU parity of the FP64 path against the CPU oracle (O2), through the C ABI."""
+"""GPU parity of the FP64 paths against the CPU oracle (O2), through the C ABI:
+the FP64 CUDA-core kernels, the FP64 tensor cores (DMMA) and the FP64-accurate
+split on the BF16 tensor cores (YGS_FP64_EMU), all at 1e-12."""
 import math
 
 import numpy as np
@@ -40,10 +42,11 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=[(c, p) for c in sorted(CASES) for p in ("fp64", "fp64tc")],
+@pytest.fixture(scope="module", params=[(c, p) for c in sorted(CASES) for p in ("fp64", "fp64tc", "fp64emu")],
                 ids=lambda cp: f"{cp[0]}-{cp[1]}")
 def case(request, cuda):
-    """Every case on the FP64 CUDA-core kernels and on the FP64 tensor cores (DMMA)."""
+    """Every case on the FP64 CUDA-core kernels, the FP64 tensor cores (DMMA)
+    and the FP64-accurate BF16 split."""
     import torch
     name, precision = request.param
     make, sym = CASES[name]
@@ -76,7 +79,7 @@ def test_moments_match_oracle(case):
 
 def test_weights_match_oracle_quadrature(case):
     name, grid, rho, plan, _, _, _ = case
-    if name.endswith("fp64tc"):
+    if name.endswith("fp64tc") or name.endswith("fp64emu"):
         pytest.skip("the same weights as the fp64 plan")
     U_ref = oracle.build_U(grid)
     Q_ref = oracle.build_Q(grid)
@@ -105,22 +108,24 @@ def test_adjoint_matches_oracle_transpose(case):
     assert abs(lhs - rhs) <= 1e-12 * (np.abs(w) @ np.abs(phi)), name
 
 
-def test_config0_fp64(cuda):
+@pytest.mark.parametrize("precision", ["fp64", "fp64emu"])
+def test_config0_fp64(cuda, precision):
     import torch
     grid, rho = W.config0()
     ref = oracle.solve(grid, rho)
-    with Plan(grid, "fp64") as plan:
+    with Plan(grid, precision) as plan:
         assert plan.info["symmetric"] == 1
         phi = ygs_solve(plan, torch.from_numpy(rho).cuda())
         torch.cuda.synchronize()
         assert rel_max(phi.cpu().numpy(), ref) <= FP64_TOL
 
 
-def test_deterministic(cuda):
+@pytest.mark.parametrize("precision", ["fp64", "fp64emu"])
+def test_deterministic(cuda, precision):
     import torch
     grid = small_yinyang(W, n_theta=13, n_phi=37, deg=4.0, n_r=67, l_max=9)
     rho = torch.from_numpy(W.random_density(grid, 2)).cuda()
-    with Plan(grid, "fp64") as plan:
+    with Plan(grid, precision) as plan:
         a = ygs_solve(plan, rho).clone()
         b = ygs_solve(plan, rho)
         torch.cuda.synchronize()
