@@ -84,19 +84,17 @@ static_assert(kEmuProducts == kEmuSlices * (kEmuSlices + 1) / 2 + kEmuSlices - 1
               "products with s, t < kEmuSlices and s + t <= kEmuSlices");
 static_assert(kEmuWindowKb * 64 * 128 * 128 <= (1 << 24), "a window's products sum exactly in FP32");
 
-// Product p of the EMU order: by total order d = s + t ascending, s ascending
-// within d (s from max(0, d - kEmuSlices + 1) to min(d, kEmuSlices - 1)).
+// Product p of the EMU order: s-major (t from 0 to min(kEmuSlices - 1,
+// kEmuSlices - s)), so that consecutive products share the A slice, which the
+// L2 then serves again.
 __device__ __forceinline__ void emu_pair(int p, int& s, int& t) {
-  int d = 0, first = 0;
-  for (;; ++d) {
-    const int lo = d < kEmuSlices ? 0 : d - kEmuSlices + 1, hi = d < kEmuSlices ? d : kEmuSlices - 1;
-    if (p < first + hi - lo + 1) {
-      s = lo + (p - first);
-      break;
-    }
-    first += hi - lo + 1;
+  int first = 0;
+  for (s = 0;; ++s) {
+    const int n = min(kEmuSlices - 1, kEmuSlices - s) + 1;
+    if (p < first + n) break;
+    first += n;
   }
-  t = d - s;
+  t = p - first;
 }
 
 template <int MODE, bool EMU = false>
@@ -105,7 +103,9 @@ struct TileShape {
   static constexpr int NMAX = MODE == 0 ? kNmaxProject : (EMU ? kNmaxSynthEmu : kNmaxSynth);
   static constexpr int NH = MODE == 0 ? kNhProject : (EMU ? kNhSynthEmu : kNhSynth);
   static constexpr int EPI_WARPS = 4 * (NMAX / NH);
-  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  // warps: TMA producer, MMA issuer, epilogue
+  static constexpr int FIRST_EPI = 2;
+  static constexpr int THREADS = 32 * FIRST_EPI + 32 * EPI_WARPS;
   static_assert(NMAX % 16 == 0 && NMAX <= 256 && NMAX % NH == 0 && NH % 8 == 0, "tile shape");
   // TMEM (512 columns): NBUF rotating accumulators of NMAX columns, plus, in
   // the synthesis, NMAX columns that hold the even-block result E of a tile
@@ -126,7 +126,7 @@ struct TcArgs {
   int n_tail;           // width of the tail shell tile (multiple of 16) or 0
   int n_tiles;          // n_full + (n_tail > 0)
   int total_tiles;      // length of the tile list
-  // ---- projection: tile = (n-tile, chunk z, m-tile), m fastest
+  // ---- projection: tile = (chunk z, m-tile, n-tile), n fastest
   int tiles_m;          // column tiles (even block, then odd block)
   int tiles_m_even;     // m-tiles of the even column block
   int a_row_odd;        // first A row of the odd column block (= rows of the even block)
@@ -250,9 +250,11 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
   Tile T;
   int n;
   if (MODE == kProject) {
-    const int per_n = a.tiles_m * a.n_chunks;
-    n = t / per_n;
-    const int rem = t % per_n;
+    // shell tiles fastest, then column tiles, then chunks: the tiles that read
+    // one A block run side by side, and a chunk's field block serves every
+    // column tile while it is in L2
+    n = t % a.n_tiles;
+    const int rem = t / a.n_tiles;
     T.z = rem / a.tiles_m;
     const int mt = rem % a.tiles_m;
     const bool odd = mt >= a.tiles_m_even;
@@ -349,6 +351,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   constexpr int kEpiWarps = TileShape<MODE, EMU>::EPI_WARPS;
   constexpr int NPASS = EMU ? kEmuProducts : 1;        // sweeps over a segment's k-blocks
   constexpr int GKB = EMU ? kEmuWindowKb : kGroupKb;   // k-blocks per exponent group of the field
+  constexpr int kFirstEpi = TileShape<MODE, EMU>::FIRST_EPI;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + C::STAGES * C::STAGE);
@@ -537,8 +540,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       mbar_wait_final(mma_done, 0);  // every issued MMA has finished before TMEM is released
     }
   } else {
-    // ================= epilogue warps 2 .. 2 + kEpiWarps - 1 =================
-    const int ew = warp - 2;
+    // ================= epilogue warps kFirstEpi .. kFirstEpi + kEpiWarps - 1 =================
+    const int ew = warp - kFirstEpi;
     const int q = warp % 4;                // TMEM lane quadrant this warp may access
     const int colq = ew / 4;               // which group of NH columns
     const int r = q * 32 + lane;           // output row within the tile
