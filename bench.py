@@ -316,7 +316,8 @@ def config2_leg(precision, steps, warmup, local, fp64_cuda_core=True):
     res, outs, moments = {}, {}, {}
     clocks = ClockSampler(local)
     clk = None
-    legs = [(precision, steps), ("fp64tc", 1)] + ([("fp64", 1)] if fp64_cuda_core else [])
+    legs = [(precision, steps), ("fp64tc", 1)] + ([("fp64", 1)] if fp64_cuda_core else []) + (
+        [("fp64emu", 2)] if precision != "fp64emu" else [])
     for prec, n in legs:
         with Plan(grid, prec, device=local) as plan:
             out = torch.empty_like(rho)
@@ -351,6 +352,13 @@ def config2_leg(precision, steps, warmup, local, fp64_cuda_core=True):
            "B_rel_err_per_l_band": {l: eB[l] for l in range(0, grid.l_max + 1, 8)},
            "M_rel_err_per_l_band": {l: eM[l] for l in range(0, grid.l_max + 1, 8)},
            "B_rel_err_max_over_l": max(eB), "M_rel_err_max_over_l": max(eM), "clocks": clk}
+    if "fp64emu" in res and precision != "fp64emu":
+        # the FP64-accurate split against the FP64 tensor cores on the same field
+        ge = outs["fp64emu"]
+        out["fp64emu"] = {"solves_per_s": 1e3 / res["fp64emu"], "speedup_vs_fp64_tensor": res["fp64tc"] / res["fp64emu"],
+                          "max_rel_err_phi_vs_fp64_tensor": float(((ge - ref).abs() / ref.abs()).max().item()),
+                          "B_rel_err_max_over_l": max(bands(moments["fp64emu"][0], moments["fp64tc"][0])),
+                          "M_rel_err_max_over_l": max(bands(moments["fp64emu"][1], moments["fp64tc"][1]))}
     if "fp64" in res:
         out["fp64_cuda_core_solves_per_s"] = 1e3 / res["fp64"]
         out["fp64_tensor_equals_cuda_core_bitwise"] = bool(torch.equal(outs["fp64"], outs["fp64tc"]))
@@ -534,7 +542,8 @@ def main():
     info = plan.info
     sym = info["symmetric"] == 1
     nang_eff = grid.nang(0) if sym else grid.nang_total
-    nprod = {"fp64": 1, "fp64tc": 1, "fp32": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3}[precision]
+    nprod = {"fp64": 1, "fp64tc": 1, "fp32": 1, "bf16x3": 3, "bf16x6": 6, "fp16x3": 3, "tf32x3": 3,
+             "fp64emu": 26}[precision]
     # algorithmic FLOPs of one contraction: one FMA per (shell, stored cell, column) and slice product
     flops_gemm = 2.0 * nprod * grid.n_r * nang_eff * grid.K
     per = [x / max(ncalls, 1) for x in phase_ms]
@@ -555,12 +564,14 @@ def main():
     else:
         if dom in (1, 3):
             achieved = flops_gemm / (per[dom] / 1e3) / 1e12
-            peak = float(peaks["bf16_tflops"])
+            # TF32 runs at half the BF16 dense rate (nominal 1.1 vs 2.25 PFLOP/s)
+            peak = float(peaks["bf16_tflops"]) * (1.1 / 2.25 if precision == "tf32x3" else 1.0)
             roof = {"kernel": names[dom], "bound": "tensor", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak,
                     "traffic": load_traffic(precision, grid.n_r, names[dom]),
                     "peak_source": f"bf16_tflops ({peak_src}, burst)" + (
-                        "; FP16 dense rate = BF16's (nominal ratio 1)" if precision == "fp16x3" else ""),
+                        "; FP16 dense rate = BF16's (nominal ratio 1)" if precision == "fp16x3" else "") + (
+                        "; x 1.1/2.25, the nominal TF32:BF16 ratio" if precision == "tf32x3" else ""),
                     "phase_ms": dict(zip(names, per))}
         else:
             # bytes of the field pass: rho in (FP64) + slices out
@@ -591,6 +602,29 @@ def main():
             rel = float(((phi_d - phi64).abs() / phi64.abs()).max().item())
         extra = {"fp64_gpu_solves_per_s": 1e3 / ms64, "speedup_vs_fp64_gpu": ms64 / ms_step,
                  "max_rel_err_vs_fp64_gpu": rel}
+        # the FP64-accurate split (YGS_FP64_EMU) on the same field: its rate,
+        # its speed-up over the FP64 CUDA-core path and its error against it
+        if precision != "fp64emu":
+            try:
+                with Plan(grid, "fp64emu", device=local) as pe:
+                    phie = torch.empty_like(rho_d)
+                    for _ in range(2):
+                        ygs_solve(pe, rho_d, phie, stream=stream)
+                    stream.synchronize()
+                    n_emu = max(3, min(args.steps, 10))
+                    f0.record(stream)
+                    for _ in range(n_emu):
+                        ygs_solve(pe, rho_d, phie, stream=stream)
+                    f1.record(stream)
+                    stream.synchronize()
+                    ms_e = f0.elapsed_time(f1) / n_emu
+                    rel_e = float(((phie - phi64).abs() / phi64.abs()).max().item())
+                extra["fp64emu"] = {"solves_per_s": 1e3 / ms_e, "ms_per_solve": ms_e,
+                                    "gcell_per_s": grid.n_cells / (ms_e / 1e3) / 1e9,
+                                    "speedup_vs_fp64_gpu": ms64 / ms_e, "max_rel_err_vs_fp64_gpu": rel_e,
+                                    "steps": n_emu}
+            except Exception as e:  # context; never lose the headline line over it
+                extra["fp64emu"] = {"error": repr(e)}
 
     # the largest single-GPU configuration beside it (config 2: 0.5 degree,
     # Nr 800, l_max 64), a short leg of the same precision
@@ -603,7 +637,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp64tc": "f64", "fp32": "f32"}.get(precision, precision), "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp64tc": "f64", "fp32": "f32", "fp64emu": "bf16x26 (fp64-accurate)"}.get(precision, precision), "data": "synthetic",
             "gcell_per_s": value * grid.n_cells / 1e9,
             "config": {"workload": workload_name(grid.n_r), "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
                        "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"], "autotune": args.autotune,

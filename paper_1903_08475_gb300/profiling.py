@@ -25,9 +25,13 @@ TRAFFIC_JSON = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 # phase names bench.py uses, by the kernel-name prefix ncu prints
 PHASE_OF_KERNEL = (("tc_gemm_kernel<2, 0", "projection"), ("tc_gemm_kernel<3, 0", "projection"),
+                   ("tc_gemm_kernel<1, 0", "projection"),
                    ("tc_gemm_kernel<2, 1", "synthesis"), ("tc_gemm_kernel<3, 1", "synthesis"),
+                   ("tc_gemm_kernel<1, 1", "synthesis"),
                    ("field16_kernel", "field_slices"), ("field_slices_kernel", "field_slices"),
-                   ("scan_ff_kernel", "radial_scan"), ("slice_m16_kernel", "radial_scan_slices"))
+                   ("field_slices_tf32_kernel", "field_slices"), ("emu_field_kernel", "field_slices"),
+                   ("scan_ff_kernel", "radial_scan"), ("emu_scan_kernel", "radial_scan"),
+                   ("slice_m16_kernel", "radial_scan_slices"), ("emu_slice_m_kernel", "radial_scan_slices"))
 
 
 def sources_sha() -> str:
