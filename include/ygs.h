@@ -248,6 +248,32 @@ ygs_status ygs_backward(ygs_plan* plan, const double* d_grad_phi, double* d_grad
  * 1.6e-7.  A caller that consumes B or M beyond 1e-6 uses FP64_EMU (or FP64). */
 ygs_status ygs_get_moments(ygs_plan* plan, double* d_B, double* d_M, void* stream);
 
+/* ---- angular sharding (Sect. 4.3, steps 2-3) ------------------------------
+ * The paper's distributed solve: every process projects its share of the
+ * angular cells (Eq. B_CS), the partial moments are summed over all
+ * processes (one reduction of n_r*K values), and every process finishes the
+ * solve (radial scans, Eq. M_C, and synthesis, Eq. gravpotmult) from the
+ * whole B.  The share is a range of the plan's FP64 split-K chunks
+ * (ygs_info.fp64_split_k of them; chunk z covers a fixed block of one
+ * patch's angular cells), so the ranges [0, c1), [c1, c2), ... [c_{n-1},
+ * fp64_split_k) of n processes cover every cell once.  Both calls run on the
+ * plan's FP64 weights and workspaces (whatever the plan's precision), enqueue
+ * work only and do not synchronise; the reduction between them is the
+ * caller's (an MPI or NCCL all-reduce, or gloo on host copies).  On an FP64
+ * plan ygs_get_moments then returns the B and M of the finish. */
+
+/* d_B (n_r*K FP64, device, row-major [i][c] in ygs_get_moments' column order)
+ * = the moments of the cells of chunks [chunk_begin, chunk_end) of d_rho
+ * (the layout of ygs_solve).  An empty range writes zeros.
+ * Errors: INVALID_ARG for NULL or unaligned pointers (16 bytes) or a range
+ * outside [0, fp64_split_k]. */
+ygs_status ygs_project_partial(ygs_plan* plan, const double* d_rho, int chunk_begin, int chunk_end, double* d_B,
+                               void* stream);
+/* d_phi (the layout of ygs_solve) from the moments d_B of the whole field
+ * (layout of ygs_project_partial): the radial scans and the synthesis.
+ * Errors: INVALID_ARG for NULL, unaligned or overlapping pointers. */
+ygs_status ygs_finish_from_moments(ygs_plan* plan, const double* d_B, double* d_phi, void* stream);
+
 /* Copies the FP64 weights of patch `patch` to HOST memory as [n_theta*n_phi][K]
  * row-major: which = 0 -> U, which = 1 -> Q.  Synchronous. */
 ygs_status ygs_get_weights(ygs_plan* plan, int which, int patch, double* h_out);

@@ -31,7 +31,8 @@ EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_
            "ygs_backward", "ygs_get_moments", "ygs_get_weights", "ygs_get_status", "ygs_status_string",
            "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
            "ygs_debug_wait_timeout", "ygs_solve_static", "ygs_batch_create", "ygs_batch_solve",
-           "ygs_batch_destroy", "ygs_batch_launches", "ygs_static_scratch_capacity")
+           "ygs_batch_destroy", "ygs_batch_launches", "ygs_static_scratch_capacity", "ygs_project_partial",
+           "ygs_finish_from_moments")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -102,6 +103,8 @@ def load_library(path: Optional[str] = None):
         L.ygs_batch_destroy.argtypes = [vp]
         L.ygs_batch_launches.argtypes = [vp]
         L.ygs_static_scratch_capacity.argtypes = []
+        L.ygs_project_partial.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.ygs_finish_from_moments.argtypes = [vp, vp, vp, vp]
         for f in EXPORTS:
             if f not in ("ygs_status_string", "ygs_last_error", "ygs_static_scratch_capacity"):
                 getattr(L, f).restype = ctypes.c_int
@@ -299,6 +302,28 @@ def ygs_get_moments(plan: Plan, stream=None):
     M = torch.empty_like(B)
     _check(load_library().ygs_get_moments(plan.handle, _ptr(B), _ptr(M), _stream_handle(stream)))
     return B, M
+
+
+def ygs_project_partial(plan: Plan, rho, chunk_begin: int, chunk_end: int, B=None, stream=None):
+    """Moments (n_r x K, FP64, natural column order) of the cells of the plan's
+    FP64 split-K chunks [chunk_begin, chunk_end) of rho: one process's share of
+    an angularly sharded solve (Sect. 4.3, steps 2-3)."""
+    import torch
+    if B is None:
+        B = torch.empty((plan.info["n_r"], plan.info["K"]), dtype=torch.float64, device=rho.device)
+    _check(load_library().ygs_project_partial(plan.handle, _ptr(rho), int(chunk_begin), int(chunk_end), _ptr(B),
+                                              _stream_handle(stream)))
+    return B
+
+
+def ygs_finish_from_moments(plan: Plan, B, out=None, stream=None):
+    """Phi from the moments B of the whole field (the sum of every process's
+    ygs_project_partial): radial scans and synthesis."""
+    import torch
+    if out is None:
+        out = torch.empty(plan.info["n_cells"], dtype=torch.float64, device=B.device)
+    _check(load_library().ygs_finish_from_moments(plan.handle, _ptr(B), _ptr(out), _stream_handle(stream)))
+    return out
 
 
 def ygs_get_weights(plan: Plan, which: str, patch: int) -> np.ndarray:

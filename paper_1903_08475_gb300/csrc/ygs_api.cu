@@ -668,6 +668,44 @@ ygs_status ygs_backward(ygs_plan* p, const double* d_gphi, double* d_grho, void*
   return YGS_OK;
 }
 
+ygs_status ygs_project_partial(ygs_plan* p, const double* d_rho, int chunk_begin, int chunk_end, double* d_B,
+                               void* stream) {
+  if (!p || !d_rho || !d_B) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  if (!aligned16(d_rho) || !aligned16(d_B)) return fail(YGS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+  if (chunk_begin < 0 || chunk_begin > chunk_end || chunk_end > p->S)
+    return fail(YGS_ERR_INVALID_ARG, "chunk range must satisfy 0 <= begin <= end <= fp64_split_k (" +
+                                         std::to_string(p->S) + ")");
+  DeviceGuard guard(p->device);
+  if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  if (chunk_begin == chunk_end) {
+    API_TRY(cudaMemsetAsync(d_B, 0, (size_t)p->n_r * p->K * sizeof(double), s));
+    return YGS_OK;
+  }
+  API_TRY(launch_project_fp64_chunks(p, d_rho, p->U, p->part, chunk_begin, chunk_end, s));
+  API_TRY(launch_sum_partials(p, p->part, chunk_end - chunk_begin, p->B, s));
+  API_TRY(launch_unpermute(p, p->B, d_B, s));
+  return YGS_OK;
+}
+
+ygs_status ygs_finish_from_moments(ygs_plan* p, const double* d_B, double* d_phi, void* stream) {
+  if (!p || !d_B || !d_phi) return fail(YGS_ERR_INVALID_ARG, "NULL argument");
+  if (!aligned16(d_B) || !aligned16(d_phi)) return fail(YGS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+  const char* cb = (const char*)d_B;
+  const char* cp = (const char*)d_phi;
+  const size_t bb = (size_t)p->n_r * p->K * sizeof(double), pb = (size_t)p->n_cells * sizeof(double);
+  if (cb < cp + pb && cp < cb + bb) return fail(YGS_ERR_INVALID_ARG, "B and Phi overlap");
+  DeviceGuard guard(p->device);
+  if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  API_TRY(launch_permute(p, d_B, p->part, s));
+  API_TRY(launch_scan_fwd(p, p->part, 1, p->B, p->M, s));
+  API_TRY(launch_synth_fp64(p, p->M, p->Q, d_phi, s));
+  return YGS_OK;
+}
+
 ygs_status ygs_get_moments(ygs_plan* p, double* d_B, double* d_M, void* stream) {
   if (!p) return fail(YGS_ERR_INVALID_ARG, "plan is NULL");
   DeviceGuard guard(p->device);

@@ -286,6 +286,26 @@ __global__ void scan_adj_kernel(int n_r, int K, int L, const int* __restrict__ c
   }
 }
 
+// B[i][c] = sum_{z < S} part[z][i][c], in order of z
+__global__ void sum_partials_kernel(long long plane, int S, const double* __restrict__ part, double* __restrict__ B) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < plane; e += (long long)gridDim.x * blockDim.x) {
+    double b = 0.0;
+    for (int z = 0; z < S; ++z) b += part[z * plane + e];
+    B[e] = b;
+  }
+}
+
+// out[i][c] = in[i][col_nat[c]]: natural column order -> internal
+__global__ void permute_kernel(int n_r, int K, const int* __restrict__ col_nat, const double* __restrict__ in,
+                               double* __restrict__ out) {
+  long long total = (long long)n_r * K;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    long long i = e / K;
+    int c = (int)(e % K);
+    out[e] = in[i * K + col_nat[c]];
+  }
+}
+
 __global__ void unpermute_kernel(int n_r, int K, const int* __restrict__ col_nat, const double* __restrict__ in,
                                  double* __restrict__ out) {
   long long total = (long long)n_r * K;
@@ -300,8 +320,11 @@ __global__ void unpermute_kernel(int n_r, int K, const int* __restrict__ col_nat
 
 namespace {
 
+// Chunks [z0, z0 + nz) of the plan's list (all of them by default) into part[0 .. nz).
 template <typename T>
-cudaError_t project_t(const ygs_plan* p, const T* field, const T* W, T* part, bool tc, cudaStream_t s) {
+cudaError_t project_t(const ygs_plan* p, const T* field, const T* W, T* part, bool tc, cudaStream_t s, int z0 = 0,
+                      int nz = -1) {
+  if (nz < 0) nz = p->S - z0;
   ProjArgs<T> a;
   a.n_r = p->n_r;
   a.K = p->K;
@@ -311,10 +334,10 @@ cudaError_t project_t(const ygs_plan* p, const T* field, const T* W, T* part, bo
   a.field = field;
   a.W = W;
   a.part = part;
-  a.chunks = p->chunks;
+  a.chunks = p->chunks + z0;
   a.pt = p->pt;
   int tiles_o = (p->K - p->K_even + BN - 1) / BN;
-  dim3 grid(a.tiles_e + tiles_o, (p->n_r + BM - 1) / BM, p->S);
+  dim3 grid(a.tiles_e + tiles_o, (p->n_r + BM - 1) / BM, nz);
   if constexpr (std::is_same<T, double>::value) {
     if (tc) {
       proj_fp64_kernel<T, true><<<grid, NT, 0, s>>>(a);
@@ -417,6 +440,21 @@ cudaError_t solve_fp32(const ygs_plan* p, const double* rho, double* phi, cudaSt
 
 cudaError_t launch_scan_adj(const ygs_plan* p, const double* part, int S, double* Bbar, cudaStream_t s) {
   scan_adj_kernel<<<(p->K + 63) / 64, 64, 0, s>>>(p->n_r, p->K, p->l_max, p->col_l, part, S, p->rad, p->Mbar, Bbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_fp64_chunks(const ygs_plan* p, const double* field, const double* W, double* part, int z0,
+                                      int z1, cudaStream_t s) {
+  return project_t<double>(p, field, W, part, p->precision == YGS_FP64_TC, s, z0, z1 - z0);
+}
+
+cudaError_t launch_sum_partials(const ygs_plan* p, const double* part, int S, double* B, cudaStream_t s) {
+  sum_partials_kernel<<<256, 256, 0, s>>>((long long)p->n_r * p->K, S, part, B);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute(const ygs_plan* p, const double* in, double* out, cudaStream_t s) {
+  permute_kernel<<<256, 256, 0, s>>>(p->n_r, p->K, p->col_nat, in, out);
   return cudaGetLastError();
 }
 

@@ -163,6 +163,13 @@ cudaError_t prepare_static_scratch();
 long long static_scratch_bytes(const ygs_plan* p);
 // out[i][col_nat[c]] = in[i][c]
 cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// out[i][c] = in[i][col_nat[c]] (natural column order -> internal)
+cudaError_t launch_permute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// The FP64 projection of the chunks [z0, z1) of the plan's list into part[0 .. z1 - z0).
+cudaError_t launch_project_fp64_chunks(const ygs_plan* p, const double* field, const double* W, double* part, int z0,
+                                      int z1, cudaStream_t s);
+// B = sum_{z < S} part[z] (fixed order).
+cudaError_t launch_sum_partials(const ygs_plan* p, const double* part, int S, double* B, cudaStream_t s);
 // FP64 -> FP32 (rounded, or truncated by integer operations)
 cudaError_t launch_to_f32(const double* in, float* out, long long n, bool trunc, cudaStream_t s);
 // The FP32 CUDA-core solve (YGS_FP32): FP32 contractions, FP64 scans; ev optional phase events 1..3
