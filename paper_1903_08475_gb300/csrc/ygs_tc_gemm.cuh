@@ -73,7 +73,7 @@ constexpr int kNmaxSynth = YGS_SYNTH_N, kNhSynth = YGS_SYNTH_NH;
 // 2^14 on a common grid, so the FP32 accumulator holds it exactly; only the
 // flushes into the float-float sums round.  The synthesis tile is 128 shells
 // wide so that E can be parked in TMEM as a (hi, lo) pair.
-constexpr int kEmuSlices = 6, kEmuProducts = 26, kEmuWindowKb = 16;
+constexpr int kEmuSlices = 6, kEmuProducts = 26, kEmuWindowKb = 1024 / BK;
 // k-blocks per shared-memory stage in EMU mode: one slice of each operand is
 // 4 MMAs per k-block, and every barrier wait of the issuing thread drains its
 // queued MMAs, so a stage carries two k-blocks (8 MMAs per wait)
@@ -82,7 +82,7 @@ static_assert(kEmuWindowKb % kEmuStageKb == 0, "a flush window holds whole stage
 constexpr int kNmaxSynthEmu = 128, kNhSynthEmu = 64;
 static_assert(kEmuProducts == kEmuSlices * (kEmuSlices + 1) / 2 + kEmuSlices - 1,
               "products with s, t < kEmuSlices and s + t <= kEmuSlices");
-static_assert(kEmuWindowKb * 64 * 128 * 128 <= (1 << 24), "a window's products sum exactly in FP32");
+static_assert(kEmuWindowKb * BK * 128 * 128 <= (1 << 24), "a window's products sum exactly in FP32");
 
 // Product p of the EMU order: s-major (t from 0 to min(kEmuSlices - 1,
 // kEmuSlices - s)), so that consecutive products share the A slice, which the
