@@ -727,15 +727,13 @@ __device__ __forceinline__ void affine_scan_up(float2& F, float2& s, int lane) {
   }
 }
 
-// Phase 2 of both scans: warp w < 2 kScanCols composes column w / 2's chunk
-// summaries upward (dir 0: sm[1] the factor, sm[0] the offset) or downward
-// (dir 1: sm[3], sm[2]) and writes each chunk's incoming carry to cr[dir].
+// Phase 2 of both scans: one warp composes column cc's chunk summaries
+// upward (dir 0: sm[1] the factor, sm[0] the offset) or downward (dir 1:
+// sm[3], sm[2]) and writes each chunk's incoming carry to cr[dir]; the CTA's
+// warps take the 2 kCols (column, direction) tasks in turn.
 template <int kCols, int kMaxP>
-__device__ __forceinline__ void carry_scan(const float2 (&sm)[4][kMaxP][kCols], float2 (&cr)[2][kMaxP][kCols],
-                                           int P) {
-  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (w >= 2 * kCols) return;
-  const int cc = w >> 1, dir = w & 1;
+__device__ __forceinline__ void carry_scan_one(const float2 (&sm)[4][kMaxP][kCols], float2 (&cr)[2][kMaxP][kCols],
+                                               int P, int cc, int dir, int lane) {
   const int q = (P + 31) / 32, t0 = lane * q, t1 = min(P, t0 + q);
   const int kF = dir ? 3 : 1, ks = dir ? 2 : 0;
   float2 F = make_float2(1.0f, 0.0f), sv = make_float2(0.0f, 0.0f);
@@ -752,6 +750,14 @@ __device__ __forceinline__ void carry_scan(const float2 (&sm)[4][kMaxP][kCols], 
     cr[dir][pp][cc] = cin;
     cin = tc::ff_fma(sm[kF][pp][cc], cin, sm[ks][pp][cc]);
   }
+}
+
+template <int kCols, int kMaxP>
+__device__ __forceinline__ void carry_scan(const float2 (&sm)[4][kMaxP][kCols], float2 (&cr)[2][kMaxP][kCols],
+                                           int P) {
+  const int lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int w = threadIdx.x / 32; w < 2 * kCols; w += nw)  // a (column, direction) task per warp
+    carry_scan_one<kCols, kMaxP>(sm, cr, P, w >> 1, w & 1, lane);
 }
 
 // The chunk partials of shell i, column pc summed over the chunks z in z
@@ -798,10 +804,13 @@ __device__ __forceinline__ void ff_slices(float2 v, int nsl, __nv_bfloat16 (&sl)
 #ifndef YGS_SCAN_COLS
 #define YGS_SCAN_COLS 2  // columns per scan CTA (256 threads: several CTAs share an SM and overlap their phases)
 #endif
-constexpr int kScanCols = YGS_SCAN_COLS, kScanMaxP = 128, kScanThreads = kScanCols * kScanMaxP;
+#ifndef YGS_SCAN_MAXP
+#define YGS_SCAN_MAXP 128  // chunks of shells per column (a thread each)
+#endif
+constexpr int kScanCols = YGS_SCAN_COLS, kScanMaxP = YGS_SCAN_MAXP, kScanThreads = kScanCols * kScanMaxP;
 constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
-static_assert(kScanCols >= 1 && kScanThreads <= 1024 && 2 * kScanCols <= kScanThreads / 32,
-              "scan: a CTA of at most 1024 threads with a warp per column and direction for the carries");
+static_assert(kScanCols >= 1 && kScanThreads <= 1024 && kScanThreads % 32 == 0 && kScanMaxP >= 32,
+              "scan: a CTA of whole warps, at most 1024 threads, at least 32 chunks per column");
 
 __global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
@@ -1215,8 +1224,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   for (const auto& c : cand) s_max = std::max(s_max, c.size());
   std::vector<int2> chunks = cand[0];
   p->tc_S = (int)chunks.size();
-  // chunks of 4 shells for the parallel scans (more for n_r > 512: at most 128 chunks, one CTA column)
-  p->tc_scan_chunk = std::max(4, (p->n_r + 127) / 128);
+  // chunks of 4 shells for the parallel scans (more when n_r > 4 kScanMaxP: at most kScanMaxP chunks)
+  p->tc_scan_chunk = std::max(4, (p->n_r + kScanMaxP - 1) / kScanMaxP);
   p->tc_scan_P = (p->n_r + p->tc_scan_chunk - 1) / p->tc_scan_chunk;
 
   const size_t kp = (size_t)p->tc_k_pad;
@@ -1460,18 +1469,24 @@ cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s
   return cudaGetLastError();
 }
 
-// The forward synthesis flushes its accumulators every 128 k-elements: its
-// terms change sign (the monopole, the one coherent sum, is added exactly in
-// the epilogue), so the FP32 accumulation drifts less than in the projection
-// (and the adjoint's synthesis with U), whose monopole column sums positive
-// terms and keeps 64.  (Measured on config 1: 2.1e-7 -> 3.4e-7 against FP64 at
-// 128, 5.4e-7 at 256.)
+// The forward synthesis flushes its accumulators every 192 k-elements (three
+// windows per 576-column segment at l_max = 32): its terms change sign (the
+// monopole, the one coherent sum, is added exactly in the epilogue), so the
+// FP32 accumulation drifts less than in the adjoint's synthesis with U, whose
+// monopole column sums positive terms and keeps 64.  (Measured on config 1
+// against FP64: 2.1e-7 at 64, 3.4e-7 at 128, 5.4e-7 at 256; 192 is 10% faster
+// than 128.)  The FP16 forward projection, whose monopole is summed exactly
+// in the field pass, flushes every 128: a flush window there must not span
+// two of the field's exponent groups (kGroup cells), whose factors differ.
 #ifndef YGS_PROJ_FLUSH_K_EXACT_MONO
 #define YGS_PROJ_FLUSH_K_EXACT_MONO 128
 #endif
 #ifndef YGS_SYNTH_FLUSH_K
-#define YGS_SYNTH_FLUSH_K 128
+#define YGS_SYNTH_FLUSH_K 192
 #endif
+static_assert(kGroup % YGS_PROJ_FLUSH_K_EXACT_MONO == 0 && YGS_PROJ_FLUSH_K_EXACT_MONO % tc::BK == 0,
+              "an FP16 projection flush covers whole k-blocks within one field exponent group");
+static_assert(YGS_SYNTH_FLUSH_K % tc::BK == 0, "a synthesis flush covers whole k-blocks");
 
 // k elements of one stage of the contractions: 64 two-byte or 32 TF32 values
 static int kblock_elems(const ygs_plan* p) { return p->tc_tf32 ? tc::BK / 2 : tc::BK; }
