@@ -28,7 +28,8 @@ _ip = ctypes.POINTER(ctypes.c_int)
 class _Grid(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("edges", _dp), ("n_patch", ctypes.c_int), ("euler", _dp),
                 ("n_theta", _ip), ("n_phi", _ip), ("theta_range", _dp), ("phi_range", _dp),
-                ("w", _dp), ("l_max", ctypes.c_int), ("G", ctypes.c_double), ("eval", ctypes.c_int)]
+                ("w", _dp), ("l_max", ctypes.c_int), ("G", ctypes.c_double), ("eval", ctypes.c_int),
+                ("kind", _ip)]
 
 
 def build(force: bool = False) -> str:
@@ -79,8 +80,11 @@ def _grid(g):
     k.tr = np.ascontiguousarray(g.theta_range, dtype=np.float64).reshape(-1)
     k.pr = np.ascontiguousarray(g.phi_range, dtype=np.float64).reshape(-1)
     k.w = np.ascontiguousarray(g.w, dtype=np.float64)
+    kind = getattr(g, "kind", None)
+    k.kind = None if kind is None else np.ascontiguousarray(kind, dtype=np.int32)
     s = _Grid(g.n_r, _p(k.edges), g.n_patch, _p(k.euler), k.nt.ctypes.data_as(_ip), k.nf.ctypes.data_as(_ip),
-              _p(k.tr), _p(k.pr), _p(k.w), g.l_max, g.G, g.eval)
+              _p(k.tr), _p(k.pr), _p(k.w), g.l_max, g.G, g.eval,
+              None if k.kind is None else k.kind.ctypes.data_as(_ip))
     k.s = s
     return k
 

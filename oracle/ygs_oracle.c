@@ -65,6 +65,7 @@ typedef struct {
   int l_max;
   double G;
   int eval;                  /* 0 = upper vertex, 1 = angular centre */
+  const int* kind;           /* n_patch: 0 = (theta, phi) patch, 1 = gnomonic cube face; NULL: all 0 */
 } ora_grid;
 
 static const double ORA_PI = 3.14159265358979323846264338327950288;
@@ -131,6 +132,23 @@ static void local_dir(double th, double ph, double* v) {
   v[2] = cos(th);
 }
 
+/* A patch's local coordinates (u, v) -> local unit vector and the solid-angle
+ * density dOmega / (du dv).  (theta, phi) patches: u = theta, v = phi,
+ * density sin(theta).  Gnomonic cube faces (the non-orthogonal patches of
+ * Sect. 6): u, v equiangular, X = tan u, Y = tan v, the direction
+ * (X, Y, 1) / sqrt(1 + X^2 + Y^2) and density (1 + X^2)(1 + Y^2) / (1 + X^2 + Y^2)^(3/2). */
+static double patch_dir(const ora_grid* g, int p, double u, double v, double* d) {
+  if (g->kind && g->kind[p] == 1) {
+    double X = tan(u), Y = tan(v), r2 = 1.0 + X * X + Y * Y, r = sqrt(r2);
+    d[0] = X / r;
+    d[1] = Y / r;
+    d[2] = 1.0 / r;
+    return (1.0 + X * X) * (1.0 + Y * Y) / (r2 * r);
+  }
+  local_dir(u, v, d);
+  return sin(u);
+}
+
 static void matvec(const double* R, const double* v, double* out) {
   for (int r = 0; r < 3; ++r) out[r] = R[3 * r] * v[0] + R[3 * r + 1] * v[1] + R[3 * r + 2] * v[2];
 }
@@ -158,9 +176,10 @@ static void harmonics_dir(int l_max, const double* nrm, const double* v, double*
   double x = v[2];
   if (x > 1.0) x = 1.0;
   if (x < -1.0) x = -1.0;
-  double th = acos(x);
   double ph = atan2(v[1], v[0]);
-  double s = sin(th);
+  /* sin(theta) is the distance from the polar axis: computing it as
+   * sin(acos(x)) would lose digits next to the poles */
+  double s = sqrt(v[0] * v[0] + v[1] * v[1]);
   /* P_mm = (2m-1)!! s^m, P_{m+1,m} = (2m+1) x P_mm,
    * (l-m) P_lm = (2l-1) x P_{l-1,m} - (l+m-1) P_{l-2,m} */
   for (int m = 0; m <= l_max; ++m) {
@@ -280,12 +299,11 @@ static int build_U(const ora_grid* g, int nq, int rotate, double* U) {
         for (int c = 0; c < K; ++c) acc[c] = 0.0;
         for (int qa = 0; qa < nq; ++qa) {
           double th = 0.5 * (t0 + t1) + 0.5 * (t1 - t0) * xq[qa];
-          double wt = 0.5 * (t1 - t0) * wq[qa] * sin(th);
+          double wt = 0.5 * (t1 - t0) * wq[qa];
           for (int qb = 0; qb < nq; ++qb) {
             double ph = 0.5 * (p0 + p1) + 0.5 * (p1 - p0) * xq[qb];
-            double wgt = wt * 0.5 * (p1 - p0) * wq[qb];
             double v[3], x[3];
-            local_dir(th, ph, v);
+            double wgt = wt * 0.5 * (p1 - p0) * wq[qb] * patch_dir(g, p, th, ph, v);
             if (rotate) matvec(R, v, x);
             else { x[0] = v[0]; x[1] = v[1]; x[2] = v[2]; }
             harmonics_dir(g->l_max, nrm, x, Y);
@@ -327,7 +345,7 @@ int ora_build_Q(const ora_grid* g, double* Q) {
       int j = (int)(a / nf), k = (int)(a % nf);
       double th, ph, v[3], x[3];
       eval_point_local(g, p, j, k, &th, &ph);
-      local_dir(th, ph, v);
+      patch_dir(g, p, th, ph, v);
       matvec(R, v, x);
       double* q = Q + (base + a) * K;
       harmonics_dir(g->l_max, nrm, x, q);
@@ -497,13 +515,13 @@ int ora_solve_direct(const ora_grid* g, int nq, const double* rho, double* phi) 
         for (int qb = 0; qb < nq; ++qb) {
           double tq = 0.5 * (t0 + t1) + 0.5 * (t1 - t0) * xq[qa];
           double pq = 0.5 * (p0 + p1) + 0.5 * (p1 - p0) * xq[qb];
-          local_dir(tq, pq, v);
+          double dens = patch_dir(g, p, tq, pq, v);
           long idx = (base + a) * nqp + qa * nq + qb;
           matvec(R, v, qdir + 3 * idx);
-          qwt[idx] = 0.25 * (t1 - t0) * (p1 - p0) * wq[qa] * wq[qb] * sin(tq);
+          qwt[idx] = 0.25 * (t1 - t0) * (p1 - p0) * wq[qa] * wq[qb] * dens;
         }
       eval_point_local(g, p, j, k, &th, &ph);
-      local_dir(th, ph, v);
+      patch_dir(g, p, th, ph, v);
       matvec(R, v, edir + 3 * (base + a));
     }
   }
@@ -577,6 +595,7 @@ int ora_solve_perpatch(const ora_grid* g, int nq, const double* rho, double* phi
     one.theta_range = g->theta_range + 2 * p;
     one.phi_range = g->phi_range + 2 * p;
     one.w = g->w + base;
+    one.kind = g->kind ? g->kind + p : NULL;
     ora_project(&one, rho + base * nr, Ul + base * K, E + (size_t)p * nr * K);
     ora_radial(&one, E + (size_t)p * nr * K, Mg + (size_t)p * nr * K);
   }
@@ -593,7 +612,7 @@ int ora_solve_perpatch(const ora_grid* g, int nq, const double* rho, double* phi
         int j = (int)(a / nf), k = (int)(a % nf);
         double th, ph, v[3], x[3];
         eval_point_local(g, pe, j, k, &th, &ph);
-        local_dir(th, ph, v);
+        patch_dir(g, pe, th, ph, v);
         matvec(Re, v, x); /* global direction */
         for (int p = 0; p < g->n_patch; ++p) {
           double Rp[9], xl[3];

@@ -49,6 +49,7 @@ class Grid:
     l_max: int
     G: float = 1.0
     eval: int = 0                # 0 = upper vertex, 1 = angular centre
+    kind: Optional[np.ndarray] = None  # (n_patch,) PATCH_LATLON / PATCH_GNOMONIC; None: all lat-lon
 
     @property
     def n_r(self) -> int:
@@ -167,17 +168,21 @@ def overlap_weights(euler, n_theta, n_phi, theta_range, phi_range, nsub: int = 1
 
 
 def make_grid(edges, euler, n_theta, n_phi, theta_range, phi_range, l_max, G=1.0, eval=0, w=None,
-              nsub_w: int = 16) -> Grid:
+              nsub_w: int = 16, kind=None) -> Grid:
     euler = np.asarray(euler, dtype=np.float64).reshape(-1, 3)
     n_theta = np.asarray(n_theta, dtype=np.int32).reshape(-1)
     n_phi = np.asarray(n_phi, dtype=np.int32).reshape(-1)
     theta_range = np.asarray(theta_range, dtype=np.float64).reshape(-1, 2)
     phi_range = np.asarray(phi_range, dtype=np.float64).reshape(-1, 2)
+    if kind is not None:
+        kind = np.asarray(kind, dtype=np.int32).reshape(-1)
+        if w is None and np.any(kind != PATCH_LATLON):
+            raise ValueError("overlap weights of gnomonic patches must be given")
     if w is None:
         w = overlap_weights(euler, n_theta, n_phi, theta_range, phi_range, nsub=nsub_w)
     return Grid(edges=np.asarray(edges, dtype=np.float64), euler=euler, n_theta=n_theta, n_phi=n_phi,
                 theta_range=theta_range, phi_range=phi_range, w=np.asarray(w, dtype=np.float64),
-                l_max=int(l_max), G=float(G), eval=int(eval))
+                l_max=int(l_max), G=float(G), eval=int(eval), kind=kind)
 
 
 def yinyang_extents(delta: float):
@@ -208,6 +213,46 @@ def polar_grid(n_theta: int, n_phi: int, edges, l_max: int, G: float = 1.0, eval
     """The single spherical polar patch (N_g = 1, zero Euler angles, w = 1)."""
     return make_grid(edges, [(0.0, 0.0, 0.0)], [n_theta], [n_phi], [(0.0, math.pi)], [(0.0, 2 * math.pi)],
                      l_max, G, eval, w=np.ones(n_theta * n_phi))
+
+
+PATCH_LATLON, PATCH_GNOMONIC = 0, 1
+
+
+def euler_from_matrix(R) -> tuple:
+    """Euler angles (alpha, beta, gamma) with rotation_matrix(alpha, beta, gamma) = R."""
+    R = np.asarray(R, dtype=np.float64)
+    import warnings
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")  # gimbal lock at beta = 0 or pi: any split of alpha + gamma will do
+        ang = Rotation.from_matrix(R.T).as_euler("ZYZ")
+    if not np.allclose(rotation_matrix(*ang), R, atol=1e-12):
+        raise ValueError("not a rotation matrix")
+    return tuple(float(x) for x in ang)
+
+
+# The six faces of the cube as rotations x = R v of a face's local frame
+# (local z = the face normal; local x, y along cube edges, right-handed).
+CUBE_FACES = (
+    np.eye(3),                                                     # +z
+    np.array([[1, 0, 0], [0, -1, 0], [0, 0, -1]], dtype=float),    # -z
+    np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], dtype=float),      # +x: x -> +y, y -> +z, z -> +x
+    np.array([[0, 0, -1], [-1, 0, 0], [0, 1, 0]], dtype=float),    # -x
+    np.array([[0, 1, 0], [0, 0, 1], [1, 0, 0]], dtype=float),      # +y: x -> +z, y -> +x, z -> +y
+    np.array([[0, 1, 0], [0, 0, -1], [-1, 0, 0]], dtype=float),    # -y
+)
+
+
+def cubed_sphere_grid(n: int, edges, l_max: int, G: float = 1.0, eval: int = 0, frame=None) -> Grid:
+    """The cubed sphere (the non-orthogonal patches of Sect. 6): six gnomonic
+    faces, each n x n cells in the equiangular coordinates (xi, eta) in
+    [-pi/4, pi/4]^2; the faces tile the sphere, so every overlap weight is 1.
+    ``frame`` (3 Euler angles) optionally rotates the whole cube."""
+    eul = [euler_from_matrix(R) for R in CUBE_FACES]
+    if frame is not None:
+        eul = [compose_euler(frame, e) for e in eul]
+    q = math.pi / 4
+    return make_grid(edges, eul, [n] * 6, [n] * 6, [(-q, q)] * 6, [(-q, q)] * 6, l_max, G, eval,
+                     w=np.ones(6 * n * n), kind=[PATCH_GNOMONIC] * 6)
 
 
 def compose_euler(outer, inner):

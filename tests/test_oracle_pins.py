@@ -101,10 +101,14 @@ def three_patch():
 @pytest.mark.parametrize("make", [lambda: small_yinyang(W, n_theta=4, n_phi=10, n_r=5, l_max=5),
                                   lambda: W.polar_grid(5, 7, W.linear_edges(4, 0.2, 1.0), 4),
                                   three_patch,
-                                  lambda: small_yinyang(W, n_theta=4, n_phi=10, n_r=4, l_max=4, eval=1)])
+                                  lambda: small_yinyang(W, n_theta=4, n_phi=10, n_r=4, l_max=4, eval=1),
+                                  lambda: W.cubed_sphere_grid(4, W.linear_edges(4, 0.2, 1.0), 5),
+                                  lambda: W.cubed_sphere_grid(3, W.log_edges(4, 0.05), 4, eval=1,
+                                                              frame=(0.3, 1.1, -0.7))])
 def test_three_oracle_routes_agree(make):
     """O1 (addition theorem with Legendre polynomials only) == O2 (global real
-    harmonics) == O3 (per-patch superposition): three independent routes."""
+    harmonics) == O3 (per-patch superposition): three independent routes, on
+    (theta, phi) patches and on the gnomonic cube faces of Sect. 6."""
     g = make()
     rho = W.random_density(g, 4)
     p2 = oracle.solve(g, rho)
@@ -114,19 +118,53 @@ def test_three_oracle_routes_agree(make):
     assert rel_max(p3, p2) < 1e-13
 
 
-def test_uniform_sphere_exact_on_polar_grid():
-    edges = np.array([0, 0.1, 0.2, 0.35, 0.5, 0.7, 0.9, 1.0])
-    g = W.polar_grid(10, 20, edges, 6, G=1.3)
-    R = 0.5
-    na = g.nang(0)
+UNIFORM_EDGES = np.array([0, 0.1, 0.2, 0.35, 0.5, 0.7, 0.9, 1.0])
+
+
+def uniform_sphere(g, R=0.5, rho0=2.0):
+    """Density rho0 in every cell of the shells inside radius R (a field layout
+    [g][i][a]), and the exact potential at the upper shell edges r_i^+ (only
+    the monopole survives: every l > 0 harmonic integrates to zero over the
+    sphere)."""
     rho = np.zeros(g.n_cells)
-    for i in range(g.n_r):
-        if edges[i + 1] <= R:
-            rho[i * na:(i + 1) * na] = 2.0
-    phi = oracle.solve(g, rho).reshape(g.n_r, na)
-    r = edges[1:]
-    exact = np.where(r >= R, -g.G * 2.0 * (4 * np.pi / 3) * R ** 3 / r, -2 * np.pi * g.G * 2.0 * (R ** 2 - r ** 2 / 3))
-    assert np.abs(phi / exact[:, None] - 1).max() < 1e-13
+    for p in range(g.n_patch):
+        off, na = g.patch_offset(p), g.nang(p)
+        for i in range(g.n_r):
+            if g.edges[i + 1] <= R:
+                rho[off + i * na: off + (i + 1) * na] = rho0
+    r = g.edges[1:]
+    exact = np.where(r >= R, -g.G * rho0 * (4 * np.pi / 3) * R ** 3 / r, -2 * np.pi * g.G * rho0 * (R ** 2 - r ** 2 / 3))
+    return rho, exact
+
+
+@pytest.mark.parametrize("make", [lambda: W.polar_grid(10, 20, UNIFORM_EDGES, 6, G=1.3),
+                                  lambda: W.cubed_sphere_grid(6, UNIFORM_EDGES, 6, G=1.3, frame=(0.4, 0.9, 2.0))])
+def test_uniform_sphere_exact(make):
+    g = make()
+    rho, exact = uniform_sphere(g)
+    phi = oracle.solve(g, rho)
+    for p in range(g.n_patch):
+        off, na = g.patch_offset(p), g.nang(p)
+        ph = phi[off: off + g.n_r * na].reshape(g.n_r, na)
+        assert np.abs(ph / exact[:, None] - 1).max() < 1e-13
+
+
+def test_cubed_sphere_tiles_the_sphere():
+    """The six gnomonic faces (equiangular coordinates in [-pi/4, pi/4]^2,
+    Sect. 6's non-orthogonal patches) cover the sphere once: the solid angles
+    of all cells add to 4 pi, 4 pi / 6 per face, and every harmonic with l > 0
+    integrates to zero over the union; the face centres are the six axes."""
+    for frame in (None, (0.4, 0.9, 2.0)):
+        g = W.cubed_sphere_grid(5, W.linear_edges(2, 0.5, 1.0), 6, frame=frame)
+        U = oracle.build_U(g)  # U[a][0] = w * solid angle (Y_00 = 1)
+        assert abs(U[:, 0].sum() - 4 * np.pi) < 1e-13
+        na = g.nang(0)
+        for p in range(6):
+            assert abs(U[p * na:(p + 1) * na, 0].sum() - 4 * np.pi / 6) < 1e-13
+        assert np.abs(U[:, 1:].sum(axis=0)).max() < 1e-13
+    axes = sorted(tuple(np.round(W.rotation_matrix(*e) @ [0, 0, 1]).astype(int))
+                  for e in W.cubed_sphere_grid(1, [0.5, 1.0], 0).euler)
+    assert axes == sorted([(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)])
 
 
 def test_polar_grid_weights_are_separable_products():
@@ -165,7 +203,8 @@ def test_rotation_invariance():
 
 
 def test_quadrature_order_converged():
-    for g in [small_yinyang(W), W.polar_grid(7, 13, W.linear_edges(3, 0.1, 1.0), 8), W.config0()[0]]:
+    for g in [small_yinyang(W), W.polar_grid(7, 13, W.linear_edges(3, 0.1, 1.0), 8), W.config0()[0],
+              W.cubed_sphere_grid(6, W.linear_edges(2, 0.5, 1.0), 10), W.cubed_sphere_grid(16, [0.5, 1.0], 24)]:
         n = oracle.default_nq(g)
         U1 = oracle.build_U(g, nq=n)
         U2 = oracle.build_U(g, nq=n + 4)
