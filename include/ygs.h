@@ -119,6 +119,21 @@ enum {
 };
 
 /* Grid descriptor.  All arrays are HOST memory, read during ygs_create only. */
+/* Patch geometry (ygs_desc.patch_kind). */
+typedef enum {
+  YGS_PATCH_LATLON = 0,  /* local spherical coordinates (Sect. 2.1): theta_range and phi_range are the local
+                            colatitude and azimuth extents; U by the Wigner-D route (Sect. 3) */
+  YGS_PATCH_GNOMONIC = 1 /* a non-orthogonal patch (Sect. 6): a cube face in equiangular gnomonic
+                            coordinates.  theta_range and phi_range hold the extents of xi and eta
+                            (radians, inside (-pi/2, pi/2)); the local direction of (xi, eta) is
+                            (tan xi, tan eta, 1) / sqrt(1 + tan^2 xi + tan^2 eta), turned by R^(g); cell
+                            (j, k) spans the j-th xi and k-th eta interval, k fastest; U is integrated
+                            numerically (10-point Gauss-Legendre panels in xi and eta with the solid-angle
+                            density (1 + X^2)(1 + Y^2) / (1 + X^2 + Y^2)^(3/2), X = tan xi, Y = tan eta);
+                            the evaluation point is the upper vertex (xi_{j+1}, eta_{k+1}) or the centre.
+                            The six faces of a cube, xi, eta in [-pi/4, pi/4], tile the sphere (w = 1). */
+} ygs_patch_kind;
+
 typedef struct {
   int n_r;                    /* number of radial shells, >= 1 */
   const double* r_edges;      /* n_r + 1 edges, strictly increasing, r_edges[0] >= 0 */
@@ -134,6 +149,7 @@ typedef struct {
   int eval;                   /* ygs_eval */
   int precision;              /* ygs_precision */
   int flags;                  /* YGS_FLAG_* */
+  const int* patch_kind;      /* n_patch ygs_patch_kind values, or NULL: every patch YGS_PATCH_LATLON */
 } ygs_desc;
 
 typedef struct ygs_plan ygs_plan;

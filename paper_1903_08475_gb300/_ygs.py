@@ -48,7 +48,7 @@ class _Desc(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("r_edges", _dp), ("n_patch", ctypes.c_int), ("euler", _dp),
                 ("n_theta", _ip), ("n_phi", _ip), ("theta_range", _dp), ("phi_range", _dp),
                 ("overlap_w", _dp), ("l_max", ctypes.c_int), ("G", ctypes.c_double), ("eval", ctypes.c_int),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_int), ("patch_kind", _ip)]
 
 
 class Info(ctypes.Structure):
@@ -150,10 +150,14 @@ class Plan:
             "pr": np.ascontiguousarray(grid.phi_range, dtype=np.float64).reshape(-1),
             "w": np.ascontiguousarray(grid.w, dtype=np.float64),
         }
+        kind = getattr(grid, "kind", None)
+        if kind is not None:
+            keep["kind"] = np.ascontiguousarray(kind, dtype=np.int32)
         d = _Desc(grid.n_r, keep["edges"].ctypes.data_as(_dp), grid.n_patch, keep["euler"].ctypes.data_as(_dp),
                   keep["nt"].ctypes.data_as(_ip), keep["nf"].ctypes.data_as(_ip), keep["tr"].ctypes.data_as(_dp),
                   keep["pr"].ctypes.data_as(_dp), keep["w"].ctypes.data_as(_dp), grid.l_max, grid.G, grid.eval,
-                  PRECISION[precision], (0 if symmetry else FLAG_NO_SYMMETRY) | (FLAG_AUTOTUNE if autotune else 0))
+                  PRECISION[precision], (0 if symmetry else FLAG_NO_SYMMETRY) | (FLAG_AUTOTUNE if autotune else 0),
+                  keep["kind"].ctypes.data_as(_ip) if "kind" in keep else None)
         h = ctypes.c_void_p()
         _check(L.ygs_create(ctypes.byref(d), device, ctypes.byref(h)))
         self._h = h

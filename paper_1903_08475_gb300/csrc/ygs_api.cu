@@ -100,6 +100,7 @@ void euler_R(const double* e, double* R) {
 // real harmonic takes the factor (-1)^m between the two patches (Sect. 4.2).
 bool detect_symmetry(const ygs_plan* p) {
   if (p->n_patch != 2 || (p->flags & YGS_FLAG_NO_SYMMETRY)) return false;
+  if (p->kind[0] != YGS_PATCH_LATLON || p->kind[1] != YGS_PATCH_LATLON) return false;
   if (p->nth[0] != p->nth[1] || p->nph[0] != p->nph[1]) return false;
   for (int k = 0; k < 2; ++k)
     if (p->theta_range[k] != p->theta_range[2 + k] || p->phi_range[k] != p->phi_range[2 + k]) return false;
@@ -138,8 +139,18 @@ ygs_status validate_desc(const ygs_desc* d) {
     double p0 = d->phi_range[2 * g], p1 = d->phi_range[2 * g + 1];
     if (!finite(t0) || !finite(t1) || !finite(p0) || !finite(p1))
       return fail(YGS_ERR_INVALID_ARG, "non-finite patch extent");
-    if (t0 < -1e-12 || t1 > pi + 1e-12 || !(t1 > t0)) return fail(YGS_ERR_INVALID_ARG, "theta_range must satisfy 0 <= lo < hi <= pi");
-    if (!(p1 > p0) || p1 - p0 > 2 * pi + 1e-12) return fail(YGS_ERR_INVALID_ARG, "phi_range must satisfy lo < hi <= lo + 2 pi");
+    const int kind = d->patch_kind ? d->patch_kind[g] : YGS_PATCH_LATLON;
+    if (kind == YGS_PATCH_GNOMONIC) {
+      // xi and eta strictly inside (-pi/2, pi/2), where tan is finite
+      const double h = 0.5 * pi - 1e-6;
+      if (t0 < -h || t1 > h || !(t1 > t0) || p0 < -h || p1 > h || !(p1 > p0))
+        return fail(YGS_ERR_INVALID_ARG, "a gnomonic patch's xi and eta ranges must satisfy -pi/2 < lo < hi < pi/2");
+    } else if (kind == YGS_PATCH_LATLON) {
+      if (t0 < -1e-12 || t1 > pi + 1e-12 || !(t1 > t0)) return fail(YGS_ERR_INVALID_ARG, "theta_range must satisfy 0 <= lo < hi <= pi");
+      if (!(p1 > p0) || p1 - p0 > 2 * pi + 1e-12) return fail(YGS_ERR_INVALID_ARG, "phi_range must satisfy lo < hi <= lo + 2 pi");
+    } else {
+      return fail(YGS_ERR_INVALID_ARG, "unknown patch kind");
+    }
     long long na = (long long)d->n_theta[g] * d->n_phi[g];
     if (na > (1LL << 30)) return fail(YGS_ERR_INVALID_ARG, "too many angular cells in one patch");
     total += na;
@@ -269,6 +280,10 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
   p->phi_range.assign(d->phi_range, d->phi_range + 2 * d->n_patch);
   p->nth.assign(d->n_theta, d->n_theta + d->n_patch);
   p->nph.assign(d->n_phi, d->n_phi + d->n_patch);
+  if (d->patch_kind)
+    p->kind.assign(d->patch_kind, d->patch_kind + d->n_patch);
+  else
+    p->kind.assign(d->n_patch, (int)YGS_PATCH_LATLON);
   long long acc = 0;
   for (int g = 0; g < p->n_patch; ++g) {
     p->nang.push_back((long long)p->nth[g] * p->nph[g]);

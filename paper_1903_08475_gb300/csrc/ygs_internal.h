@@ -40,6 +40,7 @@ struct ygs_plan {
   int n_wpatch = 0;         // patches with stored weights (1 when symmetric)
   int K_even = 0;           // internal columns [0, K_even) have even m when symmetric, else K_even = K
   std::vector<int> nth, nph;
+  std::vector<int> kind;    // ygs_patch_kind per patch
   std::vector<double> euler, theta_range, phi_range, edges, w_host;
   std::vector<long long> nang, ang_off, fld_off;
   long long nang_total = 0, nang_wtotal = 0, n_cells = 0;

@@ -16,6 +16,12 @@
 //               (Eqs. U_C/U_S in real-harmonic form);
 //   Q           -G N_lm P_lm(cos theta^+) {cos, sin}(m phi^+) at the global
 //               direction of the evaluation point (Eqs. Q_C/Q_S);
+//   gnomonic    the non-orthogonal patches of Sect. 6 (cube faces in
+//               equiangular coordinates): U = (2/delta_m) w_jk times the
+//               integral of the global real harmonic over the cell, by
+//               10-point Gauss-Legendre panels in both coordinates with the
+//               solid-angle density of the gnomonic map, instead of the
+//               separable Wigner route; Q as above at the cell's point;
 //   radial      a_i = R_in,i / (r_i^+)^(l+1), b_i = (r_i^-)^l R_out,i and the
 //               ratios (r_{i-1}^+/r_i^+)^(l+1), (r_i^+/r_{i+1}^+)^l that turn
 //               Eq. M_C into recurrences with every factor <= O(r^2)
@@ -237,11 +243,42 @@ __global__ void phi_int_kernel(int L, const double* ph_lo, const double* dph, co
 
 struct PatchGeo {
   int nth[kMaxPatch], nph[kMaxPatch];
+  int kind[kMaxPatch];           // ygs_patch_kind
   long long ang_off[kMaxPatch];  // row offset in the stored weight matrix
   long long w_off[kMaxPatch];    // offset of the patch's overlap weights
   double th_lo[kMaxPatch], dth[kMaxPatch], ph_lo[kMaxPatch], dph[kMaxPatch];
   double R[kMaxPatch][9];
 };
+
+// Global unit vector (x0, x1, x2) of the local coordinates (u, v) of patch g
+// and the solid-angle density dOmega / (du dv): (theta, phi) patches
+// (u = theta, v = phi, density sin theta), or gnomonic cube faces (X = tan u,
+// Y = tan v, direction (X, Y, 1) / sqrt(1 + X^2 + Y^2), density
+// (1 + X^2)(1 + Y^2) / (1 + X^2 + Y^2)^(3/2)).
+__device__ inline double patch_dir(const PatchGeo& geo, int g, double u, double v, double& x0, double& x1,
+                                   double& x2) {
+  double v0, v1, v2, dens;
+  if (geo.kind[g] == YGS_PATCH_GNOMONIC) {
+    const double X = tan(u), Y = tan(v), r2 = 1.0 + X * X + Y * Y, ri = rsqrt(r2);
+    v0 = X * ri;
+    v1 = Y * ri;
+    v2 = ri;
+    dens = (1.0 + X * X) * (1.0 + Y * Y) * ri / r2;
+  } else {
+    double st, ct, sp, cp;
+    sincos(u, &st, &ct);
+    sincos(v, &sp, &cp);
+    v0 = st * cp;
+    v1 = st * sp;
+    v2 = ct;
+    dens = st;
+  }
+  const double* R = geo.R[g];
+  x0 = R[0] * v0 + R[1] * v1 + R[2] * v2;
+  x1 = R[3] * v0 + R[4] * v1 + R[5] * v2;
+  x2 = R[6] * v0 + R[7] * v1 + R[8] * v2;
+  return dens;
+}
 
 // U[(ang_off + a)][c_int] for every stored patch (grid-stride over a x c).
 __global__ void u_kernel(int L, int K, int nwp, PatchGeo geo, const int* col_nat, const double* W, const double* T,
@@ -287,14 +324,8 @@ __global__ void q_kernel(int L, int K, int nwp, PatchGeo geo, int eval, double G
     double off = (eval == YGS_EVAL_CELL_CENTRE) ? 0.5 : 1.0;
     double th = geo.th_lo[g] + (j + off) * geo.dth[g];
     double ph = geo.ph_lo[g] + (k + off) * geo.dph[g];
-    double st, ct, sp, cp;
-    sincos(th, &st, &ct);
-    sincos(ph, &sp, &cp);
-    double v0 = st * cp, v1 = st * sp, v2 = ct;
-    const double* R = geo.R[g];
-    double x0 = R[0] * v0 + R[1] * v1 + R[2] * v2;
-    double x1 = R[3] * v0 + R[4] * v1 + R[5] * v2;
-    double x2 = R[6] * v0 + R[7] * v1 + R[8] * v2;
+    double x0, x1, x2;
+    patch_dir(geo, g, th, ph, x0, x1, x2);
     double s = sqrt(x0 * x0 + x1 * x1);
     double x = fmax(-1.0, fmin(1.0, x2));
     double phg = atan2(x1, x0);
@@ -318,6 +349,72 @@ __global__ void q_kernel(int L, int K, int nwp, PatchGeo geo, int eval, double G
       } else {
         Qr[col_int[l * l + 2 * m - 1]] = -G * p * cmp;
         Qr[col_int[l * l + 2 * m]] = -G * p * smp;
+      }
+    }
+  }
+}
+
+// U rows of the gnomonic patches: thread (row, m) integrates N_lm P_lm(cos
+// theta) {cos, sin}(m phi) of the global direction over the cell, for every
+// l >= m, by panels of 10-point Gauss-Legendre in both coordinates (panels no
+// wider than 0.75 / (l_max + 1), twice as fine as the (theta, phi) route's, for
+// the gnomonic map's stretching toward the face corners).  Rows of other
+// patches are left as they are.
+__global__ void u_gnomonic_kernel(int L, int K, int nwp, PatchGeo geo, const int* col_int, GL10 gl,
+                                  const double* w, double* U, long long rows) {
+  double accC[kMaxLmax + 1], accS[kMaxLmax + 1];
+  long long total = rows * (L + 1);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long row = e / (L + 1);
+    int m = (int)(e % (L + 1));
+    int g = 0;
+    while (g + 1 < nwp && geo.ang_off[g + 1] <= row) ++g;
+    if (geo.kind[g] != YGS_PATCH_GNOMONIC) continue;
+    long long a = row - geo.ang_off[g];
+    int j = (int)(a / geo.nph[g]), k = (int)(a % geo.nph[g]);
+    const double u0 = geo.th_lo[g] + j * geo.dth[g], v0 = geo.ph_lo[g] + k * geo.dph[g];
+    const int nu = (int)fmax(1.0, ceil((L + 1) * geo.dth[g] / 0.75));
+    const int nv = (int)fmax(1.0, ceil((L + 1) * geo.dph[g] / 0.75));
+    const double hu = geo.dth[g] / nu, hv = geo.dph[g] / nv;
+    for (int l = m; l <= L; ++l) accC[l] = accS[l] = 0.0;
+    for (int pu = 0; pu < nu; ++pu)
+      for (int qu = 0; qu < 10; ++qu) {
+        const double uq = u0 + pu * hu + 0.5 * hu * (1.0 + gl.x[qu]);
+        const double wu = 0.5 * hu * gl.w[qu];
+        for (int pv = 0; pv < nv; ++pv)
+          for (int qv = 0; qv < 10; ++qv) {
+            const double vq = v0 + pv * hv + 0.5 * hv * (1.0 + gl.x[qv]);
+            double x0, x1, x2;
+            const double wt = wu * 0.5 * hv * gl.w[qv] * patch_dir(geo, g, uq, vq, x0, x1, x2);
+            const double s = sqrt(x0 * x0 + x1 * x1), x = fmax(-1.0, fmin(1.0, x2));
+            double smp, cmp;
+            sincos(m * atan2(x1, x0), &smp, &cmp);
+            double pmm = 1.0;
+            for (int kk = 1; kk <= m; ++kk) pmm *= sqrt((2.0 * kk - 1.0) / (2.0 * kk)) * s;
+            double p2 = 0.0, p1 = 0.0;
+            for (int l = m; l <= L; ++l) {
+              double pl;
+              if (l == m) pl = pmm;
+              else if (l == m + 1) pl = sqrt(2.0 * m + 1.0) * x * pmm;
+              else
+                pl = ((2.0 * l - 1.0) * x * p1 - sqrt((double)(l - 1 - m) * (double)(l - 1 + m)) * p2) /
+                     sqrt((double)(l - m) * (double)(l + m));
+              p2 = p1;
+              p1 = pl;
+              accC[l] += wt * pl * cmp;
+              accS[l] += wt * pl * smp;
+            }
+          }
+      }
+    const double f = (m == 0 ? 1.0 : 2.0) * w[geo.w_off[g] + a];  // 2 / delta_m times the overlap weight
+    double* Ur = U + row * K;
+    for (int l = m; l <= L; ++l) {
+      if (m == 0) {
+        Ur[col_int[l * l]] = f * accC[l];
+      } else {
+        Ur[col_int[l * l + 2 * m - 1]] = f * accC[l];
+        Ur[col_int[l * l + 2 * m]] = f * accS[l];
       }
     }
   }
@@ -526,6 +623,7 @@ ygs_status build_weights(ygs_plan* p) {
     nph_max = std::max(nph_max, nph[g]);
     geo.nth[g] = nth[g];
     geo.nph[g] = nph[g];
+    geo.kind[g] = p->kind[g];
     geo.ang_off[g] = p->ang_off[g];
     geo.w_off[g] = p->ang_off[g];
     geo.th_lo[g] = th_lo[g];
@@ -640,6 +738,12 @@ ygs_status build_weights(ygs_plan* p) {
   long long rows = p->nang_wtotal;
   u_kernel<<<2048, 256>>>(L, K, nwp, geo, p->col_nat, d_W, d_T, tstride, d_CS, nph_max, d_w, p->U, rows);
   YGS_TRY(cudaGetLastError());
+  bool any_gnomonic = false;
+  for (int g = 0; g < nwp; ++g) any_gnomonic |= p->kind[g] == YGS_PATCH_GNOMONIC;
+  if (any_gnomonic) {  // their rows by direct quadrature (the separable route does not apply)
+    u_gnomonic_kernel<<<1024, 128>>>(L, K, nwp, geo, d_col_int, gl, d_w, p->U, rows);
+    YGS_TRY(cudaGetLastError());
+  }
   q_kernel<<<1024, 128>>>(L, K, nwp, geo, p->eval, p->G, d_col_int, p->Q, rows);
   YGS_TRY(cudaGetLastError());
   radial_kernel<<<64, 256>>>(L, p->n_r, d_edges, p->rad);
