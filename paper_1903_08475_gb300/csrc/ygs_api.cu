@@ -633,9 +633,21 @@ ygs_status ygs_batch_solve(ygs_batch* b, const double* const* d_rho, double* con
   DeviceGuard guard(b->device);
   if (!guard.ok) return fail(YGS_ERR_CUDA, "cudaSetDevice failed");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int k : b->split) API_TRY(tc_field_slices(b->plans[k], d_rho[k], s));
+  // per operand kind: the field slices, the projection, the scans (and M
+  // slicing) and the synthesis of all its members, one grouped launch each
+  auto member_fields = [&](const TcBatchGroup& G) {
+    std::vector<const double*> rho;
+    for (const ygs_plan* m : G.members)
+      for (int k : b->split)
+        if (b->plans[k] == m) rho.push_back(d_rho[k]);
+    return rho;
+  };
+  for (const TcBatchGroup& G : b->tc.groups) {
+    const std::vector<const double*> rho = member_fields(G);
+    API_TRY(tc_batch_field(G, rho.data(), s));
+  }
   for (const TcBatchGroup& G : b->tc.groups) API_TRY(tc_batch_project(G, s));
-  for (int k : b->split) API_TRY(tc_scan(b->plans[k], s));
+  for (const TcBatchGroup& G : b->tc.groups) API_TRY(tc_batch_scan(G, s));
   for (const TcBatchGroup& G : b->tc.groups) {
     std::vector<double*> phi;
     for (const ygs_plan* m : G.members)
@@ -654,8 +666,9 @@ ygs_status ygs_batch_solve(ygs_batch* b, const double* const* d_rho, double* con
 int ygs_batch_launches(const ygs_batch* b) {
   if (!b) return 0;
   int n = 0;
-  for (int k : b->split) n += (b->plans[k]->tc_fp16 || b->plans[k]->tc_emu) ? 3 : 2;  // field slices, scan (+ M slicing)
-  n += 2 * (int)b->tc.groups.size() + 3 * (int)b->fp64.size();
+  // per operand kind: field slices, projection, scan (+ M slicing), synthesis
+  for (const TcBatchGroup& G : b->tc.groups) n += (G.fp16 || G.emu) ? 5 : 4;
+  n += 3 * (int)b->fp64.size();
   return n;
 }
 

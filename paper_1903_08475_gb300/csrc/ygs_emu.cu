@@ -181,13 +181,13 @@ static_assert(kEmuWindow == 4 * kFieldThreads, "four cells per thread");
 // range (a window whose largest value is below about 2^-120 keeps fewer
 // bits; one at or above 2^127 sets the error word: the FP32 sums of the
 // contraction could not hold it).
-__global__ void __launch_bounds__(kFieldThreads) emu_field_kernel(
-    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
+__device__ __forceinline__ void emu_field_kernel_body(const tc::VBlock& vb, 
+    int n_r, int symmetric, int nwp, const PatchTable& pt, const long long* __restrict__ pad_off, long long n_pad,
     const double* __restrict__ rho, uint16_t* __restrict__ F, float* __restrict__ fac, int fac_ld,
     int* __restrict__ err) {
   __shared__ unsigned int red[32];
-  const long long G = blockIdx.x;
-  const int i = blockIdx.y;
+  const long long G = vb.x;
+  const int i = vb.y;
   const long long plane = (long long)n_r * n_pad;
   const long long nwin_all = n_pad / kEmuWindow;
   const long long ap = G * kEmuWindow;  // first padded cell of the window
@@ -263,6 +263,37 @@ __global__ void __launch_bounds__(kFieldThreads) emu_field_kernel(
     }
   }
 }
+__global__ void __launch_bounds__(256) emu_field_kernel(
+    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
+    const double* __restrict__ rho, uint16_t* __restrict__ F, float* __restrict__ fac, int fac_ld,
+    int* __restrict__ err) {
+  emu_field_kernel_body(tc::vblock_self(), n_r, symmetric, nwp, pt, pad_off, n_pad, rho, F, fac, fac_ld, err);
+}
+
+// The arguments of emu_field_kernel but the field, for a grouped launch.
+struct EmuFieldArgs {
+  int n_r;
+  int symmetric;
+  int nwp;
+  PatchTable pt;
+  const long long* pad_off;
+  long long n_pad;
+  uint16_t* F;
+  float* fac;
+  int fac_ld;
+  int* err;
+};
+
+// emu_field_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(256) emu_field_kernel_group(const EmuFieldArgs* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n, const __grid_constant__ tc::RhoList rhos) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const EmuFieldArgs& a = probs[k];
+  const double* rho = rhos.p[k];
+  emu_field_kernel_body(vb, a.n_r, a.symmetric, a.nwp, a.pt, a.pad_off, a.n_pad, rho, a.F, a.fac, a.fac_ld, a.err);
+}
+
 
 // ---- radial scans (every solve), FP64 ----------------------------------------
 // One warp per padded column; lane p owns the shells [p c, (p + 1) c), c =
@@ -301,12 +332,12 @@ constexpr int kScanWarps = 8;  // columns per CTA
 // and inner scaled recurrences of Eq. M_C, M = O + I:
 //   O_i = b_(i+1) B_(i+1) + f_out,i O_(i+1)  (O_(n-1) = 0),
 //   I_i = a_i B_i + f_in,i I_(i-1)            (I_(-1) = 0).
-__global__ void __launch_bounds__(32 * kScanWarps) emu_scan_kernel(
+__device__ __forceinline__ void emu_scan_kernel_body(const tc::VBlock& vb, 
     int n_r, int K_pad, int L, int S, const int* __restrict__ pc_l, const float2* __restrict__ part,
     const double* __restrict__ rad, double* __restrict__ B, double* __restrict__ M, float2* __restrict__ Bff,
     float2* __restrict__ Mff) {
   const int lane = threadIdx.x % 32;
-  const int c = blockIdx.x * kScanWarps + threadIdx.x / 32;
+  const int c = vb.x * kScanWarps + threadIdx.x / 32;
   if (c >= K_pad) return;  // warp-uniform
   const int l = pc_l[c];
   const long long plane = (long long)n_r * K_pad;
@@ -367,6 +398,37 @@ __global__ void __launch_bounds__(32 * kScanWarps) emu_scan_kernel(
     Mff[(long long)i * K_pad + c] = tc::ff_from_f64(m);
   }
 }
+__global__ void __launch_bounds__(32 * kScanWarps) emu_scan_kernel(
+    int n_r, int K_pad, int L, int S, const int* __restrict__ pc_l, const float2* __restrict__ part,
+    const double* __restrict__ rad, double* __restrict__ B, double* __restrict__ M, float2* __restrict__ Bff,
+    float2* __restrict__ Mff) {
+  emu_scan_kernel_body(tc::vblock_self(), n_r, K_pad, L, S, pc_l, part, rad, B, M, Bff, Mff);
+}
+
+// The arguments of emu_scan_kernel but the field, for a grouped launch.
+struct EmuScanArgs {
+  int n_r;
+  int K_pad;
+  int L;
+  int S;
+  const int* pc_l;
+  const float2* part;
+  const double* rad;
+  double* B;
+  double* M;
+  float2* Bff;
+  float2* Mff;
+};
+
+// emu_scan_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(32 * kScanWarps) emu_scan_kernel_group(const EmuScanArgs* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const EmuScanArgs& a = probs[k];
+  emu_scan_kernel_body(vb, a.n_r, a.K_pad, a.L, a.S, a.pc_l, a.part, a.rad, a.B, a.M, a.Bff, a.Mff);
+}
+
 
 // The transposed scans: Mbar_i = sum_z part[z][i][pc], then
 //   X_i = Mbar_i + f_in,(i+1) X_(i+1)      (X_n = 0),
@@ -436,11 +498,11 @@ __global__ void __launch_bounds__(32 * kScanWarps) emu_scan_adj_kernel(
 // exponent rebase that unscales the synthesis output as it is widened to
 // FP64.  One CTA per shell.
 constexpr int kSliceThreads = 256;
-__global__ void __launch_bounds__(kSliceThreads) emu_slice_m_kernel(int n_r, int K_pad, const double* __restrict__ X,
+__device__ __forceinline__ void emu_slice_m_kernel_body(const tc::VBlock& vb, int n_r, int K_pad, const double* __restrict__ X,
                                                                     uint16_t* __restrict__ Xs,
                                                                     float4* __restrict__ sc) {
   __shared__ unsigned int red[32];
-  const int i = blockIdx.x;
+  const int i = vb.x;
   const double* row = X + (long long)i * K_pad;
   unsigned int b = 0;
   for (int c = threadIdx.x; c < K_pad; c += blockDim.x) b = max(b, (unsigned int)bexp(row[c]));
@@ -455,6 +517,30 @@ __global__ void __launch_bounds__(kSliceThreads) emu_slice_m_kernel(int n_r, int
     for (int s = 0; s < kS; ++s) Xs[s * plane + (long long)i * K_pad + c] = digit_bf16(d[s], s);
   }
 }
+__global__ void __launch_bounds__(kSliceThreads) emu_slice_m_kernel(int n_r, int K_pad, const double* __restrict__ X,
+                                                                    uint16_t* __restrict__ Xs,
+                                                                    float4* __restrict__ sc) {
+  emu_slice_m_kernel_body(tc::vblock_self(), n_r, K_pad, X, Xs, sc);
+}
+
+// The arguments of emu_slice_m_kernel but the field, for a grouped launch.
+struct EmuSliceMArgs {
+  int n_r;
+  int K_pad;
+  const double* X;
+  uint16_t* Xs;
+  float4* sc;
+};
+
+// emu_slice_m_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(kSliceThreads) emu_slice_m_kernel_group(const EmuSliceMArgs* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const EmuSliceMArgs& a = probs[k];
+  emu_slice_m_kernel_body(vb, a.n_r, a.K_pad, a.X, a.Xs, a.sc);
+}
+
 
 // out[i][pc_nat[pc]] = in[i][pc] (the FP64 moments in natural column order)
 __global__ void emu_unpermute_kernel(int n_r, int K, int K_pad, const int* __restrict__ pc_nat,
@@ -503,21 +589,87 @@ cudaError_t emu_slice_weights(ygs_plan* p) {
   return e;
 }
 
-cudaError_t emu_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
+// The arguments and grids of the per-field passes, shared by the plain
+// launches and the grouped launches of a batch.
+namespace {
+EmuFieldArgs emu_field_args(const ygs_plan* p) {
   const int fld = (p->tc_np_full + (p->tc_np_tail > 0 ? 1 : 0)) * tc::kNmaxProject;
-  emu_field_kernel<<<dim3((unsigned)(p->tc_n_pad / kEmuWindow), p->n_r), kFieldThreads, 0, s>>>(
-      p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, rho,
-      reinterpret_cast<uint16_t*>(p->tc_f), p->tc_fac, fld, p->d_err);
+  return EmuFieldArgs{p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad,
+                      reinterpret_cast<uint16_t*>(p->tc_f), p->tc_fac, fld, p->d_err};
+}
+dim3 emu_field_grid(const ygs_plan* p) { return dim3((unsigned)(p->tc_n_pad / kEmuWindow), p->n_r); }
+EmuScanArgs emu_scan_args(const ygs_plan* p) {
+  return EmuScanArgs{p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_pc_l, p->tc_part, p->rad,
+                     p->tc_Bd, p->tc_Md, p->tc_B, p->tc_M};
+}
+int emu_scan_blocks(const ygs_plan* p) { return (p->tc_k_pad + kScanWarps - 1) / kScanWarps; }
+EmuSliceMArgs emu_slice_m_args(const ygs_plan* p) {
+  return EmuSliceMArgs{p->n_r, p->tc_k_pad, p->tc_Md, reinterpret_cast<uint16_t*>(p->tc_ms), p->tc_sc};
+}
+}  // namespace
+
+cudaError_t emu_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s) {
+  const EmuFieldArgs a = emu_field_args(p);
+  emu_field_kernel<<<emu_field_grid(p), kFieldThreads, 0, s>>>(a.n_r, a.symmetric, a.nwp, a.pt, a.pad_off, a.n_pad,
+                                                               rho, a.F, a.fac, a.fac_ld, a.err);
   return cudaGetLastError();
 }
 
 cudaError_t emu_scan(const ygs_plan* p, cudaStream_t s) {
-  emu_scan_kernel<<<(p->tc_k_pad + kScanWarps - 1) / kScanWarps, 32 * kScanWarps, 0, s>>>(p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_pc_l,
-                                                        p->tc_part, p->rad, p->tc_Bd, p->tc_Md, p->tc_B, p->tc_M);
+  const EmuScanArgs a = emu_scan_args(p);
+  emu_scan_kernel<<<emu_scan_blocks(p), 32 * kScanWarps, 0, s>>>(a.n_r, a.K_pad, a.L, a.S, a.pc_l, a.part, a.rad,
+                                                                 a.B, a.M, a.Bff, a.Mff);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  emu_slice_m_kernel<<<p->n_r, kSliceThreads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_Md,
-                                                      reinterpret_cast<uint16_t*>(p->tc_ms), p->tc_sc);
+  const EmuSliceMArgs m = emu_slice_m_args(p);
+  emu_slice_m_kernel<<<p->n_r, kSliceThreads, 0, s>>>(m.n_r, m.K_pad, m.X, m.Xs, m.sc);
+  return cudaGetLastError();
+}
+
+cudaError_t emu_batch_passes(const std::vector<ygs_plan*>& mem, TcBatchGroup& G) {
+  const int n = (int)mem.size();
+  std::vector<EmuFieldArgs> fa;
+  std::vector<EmuScanArgs> sa;
+  std::vector<EmuSliceMArgs> ma;
+  std::vector<int> gx, gy, one(n, 1), sx, mx;
+  for (ygs_plan* p : mem) {
+    fa.push_back(emu_field_args(p));
+    sa.push_back(emu_scan_args(p));
+    ma.push_back(emu_slice_m_args(p));
+    const dim3 d = emu_field_grid(p);
+    gx.push_back((int)d.x);
+    gy.push_back((int)d.y);
+    sx.push_back(emu_scan_blocks(p));
+    mx.push_back(p->n_r);
+  }
+  cudaError_t e;
+  if ((e = upload_grouped_pass(G.field, fa.data(), sizeof(EmuFieldArgs), n, gx.data(), gy.data(), one.data())) !=
+      cudaSuccess)
+    return e;
+  if ((e = upload_grouped_pass(G.scan, sa.data(), sizeof(EmuScanArgs), n, sx.data(), one.data(), one.data())) !=
+      cudaSuccess)
+    return e;
+  return upload_grouped_pass(G.mslice, ma.data(), sizeof(EmuSliceMArgs), n, mx.data(), one.data(), one.data());
+}
+
+cudaError_t emu_batch_field(const TcBatchGroup& G, const double* const* rho, cudaStream_t s) {
+  tc::RhoList list{};
+  const int n = (int)G.members.size();
+  for (int k = 0; k < n; ++k) list.p[k] = rho[k];
+  emu_field_kernel_group<<<G.field.blocks, kFieldThreads, 0, s>>>(static_cast<const EmuFieldArgs*>(G.field.d_args),
+                                                                  static_cast<const tc::GroupDims*>(G.field.d_dims),
+                                                                  n, list);
+  return cudaGetLastError();
+}
+
+cudaError_t emu_batch_scan(const TcBatchGroup& G, cudaStream_t s) {
+  const int n = (int)G.members.size();
+  emu_scan_kernel_group<<<G.scan.blocks, 32 * kScanWarps, 0, s>>>(static_cast<const EmuScanArgs*>(G.scan.d_args),
+                                                                  static_cast<const tc::GroupDims*>(G.scan.d_dims), n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  emu_slice_m_kernel_group<<<G.mslice.blocks, kSliceThreads, 0, s>>>(
+      static_cast<const EmuSliceMArgs*>(G.mslice.d_args), static_cast<const tc::GroupDims*>(G.mslice.d_dims), n);
   return cudaGetLastError();
 }
 

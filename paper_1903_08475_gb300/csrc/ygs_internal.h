@@ -192,17 +192,33 @@ cudaError_t tc_unpermute(const ygs_plan* p, const float2* in, double* out, cudaS
 namespace tc {
 struct TcProblem;
 }
+// One per-field pass of a batch run as a single grouped launch: its
+// problems' argument structs and grid shapes (tc::GroupDims) in device memory.
+struct TcGroupedPass {
+  void* d_args = nullptr;
+  void* d_dims = nullptr;
+  int blocks = 0;  // blocks of all problems
+};
 struct TcBatchGroup {
   int nsl = 0, fp16 = 0, tf32 = 0, emu = 0, sms = 0, total_p = 0, total_s = 0;
   std::vector<ygs_plan*> members;
   tc::TcProblem *d_proj = nullptr, *d_synth = nullptr;
   int *d_start_p = nullptr, *d_start_s = nullptr;
+  TcGroupedPass field, scan, mslice;  // field slices, scans, M slicing (FP16 and EMU)
 };
+// Uploads a grouped pass: n argument structs of arg_bytes each and the
+// problems' grid shapes (gx, gy, gz per problem).
+cudaError_t upload_grouped_pass(TcGroupedPass& P, const void* args, size_t arg_bytes, int n, const int* gx,
+                                const int* gy, const int* gz);
 struct TcBatch {
   std::vector<TcBatchGroup> groups;
 };
 ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans);
 void tc_batch_free(TcBatch* b);
+// The field slices of every member (rho[k] for member k) in one grouped launch.
+cudaError_t tc_batch_field(const TcBatchGroup& g, const double* const* rho, cudaStream_t s);
+// The scans (and M slicing) of every member in one grouped launch each.
+cudaError_t tc_batch_scan(const TcBatchGroup& g, cudaStream_t s);
 cudaError_t tc_batch_project(const TcBatchGroup& g, cudaStream_t s);
 // phi[k]: output of the group's k-th member
 cudaError_t tc_batch_synthesize(const TcBatchGroup& g, double* const* phi, cudaStream_t s);
@@ -230,6 +246,10 @@ cudaError_t emu_scan(const ygs_plan* p, cudaStream_t s);
 cudaError_t emu_scan_adj(const ygs_plan* p, cudaStream_t s);
 // out[i][natural column] = in[i][pc] for FP64 moments in the padded column order.
 cudaError_t emu_unpermute(const ygs_plan* p, const double* in, double* out, cudaStream_t s);
+// The grouped field, scan and M-slicing passes of a batch's EMU members.
+cudaError_t emu_batch_passes(const std::vector<ygs_plan*>& members, TcBatchGroup& G);
+cudaError_t emu_batch_field(const TcBatchGroup& G, const double* const* rho, cudaStream_t s);
+cudaError_t emu_batch_scan(const TcBatchGroup& G, cudaStream_t s);
 // The EMU contraction kernels (one problem, or a group of problems).
 namespace tc {
 struct TcArgs;

@@ -192,18 +192,18 @@ __device__ __forceinline__ void sigma_slices(double r0, double r1, int nsl, int 
 // Grid: (x over groups of 4 angular cells, y over shells, z over stored
 // patches).  Rows of rho whose start is 16-byte aligned are read with 16-byte
 // loads; slices are written 4 cells (8 bytes) at a time.
-__global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable pt,
+__device__ __forceinline__ void field_slices_kernel_body(const tc::VBlock& vb, int nsl, int n_r, int symmetric, const PatchTable& pt,
                                     const long long* __restrict__ pad_off, long long n_pad,
                                     const double* __restrict__ rho, __nv_bfloat16* __restrict__ F) {
   const long long plane = (long long)n_r * n_pad;
-  const int g = blockIdx.z;
-  const int i = blockIdx.y;
+  const int g = vb.z;
+  const int i = vb.y;
   const int na = (int)pt.nang[g];
   const long long row_in = pt.fld_off[g] + (long long)i * na;
   const long long row_in1 = symmetric ? pt.fld_off[1] + (long long)i * na : row_in;
   const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
   const bool vec = ((row_in | row_in1) & 1) == 0;
-  for (int a = 4 * (blockIdx.x * blockDim.x + threadIdx.x); a < na; a += 4 * gridDim.x * blockDim.x) {
+  for (int a = 4 * (vb.x * blockDim.x + threadIdx.x); a < na; a += 4 * vb.gx * blockDim.x) {
     double v0[4], v1[4];
     if (vec && a + 4 <= na) {
       const double2 x0 = *reinterpret_cast<const double2*>(rho + row_in + a);
@@ -245,6 +245,33 @@ __global__ void field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable 
       }
   }
 }
+__global__ void __launch_bounds__(128) field_slices_kernel(int nsl, int n_r, int symmetric, PatchTable pt,
+                                    const long long* __restrict__ pad_off, long long n_pad,
+                                    const double* __restrict__ rho, __nv_bfloat16* __restrict__ F) {
+  field_slices_kernel_body(tc::vblock_self(), nsl, n_r, symmetric, pt, pad_off, n_pad, rho, F);
+}
+
+// The arguments of field_slices_kernel but the field, for a grouped launch.
+struct FieldSlicesArgs {
+  int nsl;
+  int n_r;
+  int symmetric;
+  PatchTable pt;
+  const long long* pad_off;
+  long long n_pad;
+  __nv_bfloat16* F;
+};
+
+// field_slices_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(128) field_slices_kernel_group(const FieldSlicesArgs* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n, const __grid_constant__ tc::RhoList rhos) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const FieldSlicesArgs& a = probs[k];
+  const double* rho = rhos.p[k];
+  field_slices_kernel_body(vb, a.nsl, a.n_r, a.symmetric, a.pt, a.pad_off, a.n_pad, rho, a.F);
+}
+
 
 // sigma+- (or rho) of one cell as float-float pairs from the two values'
 // float-float forms (TwoSum of the heads, renormalised), as sigma_slices.
@@ -272,17 +299,17 @@ __device__ __forceinline__ void sigma_ff2(double r0, double r1, int symmetric, f
 
 // TF32 field slices, organised like field_slices_kernel: 4 cells per thread,
 // 16-byte loads where the rows allow, one 16-byte store per plane and slice.
-__global__ void field_slices_tf32_kernel(int n_r, int symmetric, PatchTable pt, const long long* __restrict__ pad_off,
+__device__ __forceinline__ void field_slices_tf32_kernel_body(const tc::VBlock& vb, int n_r, int symmetric, const PatchTable& pt, const long long* __restrict__ pad_off,
                                          long long n_pad, const double* __restrict__ rho, float* __restrict__ F) {
   const long long plane = (long long)n_r * n_pad;
-  const int g = blockIdx.z;
-  const int i = blockIdx.y;
+  const int g = vb.z;
+  const int i = vb.y;
   const int na = (int)pt.nang[g];
   const long long row_in = pt.fld_off[g] + (long long)i * na;
   const long long row_in1 = symmetric ? pt.fld_off[1] + (long long)i * na : row_in;
   const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
   const bool vec = ((row_in | row_in1) & 1) == 0;
-  for (int a = 4 * (blockIdx.x * blockDim.x + threadIdx.x); a < na; a += 4 * gridDim.x * blockDim.x) {
+  for (int a = 4 * (vb.x * blockDim.x + threadIdx.x); a < na; a += 4 * vb.gx * blockDim.x) {
     double v0[4], v1[4];
     if (vec && a + 4 <= na) {
       const double2 x0 = *reinterpret_cast<const double2*>(rho + row_in + a);
@@ -320,6 +347,31 @@ __global__ void field_slices_tf32_kernel(int n_r, int symmetric, PatchTable pt, 
       }
   }
 }
+__global__ void __launch_bounds__(128) field_slices_tf32_kernel(int n_r, int symmetric, PatchTable pt, const long long* __restrict__ pad_off,
+                                         long long n_pad, const double* __restrict__ rho, float* __restrict__ F) {
+  field_slices_tf32_kernel_body(tc::vblock_self(), n_r, symmetric, pt, pad_off, n_pad, rho, F);
+}
+
+// The arguments of field_slices_tf32_kernel but the field, for a grouped launch.
+struct FieldSlicesTf32Args {
+  int n_r;
+  int symmetric;
+  PatchTable pt;
+  const long long* pad_off;
+  long long n_pad;
+  float* F;
+};
+
+// field_slices_tf32_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(128) field_slices_tf32_kernel_group(const FieldSlicesTf32Args* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n, const __grid_constant__ tc::RhoList rhos) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const FieldSlicesTf32Args& a = probs[k];
+  const double* rho = rhos.p[k];
+  field_slices_tf32_kernel_body(vb, a.n_r, a.symmetric, a.pt, a.pad_off, a.n_pad, rho, a.F);
+}
+
 
 // ---- FP16 slices (two per value, 22 significant bits) of power-of-two-scaled rows ----
 
@@ -535,11 +587,11 @@ int fac_ld(const ygs_plan* p) { return (p->tc_np_full + (p->tc_np_tail > 0 ? 1 :
 #ifndef YGS_F16_MINB
 #define YGS_F16_MINB 4  // resident CTAs per SM the field pass's register budget is set for
 #endif
-__global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field16_kernel(
-    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
+__device__ __forceinline__ void field16_kernel_body(const tc::VBlock& vb, 
+    int n_r, int symmetric, int nwp, const PatchTable& pt, const long long* __restrict__ pad_off, long long n_pad,
     const int2* __restrict__ chunks, const double* __restrict__ rho, __half* __restrict__ F,
     float* __restrict__ fac, int fac_ld, const float2* __restrict__ u00, float2* __restrict__ mpart) {
-  const int z = blockIdx.x, i = blockIdx.y;
+  const int z = vb.x, i = vb.y;
   const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
   const long long plane = (long long)n_r * n_pad;
   const long long ngroups_all = n_pad / kGroup;
@@ -630,6 +682,39 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field16_kernel(
   const float2 m = block_ff_sum(mh, ml);
   if (threadIdx.x == 0) mpart[(long long)z * n_r + i] = m;
 }
+__global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field16_kernel(
+    int n_r, int symmetric, int nwp, PatchTable pt, const long long* __restrict__ pad_off, long long n_pad,
+    const int2* __restrict__ chunks, const double* __restrict__ rho, __half* __restrict__ F,
+    float* __restrict__ fac, int fac_ld, const float2* __restrict__ u00, float2* __restrict__ mpart) {
+  field16_kernel_body(tc::vblock_self(), n_r, symmetric, nwp, pt, pad_off, n_pad, chunks, rho, F, fac, fac_ld, u00, mpart);
+}
+
+// The arguments of field16_kernel but the field, for a grouped launch.
+struct Field16Args {
+  int n_r;
+  int symmetric;
+  int nwp;
+  PatchTable pt;
+  const long long* pad_off;
+  long long n_pad;
+  const int2* chunks;
+  __half* F;
+  float* fac;
+  int fac_ld;
+  const float2* u00;
+  float2* mpart;
+};
+
+// field16_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field16_kernel_group(const Field16Args* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n, const __grid_constant__ tc::RhoList rhos) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const Field16Args& a = probs[k];
+  const double* rho = rhos.p[k];
+  field16_kernel_body(vb, a.n_r, a.symmetric, a.nwp, a.pt, a.pad_off, a.n_pad, a.chunks, rho, a.F, a.fac, a.fac_ld, a.u00, a.mpart);
+}
+
 
 
 // Ms[s][i][pc]: FP16 slices of M's row i scaled by 2^em[i] (largest |M| over the
@@ -639,11 +724,11 @@ __global__ void __launch_bounds__(kF16Threads, YGS_F16_MINB) field16_kernel(
 // stores); FP64 values enter as float-float pairs.  Also writes the synthesis
 // epilogue's per-shell constants sc[i].
 constexpr int kSliceM16Threads = 256;
-__global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
+__device__ __forceinline__ void slice_m16_kernel_body(const tc::VBlock& vb, 
     int n_r, int K_pad, const float2* __restrict__ M, int keep_mono, __half* __restrict__ Ms, int* __restrict__ em,
     int q_exp, const float2* __restrict__ mono, float4* __restrict__ sc) {
   __shared__ float red[32];
-  const int i = blockIdx.x, npair = K_pad / 2;  // K_pad is a multiple of 64
+  const int i = vb.x, npair = K_pad / 2;  // K_pad is a multiple of 64
   const long long splane = (long long)n_r * K_pad;
   const float4* row = reinterpret_cast<const float4*>(M + (long long)i * K_pad);  // two float-float columns each
   float m = 0.0f;
@@ -680,6 +765,34 @@ __global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
     out1[q] = h2_bits(s1);
   }
 }
+__global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel(
+    int n_r, int K_pad, const float2* __restrict__ M, int keep_mono, __half* __restrict__ Ms, int* __restrict__ em,
+    int q_exp, const float2* __restrict__ mono, float4* __restrict__ sc) {
+  slice_m16_kernel_body(tc::vblock_self(), n_r, K_pad, M, keep_mono, Ms, em, q_exp, mono, sc);
+}
+
+// The arguments of slice_m16_kernel but the field, for a grouped launch.
+struct SliceM16Args {
+  int n_r;
+  int K_pad;
+  const float2* M;
+  int keep_mono;
+  __half* Ms;
+  int* em;
+  int q_exp;
+  const float2* mono;
+  float4* sc;
+};
+
+// slice_m16_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(kSliceM16Threads) slice_m16_kernel_group(const SliceM16Args* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const SliceM16Args& a = probs[k];
+  slice_m16_kernel_body(vb, a.n_r, a.K_pad, a.M, a.keep_mono, a.Ms, a.em, a.q_exp, a.mono, a.sc);
+}
+
 
 // Products of the radial ratios over every chunk of shells (per degree l),
 // as float-float:
@@ -812,7 +925,7 @@ constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
 static_assert(kScanCols >= 1 && kScanThreads <= 1024 && kScanThreads % 32 == 0 && kScanMaxP >= 32,
               "scan: a CTA of whole warps, at most 1024 threads, at least 32 chunks per column");
 
-__global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
+__device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb, 
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
     const float2* __restrict__ rad, const float2* __restrict__ cp, float2* __restrict__ B, float2* __restrict__ M,
     __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, float2 neg_G, float2* __restrict__ mono,
@@ -821,7 +934,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
   __shared__ float2 cr[2][kScanMaxP][kScanCols];
   const float2 zero = make_float2(0.0f, 0.0f), one = make_float2(1.0f, 0.0f);
   const int c = threadIdx.x % kScanCols, p = threadIdx.x / kScanCols;
-  const int pc = blockIdx.x * kScanCols + c;
+  const int pc = vb.x * kScanCols + c;
   const int l = pc < K_pad ? pc_l[pc] : -1;
   const int i0 = p * chunk, i1 = min(n_r, i0 + chunk);
   const bool live = l >= 0 && p < P && i0 < n_r;
@@ -948,6 +1061,46 @@ __global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
     emit(i, tc::ff_add(M[(long long)i * K_pad + pc], I));
   }
 }
+__global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
+    int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
+    const float2* __restrict__ rad, const float2* __restrict__ cp, float2* __restrict__ B, float2* __restrict__ M,
+    __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, float2 neg_G, float2* __restrict__ mono,
+    const int* __restrict__ eu, const float2* __restrict__ mpart) {
+  scan_ff_kernel_body(tc::vblock_self(), n_r, K_pad, L, S, chunk, P, pc_l, part, rad, cp, B, M, Ms, nsl, write_slices, neg_G, mono, eu, mpart);
+}
+
+// The arguments of scan_ff_kernel but the field, for a grouped launch.
+struct ScanFfArgs {
+  int n_r;
+  int K_pad;
+  int L;
+  int S;
+  int chunk;
+  int P;
+  const int* pc_l;
+  const float2* part;
+  const float2* rad;
+  const float2* cp;
+  float2* B;
+  float2* M;
+  __nv_bfloat16* Ms;
+  int nsl;
+  int write_slices;
+  float2 neg_G;
+  float2* mono;
+  const int* eu;
+  const float2* mpart;
+};
+
+// scan_ff_kernel over the problems of a batch, one block per problem block.
+__global__ void __launch_bounds__(kScanThreads) scan_ff_kernel_group(const ScanFfArgs* __restrict__ probs,
+    const tc::GroupDims* __restrict__ dims, int n) {
+  tc::VBlock vb;
+  const int k = tc::locate_block(dims, n, blockIdx.x, vb);
+  const ScanFfArgs& a = probs[k];
+  scan_ff_kernel_body(vb, a.n_r, a.K_pad, a.L, a.S, a.chunk, a.P, a.pc_l, a.part, a.rad, a.cp, a.B, a.M, a.Ms, a.nsl, a.write_slices, a.neg_G, a.mono, a.eu, a.mpart);
+}
+
 
 // ---- adjoint scans (transposes of the recurrences above) ----
 // With Mbar the adjoint of M, the transposed recurrences are
@@ -1444,28 +1597,46 @@ void tc_free(ygs_plan* p) {
     if (b) cudaFree(b);
 }
 
+// The arguments and grids of the per-field passes, shared by the plain
+// launches below and the grouped launches of a batch.
+static Field16Args field16_args(const ygs_plan* p, bool forward) {
+  return Field16Args{p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks,
+                     reinterpret_cast<__half*>(p->tc_f), p->tc_fac, fac_ld(p), forward ? p->tc_u00 : nullptr,
+                     forward ? p->tc_mpart : nullptr};
+}
+static dim3 field16_grid(const ygs_plan* p) { return dim3(p->tc_S, p->n_r); }
+constexpr int kFieldSlicesThreads = 128;
+static dim3 field_slices_grid(const ygs_plan* p) {
+  long long nmax = 0;
+  for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
+  const int bx = (int)std::min<long long>(64, (nmax / 4 + kFieldSlicesThreads - 1) / kFieldSlicesThreads);
+  return dim3(std::max(1, bx), p->n_r, p->n_wpatch);
+}
+static FieldSlicesArgs field_slices_args(const ygs_plan* p) {
+  return FieldSlicesArgs{p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_f};
+}
+static FieldSlicesTf32Args field_slices_tf32_args(const ygs_plan* p) {
+  return FieldSlicesTf32Args{p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d, p->tc_n_pad,
+                             reinterpret_cast<float*>(p->tc_f)};
+}
+
 cudaError_t tc_field_slices(const ygs_plan* p, const double* rho, cudaStream_t s, bool forward) {
   if (p->tc_emu) return emu_field_slices(p, rho, s);
   if (p->tc_fp16) {
-    const float2* u00 = forward ? p->tc_u00 : nullptr;
-    float2* mpart = forward ? p->tc_mpart : nullptr;
-    field16_kernel<<<dim3(p->tc_S, p->n_r), kF16Threads, 0, s>>>(
-        p->n_r, p->symmetric ? 1 : 0, p->n_wpatch, p->pt, p->tc_pad_off_d, p->tc_n_pad, p->tc_chunks, rho,
-        reinterpret_cast<__half*>(p->tc_f), p->tc_fac, fac_ld(p), u00, mpart);
+    const Field16Args a = field16_args(p, forward);
+    field16_kernel<<<field16_grid(p), kF16Threads, 0, s>>>(a.n_r, a.symmetric, a.nwp, a.pt, a.pad_off, a.n_pad,
+                                                           a.chunks, rho, a.F, a.fac, a.fac_ld, a.u00, a.mpart);
     return cudaGetLastError();
   }
-  long long nmax = 0;
-  for (int g = 0; g < p->n_wpatch; ++g) nmax = std::max(nmax, p->nang[g]);
-  const int threads = 128;
-  const int bx = (int)std::min<long long>(64, (nmax / 4 + threads - 1) / threads);
-  dim3 grid(std::max(1, bx), p->n_r, p->n_wpatch);
   if (p->tc_tf32) {
-    field_slices_tf32_kernel<<<grid, threads, 0, s>>>(p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d, p->tc_n_pad,
-                                                      rho, reinterpret_cast<float*>(p->tc_f));
+    const FieldSlicesTf32Args a = field_slices_tf32_args(p);
+    field_slices_tf32_kernel<<<field_slices_grid(p), kFieldSlicesThreads, 0, s>>>(a.n_r, a.symmetric, a.pt,
+                                                                                  a.pad_off, a.n_pad, rho, a.F);
     return cudaGetLastError();
   }
-  field_slices_kernel<<<grid, threads, 0, s>>>(p->tc_nsl, p->n_r, p->symmetric ? 1 : 0, p->pt, p->tc_pad_off_d,
-                                               p->tc_n_pad, rho, p->tc_f);
+  const FieldSlicesArgs a = field_slices_args(p);
+  field_slices_kernel<<<field_slices_grid(p), kFieldSlicesThreads, 0, s>>>(a.nsl, a.n_r, a.symmetric, a.pt,
+                                                                           a.pad_off, a.n_pad, rho, a.F);
   return cudaGetLastError();
 }
 
@@ -1536,21 +1707,31 @@ static cudaError_t project_with(const ygs_plan* p, const CUtensorMap& wmap, cuda
 
 cudaError_t tc_project(const ygs_plan* p, cudaStream_t s) { return project_with(p, p->tc_map_ut, s); }
 
-cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
-  if (p->tc_emu) return emu_scan(p, s);
-  const int P = p->tc_scan_P;
+static ScanFfArgs scan_ff_args(const ygs_plan* p) {
   const float neg_gh = (float)(-p->G);
   const float2 neg_g = make_float2(neg_gh, (float)(-p->G - (double)neg_gh));
-  scan_ff_kernel<<<(p->tc_k_pad + kScanCols - 1) / kScanCols, kScanThreads, 0, s>>>(
-      p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, P, p->tc_pc_l, p->tc_part, p->tc_radff, p->tc_cp,
-      p->tc_B, p->tc_M, p->tc_ms, p->tc_nsl, p->tc_fp16 ? 0 : (p->tc_tf32 ? 2 : 1), neg_g, p->tc_mono,
-      p->tc_fp16 ? p->tc_eu : nullptr,
-      p->tc_fp16 ? p->tc_mpart : nullptr);
+  return ScanFfArgs{p->n_r, p->tc_k_pad, p->l_max, p->tc_S, p->tc_scan_chunk, p->tc_scan_P, p->tc_pc_l, p->tc_part,
+                    p->tc_radff, p->tc_cp, p->tc_B, p->tc_M, p->tc_ms, p->tc_nsl,
+                    p->tc_fp16 ? 0 : (p->tc_tf32 ? 2 : 1), neg_g, p->tc_mono, p->tc_fp16 ? p->tc_eu : nullptr,
+                    p->tc_fp16 ? p->tc_mpart : nullptr};
+}
+static int scan_ff_blocks(const ygs_plan* p) { return (p->tc_k_pad + kScanCols - 1) / kScanCols; }
+static SliceM16Args slice_m16_args(const ygs_plan* p) {
+  return SliceM16Args{p->n_r, p->tc_k_pad, p->tc_M, 0, reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eq,
+                      p->tc_mono, p->tc_sc};
+}
+
+cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
+  if (p->tc_emu) return emu_scan(p, s);
+  const ScanFfArgs a = scan_ff_args(p);
+  scan_ff_kernel<<<scan_ff_blocks(p), kScanThreads, 0, s>>>(a.n_r, a.K_pad, a.L, a.S, a.chunk, a.P, a.pc_l, a.part,
+                                                             a.rad, a.cp, a.B, a.M, a.Ms, a.nsl, a.write_slices,
+                                                             a.neg_G, a.mono, a.eu, a.mpart);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !p->tc_fp16) return e;
-  slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(p->n_r, p->tc_k_pad, p->tc_M, 0,
-                                                       reinterpret_cast<__half*>(p->tc_ms), p->tc_em, p->tc_eq,
-                                                       p->tc_mono, p->tc_sc);
+  const SliceM16Args m = slice_m16_args(p);
+  slice_m16_kernel<<<p->n_r, kSliceM16Threads, 0, s>>>(m.n_r, m.K_pad, m.M, m.keep_mono, m.Ms, m.em, m.q_exp, m.mono,
+                                                       m.sc);
   return cudaGetLastError();
 }
 
@@ -1677,21 +1858,115 @@ ygs_status tc_batch_build(TcBatch* b, const std::vector<ygs_plan*>& plans) {
       set_error(std::string("batch descriptors: ") + cudaGetErrorString(e));
       return YGS_ERR_OOM;
     }
-    b->groups.push_back(G);
     if ((e = cudaMemcpy(G.d_proj, proj.data(), pb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(G.d_synth, syn.data(), pb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(G.d_start_p, sp.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(G.d_start_s, ss.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      b->groups.push_back(G);
       set_error(std::string("batch descriptors: ") + cudaGetErrorString(e));
       return YGS_ERR_CUDA;
+    }
+    // the per-field passes (field slices, scans, M slicing), grouped the same way
+    const int n = (int)mem.size();
+    std::vector<int> gx(n), gy(n), gz(n), sx(n), one(n, 1), mx(n);
+    for (int k = 0; k < n; ++k) {
+      const dim3 d = fp16 ? field16_grid(mem[k]) : field_slices_grid(mem[k]);
+      gx[k] = (int)d.x;
+      gy[k] = (int)d.y;
+      gz[k] = (int)d.z;
+      sx[k] = scan_ff_blocks(mem[k]);
+      mx[k] = mem[k]->n_r;
+    }
+    if (emu) {
+      e = emu_batch_passes(mem, G);
+    } else if (fp16) {
+      std::vector<Field16Args> fa;
+      std::vector<ScanFfArgs> sa;
+      std::vector<SliceM16Args> ma;
+      for (ygs_plan* p : mem) {
+        fa.push_back(field16_args(p, true));
+        sa.push_back(scan_ff_args(p));
+        ma.push_back(slice_m16_args(p));
+      }
+      if ((e = upload_grouped_pass(G.field, fa.data(), sizeof(Field16Args), n, gx.data(), gy.data(), gz.data())) ==
+              cudaSuccess &&
+          (e = upload_grouped_pass(G.scan, sa.data(), sizeof(ScanFfArgs), n, sx.data(), one.data(), one.data())) ==
+              cudaSuccess)
+        e = upload_grouped_pass(G.mslice, ma.data(), sizeof(SliceM16Args), n, mx.data(), one.data(), one.data());
+    } else {
+      std::vector<ScanFfArgs> sa;
+      for (ygs_plan* p : mem) sa.push_back(scan_ff_args(p));
+      if (tf32) {
+        std::vector<FieldSlicesTf32Args> fa;
+        for (ygs_plan* p : mem) fa.push_back(field_slices_tf32_args(p));
+        e = upload_grouped_pass(G.field, fa.data(), sizeof(FieldSlicesTf32Args), n, gx.data(), gy.data(), gz.data());
+      } else {
+        std::vector<FieldSlicesArgs> fa;
+        for (ygs_plan* p : mem) fa.push_back(field_slices_args(p));
+        e = upload_grouped_pass(G.field, fa.data(), sizeof(FieldSlicesArgs), n, gx.data(), gy.data(), gz.data());
+      }
+      if (e == cudaSuccess)
+        e = upload_grouped_pass(G.scan, sa.data(), sizeof(ScanFfArgs), n, sx.data(), one.data(), one.data());
+    }
+    b->groups.push_back(G);
+    if (e != cudaSuccess) {
+      set_error(std::string("batch descriptors: ") + cudaGetErrorString(e));
+      return e == cudaErrorMemoryAllocation ? YGS_ERR_OOM : YGS_ERR_CUDA;
     }
   }
   return YGS_OK;
 }
 
+cudaError_t upload_grouped_pass(TcGroupedPass& P, const void* args, size_t arg_bytes, int n, const int* gx,
+                                const int* gy, const int* gz) {
+  std::vector<tc::GroupDims> dims(n);
+  int start = 0;
+  for (int k = 0; k < n; ++k) {
+    dims[k] = tc::GroupDims{gx[k], gy[k], gz[k], start};
+    start += gx[k] * gy[k] * gz[k];
+  }
+  P.blocks = start;
+  cudaError_t e;
+  if ((e = dev_malloc(&P.d_args, std::max<size_t>(16, arg_bytes * n))) != cudaSuccess) return e;
+  if ((e = dev_malloc(&P.d_dims, std::max<size_t>(16, sizeof(tc::GroupDims) * n))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(P.d_args, args, arg_bytes * n, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+  return cudaMemcpy(P.d_dims, dims.data(), sizeof(tc::GroupDims) * n, cudaMemcpyHostToDevice);
+}
+
+cudaError_t tc_batch_field(const TcBatchGroup& G, const double* const* rho, cudaStream_t s) {
+  if (G.emu) return emu_batch_field(G, rho, s);
+  tc::RhoList list{};
+  const int n = (int)G.members.size();
+  for (int k = 0; k < n; ++k) list.p[k] = rho[k];
+  const tc::GroupDims* dims = static_cast<const tc::GroupDims*>(G.field.d_dims);
+  if (G.fp16)
+    field16_kernel_group<<<G.field.blocks, kF16Threads, 0, s>>>(static_cast<const Field16Args*>(G.field.d_args), dims,
+                                                                n, list);
+  else if (G.tf32)
+    field_slices_tf32_kernel_group<<<G.field.blocks, kFieldSlicesThreads, 0, s>>>(
+        static_cast<const FieldSlicesTf32Args*>(G.field.d_args), dims, n, list);
+  else
+    field_slices_kernel_group<<<G.field.blocks, kFieldSlicesThreads, 0, s>>>(
+        static_cast<const FieldSlicesArgs*>(G.field.d_args), dims, n, list);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_batch_scan(const TcBatchGroup& G, cudaStream_t s) {
+  if (G.emu) return emu_batch_scan(G, s);
+  const int n = (int)G.members.size();
+  scan_ff_kernel_group<<<G.scan.blocks, kScanThreads, 0, s>>>(static_cast<const ScanFfArgs*>(G.scan.d_args),
+                                                              static_cast<const tc::GroupDims*>(G.scan.d_dims), n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !G.fp16) return e;
+  slice_m16_kernel_group<<<G.mslice.blocks, kSliceM16Threads, 0, s>>>(
+      static_cast<const SliceM16Args*>(G.mslice.d_args), static_cast<const tc::GroupDims*>(G.mslice.d_dims), n);
+  return cudaGetLastError();
+}
+
 void tc_batch_free(TcBatch* b) {
   for (TcBatchGroup& G : b->groups) {
-    void* bufs[] = {G.d_proj, G.d_synth, G.d_start_p, G.d_start_s};
+    void* bufs[] = {G.d_proj,       G.d_synth,     G.d_start_p,    G.d_start_s,     G.field.d_args,
+                    G.field.d_dims, G.scan.d_args, G.scan.d_dims, G.mslice.d_args, G.mslice.d_dims};
     for (void* q : bufs)
       if (q) cudaFree(q);
   }

@@ -406,5 +406,39 @@ __device__ __forceinline__ void ff_to_bf16x3(float hi, float lo, __nv_bfloat16& 
   s2 = __float2bfloat16_rn(r2);
 }
 
+// ---- grouped launches of per-field kernels (batches) -----------------------
+// A kernel body takes its block indices as a VBlock: a plain launch passes its
+// own; a grouped launch runs the blocks of several problems (one per field
+// of a batch) in one grid, problem k owning the flat blocks [start, start +
+// gx gy gz) of GroupDims k, and hands each block its problem's indices.
+struct VBlock {
+  int x, y, z, gx;
+};
+__device__ __forceinline__ VBlock vblock_self() {
+  return VBlock{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x};
+}
+struct GroupDims {
+  int gx, gy, gz, start;
+};
+constexpr int kMaxGroupFields = 128;  // problems per grouped launch
+struct RhoList {                      // the fields of a grouped launch
+  const double* p[kMaxGroupFields];
+};
+// The problem of flat block b (the last with start <= b) and b's indices in it.
+__device__ __forceinline__ int locate_block(const GroupDims* __restrict__ dims, int n, int b, VBlock& vb) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (dims[mid].start <= b) lo = mid; else hi = mid - 1;
+  }
+  const GroupDims d = dims[lo];
+  const int local = b - d.start;
+  vb.x = local % d.gx;
+  vb.y = (local / d.gx) % d.gy;
+  vb.z = local / (d.gx * d.gy);
+  vb.gx = d.gx;
+  return lo;
+}
+
 }  // namespace tc
 }  // namespace ygs

@@ -94,11 +94,11 @@ def test_grouped_batch_equals_per_field(cuda):
     plans, rhos = _uneven_fields(cuda)
     ref = [ygs_solve(p, r).clone() for p, r in zip(plans, rhos)]
     with Batch(plans) as b:
-        # 7 fields: field slices + one scan (+ M slicing for FP16 and EMU) per
-        # split field, 2 grouped launches for each of the five operand kinds
-        # (FP16 two-slice, BF16 two-slice, BF16 three-slice, TF32 two-slice,
-        # EMU six-slice), 3 for the FP64 field
-        assert b.launches == 2 * 3 + 2 + 2 + 2 + 3 + 2 * 5 + 3
+        # 7 fields in five operand kinds (FP16 two-slice, BF16 two-slice, BF16
+        # three-slice, TF32 two-slice, EMU six-slice): per kind one grouped
+        # launch each for the field slices, the projection, the scans (+ the M
+        # slicing for FP16 and EMU) and the synthesis; 3 for the FP64 field
+        assert b.launches == 5 + 4 + 4 + 4 + 5 + 3
         for _ in range(2):
             outs = b.solve(rhos)
             torch.cuda.synchronize()
