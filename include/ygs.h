@@ -111,11 +111,17 @@ typedef enum {
 
 enum {
   YGS_FLAG_NO_SYMMETRY = 1, /* never use the Yin-Yang sign symmetry of Sect. 4.2 */
-  YGS_FLAG_AUTOTUNE = 2     /* split precisions: ygs_create times the projection with several
+  YGS_FLAG_AUTOTUNE = 2,    /* split precisions: ygs_create times the projection with several
                                split-K counts (angular chunks per shell tile) on this GPU and
                                keeps the fastest (a few ms more at create; results then differ
                                from an untuned plan's within the precision's bound, as the
                                chunk sums are added in another grouping) */
+  YGS_FLAG_CTA_PAIRS = 4    /* split precisions but YGS_FP64_EMU: run the synthesis on pairs of
+                               CTAs that share each MMA (cta_group::2, 256 cells per tile, each
+                               CTA staging half of the tile's shells of M) instead of one CTA
+                               per 128-cell tile.  Bitwise the same results; on GB300 at the
+                               1-degree, 400-shell grid 20% slower (the synthesis is held by its
+                               epilogue, not by operand traffic), so it is off by default */
 };
 
 /* Grid descriptor.  All arrays are HOST memory, read during ygs_create only. */
@@ -168,6 +174,8 @@ typedef struct {
                              plans; ygs_solve_static always runs those kernels) */
   long long static_scratch_bytes; /* scratch ygs_solve_static needs for this plan:
                                      (fp64_split_k + 2) * n_r * K * 8 */
+  int cta_pairs;          /* 1: the synthesis runs on CTA pairs (YGS_FLAG_CTA_PAIRS on a split
+                             plan other than YGS_FP64_EMU, and the GPU can co-schedule them) */
 } ygs_info;
 
 /* Builds the plan: validates the descriptor, allocates device memory on

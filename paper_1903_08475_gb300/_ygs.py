@@ -25,6 +25,7 @@ PRECISION = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp16x3": 3, "fp64tc": 4, "fp3
 EVAL = {"upper_vertex": 0, "cell_centre": 1}
 FLAG_NO_SYMMETRY = 1
 FLAG_AUTOTUNE = 2
+FLAG_CTA_PAIRS = 4
 
 EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_host", "ygs_solve_host_many",
            "ygs_solve_batched",
@@ -56,7 +57,7 @@ class Info(ctypes.Structure):
                 ("n_ang", ctypes.c_longlong), ("n_cells", ctypes.c_longlong), ("precision", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("split_k", ctypes.c_int), ("weight_bytes", ctypes.c_longlong),
                 ("work_bytes", ctypes.c_longlong), ("fp64_split_k", ctypes.c_int),
-                ("static_scratch_bytes", ctypes.c_longlong)]
+                ("static_scratch_bytes", ctypes.c_longlong), ("cta_pairs", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -139,7 +140,7 @@ class Plan:
     """A grid plan (``ygs_create``): FP64 weights live on the device until close()."""
 
     def __init__(self, grid, precision: str = "fp64", device: int = 0, symmetry: bool = True,
-                 autotune: bool = False):
+                 autotune: bool = False, cta_pairs: bool = False):
         L = load_library()
         self._keep = keep = {
             "edges": np.ascontiguousarray(grid.edges, dtype=np.float64),
@@ -156,7 +157,8 @@ class Plan:
         d = _Desc(grid.n_r, keep["edges"].ctypes.data_as(_dp), grid.n_patch, keep["euler"].ctypes.data_as(_dp),
                   keep["nt"].ctypes.data_as(_ip), keep["nf"].ctypes.data_as(_ip), keep["tr"].ctypes.data_as(_dp),
                   keep["pr"].ctypes.data_as(_dp), keep["w"].ctypes.data_as(_dp), grid.l_max, grid.G, grid.eval,
-                  PRECISION[precision], (0 if symmetry else FLAG_NO_SYMMETRY) | (FLAG_AUTOTUNE if autotune else 0),
+                  PRECISION[precision], ((0 if symmetry else FLAG_NO_SYMMETRY) | (FLAG_AUTOTUNE if autotune else 0)
+                   | (FLAG_CTA_PAIRS if cta_pairs else 0)),
                   keep["kind"].ctypes.data_as(_ip) if "kind" in keep else None)
         h = ctypes.c_void_p()
         _check(L.ygs_create(ctypes.byref(d), device, ctypes.byref(h)))

@@ -162,7 +162,7 @@ ygs_status validate_desc(const ygs_desc* d) {
   if (!finite(d->G)) return fail(YGS_ERR_INVALID_ARG, "G must be finite");
   if (d->eval != YGS_EVAL_UPPER_VERTEX && d->eval != YGS_EVAL_CELL_CENTRE) return fail(YGS_ERR_INVALID_ARG, "bad eval");
   if (d->precision < YGS_FP64 || d->precision > YGS_FP64_EMU) return fail(YGS_ERR_INVALID_ARG, "bad precision");
-  if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
+  if (d->flags & ~(YGS_FLAG_NO_SYMMETRY | YGS_FLAG_AUTOTUNE | YGS_FLAG_CTA_PAIRS)) return fail(YGS_ERR_INVALID_ARG, "unknown flag bits");
   if ((long long)d->n_r * total > (1LL << 40)) return fail(YGS_ERR_INVALID_ARG, "field too large");
   return YGS_OK;
 }
@@ -430,6 +430,7 @@ ygs_status ygs_get_info(const ygs_plan* p, ygs_info* info) {
   info->work_bytes = p->work_bytes;
   info->fp64_split_k = p->S;
   info->static_scratch_bytes = static_scratch_bytes(p);
+  info->cta_pairs = p->tc_pairs > 0 ? 1 : 0;
   return YGS_OK;
 }
 

@@ -86,6 +86,7 @@ struct ygs_plan {
   int tc_n_full = 0;         // full shell tiles of the synthesis
   int tc_n_tail = 0;         // width of the tail shell tile (0: none)
   int tc_sms = 0;            // CTAs of the persistent contraction kernels
+  int tc_pairs = 0;          // >0: the synthesis runs on CTA pairs, at most this many clusters of two
   int tc_k_even = 0, tc_k_pad = 0;
   long long tc_n_pad = 0;
   std::vector<long long> tc_pad_off;
@@ -125,6 +126,7 @@ struct ygs_plan {
   int tc_eus = 0;             // U (all rows)
   float2 *tc_Mbar = nullptr, *tc_Bbar = nullptr;  // float-float (EMU: n_r K_pad doubles each)
   CUtensorMap tc_map_qt, tc_map_us;
+  CUtensorMap tc_map_m2, tc_map_m2_tail;  // M slices in boxes of half a synthesis tile's shells (CTA pairs)
 };
 
 namespace ygs {

@@ -877,26 +877,50 @@ __device__ __forceinline__ void carry_scan(const float2 (&sm)[4][kMaxP][kCols], 
 // order (TwoSum), as float-float; FP16 plans' partials are unscaled by the
 // column's exponent first, and the monopole column of a forward FP16 solve
 // takes the field pass's exact chunk sums instead.
-__device__ __forceinline__ float2 sum_chunks(const float2* __restrict__ part, long long plane, int S, int i, int K_pad,
-                                             int pc, int escale, const float2* __restrict__ mp, int n_r) {
-  float hh = 0.0f, ll = 0.0f;
-  for (int z = 0; z < S; ++z) {
-    float2 v;
-    if (mp) {
-      v = mp[(long long)z * n_r + i];
-    } else {
-      v = part[z * plane + (long long)i * K_pad + pc];
-      if (escale) {
-        v.x = tc::mul_pow2f(v.x, -escale);
-        v.y = tc::mul_pow2f(v.y, -escale);
+// ... for the shells ib .. ib + G - 1 below i1 (zero for the others), with
+// the loads of kScanZ chunks of every shell of the group issued together, so
+// that a thread waits for one round trip per kScanZ chunks instead of one per
+// chunk (each shell's sum keeps its z order and operations).
+#ifndef YGS_SCAN_Z
+#define YGS_SCAN_Z 1  // chunks per round of loads (more spill at the 64-register cap)
+#endif
+constexpr int kScanZ = YGS_SCAN_Z;
+template <int G>
+__device__ __forceinline__ void sum_chunks_group(const float2* __restrict__ part, long long plane, int S, int ib,
+                                                 int i1, int K_pad, int pc, int escale,
+                                                 const float2* __restrict__ mp, int n_r, float2 (&out)[G]) {
+  float hh[G], ll[G];
+#pragma unroll
+  for (int k = 0; k < G; ++k) hh[k] = ll[k] = 0.0f;
+  for (int z0 = 0; z0 < S; z0 += kScanZ) {
+    float2 v[kScanZ][G];
+#pragma unroll
+    for (int zz = 0; zz < kScanZ; ++zz)
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const int z = z0 + zz, i = ib + k;
+        v[zz][k] = make_float2(0.0f, 0.0f);
+        if (z < S && i < i1) v[zz][k] = mp ? mp[(long long)z * n_r + i] : part[z * plane + (long long)i * K_pad + pc];
       }
-    }
-    float s, e;
-    tc::two_sum(hh, v.x, s, e);
-    hh = s;
-    ll += e + v.y;
+#pragma unroll
+    for (int zz = 0; zz < kScanZ; ++zz)
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        if (z0 + zz < S) {
+          float2 w = v[zz][k];
+          if (!mp && escale) {
+            w.x = tc::mul_pow2f(w.x, -escale);
+            w.y = tc::mul_pow2f(w.y, -escale);
+          }
+          float s, e;
+          tc::two_sum(hh[k], w.x, s, e);
+          hh[k] = s;
+          ll[k] += e + w.y;
+        }
+      }
   }
-  return tc::ff_renorm(hh, ll);
+#pragma unroll
+  for (int k = 0; k < G; ++k) out[k] = ib + k < i1 ? tc::ff_renorm(hh[k], ll[k]) : make_float2(0.0f, 0.0f);
 }
 
 __device__ __forceinline__ void ff_slices(float2 v, int nsl, __nv_bfloat16 (&sl)[3]) {
@@ -922,6 +946,9 @@ __device__ __forceinline__ void ff_slices(float2 v, int nsl, __nv_bfloat16 (&sl)
 #endif
 constexpr int kScanCols = YGS_SCAN_COLS, kScanMaxP = YGS_SCAN_MAXP, kScanThreads = kScanCols * kScanMaxP;
 constexpr int kScanGroup = 4;  // shells whose loads a thread issues together
+// CTAs of a scan kernel resident per SM (4 of 256 threads at <= 64 registers
+// hold K_pad / kScanCols = 576 CTAs of the 1-degree grid in one wave)
+constexpr int kScanMinBlocks = 1024 / kScanThreads >= 1 ? 1024 / kScanThreads : 1;
 static_assert(kScanCols >= 1 && kScanThreads <= 1024 && kScanThreads % 32 == 0 && kScanMaxP >= 32,
               "scan: a CTA of whole warps, at most 1024 threads, at least 32 chunks per column");
 
@@ -953,10 +980,7 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
       const int escale = (eu && !exact_mono) ? eu[pc] : 0;
       for (int ib = i0; ib < i1; ib += kScanGroup) {
         float2 bg[kScanGroup];
-#pragma unroll
-        for (int k = 0; k < kScanGroup; ++k)
-          bg[k] = ib + k < i1 ? sum_chunks(part, plane, S, ib + k, K_pad, pc, escale, exact_mono ? mpart : nullptr, n_r)
-                              : zero;
+        sum_chunks_group<kScanGroup>(part, plane, S, ib, i1, K_pad, pc, escale, exact_mono ? mpart : nullptr, n_r, bg);
 #pragma unroll
         for (int k = 0; k < kScanGroup; ++k) {
           if (ib + k < i1) {
@@ -1061,7 +1085,7 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
     emit(i, tc::ff_add(M[(long long)i * K_pad + pc], I));
   }
 }
-__global__ void __launch_bounds__(kScanThreads) scan_ff_kernel(
+__global__ void __launch_bounds__(kScanThreads, kScanMinBlocks) scan_ff_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
     const float2* __restrict__ rad, const float2* __restrict__ cp, float2* __restrict__ B, float2* __restrict__ M,
     __nv_bfloat16* __restrict__ Ms, int nsl, int write_slices, float2 neg_G, float2* __restrict__ mono,
@@ -1093,7 +1117,7 @@ struct ScanFfArgs {
 };
 
 // scan_ff_kernel over the problems of a batch, one block per problem block.
-__global__ void __launch_bounds__(kScanThreads) scan_ff_kernel_group(const ScanFfArgs* __restrict__ probs,
+__global__ void __launch_bounds__(kScanThreads, kScanMinBlocks) scan_ff_kernel_group(const ScanFfArgs* __restrict__ probs,
     const tc::GroupDims* __restrict__ dims, int n) {
   tc::VBlock vb;
   const int k = tc::locate_block(dims, n, blockIdx.x, vb);
@@ -1111,7 +1135,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_ff_kernel_group(const ScanF
 // [1] the product of its fout factors (upward), [2] X at its start and [3] the
 // product of its fin factors (downward), all with zero carry, are composed by
 // the same carry scan, in float-float like the forward scan.
-__global__ void __launch_bounds__(kScanThreads) scan_adj_ff_kernel(
+__global__ void __launch_bounds__(kScanThreads, kScanMinBlocks) scan_adj_ff_kernel(
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
     const float2* __restrict__ rad, float2* __restrict__ Mbar, float2* __restrict__ Bbar,
     __nv_bfloat16* __restrict__ Bs, int nsl, int write_slices, const int* __restrict__ ew) {
@@ -1137,9 +1161,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_adj_ff_kernel(
       const int escale = ew ? ew[pc] : 0;  // FP16 plans: Q^T's row scale
       for (int ib = i0; ib < i1; ib += kScanGroup) {
         float2 gg[kScanGroup];
-#pragma unroll
-        for (int k = 0; k < kScanGroup; ++k)
-          gg[k] = ib + k < i1 ? sum_chunks(part, plane, S, ib + k, K_pad, pc, escale, nullptr, n_r) : zero;
+        sum_chunks_group<kScanGroup>(part, plane, S, ib, i1, K_pad, pc, escale, nullptr, n_r, gg);
 #pragma unroll
         for (int k = 0; k < kScanGroup; ++k) {
           if (ib + k < i1) {
@@ -1288,6 +1310,68 @@ cudaError_t dispatch_gemm(int nsl, bool scale, bool tf, int grid, const CUtensor
     return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// The synthesis on CTA pairs: clusters of two CTAs, each pair one 256-cell
+// tile per step of its walk (B's maps with half-tile boxes).
+template <int NSL, bool TF>
+cudaError_t launch_synth_pair(int grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& bt,
+                              const TcArgs& args, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)tc::TileShape<tc::kSynthesize>::THREADS);
+  cfg.dynamicSmemBytes = TcCfg<NSL, tc::kSynthesize, false, 2>::SMEM;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, tc::tc_gemm_kernel<NSL, tc::kSynthesize, false, TF, false, 2>, a, b, bt, args);
+}
+template <int NSL, bool TF>
+const void* synth_pair_fn() {
+  return (const void*)tc::tc_gemm_kernel<NSL, tc::kSynthesize, false, TF, false, 2>;
+}
+cudaError_t dispatch_synth_pair(int nsl, bool tf, int grid, const CUtensorMap& a, const CUtensorMap& b,
+                                const CUtensorMap& bt, const TcArgs& args, cudaStream_t s) {
+  if (grid % 2 != 0) return cudaErrorInvalidValue;
+  if (nsl == 3 && !tf) return launch_synth_pair<3, false>(grid, a, b, bt, args, s);
+  if (nsl == 2 && tf) return launch_synth_pair<2, true>(grid, a, b, bt, args, s);
+  if (nsl == 2) return launch_synth_pair<2, false>(grid, a, b, bt, args, s);
+  return cudaErrorInvalidValue;
+}
+// Shared memory of the pair kernel of a plan's operand kind, and how many of
+// its clusters fit on the GPU at once (0: none, then the single-CTA kernel runs).
+cudaError_t setup_synth_pair(int nsl, bool tf, int sms, int& clusters) {
+  clusters = 0;
+  const void* fn = nullptr;
+  int smem = 0;
+  if (nsl == 3 && !tf) {
+    fn = synth_pair_fn<3, false>();
+    smem = TcCfg<3, tc::kSynthesize, false, 2>::SMEM;
+  } else if (nsl == 2) {
+    fn = tf ? synth_pair_fn<2, true>() : synth_pair_fn<2, false>();
+    smem = TcCfg<2, tc::kSynthesize, false, 2>::SMEM;
+  } else {
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * std::max(1, sms / 2)));
+  cfg.blockDim = dim3((unsigned)tc::TileShape<tc::kSynthesize>::THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
 }
 
 template <int MODE>
@@ -1553,6 +1637,18 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     TC_TRY(a1);
     TC_TRY(a2);
   }
+  // the synthesis on CTA pairs: M slices in boxes of half a tile's shells
+  p->tc_pairs = 0;
+  if (!p->tc_emu && (p->flags & YGS_FLAG_CTA_PAIRS) && N % 16 == 0 && Nt % 16 == 0) {
+    if (!make_map(&p->tc_map_m2, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N / 2, kind) ||
+        !make_map(&p->tc_map_m2_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt / 2, kind)) {
+      set_error("cuTensorMapEncodeTiled failed or is unavailable");
+      return YGS_ERR_CUDA;
+    }
+    int clusters = 0;
+    TC_TRY(setup_synth_pair(nsl, p->tc_tf32 != 0, p->tc_sms, clusters));
+    p->tc_pairs = clusters;
+  }
   if (cand.size() > 1) {
     // time the projection of a zero field with each candidate; keep the fastest
     cudaEvent_t e0, e1;
@@ -1735,7 +1831,8 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono) {
+// pair: tiles of 2 x 128 cells for the CTA-pair kernel.
+static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono, bool pair = false) {
   a = TcArgs{};
   fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
   // the forward synthesis excludes the monopole (added exactly) and may flush less
@@ -1752,7 +1849,8 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
     a.a_row0[g] = row;
     a.tile0[g] = t;
     row += p->nang[g];
-    t += (int)((p->nang[g] + tc::BM - 1) / tc::BM) * a.n_tiles;  // cell tiles x shell tiles, shells fastest
+    const int cells = tc::BM * (pair ? 2 : 1);
+    t += (int)((p->nang[g] + cells - 1) / cells) * a.n_tiles;  // cell tiles x shell tiles, shells fastest
   }
   a.tile0[p->n_wpatch] = t;
   a.total_tiles = t;
@@ -1765,7 +1863,11 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
 static cudaError_t synthesize_with(const ygs_plan* p, const CUtensorMap& wmap, double* phi, const float2* mono,
                                    cudaStream_t s) {
   TcArgs a;
-  synth_args(p, a, phi, mono);
+  const bool pair = p->tc_pairs > 0 && !p->tc_emu;
+  synth_args(p, a, phi, mono, pair);
+  if (pair)
+    return dispatch_synth_pair(p->tc_nsl, p->tc_tf32 != 0, 2 * std::min(a.total_tiles, p->tc_pairs), wmap,
+                               p->tc_map_m2, p->tc_map_m2_tail, a, s);
   const int grid = std::min(a.total_tiles, p->tc_sms);
   if (p->tc_emu) return emu_dispatch_gemm(tc::kSynthesize, grid, wmap, p->tc_map_m, p->tc_map_m_tail, a, s);
   return dispatch_gemm<tc::kSynthesize>(p->tc_nsl, false, p->tc_tf32 != 0, grid, wmap, p->tc_map_m,

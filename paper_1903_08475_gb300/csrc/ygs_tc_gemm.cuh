@@ -97,6 +97,8 @@ __device__ __forceinline__ void emu_pair(int p, int& s, int& t) {
   t = p - first;
 }
 
+enum Mode { kProject = 0, kSynthesize = 1 };
+
 template <int MODE, bool EMU = false>
 struct TileShape {
   // shells per full tile; columns per epilogue warp
@@ -115,7 +117,6 @@ struct TileShape {
   static_assert(NBUF >= 2, "TMEM holds 512 columns: need two accumulators");
 };
 
-enum Mode { kProject = 0, kSynthesize = 1 };
 constexpr int kGroupKb = 2;  // k-blocks per exponent group of the FP16 field slices
 
 struct TcArgs {
@@ -168,14 +169,19 @@ struct TcArgs {
   const float4* sc;
 };
 
-template <int NSL, int MODE, bool EMU = false>
+// CG = 2: a synthesis tile of 256 cells computed by a pair of CTAs (a
+// cluster of two) with cta_group::2 MMAs issued by the even CTA; each CTA
+// stages its own 128 cells of A and half of the tile's shells of B.
+template <int NSL, int MODE, bool EMU = false, int CG = 1>
 struct TcCfg {
   static_assert(!EMU || NSL == 1, "EMU stages hold one slice of each operand");
+  static_assert(CG == 1 || (CG == 2 && MODE == kSynthesize && !EMU), "CTA pairs: the split synthesis only");
   static constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
+  static_assert((NMAX / CG) % 8 == 0, "a CTA's share of B is whole 8-row swizzle atoms");
   static constexpr int NPROD = (NSL == 3) ? 6 : (NSL == 2 ? 3 : 1);
   static constexpr int KBS = EMU ? kEmuStageKb : 1;  // k-blocks per stage
   static constexpr int A_SLICE = BM * BK * 2;      // one k-block of one slice (a 128-byte-swizzled block)
-  static constexpr int B_SLICE = NMAX * BK * 2;
+  static constexpr int B_SLICE = NMAX / CG * BK * 2;
   // [A: KBS k-blocks x NSL slices | B: the same]
   static constexpr int STAGE = KBS * NSL * (A_SLICE + B_SLICE);
 #ifdef YGS_TC_STAGES
@@ -244,8 +250,10 @@ struct Tile {
   int g_patch, m_loc, z;
 };
 
-template <int MODE, int KE, bool EMU = false>
-__device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
+// CG = 2: t is a pair tile of 2 x BM cells, of which this CTA (rank) takes
+// the half `rank`.
+template <int MODE, int KE, bool EMU = false, int CG = 1>
+__device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t, int rank = 0) {
   constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
   Tile T;
   int n;
@@ -271,7 +279,7 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t) {
     int g = 0;
     while (g + 1 < a.n_wpatch && a.tile0[g + 1] <= t) ++g;
     const int rem = t - a.tile0[g];
-    T.m_loc = rem / a.n_tiles;
+    T.m_loc = CG * (rem / a.n_tiles) + rank;
     n = rem % a.n_tiles;
     T.g_patch = g;
     T.a_row0 = (int)(a.a_row0[g] + (long long)T.m_loc * BM);
@@ -339,13 +347,20 @@ struct GroupSrc {  // tiles of several problems concatenated: problem k owns [st
 // registers.  EMU: one slice of each operand per stage, the kEmuProducts
 // products one after another over the whole k range of a segment (each
 // sweep its own flush groups), flushed by a renormalised float-float add.
-template <int NSL, int MODE, bool SCALE, bool TF, bool EMU, class Src>
+//
+// CG = 2 (CTA pairs, synthesis): both CTAs walk the same list of pair tiles;
+// each loads its 128 cells of A and its half of B, the even CTA's TMA warp
+// expects the bytes of both on its `full` barriers (the odd CTA's copies
+// complete there), the even CTA issues every MMA and commits to the barriers
+// of both CTAs, and the epilogue warps of both drain their own TMEM and
+// release it on the even CTA's `tempty` barriers.
+template <int NSL, int MODE, bool SCALE, bool TF, bool EMU, int CG, class Src>
 __device__ __forceinline__ void gemm_body(const Src& src) {
   static_assert(!SCALE || MODE == kProject, "only the projection scales its flushes");
   static_assert(!(TF && SCALE), "TF32 operands need no scaling");
   static_assert(!(TF && EMU), "EMU slices are BF16");
   constexpr int KE = KElems<TF>::KE;
-  using C = TcCfg<NSL, MODE, EMU>;
+  using C = TcCfg<NSL, MODE, EMU, CG>;
   constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
   constexpr int NH = TileShape<MODE, EMU>::NH;
   constexpr int kEpiWarps = TileShape<MODE, EMU>::EPI_WARPS;
@@ -365,6 +380,9 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   static_assert((2 * C::STAGES + 2 * C::NBUF + 2) * 8 + 8 <= C::FAC_OFF, "barriers fit below the factor slots");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // this CTA's half of a pair tile; the first tile and the stride of its walk
+  const int rank = CG == 2 ? (int)cluster_ctarank() : 0;
+  const int unit0 = blockIdx.x / CG, units = gridDim.x / CG;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -373,18 +391,20 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
     }
     for (int b = 0; b < C::NBUF; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], kEpiWarps);
+      mbar_init(&tempty[b], CG * kEpiWarps);
     }
     mbar_init(mma_done, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 0) {
-    tmem_alloc(tmem_slot, 512);
-    tmem_relinquish();
+    tmem_alloc<CG>(tmem_slot, 512);
+    tmem_relinquish<CG>();
   }
   tc_fence_before();
   __syncthreads();
+  // pairs: both CTAs' barriers exist before either signals the other's
+  if constexpr (CG == 2) cluster_sync();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -394,12 +414,14 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       int issued = 0, fgroups = 0;  // k-blocks issued; factor rows issued (the ring's position)
       bool ok = true;
       int* err = nullptr;
-      for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
+      for (int t = unit0; t < src.total() && ok; t += units) {
         const TileRef R = src.locate(t);
-        const Tile T = decode_tile<MODE, KE, EMU>(*R.A, R.t);
+        const Tile T = decode_tile<MODE, KE, EMU, CG>(*R.A, R.t, rank);
         err = R.A->err;
         const CUtensorMap* mb = T.use_tail ? R.mbt : R.mb;
-        const uint32_t bytes = NSL * (C::A_SLICE + T.n_eff * BK * 2);
+        // this CTA's bytes per k-block, and its first B row (pairs: half of the tile's shells each)
+        const uint32_t bytes = NSL * (C::A_SLICE + T.n_eff / CG * BK * 2);
+        const int b_row = T.b_row0 + rank * (T.n_eff / CG);
         const float* const fac = SCALE ? R.A->fac : nullptr;
         const int flush = R.A->flush_kb;
         // segments (even and odd column blocks of the synthesis), then the
@@ -420,7 +442,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
               uint8_t* sB = sA + C::KBS * NSL * C::A_SLICE;
               const int nks = min(C::KBS, nkb - kb);          // k-blocks in this stage
               const bool fac_now = SCALE && kb % flush == 0;  // first k-block of a flush group
-              mbar_arrive_expect_tx(&full[stage], nks * bytes + (fac_now ? NMAX * 4 : 0));
+              if (rank == 0) mbar_arrive_expect_tx(&full[stage], CG * nks * bytes + (fac_now ? NMAX * 4 : 0));
               if (fac_now) {
                 const int G = (T.kstart / KE + kb0 + kb) / GKB;
                 const float* src = fac + (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
@@ -433,12 +455,19 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
                   tma_load_3d(sA + j * C::A_SLICE, R.ma, &full[stage], kx + j * KE, T.a_row0, ps);
                   tma_load_3d(sB + j * C::B_SLICE, mb, &full[stage], kx + j * KE, T.b_row0, T.b_plane0 + pt);
                 }
+              } else if (CG == 2) {
+                const uint32_t bar0 = mapa_shared(&full[stage], 0);  // the even CTA's barrier
+#pragma unroll
+                for (int s = 0; s < NSL; ++s) tma_load_3d_pair(sA + s * C::A_SLICE, R.ma, bar0, kx, T.a_row0, s);
+#pragma unroll
+                for (int s = 0; s < NSL; ++s)
+                  tma_load_3d_pair(sB + s * C::B_SLICE, mb, bar0, kx, b_row, T.b_plane0 + s);
               } else {
 #pragma unroll
                 for (int s = 0; s < NSL; ++s) tma_load_3d(sA + s * C::A_SLICE, R.ma, &full[stage], kx, T.a_row0, s);
 #pragma unroll
                 for (int s = 0; s < NSL; ++s)
-                  tma_load_3d(sB + s * C::B_SLICE, mb, &full[stage], kx, T.b_row0, T.b_plane0 + s);
+                  tma_load_3d(sB + s * C::B_SLICE, mb, &full[stage], kx, b_row, T.b_plane0 + s);
               }
               ++issued;
             }
@@ -450,27 +479,35 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
         *abort_flag = 1;
       }
       // every issued copy has landed before shared memory can be released
-      for (int d = max(0, issued - C::STAGES); d < issued; ++d)
-        mbar_wait_final(&full[d % C::STAGES], (d / C::STAGES) & 1);
+      // (the odd CTA of a pair: its copies complete on the even CTA's
+      // barriers, and the MMAs that read them have finished when its own
+      // `empty` barriers complete)
+      for (int d = max(0, issued - C::STAGES); d < issued; ++d) {
+        if (rank == 0)
+          mbar_wait_final(&full[d % C::STAGES], (d / C::STAGES) & 1);
+        else
+          mbar_wait_final(&empty[d % C::STAGES], (d / C::STAGES) & 1);
+      }
     }
   } else if (warp == 1) {
-    // ================= MMA issuer =================
-    if (lane == 0) {
+    // ================= MMA issuer (pairs: in the even CTA) =================
+    if (lane == 0 && rank == 0) {
       int consumed = 0, gglob = 0;
       bool ok = true;
       int* err = nullptr;
-      for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
+      for (int t = unit0; t < src.total() && ok; t += units) {
         const TileRef R = src.locate(t);
-        const Tile T = decode_tile<MODE, KE, EMU>(*R.A, R.t);
+        const Tile T = decode_tile<MODE, KE, EMU, CG>(*R.A, R.t, rank);
         err = R.A->err;
-        const uint32_t idesc = idesc_f16(BM, T.n_eff, R.A->ab_fmt);
+        const uint32_t idesc = idesc_f16(BM * CG, T.n_eff, R.A->ab_fmt);
         const int flush = R.A->flush_kb;  // k-blocks per accumulator flush, per problem
         for (int sp = 0; sp < 2 * NPASS && ok; ++sp) {
           const int seg = sp / NPASS;
           const int nkb = seg ? T.seg_kb1 : T.seg_kb0;
           for (int kg = 0; kg < nkb && ok; kg += flush, ++gglob) {
             const int buf = gglob % C::NBUF, use = gglob / C::NBUF;
-            if (use >= 1 && !mbar_wait(&tempty[buf], (use - 1) & 1, abort_flag)) {
+            if (use >= 1 && !(CG == 2 ? mbar_wait_cluster(&tempty[buf], (use - 1) & 1, abort_flag)
+                                      : mbar_wait(&tempty[buf], (use - 1) & 1, abort_flag))) {
               ok = false;
               break;
             }
@@ -500,11 +537,11 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
                   for (int kk = 0; kk < BK / 16; ++kk) {
                     const uint64_t ad = a0 + (uint64_t)((j * C::A_SLICE + kk * 32) >> 4);
                     const uint64_t bd = b0 + (uint64_t)((j * C::B_SLICE + kk * 32) >> 4);
-                    umma_f16(d, ad, bd, idesc, init ? 1u : 0u);
+                    umma_f16<CG>(d, ad, bd, idesc, init ? 1u : 0u);
                     init = true;
                   }
                 }
-                umma_commit(&empty[stage]);
+                umma_commit<CG>(&empty[stage]);
                 ++consumed;
                 continue;
               }
@@ -519,16 +556,16 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
                 const uint64_t ad = a0 + (uint64_t)((prod_s(p) * C::A_SLICE + kk * 32) >> 4);
                 const uint64_t bd = b0 + (uint64_t)((prod_t(p) * C::B_SLICE + kk * 32) >> 4);
                 if (TF)
-                  umma_tf32(d, ad, bd, idesc, init ? 1u : 0u);
+                  umma_tf32<CG>(d, ad, bd, idesc, init ? 1u : 0u);
                 else
-                  umma_f16(d, ad, bd, idesc, init ? 1u : 0u);
+                  umma_f16<CG>(d, ad, bd, idesc, init ? 1u : 0u);
                 init = true;
               }
-              umma_commit(&empty[stage]);
+              umma_commit<CG>(&empty[stage]);
               ++consumed;
             }
             if (!ok) break;
-            umma_commit(&tfull[buf]);
+            umma_commit<CG>(&tfull[buf]);
           }
         }
       }
@@ -536,8 +573,11 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
         set_err(err, YGS_ERR_TIMEOUT);
         *abort_flag = 1;
       }
-      umma_commit(mma_done);
+      umma_commit<CG>(mma_done);
       mbar_wait_final(mma_done, 0);  // every issued MMA has finished before TMEM is released
+    } else if (CG == 2 && lane == 0) {
+      // the odd CTA of a pair: the even CTA's MMAs write this CTA's TMEM too
+      mbar_wait_final(mma_done, 0);
     }
   } else {
     // ================= epilogue warps kFirstEpi .. kFirstEpi + kEpiWarps - 1 =================
@@ -550,9 +590,9 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
     int gglob = 0;
     bool ok = true;
     int* err = nullptr;
-    for (int t = blockIdx.x; t < src.total() && ok; t += gridDim.x) {
+    for (int t = unit0; t < src.total() && ok; t += units) {
       const TileRef R = src.locate(t);
-      const Tile T = decode_tile<MODE, KE, EMU>(*R.A, R.t);
+      const Tile T = decode_tile<MODE, KE, EMU, CG>(*R.A, R.t, rank);
       err = R.A->err;
       const int flush = R.A->flush_kb;
       const bool active = col0 < T.n_eff;  // this warp's columns exist in the tile (warp-uniform)
@@ -613,7 +653,12 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&tempty[buf]);
+          if (lane == 0) {
+            if (CG == 2 && rank != 0)
+              mbar_arrive_cluster(mapa_shared(&tempty[buf], 0));  // the issuing CTA's barrier
+            else
+              mbar_arrive(&tempty[buf]);
+          }
         }
         if (!ok) break;
         if (EMU && MODE == kSynthesize && sp == NPASS - 1 && nseg == 2 && active) {
@@ -794,15 +839,19 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
 
   tc_fence_before();
   __syncthreads();
+  // pairs: neither CTA leaves while the other may still signal its barriers
+  if constexpr (CG == 2) cluster_sync();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 512);
+  if (warp == 0) tmem_dealloc<CG>(tmem, 512);
 }
 
 // Registers: 14 warps (448 threads), at most 128 each: a CTA's warps are
 // spread over the SM's four sub-partitions (16,384 registers each), four
 // warps on two of them, so 4 x 32 x 128 is the ceiling for one CTA per SM.
 // One problem: maps and arguments in kernel parameters.
-template <int NSL, int MODE, bool SCALE, bool TF = false, bool EMU = false>
+// CG = 2: launched in clusters of two CTAs (the grid even), B's maps with
+// boxes of half a tile's shells.
+template <int NSL, int MODE, bool SCALE, bool TF = false, bool EMU = false, int CG = 1>
 __global__ void __launch_bounds__(TileShape<MODE, EMU>::THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapBt, const __grid_constant__ TcArgs args) {
@@ -812,7 +861,7 @@ __global__ void __launch_bounds__(TileShape<MODE, EMU>::THREADS, 1)
     prefetch_tmap(&mapBt);
   }
   const SingleSrc src{&args, &mapA, &mapB, &mapBt};
-  gemm_body<NSL, MODE, SCALE, TF, EMU>(src);
+  gemm_body<NSL, MODE, SCALE, TF, EMU, CG>(src);
 }
 
 // Several problems of one operand type in one persistent launch (a batch of
@@ -823,7 +872,7 @@ __global__ void __launch_bounds__(TileShape<MODE, EMU>::THREADS, 1)
     tc_gemm_group_kernel(const TcProblem* __restrict__ probs, const int* __restrict__ start, int n, int total,
                          const __grid_constant__ TcPhiList phis) {
   const GroupSrc src{probs, start, n, total, &phis};
-  gemm_body<NSL, MODE, SCALE, TF, EMU>(src);
+  gemm_body<NSL, MODE, SCALE, TF, EMU, 1>(src);
 }
 
 }  // namespace tc
