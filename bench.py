@@ -641,6 +641,7 @@ def main():
             "gcell_per_s": value * grid.n_cells / 1e9,
             "config": {"workload": workload_name(grid.n_r), "precision": precision, "n_r": grid.n_r, "l_max": grid.l_max,
                        "cells": grid.n_cells, "symmetric": sym, "split_k": info["split_k"], "autotune": args.autotune,
+                       "synth_tile_shells": info.get("synth_tile_shells"), "cta_pairs": info.get("cta_pairs"),
                        "l2": "inputs larger than L2 (rho 160 MB, weights 436 MB)",
                        "parallelism": f"replicas{ws}"},
             "e2e": {"value": ws / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(rho.nbytes),

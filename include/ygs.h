@@ -111,11 +111,17 @@ typedef enum {
 
 enum {
   YGS_FLAG_NO_SYMMETRY = 1, /* never use the Yin-Yang sign symmetry of Sect. 4.2 */
-  YGS_FLAG_AUTOTUNE = 2,    /* split precisions: ygs_create times the projection with several
-                               split-K counts (angular chunks per shell tile) on this GPU and
-                               keeps the fastest (a few ms more at create; results then differ
-                               from an untuned plan's within the precision's bound, as the
-                               chunk sums are added in another grouping) */
+  YGS_FLAG_AUTOTUNE = 2,    /* split precisions: ygs_create times, on this GPU, the projection
+                               with several split-K counts (angular chunks per shell tile) and,
+                               but for YGS_FP64_EMU, the synthesis at every distinct shell
+                               tiling of full-tile widths 80, 96, ..., 144 shells, on one CTA
+                               per 128-cell tile and on CTA pairs, and keeps the fastest of
+                               each (a few ms more at create, and a scratch Phi of n_cells
+                               doubles while it runs; ygs_info reports the choices).  The
+                               synthesis's results do not depend on its tile shape; the
+                               projection's differ from an untuned plan's within the
+                               precision's bound, as the chunk sums are added in another
+                               grouping */
   YGS_FLAG_CTA_PAIRS = 4    /* split precisions but YGS_FP64_EMU: run the synthesis on pairs of
                                CTAs that share each MMA (cta_group::2, 256 cells per tile, each
                                CTA staging half of the tile's shells of M) instead of one CTA
@@ -175,7 +181,10 @@ typedef struct {
   long long static_scratch_bytes; /* scratch ygs_solve_static needs for this plan:
                                      (fp64_split_k + 2) * n_r * K * 8 */
   int cta_pairs;          /* 1: the synthesis runs on CTA pairs (YGS_FLAG_CTA_PAIRS on a split
-                             plan other than YGS_FP64_EMU, and the GPU can co-schedule them) */
+                             plan other than YGS_FP64_EMU, and the GPU can co-schedule them,
+                             or the autotuner picked them) */
+  int synth_tile_shells;  /* split plans: shells per full synthesis tile (144, 128 for
+                             YGS_FP64_EMU, or the width YGS_FLAG_AUTOTUNE picked); 0 on FP64 plans */
 } ygs_info;
 
 /* Builds the plan: validates the descriptor, allocates device memory on

@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("n_ang", ctypes.c_longlong), ("n_cells", ctypes.c_longlong), ("precision", ctypes.c_int),
                 ("symmetric", ctypes.c_int), ("split_k", ctypes.c_int), ("weight_bytes", ctypes.c_longlong),
                 ("work_bytes", ctypes.c_longlong), ("fp64_split_k", ctypes.c_int),
-                ("static_scratch_bytes", ctypes.c_longlong), ("cta_pairs", ctypes.c_int)]
+                ("static_scratch_bytes", ctypes.c_longlong), ("cta_pairs", ctypes.c_int),
+                ("synth_tile_shells", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -431,6 +431,7 @@ ygs_status ygs_get_info(const ygs_plan* p, ygs_info* info) {
   info->fp64_split_k = p->S;
   info->static_scratch_bytes = static_scratch_bytes(p);
   info->cta_pairs = p->tc_pairs > 0 ? 1 : 0;
+  info->synth_tile_shells = p->tc_nsl ? p->tc_N : 0;
   return YGS_OK;
 }
 

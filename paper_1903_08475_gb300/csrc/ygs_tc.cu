@@ -587,6 +587,62 @@ int fac_ld(const ygs_plan* p) { return (p->tc_np_full + (p->tc_np_tail > 0 ? 1 :
 #ifndef YGS_F16_MINB
 #define YGS_F16_MINB 4  // resident CTAs per SM the field pass's register budget is set for
 #endif
+// One exponent group of the FP16 field pass: lane l holds cells 4l .. 4l + 3
+// of the group (x0: patch g or Yin, x1: Yang; zero past the patch) and the
+// monopole weights of the same cells (ua, ub; zero without u00).
+__device__ __forceinline__ void field16_group(const double (&x0)[4], const double (&x1)[4], float4 ua, float4 ub,
+                                              bool mono, int symmetric, int lane, long long G, int i,
+                                              long long ngroups_all, int fac_ld, float* __restrict__ fac,
+                                              __half* __restrict__ out, long long plane, float& mh, float& ml) {
+  float hi[4][2], lo[4][2];
+  float m0 = 0.0f, m1 = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    sigma_ff(x0[d], x1[d], symmetric, hi[d], lo[d]);
+    m0 = fmaxf(m0, fabsf(hi[d][0]));
+    m1 = fmaxf(m1, fabsf(hi[d][1]));
+  }
+  // non-negative floats order like their bit patterns
+  m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
+  m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
+  const int e[2] = {group_exp(m0), symmetric ? group_exp(m1) : 0};
+  if (lane < 2 && (lane == 0 || symmetric)) fac[((long long)lane * ngroups_all + G) * fac_ld + i] = pow2f(-e[lane]);
+  if (mono) {
+    // sigma+ times the weight in float-float (padding cells carry sigma = 0):
+    // the heads' product with its rounding error from an FMA, the tails'
+    // cross terms, the running sum by FastTwoSum (exact while the sum
+    // dominates, as it does for a positive density)
+    const float uh[4] = {ua.x, ua.z, ub.x, ub.z}, ul[4] = {ua.y, ua.w, ub.y, ub.w};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const float pr = hi[d][0] * uh[d];
+      const float pe = fmaf(hi[d][0], ul[d], fmaf(lo[d][0], uh[d], fmaf(hi[d][0], uh[d], -pr)));
+      const float s2 = mh + pr;
+      ml += (pr - (s2 - mh)) + pe;
+      mh = s2;
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (h == 1 && !symmetric) break;
+    const float f = pow2f(e[h]);
+    uint32_t w0[2], w1[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      // both cells of a pair at once: s0 = fp16(a), s1 = fp16((a - s0) + b)
+      const float a0 = hi[2 * u][h] * f, a1 = hi[2 * u + 1][h] * f;
+      const float b0 = lo[2 * u][h] * f, b1 = lo[2 * u + 1][h] * f;
+      const __half2 s0 = __floats2half2_rn(a0, a1);  // a0 in the low half
+      const float2 back = __half22float2(s0);
+      const __half2 s1 = __floats2half2_rn((a0 - back.x) + b0, (a1 - back.y) + b1);
+      w0[u] = h2_bits(s0);
+      w1[u] = h2_bits(s1);
+    }
+    *reinterpret_cast<uint2*>(out + (long long)(2 * h) * plane) = make_uint2(w0[0], w0[1]);
+    *reinterpret_cast<uint2*>(out + (long long)(2 * h + 1) * plane) = make_uint2(w1[0], w1[1]);
+  }
+}
+
 __device__ __forceinline__ void field16_kernel_body(const tc::VBlock& vb, 
     int n_r, int symmetric, int nwp, const PatchTable& pt, const long long* __restrict__ pad_off, long long n_pad,
     const int2* __restrict__ chunks, const double* __restrict__ rho, __half* __restrict__ F,
@@ -627,55 +683,9 @@ __device__ __forceinline__ void field16_kernel_body(const tc::VBlock& vb,
       const int q = q0 + b * nw;
       if (q >= ngroups) break;  // warp-uniform
       const long long c = c_chunk + (long long)q * kGroup + 4 * lane;
-      float hi[4][2], lo[4][2];
-      float m0 = 0.0f, m1 = 0.0f;
-#pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        sigma_ff(x0[b][d], x1[b][d], symmetric, hi[d], lo[d]);
-        m0 = fmaxf(m0, fabsf(hi[d][0]));
-        m1 = fmaxf(m1, fabsf(hi[d][1]));
-      }
-      // non-negative floats order like their bit patterns
-      m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
-      m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
-      const int e[2] = {group_exp(m0), symmetric ? group_exp(m1) : 0};
-      const long long G = (ch.x / kGroup) + q;
-      if (lane < 2 && (lane == 0 || symmetric)) fac[((long long)lane * ngroups_all + G) * fac_ld + i] = pow2f(-e[lane]);
-      if (uz) {
-        // sigma+ times the weight in float-float (padding cells carry sigma = 0):
-        // the heads' product with its rounding error from an FMA, the tails'
-        // cross terms, the running sum by FastTwoSum (exact while the sum
-        // dominates, as it does for a positive density)
-        const float uh[4] = {ua[b].x, ua[b].z, ub[b].x, ub[b].z}, ul[4] = {ua[b].y, ua[b].w, ub[b].y, ub[b].w};
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          const float pr = hi[d][0] * uh[d];
-          const float pe = fmaf(hi[d][0], ul[d], fmaf(lo[d][0], uh[d], fmaf(hi[d][0], uh[d], -pr)));
-          const float s2 = mh + pr;
-          ml += (pr - (s2 - mh)) + pe;
-          mh = s2;
-        }
-      }
-      __half* out = F + (long long)i * n_pad + pad_off[g] + c;  // 8-byte aligned: pad_off, c multiples of 4
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h == 1 && !symmetric) break;
-        const float f = pow2f(e[h]);
-        uint32_t w0[2], w1[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          // both cells of a pair at once: s0 = fp16(a), s1 = fp16((a - s0) + b)
-          const float a0 = hi[2 * u][h] * f, a1 = hi[2 * u + 1][h] * f;
-          const float b0 = lo[2 * u][h] * f, b1 = lo[2 * u + 1][h] * f;
-          const __half2 s0 = __floats2half2_rn(a0, a1);  // a0 in the low half
-          const float2 back = __half22float2(s0);
-          const __half2 s1 = __floats2half2_rn((a0 - back.x) + b0, (a1 - back.y) + b1);
-          w0[u] = h2_bits(s0);
-          w1[u] = h2_bits(s1);
-        }
-        *reinterpret_cast<uint2*>(out + (long long)(2 * h) * plane) = make_uint2(w0[0], w0[1]);
-        *reinterpret_cast<uint2*>(out + (long long)(2 * h + 1) * plane) = make_uint2(w1[0], w1[1]);
-      }
+      // 8-byte aligned: pad_off, c multiples of 4
+      field16_group(x0[b], x1[b], ua[b], ub[b], uz != nullptr, symmetric, lane, (ch.x / kGroup) + q, i, ngroups_all,
+                    fac_ld, fac, F + (long long)i * n_pad + pad_off[g] + c, plane, mh, ml);
     }
   }
   if (!mpart) return;
@@ -1396,6 +1406,29 @@ cudaError_t dispatch_group(int nsl, bool scale, bool tf, int grid, const tc::TcP
 
 }  // namespace
 
+// The synthesis's shell tiling at full-tile width w (a multiple of 16, at
+// most the kernel's NMAX): tile counts and the M-slice tensor maps (boxes of
+// w and of the tail width; with CTA pairs, `clusters` > 0, also boxes of half
+// of each, one per CTA of a pair).
+static bool set_synth_shape(ygs_plan* p, int w, int clusters) {
+  const int kind = slice_kind(p);
+  p->tc_N = w;
+  p->tc_n_full = p->n_r / w;
+  p->tc_n_tail = ((p->n_r % w) + 15) / 16 * 16;
+  const int Nt = p->tc_n_tail > 0 ? p->tc_n_tail : w;
+  p->tc_pairs = 0;
+  if (!make_map(&p->tc_map_m, p->tc_ms, p->tc_k_pad, p->n_r, p->tc_nsl, w, kind) ||
+      !make_map(&p->tc_map_m_tail, p->tc_ms, p->tc_k_pad, p->n_r, p->tc_nsl, Nt, kind))
+    return false;
+  if (clusters > 0) {
+    if (!make_map(&p->tc_map_m2, p->tc_ms, p->tc_k_pad, p->n_r, p->tc_nsl, w / 2, kind) ||
+        !make_map(&p->tc_map_m2_tail, p->tc_ms, p->tc_k_pad, p->n_r, p->tc_nsl, Nt / 2, kind))
+      return false;
+    p->tc_pairs = clusters;
+  }
+  return true;
+}
+
 ygs_status tc_setup(ygs_plan* p, int sms) {
   const int nsl = p->tc_nsl;
   const int K = p->K;
@@ -1640,14 +1673,12 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   // the synthesis on CTA pairs: M slices in boxes of half a tile's shells
   p->tc_pairs = 0;
   if (!p->tc_emu && (p->flags & YGS_FLAG_CTA_PAIRS) && N % 16 == 0 && Nt % 16 == 0) {
-    if (!make_map(&p->tc_map_m2, p->tc_ms, p->tc_k_pad, p->n_r, nsl, N / 2, kind) ||
-        !make_map(&p->tc_map_m2_tail, p->tc_ms, p->tc_k_pad, p->n_r, nsl, Nt / 2, kind)) {
+    int clusters = 0;
+    TC_TRY(setup_synth_pair(nsl, p->tc_tf32 != 0, p->tc_sms, clusters));
+    if (!set_synth_shape(p, N, clusters)) {
       set_error("cuTensorMapEncodeTiled failed or is unavailable");
       return YGS_ERR_CUDA;
     }
-    int clusters = 0;
-    TC_TRY(setup_synth_pair(nsl, p->tc_tf32 != 0, p->tc_sms, clusters));
-    p->tc_pairs = clusters;
   }
   if (cand.size() > 1) {
     // time the projection of a zero field with each candidate; keep the fastest
@@ -1677,6 +1708,67 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     p->tc_S = (int)chunks.size();
     TC_TRY(cudaMemcpy(p->tc_chunks, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice));
     TC_TRY(cudaDeviceSynchronize());
+  }
+  if ((p->flags & YGS_FLAG_AUTOTUNE) && !p->tc_emu) {
+    // the synthesis's tile shape: every distinct shell tiling of full-tile
+    // widths 80 ... NS (multiples of 16), on one CTA per 128-cell tile and, where
+    // the GPU co-schedules them, on CTA pairs (256-cell tiles); each timed over
+    // 5 launches on zero M slices into a scratch Phi; the fastest is kept
+    int clusters = 0;
+    if (setup_synth_pair(nsl, p->tc_tf32 != 0, p->tc_sms, clusters) != cudaSuccess) clusters = 0;
+    cudaGetLastError();
+    struct Shape { int w, pair; };
+    std::vector<Shape> shapes;
+    std::vector<std::pair<int, int>> tilings;  // (full tiles, tail width) already listed
+    for (int w = NS; w >= 80; w -= 16) {
+      const std::pair<int, int> tl(p->n_r / w, ((p->n_r % w) + 15) / 16 * 16);
+      if (std::find(tilings.begin(), tilings.end(), tl) != tilings.end()) continue;
+      tilings.push_back(tl);
+      shapes.push_back(Shape{w, 0});
+      if (clusters > 0) shapes.push_back(Shape{w, 1});
+    }
+    const Shape keep{p->tc_N, p->tc_pairs > 0 ? 1 : 0};
+    double* phi_tmp = nullptr;
+    if (shapes.size() > 1) {
+      TC_TRY(cudaMemset(p->tc_ms, 0, bytes_m));
+      TC_TRY(cudaMemset(p->tc_mono, 0, (size_t)p->n_r * sizeof(float2)));
+      if (p->tc_fp16) TC_TRY(cudaMemset(p->tc_sc, 0, (size_t)p->n_r * sizeof(float4)));
+      if ((e = dev_malloc((void**)&phi_tmp, (size_t)p->n_cells * sizeof(double))) != cudaSuccess) {
+        set_error(std::string("cudaMalloc (autotuner's scratch Phi): ") + cudaGetErrorString(e));
+        return YGS_ERR_OOM;
+      }
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      cudaError_t te = cudaEventCreate(&e0);
+      if (te == cudaSuccess) te = cudaEventCreate(&e1);
+      float best = 1e30f;
+      Shape pick = keep;
+      for (size_t c = 0; c < shapes.size() && te == cudaSuccess; ++c) {
+        if (!set_synth_shape(p, shapes[c].w, shapes[c].pair ? clusters : 0)) {
+          te = cudaErrorInvalidValue;
+          break;
+        }
+        if ((te = tc_synthesize(p, phi_tmp, 0)) != cudaSuccess) break;
+        if ((te = cudaEventRecord(e0, 0)) != cudaSuccess) break;
+        for (int r = 0; r < 5 && te == cudaSuccess; ++r) te = tc_synthesize(p, phi_tmp, 0);
+        if (te != cudaSuccess || (te = cudaEventRecord(e1, 0)) != cudaSuccess) break;
+        if ((te = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        float ms = 0.0f;
+        if ((te = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        if (ms < best) {
+          best = ms;
+          pick = shapes[c];
+        }
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      cudaFree(phi_tmp);
+      TC_TRY(te);
+      if (!set_synth_shape(p, pick.w, pick.pair ? clusters : 0)) {
+        set_error("cuTensorMapEncodeTiled failed or is unavailable");
+        return YGS_ERR_CUDA;
+      }
+      TC_TRY(cudaDeviceSynchronize());
+    }
   }
 
 #undef TC_TRY
@@ -1758,13 +1850,14 @@ static_assert(YGS_SYNTH_FLUSH_K % tc::BK == 0, "a synthesis flush covers whole k
 // k elements of one stage of the contractions: 64 two-byte or 32 TF32 values
 static int kblock_elems(const ygs_plan* p) { return p->tc_tf32 ? tc::BK / 2 : tc::BK; }
 
-static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
+static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_w, int n_full, int n_tail) {
   a.err = p->d_err;
   a.ab_fmt = p->tc_tf32 ? 2 : (p->tc_fp16 ? 0 : 1);
   // flush the FP32 accumulators into the float-float sums every 64 k-elements
   // (EMU: every window of four k-blocks, whose sums are exact)
   a.flush_kb = p->tc_emu ? tc::kEmuWindowKb : std::max(1, 64 / kblock_elems(p));
   a.n_b = p->n_r;
+  a.n_w = n_w;
   a.n_full = n_full;
   a.n_tail = n_tail;
   a.n_tiles = n_full + (n_tail > 0 ? 1 : 0);
@@ -1775,7 +1868,7 @@ static void fill_tiles(const ygs_plan* p, TcArgs& a, int n_full, int n_tail) {
 // every 128 k like the synthesis; BF16 plans and the adjoint keep 64
 static void project_args(const ygs_plan* p, TcArgs& a, bool forward = true) {
   a = TcArgs{};
-  fill_tiles(p, a, p->tc_np_full, p->tc_np_tail);
+  fill_tiles(p, a, tc::kNmaxProject, p->tc_np_full, p->tc_np_tail);
   if (forward && p->tc_fp16) a.flush_kb = std::max(1, YGS_PROJ_FLUSH_K_EXACT_MONO / kblock_elems(p));
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
@@ -1834,7 +1927,7 @@ cudaError_t tc_scan(const ygs_plan* p, cudaStream_t s) {
 // pair: tiles of 2 x 128 cells for the CTA-pair kernel.
 static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* mono, bool pair = false) {
   a = TcArgs{};
-  fill_tiles(p, a, p->tc_n_full, p->tc_n_tail);
+  fill_tiles(p, a, p->tc_N, p->tc_n_full, p->tc_n_tail);
   // the forward synthesis excludes the monopole (added exactly) and may flush less
   // often; the adjoint's U has a positive monopole column and keeps 64
   a.flush_kb = p->tc_emu ? tc::kEmuWindowKb : std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / kblock_elems(p));

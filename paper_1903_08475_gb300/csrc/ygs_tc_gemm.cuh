@@ -6,8 +6,8 @@
 //   formed (3 for two slices, 6 for three).
 //
 // Persistent kernel: one CTA per SM walks a static list of 128 x n_eff output
-// tiles (n_eff = NMAX shells, 144 by default, or the tail width for the last
-// shell tile).  Warp 0 streams A/B slice tiles of BK k-elements (128-byte
+// tiles (n_eff = n_w shells, NMAX = 144 by default or a narrower width picked
+// by the autotuner, or the tail width for the last shell tile).  Warp 0 streams A/B slice tiles of BK k-elements (128-byte
 // rows, 128-byte swizzle) through a ring of shared-memory stages with TMA;
 // warp 1 issues tcgen05.mma into FP32 TMEM accumulators; the epilogue warps
 // (2 onwards, 4 per group of NH columns) drain them with tcgen05.ld.  The
@@ -123,7 +123,9 @@ struct TcArgs {
   int* err;
   int flush_kb;         // k-blocks per TMEM group (a flush into the float-float sums)
   int n_b;              // valid B rows (shells)
-  int n_full;           // full shell tiles (NMAX wide)
+  int n_w;             // shells per full tile: NMAX, or (synthesis) a narrower width the
+                        // autotuner picked (multiple of 16, <= NMAX)
+  int n_full;           // full shell tiles (n_w wide)
   int n_tail;           // width of the tail shell tile (multiple of 16) or 0
   int n_tiles;          // n_full + (n_tail > 0)
   int total_tiles;      // length of the tile list
@@ -292,8 +294,8 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t, int rank = 0
     T.z = 0;
   }
   T.use_tail = (n >= a.n_full);
-  T.n_eff = T.use_tail ? a.n_tail : NMAX;
-  T.b_row0 = n * NMAX;
+  T.n_eff = T.use_tail ? a.n_tail : a.n_w;
+  T.b_row0 = n * a.n_w;
   return T;
 }
 
@@ -753,7 +755,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             upk2(L[j / 2], l0, l1);
             const float oh = (j & 1) ? h1 : h0, ol = (j & 1) ? l1 : l0;
             const int n = T.b_row0 + col0 + j;
-            if (n >= n_b || a_loc >= nang) continue;
+            if (col0 + j >= T.n_eff || n >= n_b || a_loc >= nang) continue;
             const unsigned int c20 = sc ? (unsigned int)__float_as_int(sc[n].x) : (896u << 20);
             if (nseg == 2 || symmetric) {
               // E from TMEM (zero without two column blocks: then the sums are E and O = 0)
@@ -797,7 +799,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           upk2(L[j / 2], l0, l1);
           const float hj = (j & 1) ? h1 : h0, lj = (j & 1) ? l1 : l0;
           const int n = T.b_row0 + col0 + j;
-          if (n >= n_b) continue;
+          // columns past the tile's width belong to the next shell tile
+          if (col0 + j >= T.n_eff || n >= n_b) continue;
           if (MODE == kProject) {
             if (T.a_row0 + r < T.a_rows_end) {
               float s, e;
