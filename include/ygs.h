@@ -72,7 +72,9 @@ typedef enum {
   YGS_ERR_UNSUPPORTED = 4, /* valid request this build does not implement */
   YGS_ERR_NUMERIC = 5,     /* a weight self-check failed, or (YGS_FP64_EMU) a field value at
                               or above 2^127, beyond what the FP32 window sums can hold */
-  YGS_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+  YGS_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+  YGS_ERR_BOUNDS = 7       /* checked builds only (ygs_checked_build): a kernel met a global index
+                              outside the buffer it addresses and skipped the access */
 } ygs_status;
 
 /* Arithmetic of the two contractions (projection and synthesis).  Weight
@@ -312,8 +314,30 @@ ygs_status ygs_finish_from_moments(ygs_plan* plan, const double* d_B, double* d_
 ygs_status ygs_get_weights(ygs_plan* plan, int which, int patch, double* h_out);
 
 /* Reads and clears the plan's device error word (set by bounded waits and
- * device-side checks).  Synchronises the plan's last stream. */
+ * device-side checks).  Synchronises the plan's last stream.  In a checked
+ * build it also reads and clears the device's out-of-range record (shared by
+ * every plan on the device; the first event since the last read) and returns
+ * YGS_ERR_BOUNDS for it, ygs_last_error naming the kernel site and index. */
 ygs_status ygs_get_status(ygs_plan* plan);
+
+/* 1 in a checked build of the library: compiled with YGS_DEBUG_BOUNDS=1
+ * (python -m paper_1903_08475_gb300.build --checked, into _build_checked/),
+ * every per-solve kernel checks the global index of its main loads and
+ * stores against the extent of the buffer it addresses and, outside it,
+ * skips the access and records the event for ygs_get_status instead of
+ * faulting.  0 in the release build, whose kernels carry no checks.  The
+ * Python binding loads another build named by the environment variable
+ * YGS_LIB.  (Sanitiser-style checking for development; no counterpart in
+ * the paper.) */
+int ygs_checked_build(void);
+
+/* Checked builds only (YGS_ERR_UNSUPPORTED otherwise): the field extent the
+ * kernels' checks hold rho and Phi to, normally n_cells, set to n in
+ * [0, n_cells] for the calls that follow.  A smaller n makes the checks
+ * report (and skip) the accesses to elements n and beyond, so a test can see
+ * a check fire without any access leaving the buffers; ygs_get_status then
+ * returns YGS_ERR_BOUNDS.  The results of such calls are incomplete. */
+ygs_status ygs_debug_set_field_extent(ygs_plan* plan, long long n);
 
 /* Phase timing for measurement.  While enabled, every ygs_solve and
  * ygs_backward on this plan records CUDA events on its stream around its four

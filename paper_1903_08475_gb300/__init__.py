@@ -9,10 +9,10 @@ from ._ygs import (EXPORTS, LIB_PATH, Batch, Info, Plan, YgsError, load_library,
                    ygs_debug_wait_timeout, ygs_get_moments, ygs_get_status, ygs_get_weights, ygs_launches_per_solve,
                    ygs_read_phase_times, ygs_set_profiling, ygs_solve, ygs_solve_batched, ygs_solve_host,
                    ygs_solve_host_many, ygs_solve_static, ygs_static_scratch_capacity, ygs_project_partial,
-                   ygs_finish_from_moments)
+                   ygs_finish_from_moments, ygs_checked_build, ygs_debug_set_field_extent)
 
 __all__ = ["EXPORTS", "LIB_PATH", "Batch", "Info", "Plan", "YgsError", "load_library", "potential", "ygs_backward",
            "ygs_debug_wait_timeout", "ygs_get_moments", "ygs_get_status", "ygs_get_weights", "ygs_launches_per_solve",
            "ygs_read_phase_times", "ygs_set_profiling", "ygs_solve", "ygs_solve_batched", "ygs_solve_host",
            "ygs_solve_host_many", "ygs_solve_static", "ygs_static_scratch_capacity", "ygs_project_partial",
-           "ygs_finish_from_moments"]
+           "ygs_finish_from_moments", "ygs_checked_build", "ygs_debug_set_field_extent"]

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libygs.so")
 
 YGS_OK = 0
 STATUS = {0: "YGS_OK", 1: "YGS_ERR_INVALID_ARG", 2: "YGS_ERR_OOM", 3: "YGS_ERR_CUDA",
-          4: "YGS_ERR_UNSUPPORTED", 5: "YGS_ERR_NUMERIC", 6: "YGS_ERR_TIMEOUT"}
+          4: "YGS_ERR_UNSUPPORTED", 5: "YGS_ERR_NUMERIC", 6: "YGS_ERR_TIMEOUT", 7: "YGS_ERR_BOUNDS"}
 PRECISION = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "fp16x3": 3, "fp64tc": 4, "fp32": 5, "tf32x3": 6,
              "fp64emu": 7}
 EVAL = {"upper_vertex": 0, "cell_centre": 1}
@@ -33,7 +33,7 @@ EXPORTS = ("ygs_create", "ygs_destroy", "ygs_get_info", "ygs_solve", "ygs_solve_
            "ygs_last_error", "ygs_set_profiling", "ygs_read_phase_times", "ygs_launches_per_solve",
            "ygs_debug_wait_timeout", "ygs_solve_static", "ygs_batch_create", "ygs_batch_solve",
            "ygs_batch_destroy", "ygs_batch_launches", "ygs_static_scratch_capacity", "ygs_project_partial",
-           "ygs_finish_from_moments")
+           "ygs_finish_from_moments", "ygs_checked_build", "ygs_debug_set_field_extent")
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -107,6 +107,8 @@ def load_library(path: Optional[str] = None):
         L.ygs_static_scratch_capacity.argtypes = []
         L.ygs_project_partial.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp]
         L.ygs_finish_from_moments.argtypes = [vp, vp, vp, vp]
+        L.ygs_checked_build.argtypes = []
+        L.ygs_debug_set_field_extent.argtypes = [vp, ctypes.c_longlong]
         for f in EXPORTS:
             if f not in ("ygs_status_string", "ygs_last_error", "ygs_static_scratch_capacity"):
                 getattr(L, f).restype = ctypes.c_int
@@ -362,6 +364,18 @@ def ygs_debug_wait_timeout(plan: Plan, spins: int = 1000, stream=None):
 
 def ygs_get_status(plan: Plan):
     _check(load_library().ygs_get_status(plan.handle))
+
+
+def ygs_debug_set_field_extent(plan: Plan, n: int):
+    """Checked builds: the field extent the kernels' bounds checks use (n_cells
+    normally); a smaller one makes them report the accesses past it."""
+    _check(load_library().ygs_debug_set_field_extent(plan.handle, int(n)))
+
+
+def ygs_checked_build() -> bool:
+    """True when the loaded library is the checked build (index bounds checks in
+    every per-solve kernel, reported by ygs_get_status as YGS_ERR_BOUNDS)."""
+    return bool(load_library().ygs_checked_build())
 
 
 def _make_autograd():

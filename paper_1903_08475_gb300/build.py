@@ -1,6 +1,6 @@
 """Builds libygs.so in-tree with nvcc for sm_103a (GB300).
 
-    python -m paper_1903_08475_gb300.build
+    python -m paper_1903_08475_gb300.build [--force] [--checked]
 
 Each translation unit under csrc/ compiles in parallel; the shared library
 links the CUDA runtime statically so it carries no dependency on a
@@ -18,6 +18,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libygs.so")
+# the checked build: the same sources with every per-solve kernel's index
+# bounds checks compiled in (YGS_DEBUG_BOUNDS=1), in a directory of its own
+CHECKED_DIR = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libygs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-warn-spills"] + ARCH + [f for f in os.environ.get("YGS_NVCC_EXTRA", "").split() if f]
@@ -39,23 +43,26 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out_dir = CHECKED_DIR if checked else OUT_DIR
+    lib = CHECKED_LIB if checked else LIB
+    nvcc_flags = NVCC_FLAGS + (["-DYGS_DEBUG_BOUNDS=1"] if checked else [])
+    os.makedirs(out_dir, exist_ok=True)
     # objects built with other flags are stale
-    stamp = os.path.join(OUT_DIR, "flags.txt")
-    flags = " ".join(NVCC_FLAGS)
+    stamp = os.path.join(out_dir, "flags.txt")
+    flags = " ".join(nvcc_flags)
     if not os.path.exists(stamp) or open(stamp).read() != flags:
         force = True
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "ygs.h"))
     srcs = sources()
-    objs = [os.path.join(OUT_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
         if not force and not _stale(obj, [src] + headers):
             return ""
-        cmd = [nvcc()] + NVCC_FLAGS + ["-c", src, "-o", obj + ".tmp"]
+        cmd = [nvcc()] + nvcc_flags + ["-c", src, "-o", obj + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
@@ -68,17 +75,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for l in logs:
             if l:
                 sys.stderr.write(l)
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(flags)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

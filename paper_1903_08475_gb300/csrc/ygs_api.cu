@@ -232,6 +232,22 @@ ygs_status check_field(const ygs_plan* p, const void* a, const void* b) {
 }  // namespace
 }  // namespace ygs
 
+namespace ygs {
+// The checked build's site names, by BoundsSite.
+const char* bounds_site_name(int site) {
+  static const char* const names[kSiteBoundsSites] = {
+      "none", "field pass FP16: rho load", "field pass FP16: slice store", "field pass FP16: factor store",
+      "field pass FP16: monopole weight load", "field pass BF16/TF32: rho load", "field pass BF16/TF32: slice store",
+      "radial scan: partial load", "radial scan: B/M store", "radial scan: M slice store", "M slicing: M load",
+      "M slicing: slice store", "contraction epilogue: Phi store", "contraction epilogue: partial store",
+      "contraction producer: factor row", "FP64 projection: field load", "FP64 projection: weight load",
+      "FP64 projection: partial store", "FP64 synthesis: moment load", "FP64 synthesis: weight load",
+      "FP64 synthesis: Phi store", "FP64 radial scan", "FP64 adjoint scan", "FP64-accurate field pass: rho load",
+      "FP64-accurate field pass: slice store", "FP64-accurate radial scan"};
+  return site > 0 && site < kSiteBoundsSites ? names[site] : "unknown site";
+}
+}  // namespace ygs
+
 using namespace ygs;
 
 extern "C" {
@@ -245,6 +261,7 @@ const char* ygs_status_string(ygs_status s) {
     case YGS_ERR_UNSUPPORTED: return "YGS_ERR_UNSUPPORTED";
     case YGS_ERR_NUMERIC: return "YGS_ERR_NUMERIC";
     case YGS_ERR_TIMEOUT: return "YGS_ERR_TIMEOUT";
+    case YGS_ERR_BOUNDS: return "YGS_ERR_BOUNDS";
   }
   return "YGS_ERR_UNKNOWN";
 }
@@ -302,6 +319,8 @@ ygs_status ygs_create(const ygs_desc* d, int device, ygs_plan** out) {
     p->pt.nang[g] = p->nang[g];
     p->pt.ang_off[g] = p->symmetric ? 0 : p->ang_off[g];
   }
+  p->pt.n_cells = p->n_cells;
+  p->pt.w_rows = p->nang_wtotal;
   // internal column order: even m first when the symmetry is used
   p->col_perm.clear();
   if (p->symmetric) {
@@ -821,7 +840,31 @@ ygs_status ygs_get_status(ygs_plan* p) {
   int err = 0;
   API_TRY(cudaMemcpy(&err, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   API_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  // checked builds: the first out-of-range index any kernel on this device met
+  int site = 0;
+  long long index = 0;
+  for (auto rd : {bounds_read_tc, bounds_read_fp64, bounds_read_emu}) {
+    int s1 = 0;
+    long long i1 = 0;
+    API_TRY(rd(&s1, &i1));
+    if (s1 && !site) {
+      site = s1;
+      index = i1;
+    }
+  }
   if (err) return fail((ygs_status)err, "device-side error word was set");
+  if (site)
+    return fail(YGS_ERR_BOUNDS, std::string("index ") + std::to_string(index) + " out of range at " +
+                                    bounds_site_name(site));
+  return YGS_OK;
+}
+
+int ygs_checked_build(void) { return YGS_DEBUG_BOUNDS; }
+
+ygs_status ygs_debug_set_field_extent(ygs_plan* p, long long n) {
+  if (!p || n < 0 || n > p->n_cells) return fail(YGS_ERR_INVALID_ARG, "bad arguments");
+  if (!YGS_DEBUG_BOUNDS) return fail(YGS_ERR_UNSUPPORTED, "not a checked build");
+  p->pt.n_cells = n;
   return YGS_OK;
 }
 

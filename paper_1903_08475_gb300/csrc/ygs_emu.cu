@@ -201,7 +201,18 @@ __device__ __forceinline__ void emu_field_kernel_body(const tc::VBlock& vb,
   const bool vec = ((reinterpret_cast<uintptr_t>(x0p) | reinterpret_cast<uintptr_t>(x1p)) & 15) == 0;
 #pragma unroll
   for (int d = 0; d < 4; ++d) x0[d] = x1[d] = 0.0;
-  if (vec && c + 4 <= na) {
+  bool in = true;  // checked builds: this thread's cells of both rows lie in the field
+#if YGS_DEBUG_BOUNDS
+  {
+    const long long nv = na - c < 4 ? na - c : 4;
+    const long long r0 = pt.fld_off[g] + (long long)i * na + c, r1 = (symmetric ? pt.fld_off[1] : pt.fld_off[g]) + (long long)i * na + c;
+    if (nv > 0)
+      in = YGS_IN_BOUNDS(r0, pt.n_cells, kSiteEmuFieldRho) && YGS_IN_BOUNDS(r0 + nv - 1, pt.n_cells, kSiteEmuFieldRho) &&
+           YGS_IN_BOUNDS(r1, pt.n_cells, kSiteEmuFieldRho) && YGS_IN_BOUNDS(r1 + nv - 1, pt.n_cells, kSiteEmuFieldRho);
+  }
+#endif
+  if (!in) {
+  } else if (vec && c + 4 <= na) {
     const double2 a0 = *reinterpret_cast<const double2*>(x0p + c), a1 = *reinterpret_cast<const double2*>(x0p + c + 2);
     x0[0] = a0.x; x0[1] = a0.y; x0[2] = a1.x; x0[3] = a1.y;
     if (symmetric) {
@@ -259,7 +270,10 @@ __device__ __forceinline__ void emu_field_kernel_body(const tc::VBlock& vb,
     for (int s = 0; s < kS; ++s) {
       const uint32_t w0 = (uint32_t)digit_bf16(dg[0][s], s) | ((uint32_t)digit_bf16(dg[1][s], s) << 16);
       const uint32_t w1 = (uint32_t)digit_bf16(dg[2][s], s) | ((uint32_t)digit_bf16(dg[3][s], s) << 16);
-      *reinterpret_cast<uint2*>(out + (long long)s * plane) = make_uint2(w0, w1);  // 8-byte aligned
+      const long long oi = (long long)(h * kS + s) * plane + (long long)i * n_pad + ap + 4 * threadIdx.x;
+      (void)oi;
+      if (YGS_IN_BOUNDS(oi + 3, (long long)(symmetric ? 2 : 1) * kS * plane, kSiteEmuFieldOut))
+        *reinterpret_cast<uint2*>(out + (long long)s * plane) = make_uint2(w0, w1);  // 8-byte aligned
     }
   }
 }
@@ -349,6 +363,9 @@ __device__ __forceinline__ void emu_scan_kernel_body(const tc::VBlock& vb,
     }
     return;
   }
+  // the column's radial tables and its last partial (warp-uniform: one column per warp)
+  if (!YGS_IN_BOUNDS(l, L + 1, kSiteEmuScan) || !YGS_IN_BOUNDS((S - 1) * plane + plane - K_pad + c, S * plane, kSiteEmuScan))
+    return;
   const long long rs = (long long)(L + 1) * n_r;
   const double* at = rad + (long long)l * n_r;
   const double* bt = rad + rs + (long long)l * n_r;
@@ -734,5 +751,8 @@ cudaError_t emu_dispatch_group(int mode, int grid, const tc::TcProblem* probs, c
   }
   return cudaGetLastError();
 }
+
+// this translation unit's out-of-range record (checked builds; a no-op otherwise)
+YGS_BOUNDS_READER(bounds_read_emu)
 
 }  // namespace ygs

@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs<T> a) {
       int e = tid + r * NT, row = e / BK, kk = e % BK;
       int i = i0 + row, k = k0 + kk;
       T v = T(0);
-      if (i < a.n_r && k < ch.a1) {
+      if (i < a.n_r && k < ch.a1 &&
+          YGS_IN_BOUNDS(a.pt.fld_off[ch.g] + i * lda + k, a.pt.n_cells, kSiteProjField) &&
+          (!A1 || YGS_IN_BOUNDS(a.pt.fld_off[1] + i * lda + k, a.pt.n_cells, kSiteProjField))) {
         v = A0[i * lda + k];
         if (A1) v += sgn * A1[i * lda + k];
       }
@@ -141,7 +143,10 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs<T> a) {
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, kk = e / BN, col = e % BN;
       int k = k0 + kk, c = c0 + col;
-      Bs[kk][col] = (k < ch.a1 && c < c1) ? Wg[(long long)k * a.K + c] : T(0);
+      Bs[kk][col] = (k < ch.a1 && c < c1 &&
+                     YGS_IN_BOUNDS((a.pt.ang_off[ch.g] + k) * (long long)a.K + c, a.pt.w_rows * a.K, kSiteProjW))
+                        ? Wg[(long long)k * a.K + c]
+                        : T(0);
     }
     __syncthreads();
     tile_step<T, TC>(As, Bs, acc);
@@ -155,7 +160,9 @@ __global__ void __launch_bounds__(NT) proj_fp64_kernel(ProjArgs<T> a) {
       int row, col;
       tile_out<TC>(r, q, row, col);
       int i = i0 + row, c = c0 + col;
-      if (i < a.n_r && c < c1) out[(long long)i * a.K + c] = acc[r][q];
+      if (i < a.n_r && c < c1 &&
+          YGS_IN_BOUNDS(((long long)z * a.n_r + i) * a.K + c, (long long)gridDim.z * a.n_r * a.K, kSiteProjPart))
+        out[(long long)i * a.K + c] = acc[r][q];
     }
 }
 
@@ -177,13 +184,19 @@ __device__ inline void synth_range(const SynthArgs<T>& s, const T* Wg, long long
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, row = e / BK, kk = e % BK;
       int i = i0 + row, k = k0 + kk;
-      As[kk][row] = (i < s.n_r && k < k_hi) ? s.X[(long long)i * s.K + k] : T(0);
+      As[kk][row] = (i < s.n_r && k < k_hi &&
+                     YGS_IN_BOUNDS((long long)i * s.K + k, (long long)s.n_r * s.K, kSiteSynthX))
+                        ? s.X[(long long)i * s.K + k]
+                        : T(0);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int e = tid + r * NT, n = e / BK, kk = e % BK;
       int a = a0 + n, k = k0 + kk;
-      Bs[kk][n] = (a < nang && k < k_hi) ? Wg[(long long)a * s.K + k] : T(0);
+      Bs[kk][n] = (a < nang && k < k_hi &&
+                   YGS_IN_BOUNDS((Wg - s.W) + (long long)a * s.K + k, s.pt.w_rows * s.K, kSiteSynthW))
+                      ? Wg[(long long)a * s.K + k]
+                      : T(0);
     }
     __syncthreads();
     tile_step<T, TC>(As, Bs, acc);
@@ -219,10 +232,13 @@ __global__ void __launch_bounds__(NT) synth_fp64_kernel(SynthArgs<T> s) {
       long long a = a0 + col;
       if (i >= s.n_r || a >= nang) continue;
       if (s.symmetric) {
-        s.out[s.pt.fld_off[0] + i * nang + a] = (double)(ae[r][q] + ao[r][q]);
-        s.out[s.pt.fld_off[1] + i * nang + a] = (double)(ae[r][q] - ao[r][q]);
+        if (YGS_IN_BOUNDS(s.pt.fld_off[0] + i * nang + a, s.pt.n_cells, kSiteSynthPhi))
+          s.out[s.pt.fld_off[0] + i * nang + a] = (double)(ae[r][q] + ao[r][q]);
+        if (YGS_IN_BOUNDS(s.pt.fld_off[1] + i * nang + a, s.pt.n_cells, kSiteSynthPhi))
+          s.out[s.pt.fld_off[1] + i * nang + a] = (double)(ae[r][q] - ao[r][q]);
       } else {
-        s.out[s.pt.fld_off[g] + i * nang + a] = (double)(ae[r][q] + ao[r][q]);
+        if (YGS_IN_BOUNDS(s.pt.fld_off[g] + i * nang + a, s.pt.n_cells, kSiteSynthPhi))
+          s.out[s.pt.fld_off[g] + i * nang + a] = (double)(ae[r][q] + ao[r][q]);
       }
     }
 }
@@ -234,6 +250,9 @@ __global__ void scan_fwd_kernel(int n_r, int K, int L, const int* __restrict__ c
   if (c >= K) return;
   const int l = col_l[c];
   const long long plane = (long long)n_r * K, rs = (long long)(L + 1) * n_r;
+  // the column's radial tables and its last element of the partials
+  if (!YGS_IN_BOUNDS(l, L + 1, kSiteScanFwd) || !YGS_IN_BOUNDS((S - 1) * plane + plane - K + c, S * plane, kSiteScanFwd))
+    return;
   const double* at = rad + (long long)l * n_r;
   const double* bt = rad + rs + (long long)l * n_r;
   const double* fin = rad + 2 * rs + (long long)l * n_r;
@@ -263,6 +282,8 @@ __global__ void scan_adj_kernel(int n_r, int K, int L, const int* __restrict__ c
   if (c >= K) return;
   const int l = col_l[c];
   const long long plane = (long long)n_r * K, rs = (long long)(L + 1) * n_r;
+  if (!YGS_IN_BOUNDS(l, L + 1, kSiteScanAdj) || !YGS_IN_BOUNDS((S - 1) * plane + plane - K + c, S * plane, kSiteScanAdj))
+    return;
   const double* at = rad + (long long)l * n_r;
   const double* bt = rad + rs + (long long)l * n_r;
   const double* fin = rad + 2 * rs + (long long)l * n_r;
@@ -462,5 +483,8 @@ cudaError_t launch_unpermute(const ygs_plan* p, const double* in, double* out, c
   unpermute_kernel<<<256, 256, 0, s>>>(p->n_r, p->K, p->col_nat, in, out);
   return cudaGetLastError();
 }
+
+// this translation unit's out-of-range record (checked builds; a no-op otherwise)
+YGS_BOUNDS_READER(bounds_read_fp64)
 
 }  // namespace ygs

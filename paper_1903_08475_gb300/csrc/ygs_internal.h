@@ -22,7 +22,67 @@ struct PatchTable {
   long long fld_off[kMaxPatch];  // element offset of patch g in a field
   long long nang[kMaxPatch];     // angular cells of patch g
   long long ang_off[kMaxPatch];  // row offset of patch g in a weight matrix
+  long long n_cells;             // elements of a whole field (the checked build's bound for rho and Phi)
+  long long w_rows;              // rows of the stored FP64 weight matrices U and Q (each w_rows x K)
 };
+
+// ---- checked builds ----
+// Built with -DYGS_DEBUG_BOUNDS=1 (build.py's debug library), every
+// per-solve kernel checks the global index of its main loads and stores
+// against the extent of the buffer it addresses, taken from the plan's sizes.
+// An index outside [0, extent) skips the access and records the first such
+// event (site, index) in a device word of the translation unit;
+// ygs_get_status reports it as YGS_ERR_BOUNDS (ygs_last_error names the site
+// and the index) and clears it.  In release builds the checks compile to
+// nothing.
+#ifndef YGS_DEBUG_BOUNDS
+#define YGS_DEBUG_BOUNDS 0
+#endif
+enum BoundsSite {
+  kSiteField16Rho = 1, kSiteField16Slices, kSiteField16Fac, kSiteField16U00, kSiteFieldSlicesRho,
+  kSiteFieldSlicesOut, kSiteScanPart, kSiteScanBM, kSiteScanMs, kSiteSliceM16In, kSiteSliceM16Out, kSiteGemmPhi,
+  kSiteGemmPart, kSiteGemmFac, kSiteProjField, kSiteProjW, kSiteProjPart, kSiteSynthX, kSiteSynthW, kSiteSynthPhi,
+  kSiteScanFwd, kSiteScanAdj, kSiteEmuFieldRho, kSiteEmuFieldOut, kSiteEmuScan, kSiteBoundsSites
+};
+const char* bounds_site_name(int site);
+#if YGS_DEBUG_BOUNDS
+static __device__ unsigned long long g_bounds[3];  // {flag, site, index} of this translation unit
+__device__ __forceinline__ bool bounds_ok(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicCAS(&g_bounds[0], 0ull, 1ull) == 0ull) {
+    g_bounds[1] = (unsigned long long)site;
+    g_bounds[2] = (unsigned long long)i;
+  }
+  return false;
+}
+#define YGS_IN_BOUNDS(i, n, site) ::ygs::bounds_ok((long long)(i), (long long)(n), (site))
+// Host: reads and clears this translation unit's word on the current device.
+#define YGS_BOUNDS_READER(fn)                                                            \
+  cudaError_t fn(int* site, long long* index) {                                          \
+    unsigned long long h[3] = {0, 0, 0};                                                 \
+    cudaError_t e = cudaMemcpyFromSymbol(h, g_bounds, sizeof(h));                        \
+    if (e != cudaSuccess) return e;                                                      \
+    *site = h[0] ? (int)h[1] : 0;                                                        \
+    *index = (long long)h[2];                                                            \
+    if (h[0]) {                                                                          \
+      const unsigned long long z[3] = {0, 0, 0};                                         \
+      e = cudaMemcpyToSymbol(g_bounds, z, sizeof(z));                                    \
+    }                                                                                    \
+    return e;                                                                            \
+  }
+#else
+#define YGS_IN_BOUNDS(i, n, site) true
+#define YGS_BOUNDS_READER(fn)                \
+  cudaError_t fn(int* site, long long* index) { \
+    *site = 0;                               \
+    *index = 0;                              \
+    return cudaSuccess;                      \
+  }
+#endif
+// the readers of the translation units with per-solve kernels
+cudaError_t bounds_read_tc(int* site, long long* index);
+cudaError_t bounds_read_fp64(int* site, long long* index);
+cudaError_t bounds_read_emu(int* site, long long* index);
 
 // One split-K chunk of the projection: angular cells [a0, a1) of patch g.
 struct Chunk {

@@ -192,6 +192,18 @@ __device__ __forceinline__ void sigma_slices(double r0, double r1, int nsl, int 
 // Grid: (x over groups of 4 angular cells, y over shells, z over stored
 // patches).  Rows of rho whose start is 16-byte aligned are read with 16-byte
 // loads; slices are written 4 cells (8 bytes) at a time.
+#if YGS_DEBUG_BOUNDS
+// Checked builds: cells [a, a + nv) of both input rows lie in the field and
+// those of every output plane in the slice buffer (planes x plane elements).
+__device__ __forceinline__ bool field_row_ok(long long in0, long long in1, long long n_cells, long long out,
+                                             long long planes, long long plane, int nv) {
+  return YGS_IN_BOUNDS(in0, n_cells, kSiteFieldSlicesRho) && YGS_IN_BOUNDS(in0 + nv - 1, n_cells, kSiteFieldSlicesRho) &&
+         YGS_IN_BOUNDS(in1, n_cells, kSiteFieldSlicesRho) && YGS_IN_BOUNDS(in1 + nv - 1, n_cells, kSiteFieldSlicesRho) &&
+         YGS_IN_BOUNDS(out, planes * plane, kSiteFieldSlicesOut) &&
+         YGS_IN_BOUNDS((planes - 1) * plane + out + nv - 1, planes * plane, kSiteFieldSlicesOut);
+}
+#endif
+
 __device__ __forceinline__ void field_slices_kernel_body(const tc::VBlock& vb, int nsl, int n_r, int symmetric, const PatchTable& pt,
                                     const long long* __restrict__ pad_off, long long n_pad,
                                     const double* __restrict__ rho, __nv_bfloat16* __restrict__ F) {
@@ -204,6 +216,11 @@ __device__ __forceinline__ void field_slices_kernel_body(const tc::VBlock& vb, i
   const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
   const bool vec = ((row_in | row_in1) & 1) == 0;
   for (int a = 4 * (vb.x * blockDim.x + threadIdx.x); a < na; a += 4 * vb.gx * blockDim.x) {
+#if YGS_DEBUG_BOUNDS
+    if (!field_row_ok(row_in + a, row_in1 + a, pt.n_cells, row_out + a, (long long)(symmetric ? 2 : 1) * nsl, plane,
+                      min(4, na - a)))
+      continue;
+#endif
     double v0[4], v1[4];
     if (vec && a + 4 <= na) {
       const double2 x0 = *reinterpret_cast<const double2*>(rho + row_in + a);
@@ -310,6 +327,11 @@ __device__ __forceinline__ void field_slices_tf32_kernel_body(const tc::VBlock& 
   const long long row_out = (long long)i * n_pad + (symmetric ? 0 : pad_off[g]);
   const bool vec = ((row_in | row_in1) & 1) == 0;
   for (int a = 4 * (vb.x * blockDim.x + threadIdx.x); a < na; a += 4 * vb.gx * blockDim.x) {
+#if YGS_DEBUG_BOUNDS
+    if (!field_row_ok(row_in + a, row_in1 + a, pt.n_cells, row_out + a, (long long)(symmetric ? 2 : 1) * 2, plane,
+                      min(4, na - a)))
+      continue;
+#endif
     double v0[4], v1[4];
     if (vec && a + 4 <= na) {
       const double2 x0 = *reinterpret_cast<const double2*>(rho + row_in + a);
@@ -593,7 +615,11 @@ int fac_ld(const ygs_plan* p) { return (p->tc_np_full + (p->tc_np_tail > 0 ? 1 :
 __device__ __forceinline__ void field16_group(const double (&x0)[4], const double (&x1)[4], float4 ua, float4 ub,
                                               bool mono, int symmetric, int lane, long long G, int i,
                                               long long ngroups_all, int fac_ld, float* __restrict__ fac,
-                                              __half* __restrict__ out, long long plane, float& mh, float& ml) {
+                                              __half* __restrict__ out, long long plane, float& mh, float& ml,
+                                              long long oidx = 0, long long f_len = 0) {
+  // oidx, f_len: out's element index within the slice buffer and its length (the checked build's bounds)
+  (void)oidx;
+  (void)f_len;
   float hi[4][2], lo[4][2];
   float m0 = 0.0f, m1 = 0.0f;
 #pragma unroll
@@ -606,7 +632,10 @@ __device__ __forceinline__ void field16_group(const double (&x0)[4], const doubl
   m0 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m0)));
   m1 = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(m1)));
   const int e[2] = {group_exp(m0), symmetric ? group_exp(m1) : 0};
-  if (lane < 2 && (lane == 0 || symmetric)) fac[((long long)lane * ngroups_all + G) * fac_ld + i] = pow2f(-e[lane]);
+  if (lane < 2 && (lane == 0 || symmetric)) {
+    const long long fi = ((long long)lane * ngroups_all + G) * fac_ld + i;
+    if (YGS_IN_BOUNDS(fi, 2 * ngroups_all * fac_ld, kSiteField16Fac)) fac[fi] = pow2f(-e[lane]);
+  }
   if (mono) {
     // sigma+ times the weight in float-float (padding cells carry sigma = 0):
     // the heads' product with its rounding error from an FMA, the tails'
@@ -638,8 +667,11 @@ __device__ __forceinline__ void field16_group(const double (&x0)[4], const doubl
       w0[u] = h2_bits(s0);
       w1[u] = h2_bits(s1);
     }
-    *reinterpret_cast<uint2*>(out + (long long)(2 * h) * plane) = make_uint2(w0[0], w0[1]);
-    *reinterpret_cast<uint2*>(out + (long long)(2 * h + 1) * plane) = make_uint2(w1[0], w1[1]);
+    if (YGS_IN_BOUNDS(oidx + (2 * h) * plane, f_len, kSiteField16Slices) &&
+        YGS_IN_BOUNDS(oidx + (2 * h + 1) * plane + 3, f_len, kSiteField16Slices)) {
+      *reinterpret_cast<uint2*>(out + (long long)(2 * h) * plane) = make_uint2(w0[0], w0[1]);
+      *reinterpret_cast<uint2*>(out + (long long)(2 * h + 1) * plane) = make_uint2(w1[0], w1[1]);
+    }
   }
 }
 
@@ -671,7 +703,18 @@ __device__ __forceinline__ void field16_kernel_body(const tc::VBlock& vb,
     for (int b = 0; b < kFieldBatch; ++b) {
       const int q = q0 + b * nw;
       const long long c = c_chunk + (long long)q * kGroup + 4 * lane;  // this lane's first cell in patch g
-      const bool live = q < ngroups;
+      bool live = q < ngroups;
+#if YGS_DEBUG_BOUNDS
+      {
+        // the first and last cell this lane reads of either row, within the field
+        const long long nv = na - c < 4 ? na - c : 4, r0 = pt.fld_off[g] + (long long)i * na + c;
+        const long long r1 = (symmetric ? pt.fld_off[1] : pt.fld_off[g]) + (long long)i * na + c;
+        if (live && nv > 0)
+          live = YGS_IN_BOUNDS(r0, pt.n_cells, kSiteField16Rho) && YGS_IN_BOUNDS(r0 + nv - 1, pt.n_cells, kSiteField16Rho) &&
+                 YGS_IN_BOUNDS(r1, pt.n_cells, kSiteField16Rho) && YGS_IN_BOUNDS(r1 + nv - 1, pt.n_cells, kSiteField16Rho);
+        if (live && uz) live = YGS_IN_BOUNDS(pad_off[g] + c + 3, n_pad, kSiteField16U00);
+      }
+#endif
       load4(x0p, c, live ? na : 0, vec, x0[b]);
       load4(x1p, c, (live && symmetric) ? na : 0, vec, x1[b]);
       // the monopole weights of the same cells (padded layout, zero in the padding)
@@ -684,8 +727,9 @@ __device__ __forceinline__ void field16_kernel_body(const tc::VBlock& vb,
       if (q >= ngroups) break;  // warp-uniform
       const long long c = c_chunk + (long long)q * kGroup + 4 * lane;
       // 8-byte aligned: pad_off, c multiples of 4
+      const long long oidx = (long long)i * n_pad + pad_off[g] + c;
       field16_group(x0[b], x1[b], ua[b], ub[b], uz != nullptr, symmetric, lane, (ch.x / kGroup) + q, i, ngroups_all,
-                    fac_ld, fac, F + (long long)i * n_pad + pad_off[g] + c, plane, mh, ml);
+                    fac_ld, fac, F + oidx, plane, mh, ml, oidx, (symmetric ? 4 : 2) * plane);
     }
   }
   if (!mpart) return;
@@ -741,6 +785,11 @@ __device__ __forceinline__ void slice_m16_kernel_body(const tc::VBlock& vb,
   const int i = vb.x, npair = K_pad / 2;  // K_pad is a multiple of 64
   const long long splane = (long long)n_r * K_pad;
   const float4* row = reinterpret_cast<const float4*>(M + (long long)i * K_pad);  // two float-float columns each
+  // (a CTA-uniform test: the whole row is in, or the CTA leaves before its reduction)
+  if (!YGS_IN_BOUNDS((long long)i * K_pad, splane, kSiteSliceM16In) ||
+      !YGS_IN_BOUNDS((long long)i * K_pad + K_pad - 1, splane, kSiteSliceM16In) ||
+      !YGS_IN_BOUNDS(splane + (long long)i * K_pad + K_pad - 1, 2 * splane, kSiteSliceM16Out))
+    return;
   float m = 0.0f;
   for (int q = threadIdx.x; q < npair; q += blockDim.x) {
     const float4 v = row[q];
@@ -910,7 +959,10 @@ __device__ __forceinline__ void sum_chunks_group(const float2* __restrict__ part
       for (int k = 0; k < G; ++k) {
         const int z = z0 + zz, i = ib + k;
         v[zz][k] = make_float2(0.0f, 0.0f);
-        if (z < S && i < i1) v[zz][k] = mp ? mp[(long long)z * n_r + i] : part[z * plane + (long long)i * K_pad + pc];
+        if (z < S && i < i1) {
+          const long long ix = mp ? (long long)z * n_r + i : z * plane + (long long)i * K_pad + pc;
+          if (YGS_IN_BOUNDS(ix, mp ? (long long)S * n_r : S * plane, kSiteScanPart)) v[zz][k] = mp ? mp[ix] : part[ix];
+        }
       }
 #pragma unroll
     for (int zz = 0; zz < kScanZ; ++zz)
@@ -962,6 +1014,11 @@ constexpr int kScanMinBlocks = 1024 / kScanThreads >= 1 ? 1024 / kScanThreads : 
 static_assert(kScanCols >= 1 && kScanThreads <= 1024 && kScanThreads % 32 == 0 && kScanMaxP >= 32,
               "scan: a CTA of whole warps, at most 1024 threads, at least 32 chunks per column");
 
+// A float-float store of the scans (B, M), index-checked in checked builds.
+__device__ __forceinline__ void st_ff(float2* __restrict__ p, long long i, long long n, float2 v) {
+  if (YGS_IN_BOUNDS(i, n, kSiteScanBM)) p[i] = v;
+}
+
 __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb, 
     int n_r, int K_pad, int L, int S, int chunk, int P, const int* __restrict__ pc_l, const float2* __restrict__ part,
     const float2* __restrict__ rad, const float2* __restrict__ cp, float2* __restrict__ B, float2* __restrict__ M,
@@ -995,7 +1052,7 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
         for (int k = 0; k < kScanGroup; ++k) {
           if (ib + k < i1) {
             const int i = ib + k;
-            B[(long long)i * K_pad + pc] = bg[k];
+            st_ff(B, (long long)i * K_pad + pc, plane, bg[k]);
             I = tc::ff_add(tc::ff_mul(at[i], bg[k]), tc::ff_mul(fin[i], I));
           }
           if (ib == i0) bb[k] = bg[k];
@@ -1019,7 +1076,7 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
       FI = cp[(long long)l * P + p];
       FP = cp[(long long)(L + 1) * P + (long long)l * P + p];
     } else if (pc < K_pad && l < 0) {
-      for (int i = i0; i < i1; ++i) B[(long long)i * K_pad + pc] = zero;
+      for (int i = i0; i < i1; ++i) st_ff(B, (long long)i * K_pad + pc, plane, zero);
     }
     if (p < kScanMaxP) {
       sm[0][p][c] = I;
@@ -1036,7 +1093,7 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
   if (pc >= K_pad || p >= P || i0 >= n_r) return;
   if (l < 0) {
     for (int i = i0; i < i1; ++i) {
-      M[(long long)i * K_pad + pc] = zero;
+      st_ff(M, (long long)i * K_pad + pc, plane, zero);
       if (write_slices == 2)
         for (int k = 0; k < 2; ++k) reinterpret_cast<float*>(Ms)[k * plane + (long long)i * K_pad + pc] = 0.0f;
       else if (write_slices)
@@ -1045,20 +1102,23 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
     return;
   }
   auto emit = [&](int i, float2 m) {
-    M[(long long)i * K_pad + pc] = m;
+    st_ff(M, (long long)i * K_pad + pc, plane, m);
     if (pc == 0) mono[i] = tc::ff_mul(neg_G, m);  // natural column 0 (l = 0) is padded column 0: the monopole
     if (write_slices == 2) {  // TF32 slices (4-byte elements)
       float s0, s1;
       ff_tf32(m.x, m.y, s0, s1);
       float* Mf = reinterpret_cast<float*>(Ms);
-      Mf[(long long)i * K_pad + pc] = s0;
-      Mf[plane + (long long)i * K_pad + pc] = s1;
+      if (YGS_IN_BOUNDS(plane + (long long)i * K_pad + pc, 2 * plane, kSiteScanMs)) {
+        Mf[(long long)i * K_pad + pc] = s0;
+        Mf[plane + (long long)i * K_pad + pc] = s1;
+      }
     } else if (write_slices) {
       __nv_bfloat16 sl[3];
       ff_slices(m, nsl, sl);
 #pragma unroll
       for (int k = 0; k < 3; ++k)  // constant indices keep sl in registers
-        if (k < nsl) Ms[k * plane + (long long)i * K_pad + pc] = sl[k];
+        if (k < nsl && YGS_IN_BOUNDS(k * plane + (long long)i * K_pad + pc, nsl * plane, kSiteScanMs))
+          Ms[k * plane + (long long)i * K_pad + pc] = sl[k];
     }
   };
   float2 Pv = cr[1][p][c];
@@ -1086,7 +1146,7 @@ __device__ __forceinline__ void scan_ff_kernel_body(const tc::VBlock& vb,
     return;
   }
   for (int i = i1 - 1; i >= i0; --i) {
-    M[(long long)i * K_pad + pc] = Pv;
+    st_ff(M, (long long)i * K_pad + pc, plane, Pv);
     const float2 fo = (i > 0) ? fout[i - 1] : zero;
     Pv = tc::ff_add(tc::ff_mul(bt[i], B[(long long)i * K_pad + pc]), tc::ff_mul(fo, Pv));
   }
@@ -2211,5 +2271,8 @@ cudaError_t tc_unpermute(const ygs_plan* p, const float2* in, double* out, cudaS
   tc_unpermute_kernel<<<256, 256, 0, s>>>(p->n_r, p->K, p->tc_k_pad, p->tc_pc_nat, in, out);
   return cudaGetLastError();
 }
+
+// this translation unit's out-of-range record (checked builds; a no-op otherwise)
+YGS_BOUNDS_READER(bounds_read_tc)
 
 }  // namespace ygs

@@ -256,7 +256,6 @@ struct Tile {
 // the half `rank`.
 template <int MODE, int KE, bool EMU = false, int CG = 1>
 __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t, int rank = 0) {
-  constexpr int NMAX = TileShape<MODE, EMU>::NMAX;
   Tile T;
   int n;
   if (MODE == kProject) {
@@ -447,7 +446,11 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
               if (rank == 0) mbar_arrive_expect_tx(&full[stage], CG * nks * bytes + (fac_now ? NMAX * 4 : 0));
               if (fac_now) {
                 const int G = (T.kstart / KE + kb0 + kb) / GKB;
-                const float* src = fac + (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
+                long long fo = (T.b_plane0 ? R.A->fac_plane : 0) + (long long)G * R.A->fac_ld + T.b_row0;
+                // (checked builds: a row outside the table is reported and row 0 copied instead, so
+                // the stage's byte count still completes)
+                if (!YGS_IN_BOUNDS(fo + NMAX - 1, 2 * R.A->fac_plane, kSiteGemmFac) || !YGS_IN_BOUNDS(fo, 2 * R.A->fac_plane, kSiteGemmFac)) fo = 0;
+                const float* src = fac + fo;
                 bulk_load(fac_ring + (fgroups % C::FAC_RING) * NMAX, src, NMAX * 4, &full[stage]);
                 ++fgroups;
               }
@@ -733,6 +736,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       const long long nang = MODE == kSynthesize ? R.A->pt.nang[T.g_patch] : 0;
       const long long off0 = MODE == kSynthesize ? R.A->pt.fld_off[symmetric ? 0 : T.g_patch] : 0;
       const long long off1 = MODE == kSynthesize && symmetric ? R.A->pt.fld_off[1] : 0;
+      const long long phi_len = R.A->pt.n_cells;  // the checked build's bound for Phi
+      (void)phi_len;
       if (EMU && MODE == kSynthesize) {
         // output in float-float: Phi_Yin = E + O, Phi_Yang = E - O (or Phi_g),
         // each widened to FP64 as head + tail with the shell's power of two
@@ -765,14 +770,14 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
               float s, e;
               two_sum(e_h, o_h, s, e);
               float2 v = ff_renorm(s, e + (e_l + o_l));
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v.x, c20) + f32_to_f64_pow2(v.y, c20);
+              if (YGS_IN_BOUNDS(off0 + (long long)n * nang + a_loc, phi_len, kSiteGemmPhi)) phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v.x, c20) + f32_to_f64_pow2(v.y, c20);
               if (symmetric) {
                 two_sum(e_h, -o_h, s, e);
                 v = ff_renorm(s, e + (e_l - o_l));
-                phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v.x, c20) + f32_to_f64_pow2(v.y, c20);
+                if (YGS_IN_BOUNDS(off1 + (long long)n * nang + a_loc, phi_len, kSiteGemmPhi)) phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v.x, c20) + f32_to_f64_pow2(v.y, c20);
               }
             } else {
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(oh, c20) + f32_to_f64_pow2(ol, c20);
+              if (YGS_IN_BOUNDS(off0 + (long long)n * nang + a_loc, phi_len, kSiteGemmPhi)) phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(oh, c20) + f32_to_f64_pow2(ol, c20);
             }
           }
         }
@@ -805,7 +810,8 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             if (T.a_row0 + r < T.a_rows_end) {
               float s, e;
               two_sum(hj, lj, s, e);
-              part[((long long)T.z * n_b + n) * ldp + T.a_row0 + r] = make_float2(s, e);
+              const long long pi = ((long long)T.z * n_b + n) * ldp + T.a_row0 + r;
+              if (YGS_IN_BOUNDS(pi, (long long)R.A->n_chunks * n_b * ldp, kSiteGemmPart)) part[pi] = make_float2(s, e);
             }
           } else {
             const long long a_loc = (long long)T.m_loc * BM + r;
@@ -825,10 +831,10 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             if (symmetric) {
               // Yin-Yang: Phi_Yin = E + O, Phi_Yang = E - O (O = 0 when there are no odd columns)
               const float ee = (nseg == 2) ? e0 : v, oo = (nseg == 2) ? v : 0.0f;
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee + oo, c20);
-              phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee - oo, c20);
+              if (YGS_IN_BOUNDS(off0 + (long long)n * nang + a_loc, phi_len, kSiteGemmPhi)) phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee + oo, c20);
+              if (YGS_IN_BOUNDS(off1 + (long long)n * nang + a_loc, phi_len, kSiteGemmPhi)) phi[off1 + (long long)n * nang + a_loc] = f32_to_f64_pow2(ee - oo, c20);
             } else {
-              phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v, c20);
+              if (YGS_IN_BOUNDS(off0 + (long long)n * nang + a_loc, phi_len, kSiteGemmPhi)) phi[off0 + (long long)n * nang + a_loc] = f32_to_f64_pow2(v, c20);
             }
           }
         }

@@ -91,3 +91,15 @@ def test_valid_descriptor_without_gpu_reports_cuda_error():
     h = ctypes.c_void_p()
     st = L.ygs_create(ctypes.byref(d), 0, ctypes.byref(h))
     assert st == 3 and h.value is None
+
+
+def test_release_build_carries_no_bounds_checks():
+    """The library the package loads by default is the release build; the
+    checked build (index bounds checks in every per-solve kernel) lives in a
+    directory of its own and is loaded only when YGS_LIB names it."""
+    from paper_1903_08475_gb300 import build as B
+    L = ygs.load_library()
+    if os.environ.get("YGS_LIB"):
+        pytest.skip("YGS_LIB selects another build")
+    assert L.ygs_checked_build() == 0
+    assert os.path.dirname(B.CHECKED_LIB) != os.path.dirname(B.LIB)
