@@ -1930,6 +1930,7 @@ static void project_args(const ygs_plan* p, TcArgs& a, bool forward = true) {
   a = TcArgs{};
   fill_tiles(p, a, tc::kNmaxProject, p->tc_np_full, p->tc_np_tail);
   if (forward && p->tc_fp16) a.flush_kb = std::max(1, YGS_PROJ_FLUSH_K_EXACT_MONO / kblock_elems(p));
+  if (!forward && p->tc_tf32) a.flush_kb = 1;  // the TF32 adjoint flushes every k-block (below)
   a.tiles_m_even = (p->tc_k_even + tc::BM - 1) / tc::BM;
   a.tiles_m = a.tiles_m_even + (p->tc_k_pad - p->tc_k_even + tc::BM - 1) / tc::BM;
   a.a_row_odd = p->tc_k_even;
@@ -1991,6 +1992,10 @@ static void synth_args(const ygs_plan* p, TcArgs& a, double* phi, const float2* 
   // the forward synthesis excludes the monopole (added exactly) and may flush less
   // often; the adjoint's U has a positive monopole column and keeps 64
   a.flush_kb = p->tc_emu ? tc::kEmuWindowKb : std::max(1, (mono ? YGS_SYNTH_FLUSH_K : 64) / kblock_elems(p));
+  // TF32 operands take K = 8 per MMA, so an accumulator is rounded twice as
+  // often per k as with 2-byte slices: the adjoint's contractions (whose
+  // synthesis sums U's positive monopole column) flush every k-block of 32 k
+  if (!mono && p->tc_tf32) a.flush_kb = 1;
   a.k_even = p->symmetric ? p->tc_k_even : p->tc_k_pad;
   a.k_total = p->tc_k_pad;
   a.symmetric = p->symmetric ? 1 : 0;
