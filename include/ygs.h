@@ -116,7 +116,7 @@ enum {
   YGS_FLAG_AUTOTUNE = 2,    /* split precisions: ygs_create times, on this GPU, the projection
                                with several split-K counts (angular chunks per shell tile) and,
                                but for YGS_FP64_EMU, the synthesis at every distinct shell
-                               tiling of full-tile widths 80, 96, ..., 144 shells, on one CTA
+                               tiling of full-tile widths 144, 96 and 48 shells, on one CTA
                                per 128-cell tile and on CTA pairs, and keeps the fastest of
                                each (a few ms more at create, and a scratch Phi of n_cells
                                doubles while it runs; ygs_info reports the choices).  The

@@ -1771,7 +1771,8 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
   }
   if ((p->flags & YGS_FLAG_AUTOTUNE) && !p->tc_emu) {
     // the synthesis's tile shape: every distinct shell tiling of full-tile
-    // widths 80 ... NS (multiples of 16), on one CTA per 128-cell tile and, where
+    // widths NS, NS - NH, ... (whole groups of an epilogue warp's NH columns:
+    // 144, 96, 48), on one CTA per 128-cell tile and, where
     // the GPU co-schedules them, on CTA pairs (256-cell tiles); each timed over
     // 5 launches on zero M slices into a scratch Phi; the fastest is kept
     int clusters = 0;
@@ -1780,7 +1781,7 @@ ygs_status tc_setup(ygs_plan* p, int sms) {
     struct Shape { int w, pair; };
     std::vector<Shape> shapes;
     std::vector<std::pair<int, int>> tilings;  // (full tiles, tail width) already listed
-    for (int w = NS; w >= 80; w -= 16) {
+    for (int w = NS; w >= tc::kNhSynth; w -= tc::kNhSynth) {  // whole epilogue-warp column groups
       const std::pair<int, int> tl(p->n_r / w, ((p->n_r % w) + 15) / 16 * 16);
       if (std::find(tilings.begin(), tilings.end(), tl) != tilings.end()) continue;
       tilings.push_back(tl);

@@ -123,8 +123,10 @@ struct TcArgs {
   int* err;
   int flush_kb;         // k-blocks per TMEM group (a flush into the float-float sums)
   int n_b;              // valid B rows (shells)
-  int n_w;             // shells per full tile: NMAX, or (synthesis) a narrower width the
-                        // autotuner picked (multiple of 16, <= NMAX)
+  int n_w;              // shells per full tile: NMAX, or (synthesis) a narrower width the
+                        // autotuner picked: a multiple of NH, so that an epilogue warp's
+                        // columns lie wholly inside a full tile or wholly past it (the
+                        // tail tile is the last, its extra columns past n_b)
   int n_full;           // full shell tiles (n_w wide)
   int n_tail;           // width of the tail shell tile (multiple of 16) or 0
   int n_tiles;          // n_full + (n_tail > 0)
@@ -292,9 +294,11 @@ __device__ __forceinline__ Tile decode_tile(const TcArgs& a, int t, int rank = 0
     T.seg_kb1 = two ? (a.k_total - a.k_even) / KE : 0;
     T.z = 0;
   }
+  // full-tile width: the projection's is always NMAX (a constant here)
+  const int nw = MODE == kProject ? TileShape<MODE, EMU>::NMAX : a.n_w;
   T.use_tail = (n >= a.n_full);
-  T.n_eff = T.use_tail ? a.n_tail : a.n_w;
-  T.b_row0 = n * a.n_w;
+  T.n_eff = T.use_tail ? a.n_tail : nw;
+  T.b_row0 = n * nw;
   return T;
 }
 
@@ -760,7 +764,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
             upk2(L[j / 2], l0, l1);
             const float oh = (j & 1) ? h1 : h0, ol = (j & 1) ? l1 : l0;
             const int n = T.b_row0 + col0 + j;
-            if (col0 + j >= T.n_eff || n >= n_b || a_loc >= nang) continue;
+            if (n >= n_b || a_loc >= nang) continue;
             const unsigned int c20 = sc ? (unsigned int)__float_as_int(sc[n].x) : (896u << 20);
             if (nseg == 2 || symmetric) {
               // E from TMEM (zero without two column blocks: then the sums are E and O = 0)
@@ -804,8 +808,7 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
           upk2(L[j / 2], l0, l1);
           const float hj = (j & 1) ? h1 : h0, lj = (j & 1) ? l1 : l0;
           const int n = T.b_row0 + col0 + j;
-          // columns past the tile's width belong to the next shell tile
-          if (col0 + j >= T.n_eff || n >= n_b) continue;
+          if (n >= n_b) continue;
           if (MODE == kProject) {
             if (T.a_row0 + r < T.a_rows_end) {
               float s, e;

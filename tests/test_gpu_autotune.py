@@ -1,14 +1,16 @@
 """Plans tuned at create (YGS_FLAG_AUTOTUNE): the projection's split-K count and
-the synthesis's tile shape (full-tile width of 80 ... 144 shells, one CTA per
-128-cell tile or CTA pairs) picked by timing candidates on this GPU.
+the synthesis's tile shape (full-tile width of 144, 96 or 48 shells, whole
+groups of an epilogue warp's columns; one CTA per 128-cell tile or CTA pairs)
+picked by timing candidates on this GPU.
 
 Every tiling computes each output element over the same k-steps in the same
 order, so the synthesis's results do not depend on the shape it runs at; a
 tuned plan whose split-K count equals the untuned plan's therefore returns
 the same Phi bit for bit, and any tuned plan stays within the precision's
 bound of the CPU FP64 oracle (forward and adjoint).  The grids have shell
-counts whose tilings differ at every candidate width (Nr = 300: tails of 16,
-48, 80, 16 and 64 shells) and a tail narrower than a tile."""
+counts whose tilings differ at every candidate width (Nr = 300: 2 full tiles
+and a 16-shell tail at 144, 3 and a 16-shell tail at 96, 6 and a 16-shell
+tail at 48; Nr = 150: a tail narrower than a tile at each)."""
 import numpy as np
 import pytest
 
@@ -41,7 +43,7 @@ def test_tuned_tile_shape_matches_oracle(case, precision):
     r = torch.from_numpy(rho).cuda()
     with Plan(grid, precision, autotune=True) as pt, Plan(grid, precision) as p0:
         w = pt.info["synth_tile_shells"]
-        assert 80 <= w <= 144 and w % 16 == 0, w
+        assert w in (48, 96, 144), w
         assert p0.info["synth_tile_shells"] == 144 and p0.info["cta_pairs"] == 0
         a = ygs_solve(pt, r)
         torch.cuda.synchronize()
