@@ -37,6 +37,12 @@ namespace tc {
 #ifndef YGS_TC_BK
 #define YGS_TC_BK 64
 #endif
+#ifndef YGS_TC_SETMAXNREG
+#define YGS_TC_SETMAXNREG 1  // move registers from the TMA/MMA warpgroup to the epilogue warpgroups
+#endif
+#ifndef YGS_TC_REGS_LOW
+#define YGS_TC_REGS_LOW 56  // registers per thread the TMA/MMA warpgroup keeps (multiple of 8)
+#endif
 #ifndef YGS_EPI_CHUNK
 #define YGS_EPI_CHUNK 24  // TMEM columns an epilogue warp loads per wait (multiple of 8)
 #endif
@@ -105,10 +111,23 @@ struct TileShape {
   static constexpr int NMAX = MODE == 0 ? kNmaxProject : (EMU ? kNmaxSynthEmu : kNmaxSynth);
   static constexpr int NH = MODE == 0 ? kNhProject : (EMU ? kNhSynthEmu : kNhSynth);
   static constexpr int EPI_WARPS = 4 * (NMAX / NH);
-  // warps: TMA producer, MMA issuer, epilogue
-  static constexpr int FIRST_EPI = 2;
+  // warps: TMA producer, MMA issuer (with YGS_TC_SETMAXNREG two idle warps
+  // complete their warpgroup), then the epilogue warpgroups
+  static constexpr int FIRST_EPI = YGS_TC_SETMAXNREG ? 4 : 2;
   static constexpr int THREADS = 32 * FIRST_EPI + 32 * EPI_WARPS;
   static_assert(NMAX % 16 == 0 && NMAX <= 256 && NMAX % NH == 0 && NH % 8 == 0, "tile shape");
+  // Registers per thread: at launch (the whole register file over THREADS,
+  // in steps of 8), then, with YGS_TC_SETMAXNREG, warpgroup 0 (TMA, MMA)
+  // gives up all but REGS_LOW and the epilogue warpgroups take the rest, so
+  // their float-float sums stay in registers.  setmaxnreg.inc draws only on
+  // the CTA's launch allocation, so the split must not exceed it.
+  static constexpr int REGS_LAUNCH = (65536 / THREADS) / 8 * 8 > 248 ? 248 : (65536 / THREADS) / 8 * 8;
+  static constexpr int REGS_LOW = YGS_TC_REGS_LOW;
+  static constexpr int REGS_EPI_RAW = (THREADS * REGS_LAUNCH - 128 * REGS_LOW) / (32 * EPI_WARPS) / 8 * 8;
+  static constexpr int REGS_EPI = REGS_EPI_RAW > 248 ? 248 : REGS_EPI_RAW;
+  static_assert(!YGS_TC_SETMAXNREG || (EPI_WARPS % 4 == 0 && REGS_EPI >= REGS_LAUNCH &&
+                                       128 * REGS_LOW + 32 * EPI_WARPS * REGS_EPI <= THREADS * REGS_LAUNCH),
+                "register split: whole warpgroups, within the launch allocation");
   // TMEM (512 columns): NBUF rotating accumulators of NMAX columns, plus, in
   // the synthesis, NMAX columns that hold the even-block result E of a tile
   // (2 NMAX in EMU mode: its head and tail).
@@ -413,6 +432,9 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  if (warp < kFirstEpi) {
+    // warpgroup 0: TMA producer, MMA issuer (and, with YGS_TC_SETMAXNREG, two idle warps)
+    if constexpr (YGS_TC_SETMAXNREG) setmaxnreg_dec<TileShape<MODE, EMU>::REGS_LOW>();
   if (warp == 0) {
     // ================= TMA producer =================
     if (lane == 0) {
@@ -588,7 +610,9 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
       // the odd CTA of a pair: the even CTA's MMAs write this CTA's TMEM too
       mbar_wait_final(mma_done, 0);
     }
+  }
   } else {
+    if constexpr (YGS_TC_SETMAXNREG) setmaxnreg_inc<TileShape<MODE, EMU>::REGS_EPI>();
     // ================= epilogue warps kFirstEpi .. kFirstEpi + kEpiWarps - 1 =================
     const int ew = warp - kFirstEpi;
     const int q = warp % 4;                // TMEM lane quadrant this warp may access
