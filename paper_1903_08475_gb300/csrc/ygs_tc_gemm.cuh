@@ -60,8 +60,16 @@ struct KElems {
 constexpr int BM = 128;        // output rows per tile (TMEM lanes)
 // Tile shapes (shells per tile, columns per epilogue warp).  144-shell tiles
 // keep the tensor core compute-bound (a 128 x 80 x 16 MMA is bound by reading
-// its operands from shared memory) and cut the operand bytes per flop.
-constexpr int kNmaxProject = 144, kNhProject = 48;
+// its operands from shared memory) and cut the operand bytes per flop.  The
+// projection's epilogue (flushes only; its output is a small partial) runs
+// best on 8 warps of 72 columns, the synthesis's (flushes, the parked E and
+// the FP64 output) on 12 of 48 (measured: projection 79.4 -> 76.4 us with 72,
+// synthesis 100.7 -> 156.7 us).
+#ifndef YGS_PROJ_NH
+#define YGS_PROJ_NH 72  // of a projection tile's 144 shells per epilogue warp (8 epilogue warps)
+#endif
+constexpr int kNmaxProject = 144, kNhProject = YGS_PROJ_NH;
+constexpr int kNhProjectEmu = 48;  // the FP64-accurate projection keeps 12 epilogue warps
 #ifndef YGS_SYNTH_N
 #define YGS_SYNTH_N 144  // shells per synthesis tile
 #endif
@@ -109,7 +117,7 @@ template <int MODE, bool EMU = false>
 struct TileShape {
   // shells per full tile; columns per epilogue warp
   static constexpr int NMAX = MODE == 0 ? kNmaxProject : (EMU ? kNmaxSynthEmu : kNmaxSynth);
-  static constexpr int NH = MODE == 0 ? kNhProject : (EMU ? kNhSynthEmu : kNhSynth);
+  static constexpr int NH = MODE == 0 ? (EMU ? kNhProjectEmu : kNhProject) : (EMU ? kNhSynthEmu : kNhSynth);
   static constexpr int EPI_WARPS = 4 * (NMAX / NH);
   // warps: TMA producer, MMA issuer (with YGS_TC_SETMAXNREG two idle warps
   // complete their warpgroup), then the epilogue warpgroups
