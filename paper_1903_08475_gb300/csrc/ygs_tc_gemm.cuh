@@ -7,10 +7,12 @@
 //
 // Persistent kernel: one CTA per SM walks a static list of 128 x n_eff output
 // tiles (n_eff = n_w shells, NMAX = 144 by default or a narrower width picked
-// by the autotuner, or the tail width for the last shell tile).  Warp 0 streams A/B slice tiles of BK k-elements (128-byte
-// rows, 128-byte swizzle) through a ring of shared-memory stages with TMA;
-// warp 1 issues tcgen05.mma into FP32 TMEM accumulators; the epilogue warps
-// (2 onwards, 4 per group of NH columns) drain them with tcgen05.ld.  The
+// by the autotuner, or the tail width for the last shell tile).  Warp 0
+// streams A/B slice tiles of BK k-elements (128-byte rows, 128-byte swizzle)
+// through a ring of shared-memory stages with TMA; warp 1 issues tcgen05.mma
+// into FP32 TMEM accumulators; the epilogue warps (from warp 4, after the two
+// idle warps that complete warpgroup 0; 4 per group of NH columns) drain them
+// with tcgen05.ld.  The
 // tensor core's FP32 accumulation loses about one unit in the last place per
 // accumulation step, always in the same direction, so every product is
 // accumulated only over a short "group" of k-blocks in one of NBUF rotating
@@ -889,9 +891,9 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   if (warp == 0) tmem_dealloc<CG>(tmem, 512);
 }
 
-// Registers: 14 warps (448 threads), at most 128 each: a CTA's warps are
-// spread over the SM's four sub-partitions (16,384 registers each), four
-// warps on two of them, so 4 x 32 x 128 is the ceiling for one CTA per SM.
+// Registers: one CTA per SM takes the whole register file at launch
+// (TileShape::REGS_LAUNCH per thread), which setmaxnreg then moves from
+// warpgroup 0 to the epilogue warpgroups (TileShape::REGS_LOW, REGS_EPI).
 // One problem: maps and arguments in kernel parameters.
 // CG = 2: launched in clusters of two CTAs (the grid even), B's maps with
 // boxes of half a tile's shells.
