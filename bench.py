@@ -275,6 +275,12 @@ def run_config3(args, ws, rank, local):
                                    "launches_per_step": sum(ygs_launches_per_solve(p) for p in plans)},
             "speedup_vs_per_field": ms_each / ms_graph, "bitwise_equal_to_per_field": identical,
             "gpu_launches": args.steps * batch.launches, "clocks": clk}
+    if args.autotune:
+        # the shapes the plans' autotuners kept: (synthesis shells per tile, CTA pairs, split-K) -> plans
+        from collections import Counter
+        kept = Counter((p.info["synth_tile_shells"], p.info["cta_pairs"], p.info["split_k"]) for p in plans)
+        line["config"]["autotune"] = True
+        line["autotuned_shapes"] = {f"w{w}-pairs{c}-splitk{k}": v for (w, c, k), v in sorted(kept.items())}
     if rank == 0:
         print(json.dumps(line), flush=True)
     batch.close()
