@@ -722,8 +722,20 @@ cudaError_t emu_set_smem_attrs() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, EmuCfg<tc::kSynthesize>::SMEM)) !=
       cudaSuccess)
     return e;
-  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<1, tc::kSynthesize, false, false, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, EmuCfg<tc::kSynthesize>::SMEM);
+  if ((e = cudaFuncSetAttribute(tc::tc_gemm_group_kernel<1, tc::kSynthesize, false, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, EmuCfg<tc::kSynthesize>::SMEM)) !=
+      cudaSuccess)
+    return e;
+  // the register split of each kernel (see check_reg_split)
+  if ((e = tc::check_reg_split<tc::kProject, true>((const void*)tc::tc_gemm_kernel<1, tc::kProject, true, false, true>)) !=
+          cudaSuccess ||
+      (e = tc::check_reg_split<tc::kProject, true>(
+           (const void*)tc::tc_gemm_group_kernel<1, tc::kProject, true, false, true>)) != cudaSuccess ||
+      (e = tc::check_reg_split<tc::kSynthesize, true>(
+           (const void*)tc::tc_gemm_kernel<1, tc::kSynthesize, false, false, true>)) != cudaSuccess)
+    return e;
+  return tc::check_reg_split<tc::kSynthesize, true>(
+      (const void*)tc::tc_gemm_group_kernel<1, tc::kSynthesize, false, false, true>);
 }
 
 cudaError_t emu_dispatch_gemm(int mode, int grid, const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& bt,

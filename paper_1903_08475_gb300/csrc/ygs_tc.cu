@@ -1357,9 +1357,13 @@ template <int NSL, int MODE, bool SCALE, bool TF = false>
 cudaError_t set_smem_attr() {
   cudaError_t e = cudaFuncSetAttribute(tc::tc_gemm_kernel<NSL, MODE, SCALE, TF>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE, SCALE, TF>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
+  if (e == cudaSuccess) e = tc::check_reg_split<MODE, false>((const void*)tc::tc_gemm_kernel<NSL, MODE, SCALE, TF>);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(tc::tc_gemm_group_kernel<NSL, MODE, SCALE, TF>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<NSL, MODE>::SMEM);
+  if (e == cudaSuccess)
+    e = tc::check_reg_split<MODE, false>((const void*)tc::tc_gemm_group_kernel<NSL, MODE, SCALE, TF>);
+  return e;
 }
 
 // scale: the projection of FP16 field slices (group factors applied at the
@@ -1429,6 +1433,7 @@ cudaError_t setup_synth_pair(int nsl, bool tf, int sms, int& clusters) {
     return cudaSuccess;
   }
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = tc::check_reg_split<tc::kSynthesize, false>(fn);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(2 * std::max(1, sms / 2)));

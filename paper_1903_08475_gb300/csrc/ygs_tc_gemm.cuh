@@ -891,6 +891,19 @@ __device__ __forceinline__ void gemm_body(const Src& src) {
   if (warp == 0) tmem_dealloc<CG>(tmem, 512);
 }
 
+// setmaxnreg.inc waits for registers out of the CTA's launch allocation, so
+// the split above holds only if the compiled kernel's register count is the
+// REGS_LAUNCH it assumes: the host refuses a kernel whose count differs (a
+// compiler that allocated fewer would otherwise leave the epilogue waiting).
+template <int MODE, bool EMU>
+inline cudaError_t check_reg_split(const void* fn) {
+  if (!YGS_TC_SETMAXNREG) return cudaSuccess;
+  cudaFuncAttributes at;
+  const cudaError_t e = cudaFuncGetAttributes(&at, fn);
+  if (e != cudaSuccess) return e;
+  return at.numRegs == TileShape<MODE, EMU>::REGS_LAUNCH ? cudaSuccess : cudaErrorInvalidKernelImage;
+}
+
 // Registers: one CTA per SM takes the whole register file at launch
 // (TileShape::REGS_LAUNCH per thread), which setmaxnreg then moves from
 // warpgroup 0 to the epilogue warpgroups (TileShape::REGS_LOW, REGS_EPI).
